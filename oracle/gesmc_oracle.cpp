@@ -1,0 +1,277 @@
+// ORACLE -- test infrastructure only, never part of the product path.
+//
+// A plain, slow, sequential CPU statement of the Global Edge Switching Markov
+// Chain (G-ES-MC) of Allendorf, Meyer, Penschuck and Tran, "Parallel Global
+// Edge Switching for the Uniform Sampling of Simple Graphs with Prescribed
+// Degrees" (arXiv 2111.03005).  Only tests/, __graft_entry__.smoke() and the
+// cpu_baseline / reference leg of bench.py may load it.  It shares no source,
+// header, table or helper with the CUDA library; both sides only agree on the
+// published definitions restated below.
+//
+// What it computes, in the paper's order:
+//   * Def. 1 (Sec. 2.2): an edge switch sigma = (i, j, g) on the indexed edge
+//     list E: e1 = E[i] = (u, v), e2 = E[j] = (x, y); tau gives
+//     g = 0 -> (u, x), (v, y) and g = 1 -> (u, y), (v, x).  The switch is
+//     rejected if a new edge is a loop or is already in E, else
+//     E[i] <- e3, E[j] <- e4.
+//   * Def. 2 (Sec. 3): a global switch runs the switches
+//     sigma_k = (pi(2k-1), pi(2k), 1[pi(2k-1) < pi(2k)]) one after another
+//     (1-based in the paper; 0-based here: pi[2k], pi[2k+1]).
+//   * Algorithm 3 (ParGlobalES): one global switch per round, r rounds.
+//
+// Readings where the paper leaves a choice open (each is listed in the design doc):
+//   * Edges are stored canonically, (min << 32) | max (Sec. 5.2 edge ids;
+//     Sec. 2.1 canonical orientation), also right after every accepted switch.
+//   * The random permutation pi of round r is the argsort of 64-bit keys
+//     K(i) = Philox4x64-10(counter = (i >> 2, r, 0, 0), key = (seed, 0))[i & 3]
+//     with ties broken by the smaller position.  Philox4x64-10 is the
+//     counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11).
+//   * Laziness (Def. 2, P_L): switch k of round r is skipped iff
+//     Philox4x64-10(counter = (k >> 2, r, 1, 0), key = (seed, 0))[k & 3]
+//     < lazy_threshold; the default threshold 0 never skips (P_L = 0).
+//   * Rounds are numbered cumulatively, so run(a) then run(b) equals run(a+b).
+//
+// Parity pins live in tests/test_oracle_pins.py (worked example of Fig. 1,
+// hand-worked global switches, special graphs, exact transition matrices
+// against Thm. 1, chi-squared uniformity over brute-forced G(d), Philox
+// against numpy's independent Philox implementation).
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+namespace {
+
+// ---- Philox4x64-10 (Salmon et al., SC'11, Sec. 3 and Table 2) --------------
+// One round: two 64x64->128 multiplications of counter words 0 and 2 by fixed
+// multipliers; the high halves are xor-ed with the other counter words and
+// the round key, and the words are permuted.  The key is bumped by two Weyl
+// constants between rounds.
+const uint64_t kPhiloxM0 = 0xD2E7470EE14C6C93ull;
+const uint64_t kPhiloxM1 = 0xCA5A826395121157ull;
+const uint64_t kPhiloxW0 = 0x9E3779B97F4A7C15ull;
+const uint64_t kPhiloxW1 = 0xBB67AE8584CAA73Bull;
+
+void philox4x64_10(const uint64_t in_ctr[4], const uint64_t in_key[2], uint64_t out[4]) {
+  uint64_t c[4] = {in_ctr[0], in_ctr[1], in_ctr[2], in_ctr[3]};
+  uint64_t k0 = in_key[0], k1 = in_key[1];
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += kPhiloxW0;
+      k1 += kPhiloxW1;
+    }
+    unsigned __int128 p0 = (unsigned __int128)kPhiloxM0 * c[0];
+    unsigned __int128 p1 = (unsigned __int128)kPhiloxM1 * c[2];
+    uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+    uint64_t n0 = hi1 ^ c[1] ^ k0;
+    uint64_t n1 = lo1;
+    uint64_t n2 = hi0 ^ c[3] ^ k1;
+    uint64_t n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+uint64_t philox_word(uint64_t seed, uint64_t round, uint64_t purpose, uint64_t index) {
+  const uint64_t ctr[4] = {index >> 2, round, purpose, 0};
+  const uint64_t key[2] = {seed, 0};
+  uint64_t out[4];
+  philox4x64_10(ctr, key, out);
+  return out[index & 3];
+}
+
+const uint64_t kPurposePermutation = 0;
+const uint64_t kPurposeLazy = 1;
+
+inline uint64_t pack(uint32_t a, uint32_t b) {
+  // canonical id of the undirected edge {a, b}: smaller node in the high half
+  uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+  return ((uint64_t)lo << 32) | hi;
+}
+
+// Outcome codes of one edge switch.
+const int kAccepted = 0;
+const int kRejectedLoop = 1;
+const int kRejectedExists = 2;
+
+// Def. 1 applied to E (positions i, j, direction bit g) against the current
+// edge set S, which always equals the set of entries of E.
+int edge_switch(uint64_t* E, std::unordered_set<uint64_t>& S, uint64_t i, uint64_t j, int g) {
+  const uint64_t e1 = E[i], e2 = E[j];
+  const uint32_t u = (uint32_t)(e1 >> 32), v = (uint32_t)e1;
+  const uint32_t x = (uint32_t)(e2 >> 32), y = (uint32_t)e2;
+  uint32_t a3, b3, a4, b4;  // e3 = (a3, b3), e4 = (a4, b4) as tau orients them
+  if (g == 0) { a3 = u; b3 = x; a4 = v; b4 = y; }
+  else        { a3 = u; b3 = y; a4 = v; b4 = x; }
+  if (a3 == b3 || a4 == b4) return kRejectedLoop;
+  const uint64_t e3 = pack(a3, b3), e4 = pack(a4, b4);
+  if (S.count(e3) || S.count(e4)) return kRejectedExists;
+  S.erase(e1);
+  S.erase(e2);
+  S.insert(e3);
+  S.insert(e4);
+  E[i] = e3;
+  E[j] = e4;
+  return kAccepted;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Statistics of a call, summed over all switches it ran.
+struct orc_stats {
+  uint64_t switches;         // floor(m/2) per round: every pair of the permutation
+  uint64_t lazy;             // switches skipped by the laziness rule
+  uint64_t accepted;
+  uint64_t rejected_loop;    // a new edge would be a loop
+  uint64_t rejected_exists;  // a new edge is already in E when the switch runs
+};
+
+// Error codes of the oracle's own input check.
+enum { ORC_OK = 0, ORC_E_INVALID = -1, ORC_E_LOOP = -2, ORC_E_MULTI = -3, ORC_E_RANGE = -4,
+       ORC_E_INVARIANT = -20 };
+
+void orc_philox4x64_10(const uint64_t* ctr, const uint64_t* key, uint64_t* out) {
+  philox4x64_10(ctr, key, out);
+}
+
+uint64_t orc_perm_key(uint64_t seed, uint64_t round, uint64_t i) {
+  return philox_word(seed, round, kPurposePermutation, i);
+}
+
+uint64_t orc_lazy_word(uint64_t seed, uint64_t round, uint64_t k) {
+  return philox_word(seed, round, kPurposeLazy, k);
+}
+
+// pi of round r: positions 0..m-1 sorted by (K(i), i).
+void orc_permutation(uint64_t seed, uint64_t round, uint64_t m, uint32_t* pi) {
+  std::vector<std::pair<uint64_t, uint32_t>> keyed(m);
+  for (uint64_t i = 0; i < m; ++i) keyed[i] = {orc_perm_key(seed, round, i), (uint32_t)i};
+  std::sort(keyed.begin(), keyed.end());
+  for (uint64_t s = 0; s < m; ++s) pi[s] = keyed[s].second;
+}
+
+// A "degree-valid" edge list is a simple graph on nodes [0, n): no loops, no
+// repeated edge, ids < n (Sec. 2.1).  n == 0 means "no bound".  The list is
+// canonicalised in place.  When several kinds of fault occur the code for a
+// loop wins over an out-of-range id, which wins over a repeated edge.
+int orc_validate(uint64_t* E, uint64_t m, uint64_t n) {
+  if (E == nullptr && m > 0) return ORC_E_INVALID;
+  if (m >= (1ull << 32)) return ORC_E_INVALID;
+  bool loop = false, range = false, multi = false;
+  std::unordered_set<uint64_t> seen;
+  seen.reserve(m * 2 + 1);
+  for (uint64_t i = 0; i < m; ++i) {
+    const uint32_t a = (uint32_t)(E[i] >> 32), b = (uint32_t)E[i];
+    if (a == b) loop = true;
+    if (n != 0 && (a >= n || b >= n)) range = true;
+    E[i] = pack(a, b);
+    if (a != b && !seen.insert(E[i]).second) multi = true;
+  }
+  if (loop) return ORC_E_LOOP;
+  if (range) return ORC_E_RANGE;
+  if (multi) return ORC_E_MULTI;
+  return ORC_OK;
+}
+
+// One edge switch (Def. 1) on a canonical simple edge list; the edge set is
+// taken from E.  Returns 0 accepted, 1 rejected (loop), 2 rejected (exists).
+int orc_edge_switch(uint64_t* E, uint64_t m, uint64_t i, uint64_t j, int g) {
+  std::unordered_set<uint64_t> S(E, E + m);
+  return edge_switch(E, S, i, j, g);
+}
+
+namespace {
+
+bool degrees_and_set_ok(const uint64_t* E, uint64_t m, const std::unordered_set<uint64_t>& S,
+                        const std::unordered_map<uint32_t, uint64_t>& deg0) {
+  if (S.size() != m) return false;
+  std::unordered_map<uint32_t, uint64_t> deg;
+  for (uint64_t i = 0; i < m; ++i) {
+    const uint32_t a = (uint32_t)(E[i] >> 32), b = (uint32_t)E[i];
+    if (a >= b) return false;  // canonical and loop-free
+    if (!S.count(E[i])) return false;
+    ++deg[a];
+    ++deg[b];
+  }
+  return deg == deg0;
+}
+
+std::unordered_map<uint32_t, uint64_t> degree_map(const uint64_t* E, uint64_t m) {
+  std::unordered_map<uint32_t, uint64_t> deg;
+  for (uint64_t i = 0; i < m; ++i) {
+    ++deg[(uint32_t)(E[i] >> 32)];
+    ++deg[(uint32_t)E[i]];
+  }
+  return deg;
+}
+
+void count(orc_stats* st, int outcome) {
+  if (!st) return;
+  if (outcome == kAccepted) ++st->accepted;
+  else if (outcome == kRejectedLoop) ++st->rejected_loop;
+  else ++st->rejected_exists;
+}
+
+}  // namespace
+
+// One global switch (Def. 2) with an explicit permutation pi of [0, m): the
+// first ell pairs run in order; skip[k] != 0 (if skip is given) skips pair k.
+int orc_global_switch(uint64_t* E, uint64_t m, const uint32_t* pi, uint64_t ell,
+                      const uint8_t* skip, orc_stats* st) {
+  if (ell > m / 2) return ORC_E_INVALID;
+  std::unordered_set<uint64_t> S(E, E + m);
+  for (uint64_t k = 0; k < ell; ++k) {
+    if (st) ++st->switches;
+    if (skip && skip[k]) {
+      if (st) ++st->lazy;
+      continue;
+    }
+    const uint64_t i = pi[2 * k], j = pi[2 * k + 1];
+    const int g = i < j ? 1 : 0;
+    count(st, edge_switch(E, S, i, j, g));
+  }
+  return ORC_OK;
+}
+
+// Algorithm 3 run sequentially: `rounds` global switches numbered
+// start_round, start_round + 1, ...  E must be a canonical simple edge list.
+// If snapshots is given it receives E after every round (rounds * m words).
+// check_every_switch re-verifies simplicity, |E| = m and the degree sequence
+// after every single switch (slow; for small graphs).
+int orc_run(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_round, uint64_t rounds,
+            uint64_t lazy_threshold, int check_every_switch, orc_stats* st, uint64_t* snapshots) {
+  if (E == nullptr && m > 0) return ORC_E_INVALID;
+  std::unordered_set<uint64_t> S;
+  S.reserve(m * 2 + 1);
+  for (uint64_t i = 0; i < m; ++i) S.insert(E[i]);
+  if (S.size() != m) return ORC_E_MULTI;
+  std::unordered_map<uint32_t, uint64_t> deg0;
+  if (check_every_switch) deg0 = degree_map(E, m);
+  std::vector<uint32_t> pi(m);
+  const uint64_t L = m / 2;
+  for (uint64_t t = 0; t < rounds; ++t) {
+    const uint64_t r = start_round + t;
+    orc_permutation(seed, r, m, pi.data());
+    for (uint64_t k = 0; k < L; ++k) {
+      if (st) ++st->switches;
+      if (lazy_threshold != 0 && orc_lazy_word(seed, r, k) < lazy_threshold) {
+        if (st) ++st->lazy;
+        continue;
+      }
+      const uint64_t i = pi[2 * k], j = pi[2 * k + 1];
+      const int g = i < j ? 1 : 0;
+      count(st, edge_switch(E, S, i, j, g));
+      if (check_every_switch && !degrees_and_set_ok(E, m, S, deg0)) return ORC_E_INVARIANT;
+    }
+    if (snapshots) std::memcpy(snapshots + t * m, E, m * sizeof(uint64_t));
+  }
+  return ORC_OK;
+}
+
+}  // extern "C"

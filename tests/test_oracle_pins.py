@@ -1,0 +1,278 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself.
+
+* Fig. 1 and hand-worked global switches (tests/golden/worked_examples.json),
+  derived by hand from Def. 1 and Def. 2.
+* Philox4x64-10 and the permutation against numpy's own Philox (a separate
+  library implementation of the same published generator).
+* Special graphs whose outcome the definitions fix (complete graph, star,
+  perfect matching, m < 2).
+* Invariants after every single switch (degree sequence, simplicity, |E| = m).
+* Thm. 1: the exact graph-level transition matrix, enumerated over all m!
+  permutations on tiny graphs, is stochastic and symmetric; G(d) is
+  brute-forced from all edge subsets; a chi-squared test of the final graph
+  after enough rounds against the uniform distribution on G(d).
+"""
+import itertools
+import json
+import math
+import os
+from collections import Counter
+
+import numpy as np
+import pytest
+from numpy.random import Philox
+
+import oracle
+from paper_2111_03005_gb300 import inputs
+
+
+def P(pairs):
+    if not pairs:
+        return np.zeros(0, dtype=np.uint64)
+    return oracle.pack([a for a, _ in pairs], [b for _, b in pairs])
+
+
+# ---------------------------------------------------------------- worked examples
+
+def test_fig1_worked_example(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "worked_examples.json")))["fig1"]
+    for case in g["cases"]:
+        outcome, after = oracle.edge_switch(P(g["edges"]), *case["switch"])
+        assert outcome == case["outcome"], case["name"]
+        assert np.array_equal(after, P(case["edges_after"])), case["name"]
+
+
+def test_hand_worked_global_switches(golden_dir):
+    cases = json.load(open(os.path.join(golden_dir, "worked_examples.json")))["global"]
+    for case in cases:
+        after, st = oracle.global_switch(P(case["edges"]), case["pi"])
+        assert np.array_equal(after, P(case["edges_after"])), case["name"]
+        assert st["accepted"] == case["accepted"], case["name"]
+
+
+# ---------------------------------------------------------------- randomness
+
+def _numpy_philox_block(ctr, key):
+    # numpy's bit generator increments its 256-bit counter before each block
+    c = sum(int(x) << (64 * t) for t, x in enumerate(ctr))
+    bg = Philox(key=np.array(key, dtype=np.uint64), counter=(c - 1) % (1 << 256))
+    return bg.random_raw(4)
+
+
+def test_philox_matches_numpy():
+    rng = np.random.default_rng(7)
+    for _ in range(100):
+        ctr = [int(x) for x in rng.integers(0, 2**63, size=4)]
+        ctr = [c * 2 + int(rng.integers(0, 2)) for c in ctr]
+        key = [int(x) for x in rng.integers(0, 2**63, size=2)]
+        assert np.array_equal(oracle.philox4x64_10(ctr, key), _numpy_philox_block(ctr, key))
+    assert np.array_equal(oracle.philox4x64_10([0] * 4, [0, 0]), _numpy_philox_block([0] * 4, [0, 0]))
+    full = (1 << 64) - 1
+    assert np.array_equal(oracle.philox4x64_10([full] * 4, [full, full]), _numpy_philox_block([full] * 4, [full, full]))
+
+
+@pytest.mark.parametrize("seed,rnd", [(0, 0), (42, 3), (2**64 - 1, 2**40 + 5)])
+def test_permutation_is_argsort_of_numpy_philox_keys(seed, rnd):
+    m = 1031
+    keys = np.empty(m, dtype=np.uint64)
+    for b in range((m + 3) // 4):
+        blk = _numpy_philox_block([b, rnd, 0, 0], [seed, 0])
+        for t in range(4):
+            if 4 * b + t < m:
+                keys[4 * b + t] = blk[t]
+    for i in (0, 1, 5, m - 1):
+        assert oracle.perm_key(seed, rnd, i) == int(keys[i])
+    expected = np.lexsort((np.arange(m), keys)).astype(np.uint32)  # by key, then position
+    assert np.array_equal(oracle.permutation(seed, rnd, m), expected)
+
+
+def test_lazy_word_stream_is_purpose_one():
+    seed, rnd = 99, 7
+    blk = _numpy_philox_block([3, rnd, 1, 0], [seed, 0])
+    for t in range(4):
+        assert oracle.lazy_word(seed, rnd, 12 + t) == int(blk[t])
+
+
+def test_permutation_uniform_chi2():
+    from scipy.stats import chisquare
+    m = 4
+    counts = Counter()
+    n_samples = 24 * 400
+    for s in range(n_samples // 8):
+        for r in range(8):
+            counts[tuple(oracle.permutation(s, r, m))] += 1
+    assert len(counts) == 24
+    obs = np.array([counts[p] for p in itertools.permutations(range(m))])
+    assert chisquare(obs).pvalue > 1e-4
+
+
+# ---------------------------------------------------------------- special graphs
+
+def test_small_m_is_noop():
+    for m, lst in ((0, []), (1, [(3, 9)])):
+        e, st = oracle.run(P(lst), seed=1, rounds=5)
+        assert np.array_equal(e, P(lst))
+        assert st["switches"] == 0 and st["accepted"] == 0
+
+
+def test_complete_graph_rejects_everything():
+    n = 7
+    kn = P([(a, b) for a in range(n) for b in range(a + 1, n)])
+    e, st = oracle.run(inputs.shuffle_edges(kn, 3), seed=5, rounds=6, check_every_switch=True)
+    assert st["accepted"] == 0
+    assert st["rejected_loop"] + st["rejected_exists"] == st["switches"] == 6 * (len(kn) // 2)
+    assert np.array_equal(e, inputs.shuffle_edges(kn, 3))
+
+
+def test_star_rejects_everything():
+    star = P([(0, v) for v in range(1, 12)])
+    e, st = oracle.run(star, seed=8, rounds=5)
+    assert st["accepted"] == 0 and np.array_equal(e, star)
+    # every pair shares the centre: one orientation is a loop, the other
+    # reproduces the two source edges, which are still in E (Def. 1)
+    assert st["rejected_loop"] > 0 and st["rejected_exists"] > 0
+
+
+def test_perfect_matching_m2_follows_the_drawn_permutation():
+    start = P([(0, 1), (2, 3)])
+    after_01 = P([(0, 3), (1, 2)])   # pi = [0, 1]: g = 1 -> (u, y), (v, x)
+    after_10 = P([(1, 3), (0, 2)])   # pi = [1, 0]: g = 0 -> (x, u), (y, v)
+    seen = Counter()
+    for seed in range(400):
+        pi = tuple(oracle.permutation(seed, 0, 2))
+        e, st = oracle.run(start, seed=seed, rounds=1)
+        assert st["accepted"] == 1
+        assert np.array_equal(e, after_01 if pi == (0, 1) else after_10)
+        seen[pi] += 1
+    assert abs(seen[(0, 1)] - 200) < 5 * math.sqrt(100)
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("seed", range(6))
+def test_invariants_after_every_switch(seed):
+    e0 = inputs.random_simple_graph(24, 50, seed)
+    e, st = oracle.run(e0, seed=seed, rounds=4, check_every_switch=True)
+    assert st["switches"] == 4 * 25
+    assert st["switches"] == st["lazy"] + st["accepted"] + st["rejected_loop"] + st["rejected_exists"]
+    deg0 = np.bincount(np.concatenate(oracle.unpack(e0)), minlength=24)
+    deg1 = np.bincount(np.concatenate(oracle.unpack(e)), minlength=24)
+    assert np.array_equal(deg0, deg1)
+    assert len(set(e.tolist())) == len(e)
+
+
+def test_invariants_power_law_graph():
+    e0 = inputs.pld_graph(300, 2.2, 1, 40, seed=11)
+    e, st = oracle.run(e0, seed=3, rounds=3, check_every_switch=True)
+    assert st["accepted"] > 0
+
+
+def test_resume_equals_one_run():
+    e0 = inputs.random_simple_graph(60, 200, 4)
+    e10, _ = oracle.run(e0, seed=77, rounds=10)
+    e5, _ = oracle.run(e0, seed=77, rounds=5)
+    e55, _ = oracle.run(e5, seed=77, rounds=5, start_round=5)
+    assert np.array_equal(e10, e55)
+
+
+def test_lazy_rate_matches_threshold():
+    e0 = inputs.random_simple_graph(200, 2000, 5)
+    _, st = oracle.run(e0, seed=1, rounds=10, lazy_threshold=1 << 62)  # P_L = 1/4
+    n = st["switches"]
+    assert abs(st["lazy"] - n / 4) < 5 * math.sqrt(n * 3 / 16)
+
+
+def test_validate_codes():
+    assert oracle.validate(P([(0, 1), (1, 2)]), 3)[0] == oracle.OK
+    assert oracle.validate(np.array([(2 << 32) | 2], dtype=np.uint64), 3)[0] == oracle.E_LOOP
+    assert oracle.validate(P([(0, 1), (1, 0)]), 3)[0] == oracle.E_MULTI
+    assert oracle.validate(P([(0, 1), (1, 5)]), 3)[0] == oracle.E_RANGE
+    code, canon = oracle.validate(np.array([(5 << 32) | 1], dtype=np.uint64), 0)
+    assert code == oracle.OK and int(canon[0]) == (1 << 32) | 5
+
+
+# ---------------------------------------------------------------- Thm. 1
+
+def enumerate_gd(deg):
+    """All simple graphs on len(deg) nodes with exactly this degree sequence."""
+    n = len(deg)
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n)]
+    m = sum(deg) // 2
+    out = []
+    for combo in itertools.combinations(range(len(pairs)), m):
+        d = [0] * n
+        for c in combo:
+            a, b = pairs[c]
+            d[a] += 1
+            d[b] += 1
+        if d == list(deg):
+            out.append(tuple(sorted(pairs[c] for c in combo)))
+    return out
+
+
+def graph_key(edges):
+    u, v = oracle.unpack(edges)
+    return tuple(sorted(zip(u.tolist(), v.tolist())))
+
+
+def transition_counts(states, m, lazy_patterns=None):
+    """counts[A][B] = #(pi, skip pattern) taking graph A to graph B."""
+    index = {s: t for t, s in enumerate(states)}
+    C = np.zeros((len(states), len(states)), dtype=np.int64)
+    perms = list(itertools.permutations(range(m)))
+    patterns = lazy_patterns or [None]
+    for a, s in enumerate(states):
+        e = P(list(s))
+        for pi in perms:
+            for pat in patterns:
+                after, _ = oracle.global_switch(e, pi, skip=pat)
+                C[a, index[graph_key(after)]] += 1
+    return C
+
+
+@pytest.mark.parametrize("deg", [(1, 1, 1, 1), (2, 2, 1, 1, 1, 1), (2, 2, 2, 2, 1, 1), (2, 2, 2, 2, 2, 2),
+                                 (3, 2, 2, 2, 2, 1)])
+def test_transition_matrix_symmetric_and_stochastic(deg):
+    states = enumerate_gd(deg)
+    m = sum(deg) // 2
+    C = transition_counts(states, m)
+    assert (C.sum(axis=1) == math.factorial(m)).all()      # every row is a distribution
+    assert np.array_equal(C, C.T)                           # Thm. 1: P_AB = P_BA
+    # irreducible and aperiodic on G(d): some power is entrywise positive
+    Pm = C / math.factorial(m)
+    Q = np.linalg.matrix_power(Pm, 4 * len(states))
+    assert (Q > 0).all()
+
+
+def test_transition_matrix_symmetric_with_laziness():
+    deg = (2, 2, 2, 2, 1, 1)
+    states = enumerate_gd(deg)
+    m = sum(deg) // 2
+    L = m // 2
+    pats = [np.array(p, dtype=np.uint8) for p in itertools.product((0, 1), repeat=L)]
+    C = transition_counts(states, m, lazy_patterns=pats)     # P_L = 1/2: equal weights
+    assert (C.sum(axis=1) == math.factorial(m) * 2**L).all()
+    assert np.array_equal(C, C.T)
+
+
+def test_final_graph_uniform_on_gd_chi2():
+    from scipy.stats import chisquare
+    deg = (2, 2, 2, 2, 2, 2)
+    states = enumerate_gd(deg)
+    assert len(states) == 70            # 60 hexagons + 10 pairs of triangles
+    m = sum(deg) // 2
+    Pm = transition_counts(states, m) / math.factorial(m)
+    start = inputs.havel_hakimi(np.array(deg, dtype=np.uint32))
+    x = np.zeros(len(states))
+    x[states.index(graph_key(start))] = 1.0
+    rounds = 0
+    while 0.5 * np.abs(x - 1.0 / len(states)).sum() > 1e-4:
+        x = x @ Pm
+        rounds += 1
+    index = {s: t for t, s in enumerate(states)}
+    counts = np.zeros(len(states), dtype=np.int64)
+    n_samples = 21000
+    for seed in range(n_samples):
+        e, _ = oracle.run(start, seed=seed + 1000, rounds=rounds)
+        counts[index[graph_key(e)]] += 1
+    assert chisquare(counts).pvalue > 1e-4
