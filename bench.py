@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the G-ES-MC global switch round (arXiv 2111.03005) on GB300.
+
+A step is one call of the public API's gesmc_run with 20 global switches
+(Def. 2; Algorithm 3) on the workload below: 20 x floor(m/2) edge switches.
+The metric is attempted edge switches per second.  Every run's result is
+bit-exact with the sequential CPU oracle (tests/test_gpu_parity.py).
+
+Default workload: G(n = 2^24, p = 16/(n-1)), about 1.34e8 edges, seeded
+synthetic (a stand-in for the paper's SynGnp family).  Device state is about
+13 GB, far above the 129 MB L2, so consecutive steps cannot run out of L2.
+
+Usage:
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gesmc|reference]
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (a single chain does not shard); value = all ranks' switches / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "edge switches/sec on 1 GB300 (bit-exact vs sequential oracle); % random-access HBM roofline"
+UNIT = "edge switches/s"
+ROUNDS_PER_STEP = 20
+
+WORKLOADS = {
+    "gnp_2p24": dict(desc="G(n=2^24, p=16/(n-1)), seed 3; 20 global switches per step", n_log2=24, deg=16.0,
+                     seed=3),
+    "gnp_2p20": dict(desc="G(n=2^20, p=16/(n-1)), seed 5", n_log2=20, deg=16.0, seed=5),
+}
+CPU_SAMPLE = "gnp_2p20"
+
+
+def make_workload(name):
+    from paper_2111_03005_gb300 import inputs
+
+    w = WORKLOADS[name]
+    n = 1 << w["n_log2"]
+    return inputs.gnp(n, w["deg"] / (n - 1), w["seed"]), n
+
+
+# --------------------------------------------------------------------- ranks
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest `value` over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- roofline
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(stage: str, m: int, L: int, cap: int, nb: int, accepted: float) -> float:
+    """DRAM bytes a stage must move per round, counting each random access as
+    the 32-byte sector it touches (64 bytes for a read-modify-write)."""
+    sector = 32.0
+    if stage == "clear":
+        return 16.0 * cap + 4.0 * L + 4.0 * nb
+    if stage == "scatter":
+        return sector * m
+    if stage == "sortpair":
+        # bucket read 8 B per position; per switch two source gathers, four
+        # table claims (sector read + write back), a 16 B record write
+        return 8.0 * m + L * (2 * sector + 4 * 2 * sector + 16.0)
+    if stage == "decide1":
+        # per switch: record read, two slot reads, status write; accepted
+        # switches write two edge-list entries
+        return L * (16.0 + 2 * sector + 4.0) + accepted * 2 * sector
+    if stage == "scan":
+        return 12.0 * nb
+    return 0.0
+
+
+def traffic_from_profile(kernel: str, workload: str):
+    """Measured DRAM bytes per launch of `kernel` from the committed ncu
+    summary, if the kernel's source has not changed since it was taken."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
+    try:
+        kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line)
+        src = open(os.path.join(ROOT, "paper_2111_03005_gb300", "csrc", "round.cu"), "rb").read()
+        if kv.get("round_cu_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------- CPU legs
+
+def cpu_sample_switches_per_s():
+    """The oracle, as it stands, on one host core: one global switch of the
+    2^20-node sample (same degree profile as the default workload)."""
+    import oracle
+
+    edges, _ = make_workload(CPU_SAMPLE)
+    oracle.build()
+    t0 = time.perf_counter()
+    _, st = oracle.run(edges, seed=11, rounds=1)
+    dt = time.perf_counter() - t0
+    return st["switches"] / dt, st["switches"], dt
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    edges, n = make_workload(CPU_SAMPLE)
+    times, done = [], 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, st = oracle.run(edges, seed=11 + step, rounds=1)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            done += st["switches"]
+    total = sum(times)
+    value = done / total
+    sample = (f"1 global switch per step on {WORKLOADS[CPU_SAMPLE]['desc']} (m={len(edges)}), "
+              f"sequential oracle, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": WORKLOADS[CPU_SAMPLE]["desc"],
+                   "parallelism": "none (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+
+def run_gesmc(args):
+    import numpy as np
+    import torch
+
+    from paper_2111_03005_gb300 import gesmc
+
+    world, rank, local = dist_env()
+    if world != args.gpus:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    edges, n = make_workload(args.workload)
+    m, L = len(edges), len(edges) // 2
+    seed = 1000 + rank
+    chain = gesmc.Chain(edges, n=n)
+    for _ in range(args.warmup):
+        chain.run(ROUNDS_PER_STEP, seed)
+    chain.reset_stats()
+    chain.set_profiling(True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        start.record(stream)
+        for _ in range(args.steps):
+            chain.run(ROUNDS_PER_STEP, seed)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    barrier(dist)
+    ms_local = start.elapsed_time(stop)
+    ms = max_over_ranks(ms_local, dist, dev)
+    st = chain.stats()
+    stage_ms, prof_rounds = chain.stage_times()
+    chain.close()
+
+    switches_rank = args.steps * ROUNDS_PER_STEP * L
+    value = world * switches_rank / (ms / 1e3)
+
+    # roofline of the dominant kernel, from its live CUDA-event time
+    cap, nb = st["table_slots"], st["buckets"]
+    acc_per_round = st["accepted"] / max(st["rounds"], 1)
+    peak, peak_kind = read_peaks()
+    per_stage = {k: v / max(prof_rounds, 1) for k, v in stage_ms.items()}
+    dom = max(per_stage, key=per_stage.get)
+    abytes = algorithmic_bytes(dom, m, L, cap, nb, acc_per_round)
+    achieved = abytes / (per_stage[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": abytes,
+                "traffic": traffic_from_profile(f"k_{dom}", args.workload)}
+    # whole-round view: all stages' algorithmic bytes over the round time
+    round_bytes = sum(algorithmic_bytes(s, m, L, cap, nb, acc_per_round) for s in per_stage)
+    round_ms = sum(per_stage.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": n, "m": m,
+                   "global_switches_per_step": ROUNDS_PER_STEP, "switches_per_step": ROUNDS_PER_STEP * L,
+                   "l2": "inputs larger than L2 (device state ~%.1f GB)" % (gesmc.gesmc_device_bytes(m, 0.5) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "round": {"ms": round_ms, "algorithmic_GBps": round_bytes / (round_ms / 1e3) / 1e9,
+                  "stages_ms": {k: round(v, 4) for k, v in per_stage.items()}},
+        "waves": {"max": st["waves_max"], "mean": st["waves_total"] / max(st["rounds"], 1),
+                  "accept_rate": st["accepted"] / max(st["switches"], 1)},
+        "gpu_launches": st["kernel_launches"],
+    }
+    clk = clocks.summary()
+    line["clocks"] = clk
+
+    # end to end through the public API from pinned host memory
+    if not args.no_e2e:
+        host_in = torch.from_numpy(edges.view(np.int64)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        e2e_times = []
+        for step in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with gesmc.Chain(host_in, n=n) as c:
+                c.run(ROUNDS_PER_STEP, seed + 7)
+                c.edges(host_out)
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_t = max_over_ranks(statistics.median(e2e_times), dist, dev)
+        line["e2e"] = {"value": world * ROUNDS_PER_STEP * L / e2e_t, "unit": UNIT,
+                       "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * m,
+                       "includes": "gesmc_create (H2D copy, validation) + gesmc_run(20) + gesmc_edges (D2H) + destroy"}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, sw, dt = cpu_sample_switches_per_s()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 global switch ({sw} switches) on {WORKLOADS[CPU_SAMPLE]['desc']}, "
+                                          f"{dt:.1f} s, sequential oracle, 1 thread"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gesmc", "reference"], default="gesmc")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="gnp_2p24")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gesmc(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * gesmc.h -- C ABI of libgesmc, the GB300 (sm_103a) global switch round of
+ * the Global Edge Switching Markov Chain (G-ES-MC) of Allendorf, Meyer,
+ * Penschuck and Tran, "Parallel Global Edge Switching for the Uniform
+ * Sampling of Simple Graphs with Prescribed Degrees" (arXiv 2111.03005).
+ *
+ * The state of a chain is an indexed edge list E[0..m) of a simple graph
+ * (Sec. 2.1).  Edge ids are 64-bit: the smaller node id in the high 32 bits,
+ * the larger in the low 32 bits (Sec. 5.2).  One call of gesmc_run performs
+ * global switches (Def. 2) one after another, each being floor(m/2) edge
+ * switches (Def. 1) over the disjoint pairs of a random permutation of the
+ * positions, with exactly the result of running them in sequence (the
+ * guarantee of ParallelSuperstep, Algorithm 1, driven as in Algorithm 3).
+ *
+ * Randomness is counter based: with Philox4x64-10 (Salmon et al., SC'11),
+ * round r's permutation is the argsort of the words
+ *   K(i) = Philox4x64-10(counter = (i >> 2, r, 0, 0), key = (seed, 0))[i & 3]
+ * (ties: smaller position first), and with a nonzero lazy threshold t,
+ * switch k of round r is skipped iff
+ *   Philox4x64-10(counter = (k >> 2, r, 1, 0), key = (seed, 0))[k & 3] < t,
+ * i.e. each switch is skipped with probability P_L = t / 2^64 (Def. 2).
+ * Rounds are numbered cumulatively per handle from opts.start_round, so
+ * run(a, s) followed by run(b, s) equals run(a + b, s).
+ *
+ * Errors: every int-returning call returns GESMC_OK (0) or a negative
+ * GESMC_E_* code.  After GESMC_E_CUDA, GESMC_E_TABLE_FULL, GESMC_E_WAVE_CAP
+ * or GESMC_E_INTERNAL from gesmc_run the edge list is unspecified and only
+ * gesmc_stats, gesmc_edges and gesmc_destroy may be called.
+ *
+ * Threading: a handle may be used by one host thread at a time.  All device
+ * work is ordered on opts.stream (the legacy default stream when NULL);
+ * every call returns only after its device work has completed.
+ */
+#ifndef GESMC_H
+#define GESMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gesmc_ctx *gesmc_t;
+
+enum {
+  GESMC_OK = 0,
+  GESMC_E_INVALID = -1,    /* null argument, m >= 2^32, bad option value     */
+  GESMC_E_LOOP = -2,       /* input edge {u, u} (not a simple graph)         */
+  GESMC_E_MULTI = -3,      /* input edge listed twice (not a simple graph)   */
+  GESMC_E_RANGE = -4,      /* input node id >= opts.n                        */
+  GESMC_E_NOMEM = -5,      /* device allocation failed                       */
+  GESMC_E_CUDA = -6,       /* a CUDA runtime call failed                     */
+  GESMC_E_TABLE_FULL = -7, /* dependency table overflow (not expected)       */
+  GESMC_E_WAVE_CAP = -8,   /* a round needed more waves than opts.max_waves  */
+  GESMC_E_INTERNAL = -9,   /* bucket overflow or stalled waves (not expected) */
+  GESMC_E_CAPACITY = -10   /* caller's output buffer too small               */
+};
+
+/* Device allocation hooks: alloc returns device memory usable on `stream`
+ * (or NULL on failure); free releases it.  Both NULL: cudaMalloc/cudaFree. */
+typedef void *(*gesmc_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*gesmc_free_fn)(void *ptr, void *ctx);
+
+typedef struct gesmc_opts {
+  uint64_t n;              /* node ids must be < n; 0: n = largest id + 1       */
+  double load_factor;      /* dependency-table load bound in (0, 0.9]; 0: 0.5   */
+  uint64_t lazy_threshold; /* Def. 2 laziness, P_L = t / 2^64; 0: never lazy   */
+  uint64_t start_round;    /* number of the first round this handle runs       */
+  uint32_t max_waves;      /* cap on resolution waves per round; 0: 10000      */
+  uint32_t reserved;
+  void *stream;            /* cudaStream_t for all device work; NULL: default  */
+  gesmc_alloc_fn alloc;    /* optional device allocator                        */
+  gesmc_free_fn free;
+  void *alloc_ctx;
+} gesmc_opts;
+
+#define GESMC_WAVE_HIST 64
+
+typedef struct gesmc_stats_s {
+  uint64_t rounds;          /* global switches run since create / reset           */
+  uint64_t switches;        /* floor(m/2) per round (Sec. 6: the unit of work)    */
+  uint64_t lazy;            /* switches skipped by the laziness rule              */
+  uint64_t accepted;        /* switches that rewired their two edges              */
+  uint64_t rejected_loop;   /* a new edge would be a loop (Def. 1)                */
+  uint64_t rejected_exists; /* a new edge is in E when the switch runs (Def. 1)   */
+  uint64_t kernel_launches; /* CUDA kernels gesmc_run launched                     */
+  uint64_t table_slots;     /* slots of the dependency table (16 bytes each)      */
+  uint64_t buckets;         /* permutation buckets per round                      */
+  uint64_t waves_total;     /* resolution waves summed over rounds (Algorithm 1's
+                               rounds of decide/delay)                            */
+  uint64_t waves_max;       /* largest wave count of one round                    */
+  uint64_t wave_hist[GESMC_WAVE_HIST]; /* rounds that needed w waves (w >= 63: last) */
+  uint64_t last_round_pending[GESMC_WAVE_HIST]; /* undecided switches entering wave
+                               w (index w, w >= 1) in the most recent round       */
+} gesmc_stats_t;
+
+/* Fill *o with the defaults named above. */
+void gesmc_opts_default(gesmc_opts *o);
+
+/* Create a chain from a simple graph (Sec. 2.1, "degree-valid edge list").
+ *   edges: m packed edge ids, either orientation; stored canonically
+ *          (min << 32 | max).  Host memory if edges_on_device == 0, else a
+ *          device pointer of the current device.  The library copies it; the
+ *          caller keeps ownership.
+ *   m:     number of edges, < 2^32.
+ *   opts:  NULL for defaults.
+ *   out:   receives the handle (owns all device state until gesmc_destroy).
+ * Returns GESMC_E_LOOP / GESMC_E_RANGE / GESMC_E_MULTI (that precedence) if
+ * the list is not a simple graph on [0, n). */
+int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const gesmc_opts *opts,
+                 gesmc_t *out);
+
+/* Run `global_switches` rounds of Algorithm 3 (ParGlobalES) with the given
+ * seed: each round draws the permutation of Def. 2 and performs its
+ * floor(m/2) edge switches with the sequential outcome (Algorithm 1). */
+int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed);
+
+/* Copy E, in position order, to `out` (host memory, or device memory if
+ * out_on_device != 0); `capacity` is out's length in edges.  *m_out (if not
+ * NULL) receives m.  Returns GESMC_E_CAPACITY if capacity < m. */
+int gesmc_edges(gesmc_t h, uint64_t *out, uint64_t capacity, int out_on_device, uint64_t *m_out);
+
+/* Counters accumulated by gesmc_run since create or gesmc_reset_stats. */
+int gesmc_stats(gesmc_t h, gesmc_stats_t *out);
+int gesmc_reset_stats(gesmc_t h);
+
+/* Stage timing.  With profiling on, gesmc_run brackets each kernel of every
+ * round with CUDA events on the handle's stream and, after the call's final
+ * synchronisation, adds each stage's elapsed time to a per-stage total.
+ * gesmc_stage_times copies the totals (milliseconds, since create or
+ * gesmc_reset_stats) of the first n_stages stages into ms and the number of
+ * profiled rounds into *rounds.  Stage i is named by gesmc_stage_name(i);
+ * GESMC_NUM_STAGES stages exist, one kernel each, in launch order. */
+#define GESMC_NUM_STAGES 8
+int gesmc_set_profiling(gesmc_t h, int enable);
+int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds);
+const char *gesmc_stage_name(int stage);
+
+/* Number of the next round the handle will run (start_round + rounds run). */
+uint64_t gesmc_next_round(gesmc_t h);
+
+/* Number of edges and nodes of the chain. */
+uint64_t gesmc_num_edges(gesmc_t h);
+uint64_t gesmc_num_nodes(gesmc_t h);
+
+/* Device bytes a handle with m edges and this load factor allocates. */
+size_t gesmc_device_bytes(uint64_t m, double load_factor);
+
+/* Release the handle and its device memory (NULL is ignored). */
+void gesmc_destroy(gesmc_t h);
+
+/* Static description of an error code. */
+const char *gesmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GESMC_H */

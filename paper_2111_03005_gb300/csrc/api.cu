@@ -1,0 +1,424 @@
+// C ABI of libgesmc (declared in include/gesmc.h): handle life cycle, device
+// memory plan, create-time validation and the round loop of Algorithm 3
+// (ParGlobalES) of arXiv 2111.03005.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gesmc.h"
+#include "gesmc_internal.cuh"
+
+using namespace gesmc;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Sizes of the pieces of one handle's single device allocation.
+struct Plan {
+  uint64_t m = 0;
+  uint32_t L = 0, B = 0, nb = 1;
+  unsigned long long cap = 0;
+  size_t off_E, off_T, off_buf, off_cnt, off_boff, off_cursor, off_sw, off_status, off_list0, off_list1,
+      off_pib, off_bnd, off_ctl, off_st, off_scratch, total;
+};
+
+bool make_plan(uint64_t m, double lf, Plan *p) {
+  p->m = m;
+  p->L = (uint32_t)(m / 2);
+  // buckets of about 2^kBucketAvgLog2 positions; one bucket while it fits
+  uint32_t B = 0;
+  if (m > (uint64_t)kBucketCap / 2) {
+    while ((m >> B) > (1ull << kBucketAvgLog2)) ++B;
+  }
+  p->B = B;
+  p->nb = 1u << B;
+  // keys in T per round: m sources + at most 2L targets
+  const double keys = (double)m + 2.0 * (double)p->L;
+  unsigned long long cap = (unsigned long long)(keys / lf) + 64;
+  cap = (cap + 63) / 64 * 64;
+  if (cap >= (unsigned long long)kSwCodeMin) return false;
+  p->cap = cap;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + (bytes ? bytes : 1));
+    return at;
+  };
+  p->off_E = take(8 * m);
+  p->off_T = take(sizeof(Slot) * cap);
+  p->off_buf = take(8 * m);
+  p->off_cnt = take(4ull * p->nb);
+  p->off_boff = take(4ull * (p->nb + 1));
+  p->off_cursor = take(4ull * p->nb);
+  p->off_sw = take(16ull * p->L);
+  p->off_status = take(4ull * p->L);
+  p->off_list0 = take(4ull * p->L);
+  p->off_list1 = take(4ull * p->L);
+  p->off_pib = take(4 * m);
+  p->off_bnd = take(4ull * (p->nb + 1));
+  p->off_ctl = take(sizeof(Counters));
+  p->off_st = take(sizeof(StatsDev));
+  p->off_scratch = take(64);
+  p->total = o;
+  return true;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct gesmc_ctx {
+  int device = 0;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;
+  gesmc_alloc_fn alloc = nullptr;
+  gesmc_free_fn free_fn = nullptr;
+  void *alloc_ctx = nullptr;
+  void *base = nullptr;
+  Plan plan;
+  uint64_t n = 0;
+  uint64_t next_round = 0;
+  uint64_t lazy_threshold = 0;
+  uint32_t max_waves = 0;
+  uint64_t rounds = 0;
+  uint64_t launches = 0;
+  int broken = 0;
+  RoundArgs args;
+  // stage timing (gesmc_set_profiling): kNumStages + 1 events per round
+  int profiling = 0;
+  std::vector<cudaEvent_t> events;
+  double stage_ms[kNumStages] = {};
+  uint64_t stage_rounds = 0;
+};
+
+namespace {
+
+void *dev_alloc(gesmc_ctx *h, size_t bytes) {
+  if (h->alloc) return h->alloc(bytes, (void *)h->stream, h->alloc_ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+void dev_free(gesmc_ctx *h, void *p) {
+  if (!p) return;
+  if (h->free_fn) h->free_fn(p, h->alloc_ctx);
+  else cudaFree(p);
+}
+
+template <class T>
+T *at(void *base, size_t off) {
+  return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+int map_device_errors(uint32_t err) {
+  if (err & kErrTableFull) return GESMC_E_TABLE_FULL;
+  if (err & kErrWaveCap) return GESMC_E_WAVE_CAP;
+  if (err & (kErrBucket | kErrNoProgress | kErrRecord)) return GESMC_E_INTERNAL;
+  return GESMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gesmc_opts_default(gesmc_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->load_factor = 0.5;
+}
+
+size_t gesmc_device_bytes(uint64_t m, double load_factor) {
+  if (load_factor <= 0.0) load_factor = 0.5;
+  Plan p;
+  if (m >= (1ull << 32) || load_factor > 0.9 || !make_plan(m, load_factor, &p)) return 0;
+  return p.total;
+}
+
+const char *gesmc_strerror(int code) {
+  switch (code) {
+    case GESMC_OK: return "ok";
+    case GESMC_E_INVALID: return "invalid argument";
+    case GESMC_E_LOOP: return "edge list contains a loop";
+    case GESMC_E_MULTI: return "edge list contains a repeated edge";
+    case GESMC_E_RANGE: return "node id out of range";
+    case GESMC_E_NOMEM: return "device allocation failed";
+    case GESMC_E_CUDA: return "CUDA runtime error";
+    case GESMC_E_TABLE_FULL: return "dependency table full";
+    case GESMC_E_WAVE_CAP: return "wave cap exceeded";
+    case GESMC_E_INTERNAL: return "internal error (permutation bucket overflow)";
+    case GESMC_E_CAPACITY: return "output buffer too small";
+    default: return "unknown error";
+  }
+}
+
+void gesmc_destroy(gesmc_t h) {
+  if (!h) return;
+  {
+    DeviceGuard g(h->device);
+    if (h->base) {
+      cudaStreamSynchronize(h->stream);
+      dev_free(h, h->base);
+    }
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  }
+  delete h;
+}
+
+int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const gesmc_opts *opts, gesmc_t *out) {
+  if (!out) return GESMC_E_INVALID;
+  *out = nullptr;
+  gesmc_opts o;
+  gesmc_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.load_factor == 0.0) o.load_factor = 0.5;
+  if (!(o.load_factor > 0.0 && o.load_factor <= 0.9)) return GESMC_E_INVALID;
+  if (m >= (1ull << 32) || (m > 0 && !edges)) return GESMC_E_INVALID;
+  if (o.n > (1ull << 32)) return GESMC_E_INVALID;
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return GESMC_E_INVALID;
+
+  gesmc_ctx *h = new (std::nothrow) gesmc_ctx();
+  if (!h) return GESMC_E_NOMEM;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return GESMC_E_CUDA;
+  }
+  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->num_sms < 1) h->num_sms = 1;
+  h->stream = (cudaStream_t)o.stream;
+  h->alloc = o.alloc;
+  h->free_fn = o.free;
+  h->alloc_ctx = o.alloc_ctx;
+  h->next_round = o.start_round;
+  h->lazy_threshold = o.lazy_threshold;
+  h->max_waves = o.max_waves;
+  if (!make_plan(m, o.load_factor, &h->plan)) {
+    delete h;
+    return GESMC_E_INVALID;
+  }
+  const Plan &p = h->plan;
+  h->base = dev_alloc(h, p.total);
+  if (!h->base) {
+    delete h;
+    return GESMC_E_NOMEM;
+  }
+  void *b = h->base;
+  RoundArgs &a = h->args;
+  a.E = at<unsigned long long>(b, p.off_E);
+  a.T = at<Slot>(b, p.off_T);
+  a.cap = p.cap;
+  a.buf = at<unsigned long long>(b, p.off_buf);
+  a.bucket_cnt = at<uint32_t>(b, p.off_cnt);
+  a.bucket_off = at<uint32_t>(b, p.off_boff);
+  a.cursor = at<uint32_t>(b, p.off_cursor);
+  a.sw = at<uint4>(b, p.off_sw);
+  a.status = at<uint32_t>(b, p.off_status);
+  a.list0 = at<uint32_t>(b, p.off_list0);
+  a.list1 = at<uint32_t>(b, p.off_list1);
+  a.pib = at<uint32_t>(b, p.off_pib);
+  a.bnd = at<uint32_t>(b, p.off_bnd);
+  a.ctl = at<Counters>(b, p.off_ctl);
+  a.st = at<StatsDev>(b, p.off_st);
+  a.m = (uint32_t)m;
+  a.L = p.L;
+  a.B = p.B;
+  a.nb = p.nb;
+  a.lazy_threshold = o.lazy_threshold;
+  a.max_waves = o.max_waves;
+
+  int rc = GESMC_OK;
+  uint32_t *flags = at<uint32_t>(b, p.off_scratch);
+  uint32_t host_flags[2] = {0, 0};
+  cudaStream_t s = h->stream;
+  bool ok = true;
+  if (m > 0)
+    ok &= cudaMemcpyAsync(a.E, edges, 8 * m, edges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          s) == cudaSuccess;
+  ok &= cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
+  if (ok && m > 0) ok &= launch_canonicalise(a.E, a.m, o.n, flags, flags + 1, s, h->num_sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    rc = GESMC_E_CUDA;
+  } else if (host_flags[0] & kFlagLoop) {
+    rc = GESMC_E_LOOP;
+  } else if (host_flags[0] & kFlagRange) {
+    rc = GESMC_E_RANGE;
+  } else {
+    h->n = o.n ? o.n : (m ? (uint64_t)host_flags[1] + 1 : 0);
+    if (m > 0) {
+      ok &= launch_clear_table(a.T, a.cap, s, h->num_sms) == cudaSuccess;
+      ok &= launch_duplicate_check(a.E, a.m, a.T, a.cap, flags, s, h->num_sms) == cudaSuccess;
+      ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+      ok &= cudaStreamSynchronize(s) == cudaSuccess;
+    }
+    if (!ok) rc = GESMC_E_CUDA;
+    else if (host_flags[0] & kFlagMulti) rc = GESMC_E_MULTI;
+    else if (host_flags[0] & kFlagTableFull) rc = GESMC_E_INTERNAL;
+  }
+  if (rc != GESMC_OK) {
+    cudaGetLastError();
+    gesmc_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return GESMC_OK;
+}
+
+int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed) {
+  if (!h) return GESMC_E_INVALID;
+  if (h->broken) return h->broken;
+  DeviceGuard g(h->device);
+  cudaStream_t s = h->stream;
+  RoundArgs a = h->args;
+  a.seed = seed;
+  if (cudaMemsetAsync(&a.ctl->err, 0, sizeof(uint32_t), s) != cudaSuccess) return GESMC_E_CUDA;
+  const size_t per_round = kNumStages + 1;
+  if (h->profiling) {
+    const size_t need = per_round * (size_t)global_switches;
+    while (h->events.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return GESMC_E_CUDA;
+      }
+      h->events.push_back(e);
+    }
+  }
+  uint32_t launches = 0;
+  for (uint64_t r = 0; r < global_switches; ++r) {
+    a.round = h->next_round + r;
+    cudaEvent_t *ev = h->profiling ? &h->events[per_round * r] : nullptr;
+    if (launch_round(a, s, h->num_sms, ev, &launches) != cudaSuccess) {
+      h->broken = GESMC_E_CUDA;
+      return GESMC_E_CUDA;
+    }
+  }
+  Counters ctl;
+  if (cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    h->broken = GESMC_E_CUDA;
+    return GESMC_E_CUDA;
+  }
+  if (h->profiling) {
+    for (uint64_t r = 0; r < global_switches; ++r) {
+      for (int st = 0; st < kNumStages; ++st) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->events[per_round * r + st], h->events[per_round * r + st + 1]) ==
+            cudaSuccess)
+          h->stage_ms[st] += ms;
+      }
+    }
+    h->stage_rounds += global_switches;
+  }
+  h->next_round += global_switches;
+  h->rounds += global_switches;
+  h->launches += launches;
+  const int rc = map_device_errors(ctl.err);
+  if (rc != GESMC_OK) h->broken = rc;
+  return rc;
+}
+
+int gesmc_edges(gesmc_t h, uint64_t *out, uint64_t capacity, int out_on_device, uint64_t *m_out) {
+  if (!h) return GESMC_E_INVALID;
+  if (m_out) *m_out = h->plan.m;
+  if (capacity < h->plan.m) return GESMC_E_CAPACITY;
+  if (h->plan.m == 0) return GESMC_OK;
+  if (!out) return GESMC_E_INVALID;
+  DeviceGuard g(h->device);
+  if (cudaMemcpyAsync(out, h->args.E, 8 * h->plan.m, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                      h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  return GESMC_OK;
+}
+
+int gesmc_stats(gesmc_t h, gesmc_stats_t *out) {
+  if (!h || !out) return GESMC_E_INVALID;
+  DeviceGuard g(h->device);
+  StatsDev st;
+  if (cudaMemcpyAsync(&st, h->args.st, sizeof(StatsDev), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->rounds = h->rounds;
+  out->switches = h->rounds * (uint64_t)h->plan.L;
+  out->lazy = st.lazy;
+  out->accepted = st.accepted;
+  out->rejected_loop = st.rej_loop;
+  out->rejected_exists = st.rej_exists;
+  out->kernel_launches = h->launches;
+  out->table_slots = h->plan.cap;
+  out->buckets = h->plan.nb;
+  out->waves_total = st.waves_total;
+  out->waves_max = st.waves_max;
+  for (int w = 0; w < GESMC_WAVE_HIST && w < kWaveHist; ++w) {
+    out->wave_hist[w] = st.wave_hist[w];
+    out->last_round_pending[w] = st.last_pending[w];
+  }
+  return GESMC_OK;
+}
+
+int gesmc_reset_stats(gesmc_t h) {
+  if (!h) return GESMC_E_INVALID;
+  DeviceGuard g(h->device);
+  if (cudaMemsetAsync(h->args.st, 0, sizeof(StatsDev), h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  h->rounds = 0;
+  h->launches = 0;
+  for (double &x : h->stage_ms) x = 0.0;
+  h->stage_rounds = 0;
+  return GESMC_OK;
+}
+
+int gesmc_set_profiling(gesmc_t h, int enable) {
+  if (!h) return GESMC_E_INVALID;
+  h->profiling = enable ? 1 : 0;
+  return GESMC_OK;
+}
+
+int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
+  if (!h || (n_stages > 0 && !ms)) return GESMC_E_INVALID;
+  for (int st = 0; st < n_stages; ++st) ms[st] = st < kNumStages ? h->stage_ms[st] : 0.0;
+  if (rounds) *rounds = h->stage_rounds;
+  return GESMC_OK;
+}
+
+const char *gesmc_stage_name(int stage) {
+  static const char *names[kNumStages] = {"clear",    "hist",     "scan",    "scatter",
+                                          "sortpair", "boundary", "decide1", "tail"};
+  return (stage >= 0 && stage < kNumStages) ? names[stage] : "";
+}
+
+uint64_t gesmc_next_round(gesmc_t h) { return h ? h->next_round : 0; }
+uint64_t gesmc_num_edges(gesmc_t h) { return h ? h->plan.m : 0; }
+uint64_t gesmc_num_nodes(gesmc_t h) { return h ? h->n : 0; }
+
+}  // extern "C"

@@ -1,0 +1,316 @@
+"""Thin ctypes binding of libgesmc (include/gesmc.h).
+
+The functions ``gesmc_create``, ``gesmc_run``, ``gesmc_edges``,
+``gesmc_stats``, ``gesmc_reset_stats``, ``gesmc_destroy`` and
+``gesmc_strerror`` mirror the C entry points one to one; ``Chain`` wraps a
+handle.  Every step of a round runs in the library's CUDA kernels; this
+module only marshals arguments.  PyTorch supplies the device memory (its
+caching allocator, through the library's allocation hooks) and the stream
+(the current torch stream).  There is no CPU fallback: if the library cannot
+be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GESMC_OK = 0
+GESMC_E_INVALID = -1
+GESMC_E_LOOP = -2
+GESMC_E_MULTI = -3
+GESMC_E_RANGE = -4
+GESMC_E_NOMEM = -5
+GESMC_E_CUDA = -6
+GESMC_E_TABLE_FULL = -7
+GESMC_E_WAVE_CAP = -8
+GESMC_E_INTERNAL = -9
+GESMC_E_CAPACITY = -10
+WAVE_HIST = 64
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class GesmcOpts(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("load_factor", ctypes.c_double),
+        ("lazy_threshold", ctypes.c_uint64),
+        ("start_round", ctypes.c_uint64),
+        ("max_waves", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class GesmcStats(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_uint64),
+        ("switches", ctypes.c_uint64),
+        ("lazy", ctypes.c_uint64),
+        ("accepted", ctypes.c_uint64),
+        ("rejected_loop", ctypes.c_uint64),
+        ("rejected_exists", ctypes.c_uint64),
+        ("kernel_launches", ctypes.c_uint64),
+        ("table_slots", ctypes.c_uint64),
+        ("buckets", ctypes.c_uint64),
+        ("waves_total", ctypes.c_uint64),
+        ("waves_max", ctypes.c_uint64),
+        ("wave_hist", ctypes.c_uint64 * WAVE_HIST),
+        ("last_round_pending", ctypes.c_uint64 * WAVE_HIST),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: int(getattr(self, f)) for f, _ in self._fields_[:11]}
+        d["wave_hist"] = [int(x) for x in self.wave_hist]
+        d["last_round_pending"] = [int(x) for x in self.last_round_pending]
+        return d
+
+
+class GesmcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {gesmc_strerror(code)} ({code})")
+
+
+_lib = None
+_lib_lock = threading.Lock()
+
+# C symbols of include/gesmc.h: (name, restype, argtypes)
+_SIGNATURES = [
+    ("gesmc_opts_default", None, [ctypes.POINTER(GesmcOpts)]),
+    ("gesmc_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(GesmcOpts),
+                                    ctypes.POINTER(ctypes.c_void_p)]),
+    ("gesmc_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]),
+    ("gesmc_edges", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    ("gesmc_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GesmcStats)]),
+    ("gesmc_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
+    ("gesmc_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("gesmc_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+    ("gesmc_stage_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("gesmc_next_round", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("gesmc_num_edges", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("gesmc_num_nodes", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("gesmc_device_bytes", ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_double]),
+    ("gesmc_destroy", None, [ctypes.c_void_p]),
+    ("gesmc_strerror", ctypes.c_char_p, [ctypes.c_int]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Load (building first if needed) libgesmc.so; raises if that fails."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build_library()
+        lib = ctypes.CDLL(path)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def gesmc_strerror(code: int) -> str:
+    return load_library().gesmc_strerror(int(code)).decode()
+
+
+def gesmc_device_bytes(m: int, load_factor: float = 0.5) -> int:
+    return int(load_library().gesmc_device_bytes(m, load_factor))
+
+
+def _check(code: int, where: str):
+    if code != GESMC_OK:
+        raise GesmcError(code, where)
+
+
+class _TorchAllocator:
+    """Allocation hooks that route the library's device memory through torch."""
+
+    def __init__(self, device_index: int):
+        import torch
+
+        self._torch = torch
+        self._device = device_index
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, _ctx):
+        try:
+            return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self._device, int(stream or 0)))
+        except Exception:  # noqa: BLE001 -- a NULL return is the library's OOM signal
+            return None
+
+    def _free(self, ptr, _ctx):
+        if ptr:
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+
+
+def _as_edge_buffer(edges):
+    """(pointer, m, on_device, keepalive) for a numpy array or torch tensor of packed ids."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(edges, torch.Tensor):
+        if edges.dtype not in (torch.int64, torch.uint64):
+            raise TypeError("edge tensor must be int64 or uint64 (packed ids)")
+        t = edges.contiguous()
+        return t.data_ptr(), t.numel(), int(t.is_cuda), t
+    a = np.ascontiguousarray(np.asarray(edges, dtype=np.uint64))
+    return a.ctypes.data, a.size, 0, a
+
+
+def gesmc_create(edges, n: int = 0, load_factor: float = 0.5, lazy_threshold: int = 0, start_round: int = 0,
+                 max_waves: int = 0, stream=None, torch_allocator: bool = True):
+    """Create a chain handle; returns (handle, keepalive).  Raises GesmcError."""
+    import torch
+
+    lib = load_library()
+    if not torch.cuda.is_available():
+        raise RuntimeError("libgesmc needs a CUDA device")
+    opts = GesmcOpts()
+    lib.gesmc_opts_default(ctypes.byref(opts))
+    opts.n = n
+    opts.load_factor = load_factor
+    opts.lazy_threshold = lazy_threshold
+    opts.start_round = start_round
+    opts.max_waves = max_waves
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
+    hooks = None
+    if torch_allocator:
+        hooks = _TorchAllocator(torch.cuda.current_device())
+        opts.alloc = hooks.alloc
+        opts.free = hooks.free
+    ptr, m, on_dev, keep = _as_edge_buffer(edges)
+    h = ctypes.c_void_p()
+    _check(lib.gesmc_create(ctypes.c_void_p(ptr), m, on_dev, ctypes.byref(opts), ctypes.byref(h)), "gesmc_create")
+    return h, (hooks, keep)
+
+
+def gesmc_run(h, global_switches: int, seed: int):
+    _check(load_library().gesmc_run(h, global_switches, seed), "gesmc_run")
+
+
+def gesmc_edges(h, out=None):
+    """Copy E (position order) into `out` (numpy uint64 or torch int64/uint64 on any device) or a new numpy array."""
+    lib = load_library()
+    m = int(lib.gesmc_num_edges(h))
+    if out is None:
+        out = np.empty(m, dtype=np.uint64)
+    ptr, cap, on_dev, _keep = _as_edge_buffer(out)
+    if isinstance(out, np.ndarray) and not out.flags.c_contiguous:
+        raise ValueError("out must be contiguous")
+    m_out = ctypes.c_uint64()
+    _check(lib.gesmc_edges(h, ctypes.c_void_p(ptr), cap, on_dev, ctypes.byref(m_out)), "gesmc_edges")
+    return out
+
+
+def gesmc_stats(h) -> dict:
+    st = GesmcStats()
+    _check(load_library().gesmc_stats(h, ctypes.byref(st)), "gesmc_stats")
+    return st.as_dict()
+
+
+def gesmc_reset_stats(h):
+    _check(load_library().gesmc_reset_stats(h), "gesmc_reset_stats")
+
+
+NUM_STAGES = 8
+
+
+def gesmc_set_profiling(h, enable: bool):
+    _check(load_library().gesmc_set_profiling(h, int(enable)), "gesmc_set_profiling")
+
+
+def gesmc_stage_name(stage: int) -> str:
+    return load_library().gesmc_stage_name(stage).decode()
+
+
+def gesmc_stage_times(h) -> tuple[dict, int]:
+    """({stage name: accumulated ms}, profiled rounds)."""
+    ms = (ctypes.c_double * NUM_STAGES)()
+    rounds = ctypes.c_uint64()
+    _check(load_library().gesmc_stage_times(h, ms, NUM_STAGES, ctypes.byref(rounds)), "gesmc_stage_times")
+    return {gesmc_stage_name(i): float(ms[i]) for i in range(NUM_STAGES)}, int(rounds.value)
+
+
+def gesmc_destroy(h):
+    if h:
+        load_library().gesmc_destroy(h)
+
+
+class Chain:
+    """One G-ES-MC chain resident on the current CUDA device."""
+
+    def __init__(self, edges, **opts):
+        self._h, self._keep = gesmc_create(edges, **opts)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def m(self) -> int:
+        return int(load_library().gesmc_num_edges(self._h))
+
+    @property
+    def n(self) -> int:
+        return int(load_library().gesmc_num_nodes(self._h))
+
+    @property
+    def next_round(self) -> int:
+        return int(load_library().gesmc_next_round(self._h))
+
+    def run(self, global_switches: int, seed: int):
+        gesmc_run(self._h, global_switches, seed)
+        return self
+
+    def edges(self, out=None):
+        return gesmc_edges(self._h, out)
+
+    def stats(self) -> dict:
+        return gesmc_stats(self._h)
+
+    def reset_stats(self):
+        gesmc_reset_stats(self._h)
+
+    def set_profiling(self, enable: bool = True):
+        gesmc_set_profiling(self._h, enable)
+
+    def stage_times(self) -> tuple[dict, int]:
+        return gesmc_stage_times(self._h)
+
+    def close(self):
+        if self._h:
+            gesmc_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

@@ -1,0 +1,76 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function include/gesmc.h declares.  No device work is started here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2111_03005_gb300 import build as libbuild
+from paper_2111_03005_gb300 import gesmc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gesmc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(gesmc_[a-z_]+)\s*\(", text))
+    names -= {"gesmc_alloc_fn", "gesmc_free_fn"}
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ctypes.CDLL(libbuild.build_library())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gesmc_create", "gesmc_run", "gesmc_edges", "gesmc_stats", "gesmc_destroy", "gesmc_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {name for name, _, _ in gesmc._SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_host_only_entry_points():
+    lib = gesmc.load_library()
+    assert gesmc.gesmc_strerror(0) == "ok"
+    assert "loop" in gesmc.gesmc_strerror(gesmc.GESMC_E_LOOP)
+    opts = gesmc.GesmcOpts()
+    lib.gesmc_opts_default(ctypes.byref(opts))
+    assert opts.load_factor == 0.5 and opts.lazy_threshold == 0 and opts.n == 0
+    # memory plan: the dependency table dominates (16 B x 2m / load factor)
+    m = 1 << 20
+    b = gesmc.gesmc_device_bytes(m, 0.5)
+    assert 16 * 4 * m <= b < 16 * 4 * m + 64 * m
+    assert gesmc.gesmc_device_bytes(1 << 32, 0.5) == 0
+    assert gesmc.gesmc_stage_name(0) == "clear" and gesmc.gesmc_stage_name(99) == ""
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device():
+    lib = gesmc.load_library()
+    h = ctypes.c_void_p()
+    assert lib.gesmc_create(None, 5, 0, None, ctypes.byref(h)) == gesmc.GESMC_E_INVALID
+    opts = gesmc.GesmcOpts()
+    lib.gesmc_opts_default(ctypes.byref(opts))
+    opts.load_factor = 0.95
+    assert lib.gesmc_create(None, 0, 0, ctypes.byref(opts), ctypes.byref(h)) == gesmc.GESMC_E_INVALID
+    assert lib.gesmc_create(None, 0, 0, None, None) == gesmc.GESMC_E_INVALID
+
+
+def test_sources_are_free_of_x86_only_code():
+    # the GPU hosts are aarch64: no x86 intrinsics in anything compiled there
+    for d in ("paper_2111_03005_gb300/csrc", "paper_2111_03005_gb300/inputs", "oracle"):
+        for f in os.listdir(os.path.join(ROOT, d)):
+            if f.endswith((".cu", ".cuh", ".c", ".cpp", ".h")):
+                src = open(os.path.join(ROOT, d, f)).read()
+                assert "immintrin" not in src and "__builtin_ia32" not in src and "march=native" not in src
