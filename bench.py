@@ -39,6 +39,7 @@ WORKLOADS = {
     "gnp_2p24": dict(desc="G(n=2^24, p=16/(n-1)), seed 3; 20 global switches per step", n_log2=24, deg=16.0,
                      seed=3),
     "gnp_2p20": dict(desc="G(n=2^20, p=16/(n-1)), seed 5", n_log2=20, deg=16.0, seed=5),
+    "gnp_2p12": dict(desc="G(n=2^12, p=16/(n-1)), seed 7 (tests)", n_log2=12, deg=16.0, seed=7),
 }
 CPU_SAMPLE = "gnp_2p20"
 
@@ -173,6 +174,28 @@ def algorithmic_bytes(stage: str, m: int, L: int, cap: int, nb: int, accepted: f
     if stage == "scan":
         return 12.0 * nb
     return 0.0
+
+
+def random_ops_per_switch(m: int, L: int, cap: int, nb: int, accept_rate: float):
+    """Random accesses and streaming bytes of one switch in this design:
+    (loads, CAS, stores, streaming bytes)."""
+    loads = 2 + 2            # two source gathers; two slot reads in wave 1
+    cas = 4                  # claims of two source and two target slots
+    stores = 2 + 2 * accept_rate   # bucket scatter of two positions; two edge writes
+    per_pos = m / max(L, 1)  # positions per switch (2, or a bit more for odd m)
+    streaming = (16.0 * cap / max(L, 1)   # table clear
+                 + 8.0 * per_pos          # bucket read
+                 + 16.0 + 16.0            # switch record write + read
+                 + 4.0 + 4.0)             # status clear + write
+    return loads, cas, stores, streaming
+
+
+def random_roofline(m, L, cap, nb, accept_rate, rates, bw_seq_gbs):
+    """Upper bound on switches/s if every random access ran at the measured
+    random-access rate of its kind and streaming bytes at the copy peak."""
+    loads, cas, stores, streaming = random_ops_per_switch(m, L, cap, nb, accept_rate)
+    t = loads / rates["load"] + cas / rates["cas"] + stores / rates["store"] + streaming / (bw_seq_gbs * 1e9)
+    return 1.0 / t
 
 
 def traffic_from_profile(kernel: str, workload: str):
@@ -315,6 +338,19 @@ def run_gesmc(args):
     clk = clocks.summary()
     line["clocks"] = clk
 
+    if not args.no_probe:
+        # random-access ceiling of this GPU: 8-byte accesses over a 4 GB buffer
+        rates = {name: gesmc.gesmc_probe_random_access(4 << 30, kind, 1 << 29)
+                 for name, kind in (("load", gesmc.RANDOM_LOAD), ("store", gesmc.RANDOM_STORE),
+                                    ("cas", gesmc.RANDOM_CAS))}
+        bound = random_roofline(m, L, cap, nb, line["waves"]["accept_rate"], rates, peak)
+        line["random_access"] = {
+            "ceiling_per_s": {k: v for k, v in rates.items()},
+            "ceiling_sector_GBps": {k: 32 * v / 1e9 for k, v in rates.items()},
+            "round_bound_switches_per_s": bound,
+            "frac_of_round_bound": (value / world) / bound,
+        }
+
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
         host_in = torch.from_numpy(edges.view(np.int64)).pin_memory()
@@ -345,6 +381,7 @@ def run_gesmc(args):
 
 
 def main(argv=None):
+    global CPU_SAMPLE
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -353,9 +390,13 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="gnp_2p24")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")
+    ap.add_argument("--cpu-sample", choices=sorted(WORKLOADS), default=CPU_SAMPLE,
+                    help="workload of the CPU (oracle) legs")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    CPU_SAMPLE = args.cpu_sample
     if args.impl == "reference":
         return run_reference(args)
     return run_gesmc(args)

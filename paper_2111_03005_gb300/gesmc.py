@@ -103,6 +103,9 @@ _SIGNATURES = [
     ("gesmc_device_bytes", ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_double]),
     ("gesmc_destroy", None, [ctypes.c_void_p]),
     ("gesmc_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    # include/gesmc_microbench.h
+    ("gesmc_probe_random_access", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
+                                                 ctypes.POINTER(ctypes.c_double)]),
 ]
 
 
@@ -255,6 +258,17 @@ def gesmc_stage_times(h) -> tuple[dict, int]:
 def gesmc_destroy(h):
     if h:
         load_library().gesmc_destroy(h)
+
+
+RANDOM_LOAD, RANDOM_STORE, RANDOM_CAS = 0, 1, 2
+
+
+def gesmc_probe_random_access(nbytes: int, kind: int, accesses: int) -> float:
+    """Uniformly random 8-byte accesses per second over an nbytes device buffer."""
+    rate = ctypes.c_double()
+    _check(load_library().gesmc_probe_random_access(nbytes, kind, accesses, ctypes.byref(rate)),
+           "gesmc_probe_random_access")
+    return float(rate.value)
 
 
 class Chain:
