@@ -54,7 +54,8 @@ enum {
   GESMC_E_TABLE_FULL = -7, /* dependency table overflow (not expected)       */
   GESMC_E_WAVE_CAP = -8,   /* a round needed more waves than opts.max_waves  */
   GESMC_E_INTERNAL = -9,   /* bucket overflow or stalled waves (not expected) */
-  GESMC_E_CAPACITY = -10   /* caller's output buffer too small               */
+  GESMC_E_CAPACITY = -10,  /* caller's output buffer too small               */
+  GESMC_E_TOO_LARGE = -11  /* m above GESMC_NOALLOC_MAX_EDGES (no-alloc call) */
 };
 
 /* Device allocation hooks: alloc returns device memory usable on `stream`
@@ -146,6 +147,38 @@ uint64_t gesmc_num_nodes(gesmc_t h);
 
 /* Device bytes a handle with m edges and this load factor allocates. */
 size_t gesmc_device_bytes(uint64_t m, double load_factor);
+
+/* Allocation-free variant of gesmc_create + gesmc_run + gesmc_edges.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory while they run, for example code running inside
+ * a framework that owns all device memory through its own pool, or a process
+ * with a fixed memory budget checked at start-up.  Such callers cannot use
+ * gesmc_create, which allocates the chain's state.
+ *
+ * It runs `global_switches` rounds, numbered start_round, start_round + 1, ...
+ * with `seed`, in place on `edges`: m packed edge ids in DEVICE memory of the
+ * current device (input: a simple graph on [0, n), any orientation, n == 0
+ * meaning largest id + 1; output: the list after the rounds, canonical, in
+ * position order).  The result equals gesmc_create on the same list (with
+ * opts.start_round = start_round) followed by gesmc_run(global_switches, seed)
+ * and gesmc_edges.  Work is ordered on `stream` (cudaStream_t; NULL: the
+ * legacy default stream) and the call returns after it has completed.
+ *
+ * All scratch memory is one fixed array of GESMC_NOALLOC_SCRATCH_BYTES in the
+ * library's device image, which every GPU that loads the library holds until
+ * the process exits.  So m is limited to GESMC_NOALLOC_MAX_EDGES; larger m
+ * returns GESMC_E_TOO_LARGE without touching the GPU.  The call makes no
+ * device allocation (no cudaMalloc, no allocating library routine).  The
+ * first call on a device looks the array's device address up; make that first
+ * call before any stream capture on that device.  Every call on a device
+ * shares the one array: calls whose device work may overlap (other streams,
+ * other host threads) race and must be serialised by the caller.
+ * Returns GESMC_OK, GESMC_E_INVALID, GESMC_E_TOO_LARGE, GESMC_E_LOOP,
+ * GESMC_E_RANGE, GESMC_E_MULTI, GESMC_E_CUDA or a round error of gesmc_run. */
+#define GESMC_NOALLOC_MAX_EDGES 65536
+#define GESMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64_t global_switches, uint64_t seed,
+                      uint64_t start_round, void *stream);
 
 /* Release the handle and its device memory (NULL is ignored). */
 void gesmc_destroy(gesmc_t h);

@@ -3,6 +3,7 @@
 // (ParGlobalES) of arXiv 2111.03005.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -165,6 +166,7 @@ const char *gesmc_strerror(int code) {
     case GESMC_E_WAVE_CAP: return "wave cap exceeded";
     case GESMC_E_INTERNAL: return "internal error (permutation bucket overflow)";
     case GESMC_E_CAPACITY: return "output buffer too small";
+    case GESMC_E_TOO_LARGE: return "edge list larger than the no-alloc scratch allows (GESMC_NOALLOC_MAX_EDGES)";
     default: return "unknown error";
   }
 }
@@ -422,3 +424,118 @@ uint64_t gesmc_num_edges(gesmc_t h) { return h ? h->plan.m : 0; }
 uint64_t gesmc_num_nodes(gesmc_t h) { return h ? h->n : 0; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// gesmc_run_noalloc: the round with every scratch byte in one fixed device
+// array, for callers that may not allocate device memory (see gesmc.h).
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GESMC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device; the host-side name of the array is not a device address).
+int noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return GESMC_E_INVALID;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return GESMC_E_CUDA;
+    }
+    g_noalloc_base[dev] = p;
+  }
+  *out = g_noalloc_base[dev];
+  return GESMC_OK;
+}
+
+}  // namespace
+
+extern "C" int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64_t global_switches, uint64_t seed,
+                                 uint64_t start_round, void *stream) {
+  if (m > GESMC_NOALLOC_MAX_EDGES) return GESMC_E_TOO_LARGE;
+  if ((m > 0 && !edges) || n > (1ull << 32)) return GESMC_E_INVALID;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+  void *base = nullptr;
+  int rc = noalloc_scratch(dev, &base);
+  if (rc != GESMC_OK) return rc;
+  Plan p;
+  if (!make_plan(m, 0.5, &p) || p.total > GESMC_NOALLOC_SCRATCH_BYTES) return GESMC_E_INTERNAL;
+
+  cudaStream_t s = (cudaStream_t)stream;
+  RoundArgs a;
+  a.E = reinterpret_cast<unsigned long long *>(edges);  // rounds run in place on the caller's list
+  a.T = at<Slot>(base, p.off_T);
+  a.cap = p.cap;
+  a.buf = at<unsigned long long>(base, p.off_buf);
+  a.bucket_cnt = at<uint32_t>(base, p.off_cnt);
+  a.bucket_off = at<uint32_t>(base, p.off_boff);
+  a.cursor = at<uint32_t>(base, p.off_cursor);
+  a.sw = at<uint4>(base, p.off_sw);
+  a.status = at<uint32_t>(base, p.off_status);
+  a.list0 = at<uint32_t>(base, p.off_list0);
+  a.list1 = at<uint32_t>(base, p.off_list1);
+  a.pib = at<uint32_t>(base, p.off_pib);
+  a.bnd = at<uint32_t>(base, p.off_bnd);
+  a.ctl = at<Counters>(base, p.off_ctl);
+  a.st = at<StatsDev>(base, p.off_st);
+  a.m = (uint32_t)m;
+  a.L = p.L;
+  a.B = p.B;
+  a.nb = p.nb;
+  a.lazy_threshold = 0;
+  a.max_waves = 0;
+  a.seed = seed;
+
+  // the array keeps the previous call's contents: zero what must start at zero
+  uint32_t *flags = at<uint32_t>(base, p.off_scratch);
+  uint32_t host_flags[2] = {0, 0};
+  bool ok = cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
+  if (ok && m > 0) ok &= launch_canonicalise(a.E, a.m, n, flags, flags + 1, s, sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  if (host_flags[0] & kFlagLoop) return GESMC_E_LOOP;
+  if (host_flags[0] & kFlagRange) return GESMC_E_RANGE;
+  if (m > 0) {
+    ok &= launch_clear_table(a.T, a.cap, s, sms) == cudaSuccess;
+    ok &= launch_duplicate_check(a.E, a.m, a.T, a.cap, flags, s, sms) == cudaSuccess;
+    ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok &= cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      return GESMC_E_CUDA;
+    }
+    if (host_flags[0] & kFlagMulti) return GESMC_E_MULTI;
+    if (host_flags[0] & kFlagTableFull) return GESMC_E_INTERNAL;
+  }
+  for (uint64_t r = 0; r < global_switches; ++r) {
+    a.round = start_round + r;
+    if (launch_round(a, s, sms, nullptr, nullptr) != cudaSuccess) {
+      cudaGetLastError();
+      return GESMC_E_CUDA;
+    }
+  }
+  Counters ctl;
+  if (cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  return map_device_errors(ctl.err);
+}

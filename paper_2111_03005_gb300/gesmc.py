@@ -29,6 +29,8 @@ GESMC_E_TABLE_FULL = -7
 GESMC_E_WAVE_CAP = -8
 GESMC_E_INTERNAL = -9
 GESMC_E_CAPACITY = -10
+GESMC_E_TOO_LARGE = -11
+NOALLOC_MAX_EDGES = 65536
 WAVE_HIST = 64
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -103,6 +105,8 @@ _SIGNATURES = [
     ("gesmc_device_bytes", ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_double]),
     ("gesmc_destroy", None, [ctypes.c_void_p]),
     ("gesmc_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("gesmc_run_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
     # include/gesmc_microbench.h
     ("gesmc_probe_random_access", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                                                  ctypes.POINTER(ctypes.c_double)]),
@@ -258,6 +262,25 @@ def gesmc_stage_times(h) -> tuple[dict, int]:
 def gesmc_destroy(h):
     if h:
         load_library().gesmc_destroy(h)
+
+
+def gesmc_run_noalloc(edges, n: int, global_switches: int, seed: int, start_round: int = 0, stream=None):
+    """Allocation-free rounds in place on a CUDA tensor of packed ids (int64/uint64).
+
+    For callers that may not allocate device memory; m <= NOALLOC_MAX_EDGES.
+    The library's fixed scratch array is shared by all calls on a device, so
+    calls whose device work may overlap must be serialised by the caller."""
+    import torch
+
+    if not (isinstance(edges, torch.Tensor) and edges.is_cuda and edges.is_contiguous()
+            and edges.dtype in (torch.int64, torch.uint64)):
+        raise TypeError("edges must be a contiguous int64/uint64 CUDA tensor")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
+    _check(load_library().gesmc_run_noalloc(ctypes.c_void_p(edges.data_ptr()), edges.numel(), n, global_switches,
+                                            seed, start_round, s), "gesmc_run_noalloc")
+    return edges
 
 
 RANDOM_LOAD, RANDOM_STORE, RANDOM_CAS = 0, 1, 2
