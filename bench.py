@@ -155,47 +155,33 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(stage: str, m: int, L: int, cap: int, nb: int, accepted: float) -> float:
-    """DRAM bytes a stage must move per round, counting each random access as
-    the 32-byte sector it touches (64 bytes for a read-modify-write)."""
-    sector = 32.0
-    if stage == "clear":
-        return 16.0 * cap + 4.0 * L + 4.0 * nb
-    if stage == "scatter":
-        return sector * m
+def algorithmic_bytes(stage: str, m: int, L: int, nb: int, npart: int, accepted: float) -> float:
+    """DRAM bytes a stage must move per round (streaming reads + writes).
+
+    Per switch (two positions, four dependency tuples of 12 bytes):
+      permute:       read the list in slot order (2 x 12 B) and the status word (4 B),
+                     write two 16-byte bucket records (their write frontiers stay in L2)
+      sortpair:      read the two records (32 B); write the list in slot order (24 B),
+                     the reject word (4 B), the dependency-entry pair (8 B) and four tuples (48 B)
+      tuple_scatter: read four tuples, write them grouped by hash partition (48 B + 48 B)
+      group:         read four grouped tuples (48 B)
+      wave1:         read the reject word, write the status word (8 B)
+    The scans and the clear move a few bytes per bucket or partition."""
+    if stage == "permute":
+        return 12.0 * m + 4.0 * L + 16.0 * m
     if stage == "sortpair":
-        # bucket read 8 B per position; per switch two source gathers, four
-        # table claims (sector read + write back), a 16 B record write
-        return 8.0 * m + L * (2 * sector + 4 * 2 * sector + 16.0)
-    if stage == "decide1":
-        # per switch: record read, two slot reads, status write; accepted
-        # switches write two edge-list entries
-        return L * (16.0 + 2 * sector + 4.0) + accepted * 2 * sector
-    if stage == "scan":
-        return 12.0 * nb
+        return 16.0 * m + 12.0 * m + L * (4.0 + 8.0 + 48.0)
+    if stage == "tuple_scatter":
+        return 2 * 48.0 * L
+    if stage == "group":
+        return 48.0 * L
+    if stage == "wave1":
+        return 8.0 * L
+    if stage in ("scan_perm", "clear"):
+        return 12.0 * nb + 12.0 * npart
+    if stage == "scan_tuples":
+        return 12.0 * npart
     return 0.0
-
-
-def random_ops_per_switch(m: int, L: int, cap: int, nb: int, accept_rate: float):
-    """Random accesses and streaming bytes of one switch in this design:
-    (loads, CAS, stores, streaming bytes)."""
-    loads = 2 + 2            # two source gathers; two slot reads in wave 1
-    cas = 4                  # claims of two source and two target slots
-    stores = 2 + 2 * accept_rate   # bucket scatter of two positions; two edge writes
-    per_pos = m / max(L, 1)  # positions per switch (2, or a bit more for odd m)
-    streaming = (16.0 * cap / max(L, 1)   # table clear
-                 + 8.0 * per_pos          # bucket read
-                 + 16.0 + 16.0            # switch record write + read
-                 + 4.0 + 4.0)             # status clear + write
-    return loads, cas, stores, streaming
-
-
-def random_roofline(m, L, cap, nb, accept_rate, rates, bw_seq_gbs):
-    """Upper bound on switches/s if every random access ran at the measured
-    random-access rate of its kind and streaming bytes at the copy peak."""
-    loads, cas, stores, streaming = random_ops_per_switch(m, L, cap, nb, accept_rate)
-    t = loads / rates["load"] + cas / rates["cas"] + stores / rates["store"] + streaming / (bw_seq_gbs * 1e9)
-    return 1.0 / t
 
 
 def traffic_from_profile(kernel: str, workload: str):
@@ -281,7 +267,7 @@ def run_gesmc(args):
     edges, n = make_workload(args.workload)
     m, L = len(edges), len(edges) // 2
     seed = 1000 + rank
-    chain = gesmc.Chain(edges, n=n)
+    chain = gesmc.Chain(edges, n=n, tuple_log2=args.tuple_log2, group_log2=args.group_log2)
     for _ in range(args.warmup):
         chain.run(ROUNDS_PER_STEP, seed)
     chain.reset_stats()
@@ -306,18 +292,18 @@ def run_gesmc(args):
     value = world * switches_rank / (ms / 1e3)
 
     # roofline of the dominant kernel, from its live CUDA-event time
-    cap, nb = st["table_slots"], st["buckets"]
+    nb, npart = st["perm_buckets"], st["tuple_partitions"]
     acc_per_round = st["accepted"] / max(st["rounds"], 1)
     peak, peak_kind = read_peaks()
     per_stage = {k: v / max(prof_rounds, 1) for k, v in stage_ms.items()}
     dom = max(per_stage, key=per_stage.get)
-    abytes = algorithmic_bytes(dom, m, L, cap, nb, acc_per_round)
+    abytes = algorithmic_bytes(dom, m, L, nb, npart, acc_per_round)
     achieved = abytes / (per_stage[dom] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": abytes,
                 "traffic": traffic_from_profile(f"k_{dom}", args.workload)}
     # whole-round view: all stages' algorithmic bytes over the round time
-    round_bytes = sum(algorithmic_bytes(s, m, L, cap, nb, acc_per_round) for s in per_stage)
+    round_bytes = sum(algorithmic_bytes(s, m, L, nb, npart, acc_per_round) for s in per_stage)
     round_ms = sum(per_stage.values())
 
     line = {
@@ -326,11 +312,12 @@ def run_gesmc(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload]["desc"], "n": n, "m": m,
                    "global_switches_per_step": ROUNDS_PER_STEP, "switches_per_step": ROUNDS_PER_STEP * L,
-                   "l2": "inputs larger than L2 (device state ~%.1f GB)" % (gesmc.gesmc_device_bytes(m, 0.5) / 1e9),
+                   "l2": "inputs larger than L2 (device state ~%.1f GB)" % (gesmc.gesmc_device_bytes(m) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "round": {"ms": round_ms, "algorithmic_GBps": round_bytes / (round_ms / 1e3) / 1e9,
                   "stages_ms": {k: round(v, 4) for k, v in per_stage.items()}},
+        "tuning": {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2},
         "waves": {"max": st["waves_max"], "mean": st["waves_total"] / max(st["rounds"], 1),
                   "accept_rate": st["accepted"] / max(st["switches"], 1)},
         "gpu_launches": st["kernel_launches"],
@@ -338,17 +325,18 @@ def run_gesmc(args):
     clk = clocks.summary()
     line["clocks"] = clk
 
+    line["round"]["bytes_per_switch"] = round_bytes / max(L, 1)
+    line["round"]["frac_of_peak"] = line["round"]["algorithmic_GBps"] / peak
+    line["round"]["streaming_bound_switches_per_s"] = peak * 1e9 / (round_bytes / max(L, 1))
     if not args.no_probe:
-        # random-access ceiling of this GPU: 8-byte accesses over a 4 GB buffer
+        # random-access ceiling of this GPU (8-byte accesses over a 4 GB buffer), for context: the round is
+        # laid out so that no step depends on it
         rates = {name: gesmc.gesmc_probe_random_access(4 << 30, kind, 1 << 29)
                  for name, kind in (("load", gesmc.RANDOM_LOAD), ("store", gesmc.RANDOM_STORE),
                                     ("cas", gesmc.RANDOM_CAS))}
-        bound = random_roofline(m, L, cap, nb, line["waves"]["accept_rate"], rates, peak)
         line["random_access"] = {
             "ceiling_per_s": {k: v for k, v in rates.items()},
             "ceiling_sector_GBps": {k: 32 * v / 1e9 for k, v in rates.items()},
-            "round_bound_switches_per_s": bound,
-            "frac_of_round_bound": (value / world) / bound,
         }
 
     # end to end through the public API from pinned host memory
@@ -391,6 +379,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")
+    ap.add_argument("--tuple-log2", type=int, default=0, help="tuning: mean tuples per partition (log2)")
+    ap.add_argument("--group-log2", type=int, default=0, help="tuning: grouping table slots (log2)")
     ap.add_argument("--cpu-sample", choices=sorted(WORKLOADS), default=CPU_SAMPLE,
                     help="workload of the CPU (oracle) legs")
     args = ap.parse_args(argv)

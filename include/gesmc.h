@@ -45,7 +45,7 @@ typedef struct gesmc_ctx *gesmc_t;
 
 enum {
   GESMC_OK = 0,
-  GESMC_E_INVALID = -1,    /* null argument, m >= 2^32, bad option value     */
+  GESMC_E_INVALID = -1,    /* null argument, m >= 2^31, bad option value     */
   GESMC_E_LOOP = -2,       /* input edge {u, u} (not a simple graph)         */
   GESMC_E_MULTI = -3,      /* input edge listed twice (not a simple graph)   */
   GESMC_E_RANGE = -4,      /* input node id >= opts.n                        */
@@ -65,10 +65,13 @@ typedef void (*gesmc_free_fn)(void *ptr, void *ctx);
 
 typedef struct gesmc_opts {
   uint64_t n;              /* node ids must be < n; 0: n = largest id + 1       */
-  double load_factor;      /* dependency-table load bound in (0, 0.9]; 0: 0.5   */
   uint64_t lazy_threshold; /* Def. 2 laziness, P_L = t / 2^64; 0: never lazy   */
   uint64_t start_round;    /* number of the first round this handle runs       */
   uint32_t max_waves;      /* cap on resolution waves per round; 0: 10000      */
+  uint32_t tuple_log2;     /* tuning: log2 of the mean tuples per dependency
+                              partition, 8..16; 0: default                      */
+  uint32_t group_log2;     /* tuning: log2 of the shared-memory grouping table
+                              slots, 10..13; 0: default                          */
   uint32_t reserved;
   void *stream;            /* cudaStream_t for all device work; NULL: default  */
   gesmc_alloc_fn alloc;    /* optional device allocator                        */
@@ -86,8 +89,8 @@ typedef struct gesmc_stats_s {
   uint64_t rejected_loop;   /* a new edge would be a loop (Def. 1)                */
   uint64_t rejected_exists; /* a new edge is in E when the switch runs (Def. 1)   */
   uint64_t kernel_launches; /* CUDA kernels gesmc_run launched                     */
-  uint64_t table_slots;     /* slots of the dependency table (16 bytes each)      */
-  uint64_t buckets;         /* permutation buckets per round                      */
+  uint64_t perm_buckets;    /* permutation buckets per round                      */
+  uint64_t tuple_partitions; /* hash partitions of the dependency tuples per round */
   uint64_t waves_total;     /* resolution waves summed over rounds (Algorithm 1's
                                rounds of decide/delay)                            */
   uint64_t waves_max;       /* largest wave count of one round                    */
@@ -104,7 +107,7 @@ void gesmc_opts_default(gesmc_opts *o);
  *          (min << 32 | max).  Host memory if edges_on_device == 0, else a
  *          device pointer of the current device.  The library copies it; the
  *          caller keeps ownership.
- *   m:     number of edges, < 2^32.
+ *   m:     number of edges, < 2^31.
  *   opts:  NULL for defaults.
  *   out:   receives the handle (owns all device state until gesmc_destroy).
  * Returns GESMC_E_LOOP / GESMC_E_RANGE / GESMC_E_MULTI (that precedence) if
@@ -133,7 +136,7 @@ int gesmc_reset_stats(gesmc_t h);
  * gesmc_reset_stats) of the first n_stages stages into ms and the number of
  * profiled rounds into *rounds.  Stage i is named by gesmc_stage_name(i);
  * GESMC_NUM_STAGES stages exist, one kernel each, in launch order. */
-#define GESMC_NUM_STAGES 8
+#define GESMC_NUM_STAGES 10
 int gesmc_set_profiling(gesmc_t h, int enable);
 int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds);
 const char *gesmc_stage_name(int stage);
@@ -145,8 +148,8 @@ uint64_t gesmc_next_round(gesmc_t h);
 uint64_t gesmc_num_edges(gesmc_t h);
 uint64_t gesmc_num_nodes(gesmc_t h);
 
-/* Device bytes a handle with m edges and this load factor allocates. */
-size_t gesmc_device_bytes(uint64_t m, double load_factor);
+/* Device bytes a handle with m edges allocates (0 if m is too large). */
+size_t gesmc_device_bytes(uint64_t m);
 
 /* Allocation-free variant of gesmc_create + gesmc_run + gesmc_edges.
  * The paper has no counterpart: this entry point exists for callers that may

@@ -21,51 +21,144 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Sizes of the pieces of one handle's single device allocation.
 struct Plan {
   uint64_t m = 0;
-  uint32_t L = 0, B = 0, nb = 1;
-  unsigned long long cap = 0;
-  size_t off_E, off_T, off_buf, off_cnt, off_boff, off_cursor, off_sw, off_status, off_list0, off_list1,
-      off_pib, off_bnd, off_ctl, off_st, off_scratch, total;
+  uint32_t L = 0, B = 0, nb = 1, P = 0, np = 1, group_log2 = 0;
+  size_t off_E, off_cpos, off_cedge, off_prec, off_pcount, off_poff, off_pib_pos, off_pib_edge, off_bnd, off_word,
+      off_sw, off_status, off_list0, off_list1, off_tkey, off_tval, off_pkey, off_pval, off_tcount, off_toff,
+      off_tcursor, off_dep, off_ctl, off_st, off_scratch, total;
 };
 
-bool make_plan(uint64_t m, double lf, Plan *p) {
+// Largest m: switch indices must fit the 30 bits a tuple gives them.
+constexpr uint64_t kMaxEdges = (1ull << 31) - 1;
+
+bool make_plan(uint64_t m, Plan *p, uint32_t tuple_log2 = 0, uint32_t group_log2 = 0) {
+  if (m > kMaxEdges) return false;
+  if (!tuple_log2) tuple_log2 = kDefaultTupleLog2;
+  if (!group_log2) group_log2 = kDefaultGroupLog2;
+  if (tuple_log2 < 8 || tuple_log2 > 16 || group_log2 < 10 || group_log2 > 13) return false;
+  p->group_log2 = group_log2;
   p->m = m;
   p->L = (uint32_t)(m / 2);
-  // buckets of about 2^kBucketAvgLog2 positions; one bucket while it fits
-  uint32_t B = 0;
-  if (m > (uint64_t)kBucketCap / 2) {
-    while ((m >> B) > (1ull << kBucketAvgLog2)) ++B;
-  }
+  uint32_t B = 0;  // permutation buckets of about 2^kPermAvgLog2 positions
+  while ((m >> B) > (1ull << kPermAvgLog2)) ++B;
   p->B = B;
   p->nb = 1u << B;
-  // keys in T per round: m sources + at most 2L targets
-  const double keys = (double)m + 2.0 * (double)p->L;
-  unsigned long long cap = (unsigned long long)(keys / lf) + 64;
-  cap = (cap + 63) / 64 * 64;
-  if (cap >= (unsigned long long)kSwCodeMin) return false;
-  p->cap = cap;
+  const uint64_t ntuple = 4ull * p->L + 1;
+  uint32_t P = 0;  // tuple partitions of about 2^tuple_log2 tuples
+  while ((ntuple >> P) > (1ull << tuple_log2)) ++P;
+  p->P = P;
+  p->np = 1u << P;
   size_t o = 0;
   auto take = [&o](size_t bytes) {
     const size_t at = o;
     o = align_up(o + (bytes ? bytes : 1));
     return at;
   };
+  const size_t L = p->L;
   p->off_E = take(8 * m);
-  p->off_T = take(sizeof(Slot) * cap);
-  p->off_buf = take(8 * m);
-  p->off_cnt = take(4ull * p->nb);
-  p->off_boff = take(4ull * (p->nb + 1));
-  p->off_cursor = take(4ull * p->nb);
-  p->off_sw = take(16ull * p->L);
-  p->off_status = take(4ull * p->L);
-  p->off_list0 = take(4ull * p->L);
-  p->off_list1 = take(4ull * p->L);
-  p->off_pib = take(4 * m);
+  p->off_cpos = take(4 * m);
+  p->off_cedge = take(8 * m);
+  p->off_prec = take(16ull * p->nb * kPermBucketCap);
+  p->off_pcount = take(4ull * p->nb);
+  p->off_poff = take(4ull * (p->nb + 1));
+  p->off_pib_pos = take(4 * m);
+  p->off_pib_edge = take(8 * m);
   p->off_bnd = take(4ull * (p->nb + 1));
+  p->off_word = take(4 * L);
+  p->off_sw = take(8 * L);
+  p->off_status = take(4 * L);
+  p->off_list0 = take(4 * L);
+  p->off_list1 = take(4 * L);
+  p->off_tkey = take(8 * ntuple);
+  p->off_tval = take(4 * ntuple);
+  p->off_pkey = take(8 * ntuple);
+  p->off_pval = take(4 * ntuple);
+  p->off_tcount = take(4ull * p->np);
+  p->off_toff = take(4ull * (p->np + 1));
+  p->off_tcursor = take(4ull * p->np);
+  p->off_dep = take(8 * (2 * L + 1));
   p->off_ctl = take(sizeof(Counters));
   p->off_st = take(sizeof(StatsDev));
   p->off_scratch = take(64);
   p->total = o;
   return true;
+}
+
+template <class T>
+T *at(void *base, size_t off) {
+  return reinterpret_cast<T *>(static_cast<char *>(base) + off);
+}
+
+// Round arguments for a plan laid out at `base` (the edge list E is the
+// plan's own piece unless `E` is given).
+RoundArgs args_for(const Plan &p, void *base) {
+  RoundArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.cpos = at<uint32_t>(base, p.off_cpos);
+  a.cedge = at<unsigned long long>(base, p.off_cedge);
+  a.prec = at<uint4>(base, p.off_prec);
+  a.pcount = at<uint32_t>(base, p.off_pcount);
+  a.poff = at<uint32_t>(base, p.off_poff);
+  a.pib_pos = at<uint32_t>(base, p.off_pib_pos);
+  a.pib_edge = at<unsigned long long>(base, p.off_pib_edge);
+  a.bnd = at<uint32_t>(base, p.off_bnd);
+  a.word = at<uint32_t>(base, p.off_word);
+  a.sw = at<uint2>(base, p.off_sw);
+  a.status = at<uint32_t>(base, p.off_status);
+  a.list0 = at<uint32_t>(base, p.off_list0);
+  a.list1 = at<uint32_t>(base, p.off_list1);
+  a.tkey = at<unsigned long long>(base, p.off_tkey);
+  a.tval = at<uint32_t>(base, p.off_tval);
+  a.pkey = at<unsigned long long>(base, p.off_pkey);
+  a.pval = at<uint32_t>(base, p.off_pval);
+  a.tcount = at<uint32_t>(base, p.off_tcount);
+  a.toff = at<uint32_t>(base, p.off_toff);
+  a.tcursor = at<uint32_t>(base, p.off_tcursor);
+  a.dep = at<uint2>(base, p.off_dep);
+  a.ctl = at<Counters>(base, p.off_ctl);
+  a.st = at<StatsDev>(base, p.off_st);
+  a.m = (uint32_t)p.m;
+  a.L = p.L;
+  a.B = p.B;
+  a.nb = p.nb;
+  a.P = p.P;
+  a.np = p.np;
+  a.group_log2 = p.group_log2;
+  a.apply = 0;
+  return a;
+}
+
+// Validate and canonicalise E in place (loops, ids >= n_bound, repeated
+// edges, in that precedence), then load it as the slot-order state of `a`.
+// *n_out receives n_bound, or largest id + 1 if n_bound is 0.  Synchronises
+// the stream.  The tuple arrays serve as the duplicate set's scratch.
+int validate_and_load(const RoundArgs &a, unsigned long long *E, uint64_t m, uint64_t n_bound, uint32_t *flags,
+                      cudaStream_t s, int sms, uint64_t *n_out) {
+  uint32_t host_flags[2] = {0, 0};
+  bool ok = cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
+  if (ok && m > 0) ok &= launch_canonicalise(E, (uint32_t)m, n_bound, flags, flags + 1, s, sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  if (host_flags[0] & kFlagLoop) return GESMC_E_LOOP;
+  if (host_flags[0] & kFlagRange) return GESMC_E_RANGE;
+  *n_out = n_bound ? n_bound : (m ? (uint64_t)host_flags[1] + 1 : 0);
+  if (m == 0) return GESMC_OK;
+  ok &= launch_duplicate_check(E, (uint32_t)m, a.tkey, 4ull * a.L + 1, flags, s, sms) == cudaSuccess;
+  ok &= launch_load_state(a, E, s, sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  if (host_flags[0] & kFlagMulti) return GESMC_E_MULTI;
+  if (host_flags[0] & kFlagTableFull) return GESMC_E_INTERNAL;
+  return GESMC_OK;
 }
 
 struct DeviceGuard {
@@ -124,15 +217,10 @@ void dev_free(gesmc_ctx *h, void *p) {
   else cudaFree(p);
 }
 
-template <class T>
-T *at(void *base, size_t off) {
-  return reinterpret_cast<T *>(static_cast<char *>(base) + off);
-}
-
 int map_device_errors(uint32_t err) {
   if (err & kErrTableFull) return GESMC_E_TABLE_FULL;
   if (err & kErrWaveCap) return GESMC_E_WAVE_CAP;
-  if (err & (kErrBucket | kErrNoProgress | kErrRecord)) return GESMC_E_INTERNAL;
+  if (err & (kErrBucket | kErrNoProgress | kErrRecord | kErrGroup)) return GESMC_E_INTERNAL;
   return GESMC_OK;
 }
 
@@ -143,13 +231,11 @@ extern "C" {
 void gesmc_opts_default(gesmc_opts *o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
-  o->load_factor = 0.5;
 }
 
-size_t gesmc_device_bytes(uint64_t m, double load_factor) {
-  if (load_factor <= 0.0) load_factor = 0.5;
+size_t gesmc_device_bytes(uint64_t m) {
   Plan p;
-  if (m >= (1ull << 32) || load_factor > 0.9 || !make_plan(m, load_factor, &p)) return 0;
+  if (!make_plan(m, &p)) return 0;
   return p.total;
 }
 
@@ -190,9 +276,7 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   gesmc_opts o;
   gesmc_opts_default(&o);
   if (opts) o = *opts;
-  if (o.load_factor == 0.0) o.load_factor = 0.5;
-  if (!(o.load_factor > 0.0 && o.load_factor <= 0.9)) return GESMC_E_INVALID;
-  if (m >= (1ull << 32) || (m > 0 && !edges)) return GESMC_E_INVALID;
+  if (m > kMaxEdges || (m > 0 && !edges)) return GESMC_E_INVALID;
   if (o.n > (1ull << 32)) return GESMC_E_INVALID;
   if ((o.alloc == nullptr) != (o.free == nullptr)) return GESMC_E_INVALID;
 
@@ -211,9 +295,14 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   h->next_round = o.start_round;
   h->lazy_threshold = o.lazy_threshold;
   h->max_waves = o.max_waves;
-  if (!make_plan(m, o.load_factor, &h->plan)) {
+  if (!make_plan(m, &h->plan, o.tuple_log2, o.group_log2)) {
     delete h;
     return GESMC_E_INVALID;
+  }
+  if (prepare_kernels(h->plan.group_log2) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return GESMC_E_CUDA;
   }
   const Plan &p = h->plan;
   h->base = dev_alloc(h, p.total);
@@ -221,64 +310,19 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
     delete h;
     return GESMC_E_NOMEM;
   }
-  void *b = h->base;
-  RoundArgs &a = h->args;
-  a.E = at<unsigned long long>(b, p.off_E);
-  a.T = at<Slot>(b, p.off_T);
-  a.cap = p.cap;
-  a.buf = at<unsigned long long>(b, p.off_buf);
-  a.bucket_cnt = at<uint32_t>(b, p.off_cnt);
-  a.bucket_off = at<uint32_t>(b, p.off_boff);
-  a.cursor = at<uint32_t>(b, p.off_cursor);
-  a.sw = at<uint4>(b, p.off_sw);
-  a.status = at<uint32_t>(b, p.off_status);
-  a.list0 = at<uint32_t>(b, p.off_list0);
-  a.list1 = at<uint32_t>(b, p.off_list1);
-  a.pib = at<uint32_t>(b, p.off_pib);
-  a.bnd = at<uint32_t>(b, p.off_bnd);
-  a.ctl = at<Counters>(b, p.off_ctl);
-  a.st = at<StatsDev>(b, p.off_st);
-  a.m = (uint32_t)m;
-  a.L = p.L;
-  a.B = p.B;
-  a.nb = p.nb;
-  a.lazy_threshold = o.lazy_threshold;
-  a.max_waves = o.max_waves;
-
+  h->args = args_for(p, h->base);
+  h->args.lazy_threshold = o.lazy_threshold;
+  h->args.max_waves = o.max_waves;
+  unsigned long long *E = at<unsigned long long>(h->base, p.off_E);
   int rc = GESMC_OK;
-  uint32_t *flags = at<uint32_t>(b, p.off_scratch);
-  uint32_t host_flags[2] = {0, 0};
-  cudaStream_t s = h->stream;
-  bool ok = true;
-  if (m > 0)
-    ok &= cudaMemcpyAsync(a.E, edges, 8 * m, edges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                          s) == cudaSuccess;
-  ok &= cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
-  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
-  ok &= cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
-  if (ok && m > 0) ok &= launch_canonicalise(a.E, a.m, o.n, flags, flags + 1, s, h->num_sms) == cudaSuccess;
-  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok &= cudaStreamSynchronize(s) == cudaSuccess;
-  if (!ok) {
-    rc = GESMC_E_CUDA;
-  } else if (host_flags[0] & kFlagLoop) {
-    rc = GESMC_E_LOOP;
-  } else if (host_flags[0] & kFlagRange) {
-    rc = GESMC_E_RANGE;
-  } else {
-    h->n = o.n ? o.n : (m ? (uint64_t)host_flags[1] + 1 : 0);
-    if (m > 0) {
-      ok &= launch_clear_table(a.T, a.cap, s, h->num_sms) == cudaSuccess;
-      ok &= launch_duplicate_check(a.E, a.m, a.T, a.cap, flags, s, h->num_sms) == cudaSuccess;
-      ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-      ok &= cudaStreamSynchronize(s) == cudaSuccess;
-    }
-    if (!ok) rc = GESMC_E_CUDA;
-    else if (host_flags[0] & kFlagMulti) rc = GESMC_E_MULTI;
-    else if (host_flags[0] & kFlagTableFull) rc = GESMC_E_INTERNAL;
-  }
-  if (rc != GESMC_OK) {
+  if (m > 0 && cudaMemcpyAsync(E, edges, 8 * m, edges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               h->stream) != cudaSuccess) {
     cudaGetLastError();
+    rc = GESMC_E_CUDA;
+  }
+  if (rc == GESMC_OK)
+    rc = validate_and_load(h->args, E, m, o.n, at<uint32_t>(h->base, p.off_scratch), h->stream, h->num_sms, &h->n);
+  if (rc != GESMC_OK) {
     gesmc_destroy(h);
     return rc;
   }
@@ -314,6 +358,8 @@ int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed) {
       h->broken = GESMC_E_CUDA;
       return GESMC_E_CUDA;
     }
+    a.apply = 1;  // status[] now holds this round's decisions
+    h->args.apply = 1;
   }
   Counters ctl;
   if (cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -348,9 +394,14 @@ int gesmc_edges(gesmc_t h, uint64_t *out, uint64_t capacity, int out_on_device, 
   if (h->plan.m == 0) return GESMC_OK;
   if (!out) return GESMC_E_INVALID;
   DeviceGuard g(h->device);
-  if (cudaMemcpyAsync(out, h->args.E, 8 * h->plan.m, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                      h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess) {
+  // the list is kept in the last round's slot order: write it by position
+  unsigned long long *E = out_on_device ? reinterpret_cast<unsigned long long *>(out)
+                                        : at<unsigned long long>(h->base, h->plan.off_E);
+  bool ok = launch_store_state(h->args, E, h->stream, h->num_sms) == cudaSuccess;
+  if (ok && !out_on_device)
+    ok = cudaMemcpyAsync(out, E, 8 * h->plan.m, cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
@@ -374,8 +425,8 @@ int gesmc_stats(gesmc_t h, gesmc_stats_t *out) {
   out->rejected_loop = st.rej_loop;
   out->rejected_exists = st.rej_exists;
   out->kernel_launches = h->launches;
-  out->table_slots = h->plan.cap;
-  out->buckets = h->plan.nb;
+  out->perm_buckets = h->plan.nb;
+  out->tuple_partitions = h->plan.np;
   out->waves_total = st.waves_total;
   out->waves_max = st.waves_max;
   for (int w = 0; w < GESMC_WAVE_HIST && w < kWaveHist; ++w) {
@@ -414,8 +465,8 @@ int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
 }
 
 const char *gesmc_stage_name(int stage) {
-  static const char *names[kNumStages] = {"clear",    "hist",     "scan",    "scatter",
-                                          "sortpair", "boundary", "decide1", "tail"};
+  static const char *names[kNumStages] = {"clear",         "permute", "scan_perm", "sortpair", "boundary",
+                                          "scan_tuples",   "tuple_scatter", "group", "wave1", "tail"};
   return (stage >= 0 && stage < kNumStages) ? names[stage] : "";
 }
 
@@ -470,69 +521,32 @@ extern "C" int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64
   int rc = noalloc_scratch(dev, &base);
   if (rc != GESMC_OK) return rc;
   Plan p;
-  if (!make_plan(m, 0.5, &p) || p.total > GESMC_NOALLOC_SCRATCH_BYTES) return GESMC_E_INTERNAL;
-
-  cudaStream_t s = (cudaStream_t)stream;
-  RoundArgs a;
-  a.E = reinterpret_cast<unsigned long long *>(edges);  // rounds run in place on the caller's list
-  a.T = at<Slot>(base, p.off_T);
-  a.cap = p.cap;
-  a.buf = at<unsigned long long>(base, p.off_buf);
-  a.bucket_cnt = at<uint32_t>(base, p.off_cnt);
-  a.bucket_off = at<uint32_t>(base, p.off_boff);
-  a.cursor = at<uint32_t>(base, p.off_cursor);
-  a.sw = at<uint4>(base, p.off_sw);
-  a.status = at<uint32_t>(base, p.off_status);
-  a.list0 = at<uint32_t>(base, p.off_list0);
-  a.list1 = at<uint32_t>(base, p.off_list1);
-  a.pib = at<uint32_t>(base, p.off_pib);
-  a.bnd = at<uint32_t>(base, p.off_bnd);
-  a.ctl = at<Counters>(base, p.off_ctl);
-  a.st = at<StatsDev>(base, p.off_st);
-  a.m = (uint32_t)m;
-  a.L = p.L;
-  a.B = p.B;
-  a.nb = p.nb;
-  a.lazy_threshold = 0;
-  a.max_waves = 0;
-  a.seed = seed;
-
-  // the array keeps the previous call's contents: zero what must start at zero
-  uint32_t *flags = at<uint32_t>(base, p.off_scratch);
-  uint32_t host_flags[2] = {0, 0};
-  bool ok = cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
-  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
-  ok &= cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
-  if (ok && m > 0) ok &= launch_canonicalise(a.E, a.m, n, flags, flags + 1, s, sms) == cudaSuccess;
-  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok &= cudaStreamSynchronize(s) == cudaSuccess;
-  if (!ok) {
+  if (!make_plan(m, &p) || p.total > GESMC_NOALLOC_SCRATCH_BYTES) return GESMC_E_INTERNAL;
+  if (prepare_kernels(p.group_log2) != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
-  if (host_flags[0] & kFlagLoop) return GESMC_E_LOOP;
-  if (host_flags[0] & kFlagRange) return GESMC_E_RANGE;
-  if (m > 0) {
-    ok &= launch_clear_table(a.T, a.cap, s, sms) == cudaSuccess;
-    ok &= launch_duplicate_check(a.E, a.m, a.T, a.cap, flags, s, sms) == cudaSuccess;
-    ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-    ok &= cudaStreamSynchronize(s) == cudaSuccess;
-    if (!ok) {
-      cudaGetLastError();
-      return GESMC_E_CUDA;
-    }
-    if (host_flags[0] & kFlagMulti) return GESMC_E_MULTI;
-    if (host_flags[0] & kFlagTableFull) return GESMC_E_INTERNAL;
-  }
+
+  cudaStream_t s = (cudaStream_t)stream;
+  RoundArgs a = args_for(p, base);
+  a.seed = seed;
+  unsigned long long *E = reinterpret_cast<unsigned long long *>(edges);  // in place on the caller's list
+  uint64_t n_eff = 0;
+  // the array keeps the previous call's contents: validate_and_load zeroes
+  // the counters and rebuilds all state from the caller's list
+  rc = validate_and_load(a, E, m, n, at<uint32_t>(base, p.off_scratch), s, sms, &n_eff);
+  if (rc != GESMC_OK) return rc;
   for (uint64_t r = 0; r < global_switches; ++r) {
     a.round = start_round + r;
     if (launch_round(a, s, sms, nullptr, nullptr) != cudaSuccess) {
       cudaGetLastError();
       return GESMC_E_CUDA;
     }
+    a.apply = 1;
   }
   Counters ctl;
-  if (cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (launch_store_state(a, E, s, sms) != cudaSuccess ||
+      cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;

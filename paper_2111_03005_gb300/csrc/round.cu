@@ -1,23 +1,35 @@
-// One global switch round (Def. 2 of arXiv 2111.03005) on one GB300.
+// One global switch round (Def. 2 of arXiv 2111.03005) on one GB300, laid
+// out as streaming passes so that no step needs a random DRAM access per
+// switch.
 //
-// Steps (the round of Algorithm 3, with Algorithm 1 as its superstep):
-//   k_clear      empty the dependency table T, switch statuses, bucket counts
-//   k_hist       Philox keys of all positions -> bucket histogram
-//   k_scan       bucket offsets
-//   k_scatter    positions into buckets (32 further key bits carried along)
-//   k_sortpair   per bucket: exact in-shared-memory sort by (key, position),
-//                then for every pair of consecutive slots (one edge switch,
-//                Def. 1) gather both source edges, apply tau and the loop
-//                rule, and record the four tuples of Algorithm 1 in T
-//   k_boundary   the same for pairs whose two slots lie in different buckets
-//   k_decide1    wave 1 of the decide/delay loop over all switches: decide
-//                what is decidable, rewire legal switches, list the rest
-//   k_tail       waves 2, 3, ... until no switch is undecided
+//   k_clear          zero the per-round counters
+//   k_permute        read the list in last-round slot order (applying the
+//                    last round's legal switches on the fly), compute each
+//                    position's Philox key and append (key bits, position,
+//                    edge) to its bucket; the buckets' write frontiers stay
+//                    in L2, so DRAM sees whole lines
+//   k_scan_perm      bucket slot offsets
+//   k_sortpair       per bucket: exact sort by (key, position) in shared
+//                    memory; write the list back in this round's slot order;
+//                    for each pair of slots (edge switch sigma_k, Def. 1)
+//                    apply tau, the loop and shared-node rules and laziness,
+//                    and write Algorithm 1's four tuples (e1, k, ERASE),
+//                    (e2, k, ERASE), (e3, k, INSERT), (e4, k, INSERT)
+//   k_boundary       the same for pairs whose slots lie in two buckets
+//   k_scan_tuples    tuple partition offsets
+//   k_tuple_scatter  group the tuples by hash partition of their edge id
+//   k_group          per partition: group by edge id in a shared-memory
+//                    table and decide every target of wave 1 (Algorithm 1's
+//                    first round): certainly present, free, or dependent on
+//                    an undecided switch; edge ids with a dependency get an
+//                    entry {p, q} for the later waves
+//   k_wave1          per switch: legal, illegal or pending
+//   k_tail           waves 2, 3, ... over the pending switches
 //
 // The waves are Jacobi steps: a switch decided in wave w only uses decisions
 // of waves < w (status words carry their wave), so the result and the wave
-// count do not depend on thread timing.  The edge list after the round is
-// the one the sequential loop of Def. 2 produces.
+// count do not depend on thread timing.  The list after the round is the one
+// the sequential loop of Def. 2 produces.
 #include "gesmc_internal.cuh"
 
 namespace gesmc {
@@ -56,11 +68,6 @@ __device__ __forceinline__ U64x4 philox(unsigned long long c0, unsigned long lon
   return out;
 }
 
-// Permutation keys of positions 4b .. 4b+3 of round `round`.
-__device__ __forceinline__ U64x4 perm_block(unsigned long long seed, unsigned long long round, unsigned long long b) {
-  return philox(b, round, 0, 0, seed, 0);
-}
-
 // Word t of a block, t in 0..3 (selects, so the block stays in registers).
 __device__ __forceinline__ unsigned long long word_of(const U64x4 &w, uint32_t t) {
   const unsigned long long lo = (t & 1) ? w.w[1] : w.w[0];
@@ -68,9 +75,10 @@ __device__ __forceinline__ unsigned long long word_of(const U64x4 &w, uint32_t t
   return (t & 2) ? hi : lo;
 }
 
+// Permutation key K(i) of round `round` (purpose 0).
 __device__ __forceinline__ unsigned long long perm_key(unsigned long long seed, unsigned long long round,
                                                        uint32_t i) {
-  return word_of(perm_block(seed, round, i >> 2), i & 3);
+  return word_of(philox(i >> 2, round, 0, 0, seed, 0), i & 3);
 }
 
 __device__ __forceinline__ bool is_lazy(const RoundArgs &a, uint32_t k) {
@@ -87,7 +95,7 @@ __device__ __forceinline__ uint32_t mid_of(unsigned long long key, uint32_t B) {
   return (uint32_t)((key << B) >> 32);
 }
 
-// ---------------------------------------------------------------- table T
+// ---------------------------------------------------------------- edges
 __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
   // MurmurHash3's 64-bit finaliser (Appleby): a bijective avalanche mixer
   k ^= k >> 33;
@@ -98,27 +106,8 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
   return k;
 }
 
-__device__ __forceinline__ unsigned long long home_slot(unsigned long long key, unsigned long long cap) {
-  return __umul64hi(mix64(key), cap);
-}
-
-__device__ __forceinline__ unsigned long long ld_cg(const unsigned long long *p) { return __ldcg(p); }
-
-// Slot holding `key`, claiming an empty one if the key is absent.  Returns
-// cap if every slot was visited (table full; cannot happen when the table
-// has more slots than keys).
-__device__ __forceinline__ unsigned long long find_or_claim(Slot *T, unsigned long long cap, unsigned long long key) {
-  unsigned long long s = home_slot(key, cap);
-  for (unsigned long long n = 0; n < cap; ++n) {
-    const unsigned long long cur = ld_cg(&T[s].key);
-    if (cur == key) return s;
-    if (cur == kEmptyKey) {
-      const unsigned long long prev = atomicCAS(&T[s].key, kEmptyKey, key);
-      if (prev == kEmptyKey || prev == key) return s;
-    }
-    if (++s == cap) s = 0;
-  }
-  return cap;
+__device__ __forceinline__ uint32_t partition_of(unsigned long long h, uint32_t P) {
+  return P ? (uint32_t)(h >> (64 - P)) : 0u;
 }
 
 __device__ __forceinline__ unsigned long long pack_edge(uint32_t a, uint32_t b) {
@@ -126,75 +115,71 @@ __device__ __forceinline__ unsigned long long pack_edge(uint32_t a, uint32_t b) 
   return ((unsigned long long)lo << 32) | hi;
 }
 
-// Build switch k = (i, j, g = [i < j]) (Def. 2): gather its source edges,
-// compute its targets with tau (Def. 1), and store Algorithm 1's tuples:
-// (e1, k, ERASE), (e2, k, ERASE), (e3, k, INSERT), (e4, k, INSERT).
-// Switches rejected outright (loop, shared node, lazy) store their sources
-// as never erased and no targets.
-__device__ __forceinline__ void build_switch(const RoundArgs &a, uint32_t k, uint32_t i, uint32_t j) {
-  const unsigned long long e1 = __ldcg(&a.E[i]);
-  const unsigned long long e2 = __ldcg(&a.E[j]);
-  uint32_t code = 0;
-  uint32_t a3 = 0, b3 = 0, a4 = 0, b4 = 0;
-  if (is_lazy(a, k)) {
-    code = kSwLazy;
-  } else {
-    const uint32_t u = (uint32_t)(e1 >> 32), v = (uint32_t)e1;
-    const uint32_t x = (uint32_t)(e2 >> 32), y = (uint32_t)e2;
-    if (i < j) {  // g = 1: (u, y), (v, x)
-      a3 = u; b3 = y; a4 = v; b4 = x;
-    } else {      // g = 0: (u, x), (v, y)
-      a3 = u; b3 = x; a4 = v; b4 = y;
-    }
-    if (a3 == b3 || a4 == b4) code = kSwLoop;
-    else if (u == x || u == y || v == x || v == y) code = kSwShared;
+// Edge switch (i, j, g = [i < j]) on e1 = E[i], e2 = E[j] (Def. 1 with the
+// direction bit of Def. 2): the canonical new edges e3 (for position i) and
+// e4 (for j), and the outright-reject code: a new edge is a loop, or the
+// sources share a node (then every outcome of tau is a loop or re-creates
+// the two source edges, which are in E when the switch runs).
+__device__ __forceinline__ uint32_t tau(uint32_t i, uint32_t j, unsigned long long e1, unsigned long long e2,
+                                        unsigned long long &e3, unsigned long long &e4) {
+  const uint32_t u = (uint32_t)(e1 >> 32), v = (uint32_t)e1;
+  const uint32_t x = (uint32_t)(e2 >> 32), y = (uint32_t)e2;
+  uint32_t a3, b3, a4, b4;
+  if (i < j) {  // g = 1: (u, y), (v, x)
+    a3 = u; b3 = y; a4 = v; b4 = x;
+  } else {      // g = 0: (u, x), (v, y)
+    a3 = u; b3 = x; a4 = v; b4 = y;
   }
-  const uint32_t p = code ? kPKeep : k;
-  const unsigned long long s1 = find_or_claim(a.T, a.cap, e1);
-  const unsigned long long s2 = find_or_claim(a.T, a.cap, e2);
-  unsigned long long s3 = 0, s4 = 0;
-  if (!code) {
-    s3 = find_or_claim(a.T, a.cap, pack_edge(a3, b3));
-    s4 = find_or_claim(a.T, a.cap, pack_edge(a4, b4));
-  }
-  bool full = (s1 == a.cap) || (s2 == a.cap) || (!code && (s3 == a.cap || s4 == a.cap));
-  if (full) {
-    atomicOr(&a.ctl->err, kErrTableFull);
-    a.sw[k] = make_uint4(i, j, kSwLoop, 0);  // keeps later kernels in bounds
-    return;
-  }
-  a.T[s1].p = p;
-  a.T[s2].p = p;
-  if (!code) {
-    atomicMin(&a.T[s3].q, k);
-    atomicMin(&a.T[s4].q, k);
-    a.sw[k] = make_uint4(i, j, (uint32_t)s3, (uint32_t)s4);
-  } else {
-    a.sw[k] = make_uint4(i, j, code, 0);
+  e3 = pack_edge(a3, b3);
+  e4 = pack_edge(a4, b4);
+  if (a3 == b3 || a4 == b4) return kCodeLoop;
+  if (u == x || u == y || v == x || v == y) return kCodeShared;
+  return 0;
+}
+
+// The values of slots 2k, 2k+1 at the start of this round: the last round's
+// switch k rewired them if it was legal.
+__device__ __forceinline__ void apply_last(const RoundArgs &a, uint32_t k, uint32_t i, uint32_t j,
+                                           unsigned long long &e1, unsigned long long &e2) {
+  if (a.apply && k < a.L && (__ldcs(&a.status[k]) & 3u) == kLegal) {
+    unsigned long long e3, e4;
+    tau(i, j, e1, e2, e3, e4);
+    e1 = e3;
+    e2 = e4;
   }
 }
 
-// An edge of E that no switch of the round touches keeps p = kPKeep.
-__device__ __forceinline__ void keep_source(const RoundArgs &a, uint32_t i) {
-  const unsigned long long e = __ldcg(&a.E[i]);
-  const unsigned long long s = find_or_claim(a.T, a.cap, e);
-  if (s == a.cap) {
-    atomicOr(&a.ctl->err, kErrTableFull);
-    return;
+// ---------------------------------------------------------------- build
+// Switch k = (i, j, g) of this round with sources e1, e2: record its reject
+// code and Algorithm 1's four tuples (slots 4k .. 4k+3 of the staging
+// arrays), and count them per tuple partition.
+__device__ __forceinline__ void build_switch(const RoundArgs &a, uint32_t k, uint32_t i, unsigned long long e1,
+                                             uint32_t j, unsigned long long e2) {
+  unsigned long long e3 = kEmptyKey, e4 = kEmptyKey;
+  const uint32_t code = is_lazy(a, k) ? kCodeLazy : tau(i, j, e1, e2, e3, e4);
+  a.word[k] = code;
+  a.sw[k] = make_uint2(kTrivial, kTrivial);
+  const uint32_t src = kTupleSource | (code ? kKeepK : k);
+  if (code) e3 = e4 = kEmptyKey;
+  reinterpret_cast<ulonglong2 *>(a.tkey)[2 * (size_t)k] = make_ulonglong2(e1, e2);
+  reinterpret_cast<ulonglong2 *>(a.tkey)[2 * (size_t)k + 1] = make_ulonglong2(e3, e4);
+  reinterpret_cast<uint4 *>(a.tval)[k] = make_uint4(src, src, k, k | kTupleWhich);
+  atomicAdd(&a.tcount[partition_of(mix64(e1), a.P)], 1u);
+  atomicAdd(&a.tcount[partition_of(mix64(e2), a.P)], 1u);
+  if (!code) {
+    atomicAdd(&a.tcount[partition_of(mix64(e3), a.P)], 1u);
+    atomicAdd(&a.tcount[partition_of(mix64(e4), a.P)], 1u);
   }
-  a.T[s].p = kPKeep;
+}
+
+// The unpaired last position of an odd list: a source no switch erases.
+__device__ __forceinline__ void keep_source(const RoundArgs &a, unsigned long long e) {
+  a.tkey[4 * (size_t)a.L] = e;
+  a.tval[4 * (size_t)a.L] = kTupleSource | kKeepK;
+  atomicAdd(&a.tcount[partition_of(mix64(e), a.P)], 1u);
 }
 
 // ---------------------------------------------------------------- decide
-__device__ __forceinline__ Slot load_slot(const Slot *p) {
-  const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
-  Slot s;
-  s.key = ((unsigned long long)v.y << 32) | v.x;
-  s.p = v.z;
-  s.q = v.w;
-  return s;
-}
-
 constexpr int kOk = 0, kWait = 1, kBad = 2;
 
 __device__ __forceinline__ bool decided_before(uint32_t st, uint32_t wave) {
@@ -202,10 +187,13 @@ __device__ __forceinline__ bool decided_before(uint32_t st, uint32_t wave) {
   return w != 0 && w < wave;
 }
 
-// Algorithm 1's test of one target edge of switch k in wave `wave`, reading
-// the table slot (p, q): kBad if the edge exists when k runs, kOk if it
-// certainly does not, kWait if that depends on an undecided switch.
-__device__ __forceinline__ int check_target(const RoundArgs &a, uint32_t k, uint32_t p, uint32_t q, uint32_t wave) {
+// Algorithm 1's test of one target edge of switch k in wave `wave` >= 2,
+// from its dependency entry (p, q): kBad if the edge exists when k runs,
+// kOk if it certainly does not, kWait if that depends on an undecided switch.
+__device__ __forceinline__ int check_target(const RoundArgs &a, uint32_t k, uint32_t d, uint32_t wave) {
+  if (d == kTrivial) return kOk;
+  const uint2 pq = __ldcg(&a.dep[d]);
+  const uint32_t p = pq.x, q = pq.y;
   int res = kOk;
   if (p != kPNone) {             // the edge is in E at the start of the round
     if (p >= k) return kBad;     // erased later than k, or never
@@ -230,44 +218,11 @@ struct Tally {
   uint32_t accepted = 0, rej_loop = 0, rej_exists = 0, lazy = 0;
 };
 
-// Decide switch k in wave `wave`.  Returns kOk (legal), kBad (illegal) or
-// kWait.  Legal switches rewire E at once: positions i and j belong to k
-// alone in this round, and their old values were read when k was built.
-__device__ __forceinline__ int decide_one(const RoundArgs &a, uint32_t k, uint32_t wave, Tally &t) {
-  const uint4 rec = __ldcg(&a.sw[k]);
-  if (rec.z < kSwCodeMin && (rec.z >= a.cap || rec.w >= a.cap || rec.x >= a.m || rec.y >= a.m)) {
-    // a record the round did not write (only after a reported bucket overflow)
-    atomicOr(&a.ctl->err, kErrRecord);
-    a.status[k] = (wave << 2) | kIllegal;
-    return kBad;
-  }
-  if (rec.z >= kSwCodeMin) {
-    a.status[k] = (wave << 2) | kIllegal;
-    if (rec.z == kSwLazy) ++t.lazy;
-    else if (rec.z == kSwLoop) ++t.rej_loop;
-    else ++t.rej_exists;
-    return kBad;
-  }
-  // through L2: inside k_tail the slots change between waves (atomics)
-  const Slot s3 = load_slot(&a.T[rec.z]);
-  const Slot s4 = load_slot(&a.T[rec.w]);
-  const int r3 = check_target(a, k, s3.p, s3.q, wave);
-  const int r4 = check_target(a, k, s4.p, s4.q, wave);
-  if (r3 == kBad || r4 == kBad) {
-    a.status[k] = (wave << 2) | kIllegal;
-    // an illegal switch no longer counts as an inserter: if it was the
-    // smallest one, clear the field; the waiting inserters re-register
-    if (s3.q == k) atomicCAS(&a.T[rec.z].q, k, kQNone);
-    if (s4.q == k) atomicCAS(&a.T[rec.w].q, k, kQNone);
-    ++t.rej_exists;
-    return kBad;
-  }
-  if (r3 == kWait || r4 == kWait) return kWait;
-  a.E[rec.x] = s3.key;
-  a.E[rec.y] = s4.key;
-  a.status[k] = (wave << 2) | kLegal;
-  ++t.accepted;
-  return kOk;
+// An illegal switch no longer counts as an inserter: where it was the
+// smallest one, clear the field; the waiting inserters re-register.
+__device__ __forceinline__ void drop_inserter(const RoundArgs &a, uint32_t k, uint2 s) {
+  if (s.x != kTrivial && __ldcg(&a.dep[s.x].y) == k) atomicCAS(&a.dep[s.x].y, k, kQNone);
+  if (s.y != kTrivial && __ldcg(&a.dep[s.y].y) == k) atomicCAS(&a.dep[s.y].y, k, kQNone);
 }
 
 __device__ __forceinline__ void flush_tally(const RoundArgs &a, Tally t) {
@@ -301,63 +256,65 @@ __device__ __forceinline__ void append_if(bool take, uint32_t k, uint32_t *list,
 // ---------------------------------------------------------------- kernels
 
 __global__ void k_clear(RoundArgs a) {
-  const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-  const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
-  uint4 *T4 = reinterpret_cast<uint4 *>(a.T);
-  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
-  for (unsigned long long s = tid; s < a.cap; s += nth) __stcg(&T4[s], ones);
-  for (unsigned long long k = tid; k < a.L; k += nth) a.status[k] = 0;
-  for (unsigned long long b = tid; b < a.nb; b += nth) a.bucket_cnt[b] = 0;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+  for (uint32_t b = tid; b < a.nb; b += nth) a.pcount[b] = 0;
+  for (uint32_t p = tid; p < a.np; p += nth) a.tcount[p] = 0;
   if (tid == 0) {
     a.ctl->pending[0] = 0;
     a.ctl->pending[1] = 0;
     a.ctl->boundary = 0;
     a.ctl->waves = 0;
+    a.ctl->dep_count = 0;
+    a.tkey[4 * (size_t)a.L] = kEmptyKey;  // the odd-m slot, overwritten when m is odd
   }
 }
 
-constexpr int kHistSmem = 4096;
+__device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uint32_t idx, unsigned long long K,
+                                             uint32_t pos, unsigned long long e) {
+  if (idx < (uint32_t)kPermBucketCap)
+    a.prec[(size_t)b * kPermBucketCap + idx] = make_uint4(mid_of(K, a.B), pos, (uint32_t)e, (uint32_t)(e >> 32));
+  else
+    atomicOr(&a.ctl->err, kErrBucket);
+}
 
-__global__ void k_hist(RoundArgs a) {
-  __shared__ uint32_t h[kHistSmem];
-  const bool local = a.nb <= kHistSmem;
-  if (local) {
-    for (uint32_t b = threadIdx.x; b < a.nb; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-  }
-  const uint32_t nblk = (a.m + 3) >> 2;
-  for (uint32_t blk = blockIdx.x * blockDim.x + threadIdx.x; blk < nblk; blk += gridDim.x * blockDim.x) {
-    const U64x4 w = perm_block(a.seed, a.round, blk);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (4 * blk + t < a.m) {
-        const uint32_t b = bucket_of(w.w[t], a.B);
-        if (local) atomicAdd(&h[b], 1u);
-        else atomicAdd(&a.bucket_cnt[b], 1u);
-      }
+// Append every position, with its current edge, to its permutation bucket.
+__global__ void k_permute(RoundArgs a) {
+  const uint32_t npair = (a.m + 1) >> 1;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < npair; k += nth) {
+    const uint32_t s0 = 2 * k;
+    if (s0 + 1 < a.m) {
+      const uint2 ij = __ldcs(reinterpret_cast<const uint2 *>(a.cpos) + k);
+      const ulonglong2 ee = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + k);
+      unsigned long long e1 = ee.x, e2 = ee.y;
+      apply_last(a, k, ij.x, ij.y, e1, e2);
+      // both keys and both atomics before the two stores
+      const unsigned long long K1 = perm_key(a.seed, a.round, ij.x);
+      const unsigned long long K2 = perm_key(a.seed, a.round, ij.y);
+      const uint32_t b1 = bucket_of(K1, a.B), b2 = bucket_of(K2, a.B);
+      const uint32_t x1 = atomicAdd(&a.pcount[b1], 1u);
+      const uint32_t x2 = atomicAdd(&a.pcount[b2], 1u);
+      store_record(a, b1, x1, K1, ij.x, e1);
+      store_record(a, b2, x2, K2, ij.y, e2);
+    } else {  // odd m: the last slot has no partner
+      const uint32_t pos = a.cpos[s0];
+      const unsigned long long K = perm_key(a.seed, a.round, pos);
+      const uint32_t b = bucket_of(K, a.B);
+      store_record(a, b, atomicAdd(&a.pcount[b], 1u), K, pos, a.cedge[s0]);
     }
   }
-  if (local) {
-    __syncthreads();
-    for (uint32_t b = threadIdx.x; b < a.nb; b += blockDim.x)
-      if (h[b]) atomicAdd(&a.bucket_cnt[b], h[b]);
-  }
 }
 
-// Exclusive scan of the bucket counts (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_scan(RoundArgs a) {
+// Exclusive scan of n counters (n + 1 offsets) by one CTA of 1024 threads;
+// counts above `clamp` are clamped (their overflow was already reported).
+__device__ __forceinline__ void cta_scan_1024(const uint32_t *count, uint32_t *off, uint32_t *copy, uint32_t n,
+                                              uint32_t clamp) {
   __shared__ uint32_t part[1024];
   const uint32_t tid = threadIdx.x;
-  const uint32_t per = (a.nb + 1023) / 1024;
-  const uint32_t beg = min(tid * per, a.nb), end = min(beg + per, a.nb);
+  const uint32_t per = (n + 1023) / 1024;
+  const uint32_t beg = min(tid * per, n), end = min(beg + per, n);
   uint32_t sum = 0;
-  bool over = false;
-  for (uint32_t b = beg; b < end; ++b) {
-    const uint32_t c = a.bucket_cnt[b];
-    sum += c;
-    over |= c > (uint32_t)kBucketCap;
-  }
-  if (over) atomicOr(&a.ctl->err, kErrBucket);
+  for (uint32_t b = beg; b < end; ++b) sum += min(count[b], clamp);
   part[tid] = sum;
   __syncthreads();
   for (uint32_t d = 1; d < 1024; d <<= 1) {
@@ -366,33 +323,24 @@ __global__ void __launch_bounds__(1024) k_scan(RoundArgs a) {
     part[tid] += v;
     __syncthreads();
   }
-  uint32_t run = part[tid] - sum;  // exclusive prefix
+  uint32_t run = part[tid] - sum;
   for (uint32_t b = beg; b < end; ++b) {
-    a.bucket_off[b] = run;
-    a.cursor[b] = run;
-    run += a.bucket_cnt[b];
+    off[b] = run;
+    if (copy) copy[b] = run;
+    run += min(count[b], clamp);
   }
-  if (tid == 1023) a.bucket_off[a.nb] = part[1023];
+  if (tid == 1023) off[n] = part[1023];
 }
 
-__global__ void k_scatter(RoundArgs a) {
-  const uint32_t nblk = (a.m + 3) >> 2;
-  for (uint32_t blk = blockIdx.x * blockDim.x + threadIdx.x; blk < nblk; blk += gridDim.x * blockDim.x) {
-    const U64x4 w = perm_block(a.seed, a.round, blk);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const uint32_t i = 4 * blk + t;
-      if (i < a.m) {
-        const uint32_t b = bucket_of(w.w[t], a.B);
-        const uint32_t pos = atomicAdd(&a.cursor[b], 1u);
-        a.buf[pos] = ((unsigned long long)mid_of(w.w[t], a.B) << 32) | i;
-      }
-    }
-  }
+__global__ void __launch_bounds__(1024) k_scan_perm(RoundArgs a) {
+  cta_scan_1024(a.pcount, a.poff, nullptr, a.nb, kPermBucketCap);
 }
 
-// In-place exclusive scan of n = 2^kSubBits counters by a CTA of
-// kSortThreads threads (each owns a contiguous run of n / kSortThreads).
+__global__ void __launch_bounds__(1024) k_scan_tuples(RoundArgs a) {
+  cta_scan_1024(a.tcount, a.toff, a.tcursor, a.np, 0xFFFFFFFFu);
+}
+
+// In-place exclusive scan of 2^kSubBits counters by a CTA of kSortThreads.
 __device__ __forceinline__ void cta_exclusive_scan(uint32_t *h, uint32_t *warp_tot) {
   constexpr int n = 1 << kSubBits;
   constexpr int per = n / kSortThreads;
@@ -435,33 +383,36 @@ __device__ __forceinline__ bool full_key_less(const RoundArgs &a, uint32_t i, ui
   return ki < kj || (ki == kj && i < j);
 }
 
-// One CTA per bucket: exact sort of the bucket by (key, position), then the
-// edge switches of every pair of consecutive slots inside the bucket.
+// One CTA per bucket: exact sort of the bucket by (key, position), the list
+// written back in this round's slot order, and the switches of all pairs of
+// consecutive slots inside the bucket.
 __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
-  __shared__ unsigned long long sorted[kBucketCap];
+  __shared__ unsigned long long scomp[kPermBucketCap];  // (32 key bits << 32) | position
+  __shared__ unsigned long long sedge[kPermBucketCap];
+  __shared__ uint16_t slidx[kPermBucketCap];            // record index inside the bucket
   __shared__ uint32_t hist[1 << kSubBits];
   __shared__ uint32_t warp_tot[kSortThreads / 32];
   const int tid = threadIdx.x;
   constexpr int nsub = 1 << kSubBits;
   for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-    const uint32_t off = a.bucket_off[b];
-    const uint32_t cnt = a.bucket_off[b + 1] - off;
-    if (cnt > (uint32_t)kBucketCap) {  // reported by k_scan; the round is void
-      continue;
-    }
+    const uint32_t off = a.poff[b];
+    const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
+    const uint4 *rec = a.prec + (size_t)b * kPermBucketCap;
     for (int s = tid; s < nsub; s += kSortThreads) hist[s] = 0;
     unsigned long long v[kPerThread];
 #pragma unroll
     for (int r = 0; r < kPerThread; ++r) {
       const uint32_t idx = tid + r * kSortThreads;
-      v[r] = idx < cnt ? __ldcs(&a.buf[off + idx]) : 0ull;
+      v[r] = 0;
+      if (idx < cnt) {
+        const uint2 kp = *reinterpret_cast<const uint2 *>(&rec[idx]);  // key bits, position
+        v[r] = ((unsigned long long)kp.x << 32) | kp.y;
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kPerThread; ++r) {
-      const uint32_t idx = tid + r * kSortThreads;
-      if (idx < cnt) atomicAdd(&hist[(uint32_t)(v[r] >> (64 - kSubBits))], 1u);
-    }
+    for (int r = 0; r < kPerThread; ++r)
+      if (tid + r * kSortThreads < cnt) atomicAdd(&hist[(uint32_t)(v[r] >> (64 - kSubBits))], 1u);
     __syncthreads();
     cta_exclusive_scan(hist, warp_tot);
     __syncthreads();
@@ -470,7 +421,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
       const uint32_t idx = tid + r * kSortThreads;
       if (idx < cnt) {
         const uint32_t pos = atomicAdd(&hist[(uint32_t)(v[r] >> (64 - kSubBits))], 1u);
-        sorted[pos] = v[r];
+        scomp[pos] = v[r];
+        slidx[pos] = (uint16_t)idx;
       }
     }
     __syncthreads();
@@ -478,51 +430,70 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
     for (int s = tid; s < nsub; s += kSortThreads) {
       const uint32_t beg = s ? hist[s - 1] : 0, end = hist[s];
       for (uint32_t x = beg + 1; x < end; ++x) {
-        const unsigned long long val = sorted[x];
+        const unsigned long long val = scomp[x];
+        const uint16_t li = slidx[x];
         uint32_t y = x;
-        while (y > beg && sorted[y - 1] > val) {
-          sorted[y] = sorted[y - 1];
+        while (y > beg && scomp[y - 1] > val) {
+          scomp[y] = scomp[y - 1];
+          slidx[y] = slidx[y - 1];
           --y;
         }
-        sorted[y] = val;
+        scomp[y] = val;
+        slidx[y] = li;
       }
     }
     __syncthreads();
     // equal 32-bit key parts: order those runs by the full key
     for (uint32_t t = tid; t + 1 < cnt; t += kSortThreads) {
-      const uint32_t mt = (uint32_t)(sorted[t] >> 32);
-      if ((uint32_t)(sorted[t + 1] >> 32) == mt && (t == 0 || (uint32_t)(sorted[t - 1] >> 32) != mt)) {
+      const uint32_t mt = (uint32_t)(scomp[t] >> 32);
+      if ((uint32_t)(scomp[t + 1] >> 32) == mt && (t == 0 || (uint32_t)(scomp[t - 1] >> 32) != mt)) {
         uint32_t e = t + 2;
-        while (e < cnt && (uint32_t)(sorted[e] >> 32) == mt) ++e;
+        while (e < cnt && (uint32_t)(scomp[e] >> 32) == mt) ++e;
         for (uint32_t x = t + 1; x < e; ++x) {
-          const unsigned long long val = sorted[x];
+          const unsigned long long val = scomp[x];
+          const uint16_t li = slidx[x];
           uint32_t y = x;
-          while (y > t && full_key_less(a, (uint32_t)val, (uint32_t)sorted[y - 1])) {
-            sorted[y] = sorted[y - 1];
+          while (y > t && full_key_less(a, (uint32_t)val, (uint32_t)scomp[y - 1])) {
+            scomp[y] = scomp[y - 1];
+            slidx[y] = slidx[y - 1];
             --y;
           }
-          sorted[y] = val;
+          scomp[y] = val;
+          slidx[y] = li;
         }
       }
     }
     __syncthreads();
-    // slots off .. off+cnt-1 now hold pi in order
+    // slots off .. off+cnt-1 hold pi in order: write the list in slot order
+    for (uint32_t t = tid; t < cnt; t += kSortThreads) {
+      const uint2 eh = *reinterpret_cast<const uint2 *>(&rec[slidx[t]].z);  // edge lo, hi
+      const unsigned long long e = ((unsigned long long)eh.y << 32) | eh.x;
+      sedge[t] = e;
+      a.cpos[off + t] = (uint32_t)scomp[t];
+      a.cedge[off + t] = e;
+    }
+    __syncthreads();
     const uint32_t t0 = off & 1u;
     const uint32_t npairs = cnt > t0 ? (cnt - t0) >> 1 : 0;
-    for (uint32_t pidx = tid; pidx < npairs; pidx += kSortThreads) {
-      const uint32_t t = t0 + 2 * pidx;
-      build_switch(a, (off + t) >> 1, (uint32_t)sorted[t], (uint32_t)sorted[t + 1]);
+    for (uint32_t p = tid; p < npairs; p += kSortThreads) {
+      const uint32_t t = t0 + 2 * p;
+      build_switch(a, (off + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1], sedge[t + 1]);
     }
     if (tid == 0 && cnt > 0) {
       if (t0 == 1) {  // slot off is the second of a pair started in an earlier bucket
-        a.pib[off] = (uint32_t)sorted[0];
+        a.pib_pos[off] = (uint32_t)scomp[0];
+        a.pib_edge[off] = sedge[0];
         const uint32_t idx = atomicAdd(&a.ctl->boundary, 1u);
         a.bnd[idx] = (off - 1) >> 1;
       }
       const uint32_t last = off + cnt - 1;
       if ((last & 1u) == 0) {  // first of a pair whose partner is in a later bucket
-        if (last + 1 == a.m) keep_source(a, (uint32_t)sorted[cnt - 1]);  // odd m: unpaired
-        else a.pib[last] = (uint32_t)sorted[cnt - 1];
+        if (last + 1 == a.m) {
+          keep_source(a, sedge[cnt - 1]);  // odd m: unpaired
+        } else {
+          a.pib_pos[last] = (uint32_t)scomp[cnt - 1];
+          a.pib_edge[last] = sedge[cnt - 1];
+        }
       }
     }
     __syncthreads();
@@ -533,29 +504,198 @@ __global__ void k_boundary(RoundArgs a) {
   const uint32_t n = a.ctl->boundary;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
     const uint32_t k = a.bnd[idx];
-    const uint32_t i = a.pib[2 * k], j = a.pib[2 * k + 1];
-    if (k >= a.L || i >= a.m || j >= a.m) {  // only after a reported bucket overflow
+    if (k >= a.L) {  // cannot happen unless a bucket overflowed (reported)
       atomicOr(&a.ctl->err, kErrRecord);
       continue;
     }
-    build_switch(a, k, i, j);
+    build_switch(a, k, a.pib_pos[2 * k], a.pib_edge[2 * k], a.pib_pos[2 * k + 1], a.pib_edge[2 * k + 1]);
   }
 }
 
-__global__ void k_decide1(RoundArgs a) {
+__global__ void k_tuple_scatter(RoundArgs a) {
+  const size_t n = 4 * (size_t)a.L + 1;
+  const uint32_t total = a.toff[a.np];
+  const size_t nth = (size_t)gridDim.x * blockDim.x;
+  for (size_t base = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; base < n; base += 4 * nth) {
+    unsigned long long key[4];
+    uint32_t val[4], dst[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      key[u] = base + u < n ? __ldcs(&a.tkey[base + u]) : kEmptyKey;
+      val[u] = base + u < n ? __ldcs(&a.tval[base + u]) : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      dst[u] = key[u] != kEmptyKey ? atomicAdd(&a.tcursor[partition_of(mix64(key[u]), a.P)], 1u) : 0xFFFFFFFFu;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (dst[u] < total) {
+        a.pkey[dst[u]] = key[u];
+        a.pval[dst[u]] = val[u];
+      } else if (key[u] != kEmptyKey) {
+        atomicOr(&a.ctl->err, kErrRecord);
+      }
+    }
+  }
+}
+
+// Group one tuple partition by edge id and decide wave 1 for its targets.
+// The shared-memory table holds the partition's distinct edge ids (key, p,
+// smallest inserter q, number of inserters c).  If the partition has more
+// distinct ids than slots, it is processed in sub-passes that each take the
+// ids whose hash bits 32.. select them (split further until they fit).
+__global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
+  extern __shared__ unsigned long long group_smem[];
+  const uint32_t S = 1u << a.group_log2;
+  unsigned long long *gk = group_smem;
+  uint32_t *gp = reinterpret_cast<uint32_t *>(gk + S);
+  uint32_t *gq = gp + S;
+  uint32_t *gc = gq + S;
+  __shared__ uint32_t stk_sub[64], stk_n[64];
+  __shared__ int stk_top;
+  __shared__ uint32_t overflow;
+  const int tid = threadIdx.x;
+  for (uint32_t part = blockIdx.x; part < a.np; part += gridDim.x) {
+    const uint32_t beg = a.toff[part], end = a.toff[part + 1];
+    if (tid == 0) {
+      stk_top = 1;
+      stk_sub[0] = 0;
+      stk_n[0] = 1;
+    }
+    __syncthreads();
+    while (stk_top > 0) {
+      const uint32_t sub = stk_sub[stk_top - 1], ns = stk_n[stk_top - 1];
+      __syncthreads();
+      if (tid == 0) {
+        --stk_top;
+        overflow = 0;
+      }
+      for (uint32_t s = tid; s < S; s += kGroupThreads) {
+        gk[s] = kEmptyKey;
+        gp[s] = kPNone;
+        gq[s] = kQNone;
+        gc[s] = 0;
+      }
+      __syncthreads();
+      // insert every tuple of this sub-pass
+      for (uint32_t t = beg + tid; t < end; t += kGroupThreads) {
+        const unsigned long long key = a.pkey[t];
+        const unsigned long long h = mix64(key);
+        if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
+        const uint32_t v = a.pval[t];
+        uint32_t s = (uint32_t)h & (S - 1), n = 0;
+        for (; n < (uint32_t)S; ++n) {
+          const unsigned long long cur = gk[s];
+          if (cur == key) break;
+          if (cur == kEmptyKey) {
+            const unsigned long long prev = atomicCAS(&gk[s], kEmptyKey, key);
+            if (prev == kEmptyKey || prev == key) break;
+          }
+          s = (s + 1) & (S - 1);
+        }
+        if (n == (uint32_t)S) {
+          overflow = 1;
+          continue;
+        }
+        if (v & kTupleSource) {
+          const uint32_t kk = v & kTupleK;
+          gp[s] = kk == kKeepK ? kPKeep : kk;  // one source per edge id (Obs. 2)
+        } else {
+          atomicMin(&gq[s], v & kTupleK);
+          atomicAdd(&gc[s], 1u);
+        }
+      }
+      __syncthreads();
+      if (overflow) {
+        if (tid == 0) {
+          if (ns >= (1u << 16) || stk_top + 2 > 64) {
+            atomicOr(&a.ctl->err, kErrGroup);
+          } else {
+            stk_sub[stk_top] = sub + ns;
+            stk_n[stk_top] = 2 * ns;
+            stk_sub[stk_top + 1] = sub;
+            stk_n[stk_top + 1] = 2 * ns;
+            stk_top += 2;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
+      // one dependency entry per edge id that some target depends on: an id
+      // inserted more than once, or inserted while in E at the round start
+      for (uint32_t s = tid; s < S; s += kGroupThreads) {
+        const bool need = gk[s] != kEmptyKey && (gc[s] >= 2 || (gc[s] >= 1 && gp[s] != kPNone));
+        uint32_t idx = kTrivial;
+        if (need) {
+          idx = atomicAdd(&a.ctl->dep_count, 1u);
+          if (idx <= 2 * a.L) {
+            a.dep[idx] = make_uint2(gp[s], gq[s]);
+          } else {
+            idx = kTrivial;
+            atomicOr(&a.ctl->err, kErrRecord);
+          }
+        }
+        gc[s] = idx;  // gc now holds the entry index
+      }
+      __syncthreads();
+      // wave 1 for every target of this sub-pass
+      for (uint32_t t = beg + tid; t < end; t += kGroupThreads) {
+        const uint32_t v = a.pval[t];
+        if (v & kTupleSource) continue;
+        const unsigned long long key = a.pkey[t];
+        const unsigned long long h = mix64(key);
+        if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
+        uint32_t s = (uint32_t)h & (S - 1);
+        for (uint32_t n = 0; n < (uint32_t)S && gk[s] != key; ++n) s = (s + 1) & (S - 1);
+        const uint32_t k = v & kTupleK;
+        const uint32_t p = gp[s], q = gq[s];
+        if (p != kPNone && p >= k) atomicOr(&a.word[k], kFlagBad);       // present when k runs
+        else if (p != kPNone || q != k) atomicOr(&a.word[k], kFlagDep);  // erased or inserted earlier, maybe
+        const uint32_t d = gc[s];
+        if (d != kTrivial) {
+          if (v & kTupleWhich) a.sw[k].y = d;
+          else a.sw[k].x = d;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_wave1(RoundArgs a) {
   Tally t;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < a.L; base += stride) {
     const uint32_t k = base + threadIdx.x;
-    int r = kOk;
-    if (k < a.L) r = decide_one(a, k, 1u, t);
-    append_if(k < a.L && r == kWait, k, a.list0, &a.ctl->pending[0]);
+    bool wait = false;
+    if (k < a.L) {
+      const uint32_t w = __ldcs(&a.word[k]);
+      const uint32_t code = w & kCodeMask;
+      uint32_t state = kLegal;
+      if (code) {
+        state = kIllegal;
+        if (code == kCodeLazy) ++t.lazy;
+        else if (code == kCodeLoop) ++t.rej_loop;
+        else ++t.rej_exists;
+      } else if (w & kFlagBad) {
+        state = kIllegal;
+        ++t.rej_exists;
+        drop_inserter(a, k, a.sw[k]);
+      } else if (w & kFlagDep) {
+        state = kUndecided;
+        wait = true;
+      } else {
+        ++t.accepted;
+      }
+      a.status[k] = state == kUndecided ? 0u : ((1u << 2) | state);
+    }
+    append_if(wait, k, a.list0, &a.ctl->pending[0]);
   }
   flush_tally(a, t);
 }
 
 // Waves 2, 3, ... on one CTA: undecided switches re-register as inserters
-// (the table's q fields of illegal minima were cleared), then decide.
+// (the q fields of illegal minima were cleared), then decide.
 __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
   __shared__ uint32_t s_n;
   Tally t;
@@ -580,11 +720,9 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
     uint32_t *out = cur ? a.list0 : a.list1;
     for (uint32_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
       const uint32_t k = in[idx];
-      const uint4 rec = __ldcg(&a.sw[k]);
-      if (rec.z < a.cap && rec.w < a.cap) {  // always true for a listed switch
-        atomicMin(&a.T[rec.z].q, k);
-        atomicMin(&a.T[rec.w].q, k);
-      }
+      const uint2 s = __ldcg(&a.sw[k]);
+      if (s.x != kTrivial) atomicMin(&a.dep[s.x].y, k);
+      if (s.y != kTrivial) atomicMin(&a.dep[s.y].y, k);
     }
     if (threadIdx.x == 0) {
       pend[cur ^ 1] = 0;
@@ -593,13 +731,25 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
     __syncthreads();
     for (uint32_t base = 0; base < n; base += blockDim.x) {
       const uint32_t idx = base + threadIdx.x;
-      int r = kOk;
+      bool wait = false;
       uint32_t k = 0;
       if (idx < n) {
         k = in[idx];
-        r = decide_one(a, k, wave, t);
+        const uint2 s = __ldcg(&a.sw[k]);
+        const int r3 = check_target(a, k, s.x, wave);
+        const int r4 = check_target(a, k, s.y, wave);
+        if (r3 == kBad || r4 == kBad) {
+          a.status[k] = (wave << 2) | kIllegal;
+          drop_inserter(a, k, s);
+          ++t.rej_exists;
+        } else if (r3 == kWait || r4 == kWait) {
+          wait = true;
+        } else {
+          a.status[k] = (wave << 2) | kLegal;
+          ++t.accepted;
+        }
       }
-      append_if(idx < n && r == kWait, k, out, (uint32_t *)&pend[cur ^ 1]);
+      append_if(wait, k, out, (uint32_t *)&pend[cur ^ 1]);
     }
     cur ^= 1;
     ++wave;
@@ -613,6 +763,31 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
     a.st->wave_hist[waves < kWaveHist ? waves : kWaveHist - 1] += 1;
     a.st->last_pending[1] = a.L;
     for (uint32_t w = wave; w < kWaveHist; ++w) a.st->last_pending[w] = 0;
+  }
+}
+
+// ---------------------------------------------------------------- state in / out
+
+__global__ void k_load_state(RoundArgs a, const unsigned long long *E) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.m; s += gridDim.x * blockDim.x) {
+    a.cpos[s] = s;
+    a.cedge[s] = E[s];
+  }
+}
+
+__global__ void k_store_state(RoundArgs a, unsigned long long *E) {
+  const uint32_t npair = (a.m + 1) >> 1;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < npair; k += gridDim.x * blockDim.x) {
+    const uint32_t s0 = 2 * k;
+    if (s0 + 1 < a.m) {
+      const uint32_t i = a.cpos[s0], j = a.cpos[s0 + 1];
+      unsigned long long e1 = a.cedge[s0], e2 = a.cedge[s0 + 1];
+      apply_last(a, k, i, j, e1, e2);
+      E[i] = e1;
+      E[j] = e2;
+    } else {
+      E[a.cpos[s0]] = a.cedge[s0];
+    }
   }
 }
 
@@ -633,14 +808,20 @@ __global__ void k_canonicalise(unsigned long long *E, uint32_t m, unsigned long 
   if (m) atomicMax(max_id, mx);
 }
 
-__global__ void k_duplicates(const unsigned long long *E, uint32_t m, Slot *T, unsigned long long cap,
+__global__ void k_fill_u64(unsigned long long *p, unsigned long long n, unsigned long long v) {
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void k_duplicates(const unsigned long long *E, uint32_t m, unsigned long long *set, unsigned long long cap,
                              uint32_t *flags) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     const unsigned long long key = E[i];
-    unsigned long long s = home_slot(key, cap);
+    unsigned long long s = __umul64hi(mix64(key), cap);
     bool placed = false;
     for (unsigned long long n = 0; n < cap && !placed; ++n) {
-      const unsigned long long prev = atomicCAS(&T[s].key, kEmptyKey, key);
+      const unsigned long long prev = atomicCAS(&set[s], kEmptyKey, key);
       if (prev == kEmptyKey) placed = true;
       else if (prev == key) {
         atomicOr(flags, kFlagMulti);
@@ -653,14 +834,6 @@ __global__ void k_duplicates(const unsigned long long *E, uint32_t m, Slot *T, u
   }
 }
 
-__global__ void k_clear_table(Slot *T, unsigned long long cap) {
-  uint4 *T4 = reinterpret_cast<uint4 *>(T);
-  const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
-  for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < cap;
-       s += (unsigned long long)gridDim.x * blockDim.x)
-    T4[s] = ones;
-}
-
 inline int grid_for(unsigned long long work, int threads, int num_sms, int per_sm) {
   unsigned long long g = (work + threads - 1) / threads;
   const unsigned long long lim = (unsigned long long)num_sms * per_sm;
@@ -671,6 +844,13 @@ inline int grid_for(unsigned long long work, int threads, int num_sms, int per_s
 
 }  // namespace
 
+size_t group_smem_bytes(uint32_t group_log2) { return (size_t)kGroupSlotBytes << group_log2; }
+
+cudaError_t prepare_kernels(uint32_t group_log2) {
+  return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)group_smem_bytes(group_log2));
+}
+
 cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEvent_t *ev, uint32_t *launches) {
   // ev (optional) receives kNumStages + 1 stage boundaries; stages that do
   // not run for tiny m still get both of their events (zero duration).
@@ -678,28 +858,44 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
     if (ev) cudaEventRecord(ev[stage], s);
   };
   uint32_t n = 0;
-  const unsigned long long clear_work = a.cap > a.L ? a.cap : a.L;
   const bool work = a.m >= 2;
-  const uint32_t nblk = (a.m + 3) / 4;
+  const uint32_t npair = (a.m + 1) / 2;
+  const unsigned long long ntuple = 4ull * a.L + 1;
   mark(kStageClear);
-  k_clear<<<grid_for(clear_work, 256, num_sms, 16), 256, 0, s>>>(a);
+  k_clear<<<grid_for(a.nb > a.np ? a.nb : a.np, 256, num_sms, 4), 256, 0, s>>>(a);
   ++n;
-  mark(kStageHist);
-  if (work) { k_hist<<<grid_for(nblk, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
-  mark(kStageScan);
-  if (work) { k_scan<<<1, 1024, 0, s>>>(a); ++n; }
-  mark(kStageScatter);
-  if (work) { k_scatter<<<grid_for(nblk, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  mark(kStagePermute);
+  if (work) { k_permute<<<grid_for(npair, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  mark(kStageScanPerm);
+  if (work) { k_scan_perm<<<1, 1024, 0, s>>>(a); ++n; }
   mark(kStageSortPair);
   if (work) { k_sortpair<<<a.nb, kSortThreads, 0, s>>>(a); ++n; }
   mark(kStageBoundary);
   if (work) { k_boundary<<<grid_for(a.nb, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
-  mark(kStageDecide1);
-  if (work) { k_decide1<<<grid_for(a.L, 256, num_sms, 16), 256, 0, s>>>(a); ++n; }
+  mark(kStageScanTuples);
+  if (work) { k_scan_tuples<<<1, 1024, 0, s>>>(a); ++n; }
+  mark(kStageTupleScatter);
+  if (work) { k_tuple_scatter<<<grid_for((ntuple + 3) / 4, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  mark(kStageGroup);
+  if (work) { k_group<<<a.np, kGroupThreads, group_smem_bytes(a.group_log2), s>>>(a); ++n; }
+  mark(kStageWave1);
+  if (work) { k_wave1<<<grid_for(a.L, 256, num_sms, 16), 256, 0, s>>>(a); ++n; }
   mark(kStageTail);
   if (work) { k_tail<<<1, 1024, 0, s>>>(a); ++n; }
   mark(kNumStages);
   if (launches) *launches += n;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_state(const RoundArgs &a, const unsigned long long *E, cudaStream_t s, int num_sms) {
+  if (a.m == 0) return cudaSuccess;
+  k_load_state<<<grid_for(a.m, 256, num_sms, 8), 256, 0, s>>>(a, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_store_state(const RoundArgs &a, unsigned long long *E, cudaStream_t s, int num_sms) {
+  if (a.m == 0) return cudaSuccess;
+  k_store_state<<<grid_for((a.m + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a, E);
   return cudaGetLastError();
 }
 
@@ -709,14 +905,10 @@ cudaError_t launch_canonicalise(unsigned long long *E, uint32_t m, unsigned long
   return cudaGetLastError();
 }
 
-cudaError_t launch_duplicate_check(const unsigned long long *E, uint32_t m, Slot *T, unsigned long long cap,
-                                   uint32_t *flags, cudaStream_t s, int num_sms) {
-  k_duplicates<<<grid_for(m, 256, num_sms, 8), 256, 0, s>>>(E, m, T, cap, flags);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_clear_table(Slot *T, unsigned long long cap, cudaStream_t s, int num_sms) {
-  k_clear_table<<<grid_for(cap, 256, num_sms, 16), 256, 0, s>>>(T, cap);
+cudaError_t launch_duplicate_check(const unsigned long long *E, uint32_t m, unsigned long long *set,
+                                   unsigned long long cap, uint32_t *flags, cudaStream_t s, int num_sms) {
+  k_fill_u64<<<grid_for(cap, 256, num_sms, 8), 256, 0, s>>>(set, cap, kEmptyKey);
+  k_duplicates<<<grid_for(m, 256, num_sms, 8), 256, 0, s>>>(E, m, set, cap, flags);
   return cudaGetLastError();
 }
 

@@ -40,10 +40,11 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class GesmcOpts(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_uint64),
-        ("load_factor", ctypes.c_double),
         ("lazy_threshold", ctypes.c_uint64),
         ("start_round", ctypes.c_uint64),
         ("max_waves", ctypes.c_uint32),
+        ("tuple_log2", ctypes.c_uint32),
+        ("group_log2", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
@@ -61,8 +62,8 @@ class GesmcStats(ctypes.Structure):
         ("rejected_loop", ctypes.c_uint64),
         ("rejected_exists", ctypes.c_uint64),
         ("kernel_launches", ctypes.c_uint64),
-        ("table_slots", ctypes.c_uint64),
-        ("buckets", ctypes.c_uint64),
+        ("perm_buckets", ctypes.c_uint64),
+        ("tuple_partitions", ctypes.c_uint64),
         ("waves_total", ctypes.c_uint64),
         ("waves_max", ctypes.c_uint64),
         ("wave_hist", ctypes.c_uint64 * WAVE_HIST),
@@ -102,7 +103,7 @@ _SIGNATURES = [
     ("gesmc_next_round", ctypes.c_uint64, [ctypes.c_void_p]),
     ("gesmc_num_edges", ctypes.c_uint64, [ctypes.c_void_p]),
     ("gesmc_num_nodes", ctypes.c_uint64, [ctypes.c_void_p]),
-    ("gesmc_device_bytes", ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_double]),
+    ("gesmc_device_bytes", ctypes.c_size_t, [ctypes.c_uint64]),
     ("gesmc_destroy", None, [ctypes.c_void_p]),
     ("gesmc_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("gesmc_run_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -137,8 +138,8 @@ def gesmc_strerror(code: int) -> str:
     return load_library().gesmc_strerror(int(code)).decode()
 
 
-def gesmc_device_bytes(m: int, load_factor: float = 0.5) -> int:
-    return int(load_library().gesmc_device_bytes(m, load_factor))
+def gesmc_device_bytes(m: int) -> int:
+    return int(load_library().gesmc_device_bytes(m))
 
 
 def _check(code: int, where: str):
@@ -183,8 +184,8 @@ def _as_edge_buffer(edges):
     return a.ctypes.data, a.size, 0, a
 
 
-def gesmc_create(edges, n: int = 0, load_factor: float = 0.5, lazy_threshold: int = 0, start_round: int = 0,
-                 max_waves: int = 0, stream=None, torch_allocator: bool = True):
+def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 0, max_waves: int = 0, stream=None,
+                 torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0):
     """Create a chain handle; returns (handle, keepalive).  Raises GesmcError."""
     import torch
 
@@ -194,10 +195,11 @@ def gesmc_create(edges, n: int = 0, load_factor: float = 0.5, lazy_threshold: in
     opts = GesmcOpts()
     lib.gesmc_opts_default(ctypes.byref(opts))
     opts.n = n
-    opts.load_factor = load_factor
     opts.lazy_threshold = lazy_threshold
     opts.start_round = start_round
     opts.max_waves = max_waves
+    opts.tuple_log2 = tuple_log2
+    opts.group_log2 = group_log2
     if stream is None:
         stream = torch.cuda.current_stream()
     opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
@@ -240,7 +242,7 @@ def gesmc_reset_stats(h):
     _check(load_library().gesmc_reset_stats(h), "gesmc_reset_stats")
 
 
-NUM_STAGES = 8
+NUM_STAGES = 10
 
 
 def gesmc_set_profiling(h, enable: bool):

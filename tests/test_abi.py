@@ -48,12 +48,12 @@ def test_host_only_entry_points():
     assert "loop" in gesmc.gesmc_strerror(gesmc.GESMC_E_LOOP)
     opts = gesmc.GesmcOpts()
     lib.gesmc_opts_default(ctypes.byref(opts))
-    assert opts.load_factor == 0.5 and opts.lazy_threshold == 0 and opts.n == 0
-    # memory plan: the dependency table dominates (16 B x 2m / load factor)
+    assert opts.lazy_threshold == 0 and opts.n == 0 and opts.max_waves == 0
+    # memory plan: about 120 bytes per edge, no table sized by a load factor
     m = 1 << 20
-    b = gesmc.gesmc_device_bytes(m, 0.5)
-    assert 16 * 4 * m <= b < 16 * 4 * m + 64 * m
-    assert gesmc.gesmc_device_bytes(1 << 32, 0.5) == 0
+    b = gesmc.gesmc_device_bytes(m)
+    assert 80 * m <= b < 200 * m
+    assert gesmc.gesmc_device_bytes(1 << 31) == 0
     assert gesmc.gesmc_stage_name(0) == "clear" and gesmc.gesmc_stage_name(99) == ""
 
 
@@ -63,8 +63,9 @@ def test_create_rejects_bad_arguments_before_touching_a_device():
     assert lib.gesmc_create(None, 5, 0, None, ctypes.byref(h)) == gesmc.GESMC_E_INVALID
     opts = gesmc.GesmcOpts()
     lib.gesmc_opts_default(ctypes.byref(opts))
-    opts.load_factor = 0.95
+    opts.n = (1 << 32) + 1
     assert lib.gesmc_create(None, 0, 0, ctypes.byref(opts), ctypes.byref(h)) == gesmc.GESMC_E_INVALID
+    assert lib.gesmc_create(None, 1 << 31, 0, None, ctypes.byref(h)) == gesmc.GESMC_E_INVALID
     assert lib.gesmc_create(None, 0, 0, None, None) == gesmc.GESMC_E_INVALID
 
 
