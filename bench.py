@@ -38,6 +38,7 @@ ROUNDS_PER_STEP = 20
 WORKLOADS = {
     "gnp_2p24": dict(desc="G(n=2^24, p=16/(n-1)), seed 3; 20 global switches per step", n_log2=24, deg=16.0,
                      seed=3),
+    "gnp_2p22": dict(desc="G(n=2^22, p=16/(n-1)), seed 4", n_log2=22, deg=16.0, seed=4),
     "gnp_2p20": dict(desc="G(n=2^20, p=16/(n-1)), seed 5", n_log2=20, deg=16.0, seed=5),
     "gnp_2p12": dict(desc="G(n=2^12, p=16/(n-1)), seed 7 (tests)", n_log2=12, deg=16.0, seed=7),
 }
@@ -158,29 +159,26 @@ def read_peaks():
 def algorithmic_bytes(stage: str, m: int, L: int, nb: int, npart: int, accepted: float) -> float:
     """DRAM bytes a stage must move per round (streaming reads + writes).
 
-    Per switch (two positions, four dependency tuples of 12 bytes):
-      permute:       read the list in slot order (2 x 12 B) and the status word (4 B),
-                     write two 16-byte bucket records (their write frontiers stay in L2)
-      sortpair:      read the two records (32 B); write the list in slot order (24 B),
-                     the reject word (4 B), the dependency-entry pair (8 B) and four tuples (48 B)
-      tuple_scatter: read four tuples, write them grouped by hash partition (48 B + 48 B)
-      group:         read four grouped tuples (48 B)
-      wave1:         read the reject word, write the status word (8 B)
-    The scans and the clear move a few bytes per bucket or partition."""
+    Per switch (two positions, four 16-byte dependency tuples):
+      permute:   read the list in slot order (2 x 12 B) and the status word (4 B),
+                 write two 16-byte bucket records (their write frontiers stay in L2)
+      sortpair:  read the two records (32 B); write the list in slot order (24 B),
+                 the reject word (4 B), the dependency-entry pair (8 B) and append
+                 four tuples to their hash partitions (64 B)
+      group:     read the four tuples of the partition (64 B)
+      wave1:     read the reject word, write the status word (8 B)
+    The scans, the clear and the (normally empty) overflow pass move a few
+    bytes per bucket or partition."""
     if stage == "permute":
         return 12.0 * m + 4.0 * L + 16.0 * m
     if stage == "sortpair":
-        return 16.0 * m + 12.0 * m + L * (4.0 + 8.0 + 48.0)
-    if stage == "tuple_scatter":
-        return 2 * 48.0 * L
+        return 16.0 * m + 12.0 * m + L * (4.0 + 8.0 + 64.0)
     if stage == "group":
-        return 48.0 * L
+        return 64.0 * L
     if stage == "wave1":
         return 8.0 * L
     if stage in ("scan_perm", "clear"):
-        return 12.0 * nb + 12.0 * npart
-    if stage == "scan_tuples":
-        return 12.0 * npart
+        return 12.0 * nb + 8.0 * npart
     return 0.0
 
 

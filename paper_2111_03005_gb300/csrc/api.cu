@@ -23,8 +23,9 @@ struct Plan {
   uint64_t m = 0;
   uint32_t L = 0, B = 0, nb = 1, P = 0, np = 1, group_log2 = 0;
   size_t off_E, off_cpos, off_cedge, off_prec, off_pcount, off_poff, off_pib_pos, off_pib_edge, off_bnd, off_word,
-      off_sw, off_status, off_list0, off_list1, off_tkey, off_tval, off_pkey, off_pval, off_tcount, off_toff,
-      off_tcursor, off_dep, off_ctl, off_st, off_scratch, total;
+      off_sw, off_status, off_list0, off_list1, off_ptup, off_otup, off_stup, off_tcount, off_ocount, off_ooff,
+      off_ocursor, off_dep, off_ctl, off_st, off_scratch, total;
+  uint32_t capt = 0;
 };
 
 // Largest m: switch indices must fit the 30 bits a tuple gives them.
@@ -68,13 +69,15 @@ bool make_plan(uint64_t m, Plan *p, uint32_t tuple_log2 = 0, uint32_t group_log2
   p->off_status = take(4 * L);
   p->off_list0 = take(4 * L);
   p->off_list1 = take(4 * L);
-  p->off_tkey = take(8 * ntuple);
-  p->off_tval = take(4 * ntuple);
-  p->off_pkey = take(8 * ntuple);
-  p->off_pval = take(4 * ntuple);
+  // a partition has room for twice its mean (at least 64 tuples)
+  p->capt = (uint32_t)((ntuple >> P) * 2 + 64);
+  p->off_ptup = take(16ull * p->np * p->capt);
+  p->off_otup = take(16 * ntuple);
+  p->off_stup = take(16 * ntuple);
   p->off_tcount = take(4ull * p->np);
-  p->off_toff = take(4ull * (p->np + 1));
-  p->off_tcursor = take(4ull * p->np);
+  p->off_ocount = take(4ull * p->np);
+  p->off_ooff = take(4ull * (p->np + 1));
+  p->off_ocursor = take(4ull * p->np);
   p->off_dep = take(8 * (2 * L + 1));
   p->off_ctl = take(sizeof(Counters));
   p->off_st = take(sizeof(StatsDev));
@@ -106,13 +109,14 @@ RoundArgs args_for(const Plan &p, void *base) {
   a.status = at<uint32_t>(base, p.off_status);
   a.list0 = at<uint32_t>(base, p.off_list0);
   a.list1 = at<uint32_t>(base, p.off_list1);
-  a.tkey = at<unsigned long long>(base, p.off_tkey);
-  a.tval = at<uint32_t>(base, p.off_tval);
-  a.pkey = at<unsigned long long>(base, p.off_pkey);
-  a.pval = at<uint32_t>(base, p.off_pval);
+  a.ptup = at<uint4>(base, p.off_ptup);
+  a.otup = at<uint4>(base, p.off_otup);
+  a.stup = at<uint4>(base, p.off_stup);
   a.tcount = at<uint32_t>(base, p.off_tcount);
-  a.toff = at<uint32_t>(base, p.off_toff);
-  a.tcursor = at<uint32_t>(base, p.off_tcursor);
+  a.ocount = at<uint32_t>(base, p.off_ocount);
+  a.ooff = at<uint32_t>(base, p.off_ooff);
+  a.ocursor = at<uint32_t>(base, p.off_ocursor);
+  a.capt = p.capt;
   a.dep = at<uint2>(base, p.off_dep);
   a.ctl = at<Counters>(base, p.off_ctl);
   a.st = at<StatsDev>(base, p.off_st);
@@ -130,7 +134,7 @@ RoundArgs args_for(const Plan &p, void *base) {
 // Validate and canonicalise E in place (loops, ids >= n_bound, repeated
 // edges, in that precedence), then load it as the slot-order state of `a`.
 // *n_out receives n_bound, or largest id + 1 if n_bound is 0.  Synchronises
-// the stream.  The tuple arrays serve as the duplicate set's scratch.
+// the stream.
 int validate_and_load(const RoundArgs &a, unsigned long long *E, uint64_t m, uint64_t n_bound, uint32_t *flags,
                       cudaStream_t s, int sms, uint64_t *n_out) {
   uint32_t host_flags[2] = {0, 0};
@@ -148,7 +152,9 @@ int validate_and_load(const RoundArgs &a, unsigned long long *E, uint64_t m, uin
   if (host_flags[0] & kFlagRange) return GESMC_E_RANGE;
   *n_out = n_bound ? n_bound : (m ? (uint64_t)host_flags[1] + 1 : 0);
   if (m == 0) return GESMC_OK;
-  ok &= launch_duplicate_check(E, (uint32_t)m, a.tkey, 4ull * a.L + 1, flags, s, sms) == cudaSuccess;
+  // the overflow-tuple array (16 bytes x (4L + 1)) serves as the duplicate set's slots
+  ok &= launch_duplicate_check(E, (uint32_t)m, reinterpret_cast<unsigned long long *>(a.otup), 2 * (4ull * a.L + 1),
+                               flags, s, sms) == cudaSuccess;
   ok &= launch_load_state(a, E, s, sms) == cudaSuccess;
   ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
   ok &= cudaStreamSynchronize(s) == cudaSuccess;
@@ -465,8 +471,8 @@ int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
 }
 
 const char *gesmc_stage_name(int stage) {
-  static const char *names[kNumStages] = {"clear",         "permute", "scan_perm", "sortpair", "boundary",
-                                          "scan_tuples",   "tuple_scatter", "group", "wave1", "tail"};
+  static const char *names[kNumStages] = {"clear",    "permute", "scan_perm", "sortpair", "boundary",
+                                          "overflow", "group",   "wave1",     "tail"};
   return (stage >= 0 && stage < kNumStages) ? names[stage] : "";
 }
 

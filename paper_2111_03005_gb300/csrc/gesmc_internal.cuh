@@ -14,8 +14,10 @@
 //   word         u32[L]            per switch: outright-reject code | flags
 //   sw           uint2[L]          per switch: dependency entry of e3, e4
 //   status       u32[L]            (wave << 2) | state of each switch
-//   tkey/tval    u64/u32[4L+1]     Algorithm 1's tuples, four per switch
-//   pkey/pval    u64/u32[4L+1]     the same, grouped by hash partition
+//   ptup         uint4[np * capt]  Algorithm 1's tuples (four per switch),
+//                                  appended to fixed-capacity hash partitions
+//   otup/stup    uint4[4L+1]       tuples beyond a partition's capacity, and
+//                                  the same grouped by partition (rare)
 //   dep          uint2[2L+1]       {p, q} of every edge id with a dependency
 //   E            u64[m]            position-order copy (input / output only)
 #pragma once
@@ -75,8 +77,9 @@ constexpr int kPerThread = kPermBucketCap / kSortThreads;
 constexpr int kSubBits = 11;
 
 // Tuple partitions: 2^P partitions by the top P bits of the hash of the
-// edge id (about 2^tuple_log2 tuples each); one CTA groups a partition by
-// edge id in a shared-memory table of 2^group_log2 slots (20 bytes each).
+// edge id (about 2^tuple_log2 tuples each, room for twice that); one CTA
+// groups a partition by edge id in a shared-memory table of 2^group_log2
+// slots (20 bytes each).  A tuple is {edge id lo, edge id hi, value, 0}.
 constexpr int kDefaultTupleLog2 = 10;
 constexpr int kDefaultGroupLog2 = 11;
 constexpr int kGroupThreads = 256;
@@ -91,7 +94,8 @@ struct Counters {
   uint32_t err;         // sticky error bits (cleared by the host per call)
   uint32_t waves;       // waves the last round needed
   uint32_t dep_count;   // dependency entries allocated this round
-  uint32_t pad[2];
+  uint32_t ovf_count;   // tuples that did not fit their partition
+  uint32_t pad;
 };
 
 // Device-resident statistics, accumulated over rounds.
@@ -117,19 +121,20 @@ struct RoundArgs {
   uint32_t *status;
   uint32_t *list0;
   uint32_t *list1;
-  unsigned long long *tkey;
-  uint32_t *tval;
-  unsigned long long *pkey;
-  uint32_t *pval;
-  uint32_t *tcount;   // np: tuples per partition
-  uint32_t *toff;     // np + 1
-  uint32_t *tcursor;  // np
+  uint4 *ptup;        // np * capt
+  uint4 *otup;        // 4L + 1
+  uint4 *stup;        // 4L + 1
+  uint32_t *tcount;   // np: tuples appended per partition (may exceed capt)
+  uint32_t *ocount;   // np: overflow tuples per partition
+  uint32_t *ooff;     // np + 1
+  uint32_t *ocursor;  // np
   uint2 *dep;
   Counters *ctl;
   StatsDev *st;
   unsigned long long seed, round, lazy_threshold;
   uint32_t m, L, B, nb, P, np, max_waves;
   uint32_t group_log2;  // shared-memory grouping table: 2^group_log2 slots
+  uint32_t capt;        // tuple capacity of a partition
   uint32_t apply;  // 1 if status[] holds the last round's decisions (apply them when reading)
 };
 
@@ -140,8 +145,7 @@ enum Stage {
   kStageScanPerm,
   kStageSortPair,
   kStageBoundary,
-  kStageScanTuples,
-  kStageTupleScatter,
+  kStageOverflow,
   kStageGroup,
   kStageWave1,
   kStageTail,

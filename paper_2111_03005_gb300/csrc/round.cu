@@ -13,11 +13,11 @@
 //                    memory; write the list back in this round's slot order;
 //                    for each pair of slots (edge switch sigma_k, Def. 1)
 //                    apply tau, the loop and shared-node rules and laziness,
-//                    and write Algorithm 1's four tuples (e1, k, ERASE),
-//                    (e2, k, ERASE), (e3, k, INSERT), (e4, k, INSERT)
+//                    and append Algorithm 1's four tuples (e1, k, ERASE),
+//                    (e2, k, ERASE), (e3, k, INSERT), (e4, k, INSERT) to
+//                    the hash partitions of their edge ids
 //   k_boundary       the same for pairs whose slots lie in two buckets
-//   k_scan_tuples    tuple partition offsets
-//   k_tuple_scatter  group the tuples by hash partition of their edge id
+//   k_overflow_*     group the (rare) tuples that found their partition full
 //   k_group          per partition: group by edge id in a shared-memory
 //                    table and decide every target of wave 1 (Algorithm 1's
 //                    first round): certainly present, free, or dependent on
@@ -150,9 +150,35 @@ __device__ __forceinline__ void apply_last(const RoundArgs &a, uint32_t k, uint3
 }
 
 // ---------------------------------------------------------------- build
+// Append tuples to their hash partitions: partition ids and cursor atomics
+// first (independent, in flight together), then the 16-byte stores.  A
+// tuple that finds its partition full goes to the overflow list.
+template <int N>
+__device__ __forceinline__ void emit_tuples(const RoundArgs &a, const unsigned long long (&key)[N],
+                                            const uint32_t (&val)[N]) {
+  uint32_t part[N], idx[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    part[t] = partition_of(mix64(key[t]), a.P);
+    idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[part[t]], 1u) : 0u;
+  }
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    if (key[t] == kEmptyKey) continue;
+    const uint4 rec = make_uint4((uint32_t)key[t], (uint32_t)(key[t] >> 32), val[t], 0u);
+    if (idx[t] < a.capt) {
+      a.ptup[(size_t)part[t] * a.capt + idx[t]] = rec;
+    } else {
+      const uint32_t o = atomicAdd(&a.ctl->ovf_count, 1u);
+      if (o <= 4 * a.L) a.otup[o] = rec;  // at most 4L + 1 tuples exist
+    }
+  }
+}
+
 // Switch k = (i, j, g) of this round with sources e1, e2: record its reject
-// code and Algorithm 1's four tuples (slots 4k .. 4k+3 of the staging
-// arrays), and count them per tuple partition.
+// code and Algorithm 1's four tuples (e1, k, ERASE), (e2, k, ERASE),
+// (e3, k, INSERT), (e4, k, INSERT).  A switch rejected outright stores its
+// sources as never erased and no targets.
 __device__ __forceinline__ void build_switch(const RoundArgs &a, uint32_t k, uint32_t i, unsigned long long e1,
                                              uint32_t j, unsigned long long e2) {
   unsigned long long e3 = kEmptyKey, e4 = kEmptyKey;
@@ -161,22 +187,16 @@ __device__ __forceinline__ void build_switch(const RoundArgs &a, uint32_t k, uin
   a.sw[k] = make_uint2(kTrivial, kTrivial);
   const uint32_t src = kTupleSource | (code ? kKeepK : k);
   if (code) e3 = e4 = kEmptyKey;
-  reinterpret_cast<ulonglong2 *>(a.tkey)[2 * (size_t)k] = make_ulonglong2(e1, e2);
-  reinterpret_cast<ulonglong2 *>(a.tkey)[2 * (size_t)k + 1] = make_ulonglong2(e3, e4);
-  reinterpret_cast<uint4 *>(a.tval)[k] = make_uint4(src, src, k, k | kTupleWhich);
-  atomicAdd(&a.tcount[partition_of(mix64(e1), a.P)], 1u);
-  atomicAdd(&a.tcount[partition_of(mix64(e2), a.P)], 1u);
-  if (!code) {
-    atomicAdd(&a.tcount[partition_of(mix64(e3), a.P)], 1u);
-    atomicAdd(&a.tcount[partition_of(mix64(e4), a.P)], 1u);
-  }
+  const unsigned long long key[4] = {e1, e2, e3, e4};
+  const uint32_t val[4] = {src, src, k, k | kTupleWhich};
+  emit_tuples<4>(a, key, val);
 }
 
 // The unpaired last position of an odd list: a source no switch erases.
 __device__ __forceinline__ void keep_source(const RoundArgs &a, unsigned long long e) {
-  a.tkey[4 * (size_t)a.L] = e;
-  a.tval[4 * (size_t)a.L] = kTupleSource | kKeepK;
-  atomicAdd(&a.tcount[partition_of(mix64(e), a.P)], 1u);
+  const unsigned long long key[1] = {e};
+  const uint32_t val[1] = {kTupleSource | kKeepK};
+  emit_tuples<1>(a, key, val);
 }
 
 // ---------------------------------------------------------------- decide
@@ -258,14 +278,17 @@ __device__ __forceinline__ void append_if(bool take, uint32_t k, uint32_t *list,
 __global__ void k_clear(RoundArgs a) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (uint32_t b = tid; b < a.nb; b += nth) a.pcount[b] = 0;
-  for (uint32_t p = tid; p < a.np; p += nth) a.tcount[p] = 0;
+  for (uint32_t p = tid; p < a.np; p += nth) {
+    a.tcount[p] = 0;
+    a.ocount[p] = 0;
+  }
   if (tid == 0) {
     a.ctl->pending[0] = 0;
     a.ctl->pending[1] = 0;
     a.ctl->boundary = 0;
     a.ctl->waves = 0;
     a.ctl->dep_count = 0;
-    a.tkey[4 * (size_t)a.L] = kEmptyKey;  // the odd-m slot, overwritten when m is odd
+    a.ctl->ovf_count = 0;
   }
 }
 
@@ -336,8 +359,30 @@ __global__ void __launch_bounds__(1024) k_scan_perm(RoundArgs a) {
   cta_scan_1024(a.pcount, a.poff, nullptr, a.nb, kPermBucketCap);
 }
 
-__global__ void __launch_bounds__(1024) k_scan_tuples(RoundArgs a) {
-  cta_scan_1024(a.tcount, a.toff, a.tcursor, a.np, 0xFFFFFFFFu);
+// Overflow tuples (those that found their partition full), grouped by
+// partition with exact counts.  All three kernels return at once when there
+// is no overflow, which is the normal case.
+__global__ void k_overflow_count(RoundArgs a) {
+  const uint32_t n = min(a.ctl->ovf_count, 4 * a.L + 1);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const uint4 r = a.otup[t];
+    atomicAdd(&a.ocount[partition_of(mix64(((unsigned long long)r.y << 32) | r.x), a.P)], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_overflow_scan(RoundArgs a) {
+  if (a.ctl->ovf_count == 0) return;
+  cta_scan_1024(a.ocount, a.ooff, a.ocursor, a.np, 0xFFFFFFFFu);
+}
+
+__global__ void k_overflow_scatter(RoundArgs a) {
+  const uint32_t n = min(a.ctl->ovf_count, 4 * a.L + 1);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const uint4 r = a.otup[t];
+    const uint32_t part = partition_of(mix64(((unsigned long long)r.y << 32) | r.x), a.P);
+    const uint32_t dst = atomicAdd(&a.ocursor[part], 1u);
+    if (dst < n) a.stup[dst] = r;
+  }
 }
 
 // In-place exclusive scan of 2^kSubBits counters by a CTA of kSortThreads.
@@ -512,33 +557,6 @@ __global__ void k_boundary(RoundArgs a) {
   }
 }
 
-__global__ void k_tuple_scatter(RoundArgs a) {
-  const size_t n = 4 * (size_t)a.L + 1;
-  const uint32_t total = a.toff[a.np];
-  const size_t nth = (size_t)gridDim.x * blockDim.x;
-  for (size_t base = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; base < n; base += 4 * nth) {
-    unsigned long long key[4];
-    uint32_t val[4], dst[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      key[u] = base + u < n ? __ldcs(&a.tkey[base + u]) : kEmptyKey;
-      val[u] = base + u < n ? __ldcs(&a.tval[base + u]) : 0u;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      dst[u] = key[u] != kEmptyKey ? atomicAdd(&a.tcursor[partition_of(mix64(key[u]), a.P)], 1u) : 0xFFFFFFFFu;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (dst[u] < total) {
-        a.pkey[dst[u]] = key[u];
-        a.pval[dst[u]] = val[u];
-      } else if (key[u] != kEmptyKey) {
-        atomicOr(&a.ctl->err, kErrRecord);
-      }
-    }
-  }
-}
-
 // Group one tuple partition by edge id and decide wave 1 for its targets.
 // The shared-memory table holds the partition's distinct edge ids (key, p,
 // smallest inserter q, number of inserters c).  If the partition has more
@@ -555,8 +573,13 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
   __shared__ int stk_top;
   __shared__ uint32_t overflow;
   const int tid = threadIdx.x;
+  const bool ovf = a.ctl->ovf_count != 0;
   for (uint32_t part = blockIdx.x; part < a.np; part += gridDim.x) {
-    const uint32_t beg = a.toff[part], end = a.toff[part + 1];
+    // the partition's tuples: its own region, then its overflow tuples
+    const uint4 *prim = a.ptup + (size_t)part * a.capt;
+    const uint32_t nprim = min(a.tcount[part], a.capt);
+    const uint32_t obeg = ovf ? a.ooff[part] : 0, oend = ovf ? a.ooff[part + 1] : 0;
+    const uint32_t ntup = nprim + (oend - obeg);
     if (tid == 0) {
       stk_top = 1;
       stk_sub[0] = 0;
@@ -578,11 +601,12 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
       }
       __syncthreads();
       // insert every tuple of this sub-pass
-      for (uint32_t t = beg + tid; t < end; t += kGroupThreads) {
-        const unsigned long long key = a.pkey[t];
+      for (uint32_t t = tid; t < ntup; t += kGroupThreads) {
+        const uint4 r = t < nprim ? prim[t] : a.stup[obeg + (t - nprim)];
+        const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
         const unsigned long long h = mix64(key);
         if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
-        const uint32_t v = a.pval[t];
+        const uint32_t v = r.z;
         uint32_t s = (uint32_t)h & (S - 1), n = 0;
         for (; n < (uint32_t)S; ++n) {
           const unsigned long long cur = gk[s];
@@ -639,10 +663,11 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
       }
       __syncthreads();
       // wave 1 for every target of this sub-pass
-      for (uint32_t t = beg + tid; t < end; t += kGroupThreads) {
-        const uint32_t v = a.pval[t];
+      for (uint32_t t = tid; t < ntup; t += kGroupThreads) {
+        const uint4 r = t < nprim ? prim[t] : a.stup[obeg + (t - nprim)];
+        const uint32_t v = r.z;
         if (v & kTupleSource) continue;
-        const unsigned long long key = a.pkey[t];
+        const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
         const unsigned long long h = mix64(key);
         if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
         uint32_t s = (uint32_t)h & (S - 1);
@@ -872,10 +897,14 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   if (work) { k_sortpair<<<a.nb, kSortThreads, 0, s>>>(a); ++n; }
   mark(kStageBoundary);
   if (work) { k_boundary<<<grid_for(a.nb, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
-  mark(kStageScanTuples);
-  if (work) { k_scan_tuples<<<1, 1024, 0, s>>>(a); ++n; }
-  mark(kStageTupleScatter);
-  if (work) { k_tuple_scatter<<<grid_for((ntuple + 3) / 4, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  mark(kStageOverflow);
+  if (work) {
+    const int g = grid_for(ntuple, 256, num_sms, 2);
+    k_overflow_count<<<g, 256, 0, s>>>(a);
+    k_overflow_scan<<<1, 1024, 0, s>>>(a);
+    k_overflow_scatter<<<g, 256, 0, s>>>(a);
+    n += 3;
+  }
   mark(kStageGroup);
   if (work) { k_group<<<a.np, kGroupThreads, group_smem_bytes(a.group_log2), s>>>(a); ++n; }
   mark(kStageWave1);
