@@ -35,7 +35,7 @@ bool make_plan(uint64_t m, Plan *p, uint32_t tuple_log2 = 0, uint32_t group_log2
   if (m > kMaxEdges) return false;
   if (!tuple_log2) tuple_log2 = kDefaultTupleLog2;
   if (!group_log2) group_log2 = kDefaultGroupLog2;
-  if (tuple_log2 < 8 || tuple_log2 > 16 || group_log2 < 10 || group_log2 > 13) return false;
+  if (tuple_log2 < 8 || tuple_log2 > 16 || group_log2 < 10 || group_log2 > (uint32_t)kMaxGroupLog2) return false;
   p->group_log2 = group_log2;
   p->m = m;
   p->L = (uint32_t)(m / 2);
@@ -305,7 +305,8 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
     delete h;
     return GESMC_E_INVALID;
   }
-  if (prepare_kernels(h->plan.group_log2) != cudaSuccess) {
+  uint32_t group_grid = 0;
+  if (prepare_kernels(h->plan.group_log2, h->num_sms, &group_grid) != cudaSuccess) {
     cudaGetLastError();
     delete h;
     return GESMC_E_CUDA;
@@ -317,6 +318,7 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
     return GESMC_E_NOMEM;
   }
   h->args = args_for(p, h->base);
+  h->args.group_grid = group_grid;
   h->args.lazy_threshold = o.lazy_threshold;
   h->args.max_waves = o.max_waves;
   unsigned long long *E = at<unsigned long long>(h->base, p.off_E);
@@ -528,13 +530,15 @@ extern "C" int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64
   if (rc != GESMC_OK) return rc;
   Plan p;
   if (!make_plan(m, &p) || p.total > GESMC_NOALLOC_SCRATCH_BYTES) return GESMC_E_INTERNAL;
-  if (prepare_kernels(p.group_log2) != cudaSuccess) {
+  uint32_t group_grid = 0;
+  if (prepare_kernels(p.group_log2, sms, &group_grid) != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
 
   cudaStream_t s = (cudaStream_t)stream;
   RoundArgs a = args_for(p, base);
+  a.group_grid = group_grid;
   a.seed = seed;
   unsigned long long *E = reinterpret_cast<unsigned long long *>(edges);  // in place on the caller's list
   uint64_t n_eff = 0;

@@ -79,11 +79,13 @@ constexpr int kSubBits = 11;
 // Tuple partitions: 2^P partitions by the top P bits of the hash of the
 // edge id (about 2^tuple_log2 tuples each, room for twice that); one CTA
 // groups a partition by edge id in a shared-memory table of 2^group_log2
-// slots (20 bytes each).  A tuple is {edge id lo, edge id hi, value, 0}.
+// slots (22 bytes each, with the used-slot list).  A tuple is {edge id lo,
+// edge id hi, value, 0}.
 constexpr int kDefaultTupleLog2 = 10;
 constexpr int kDefaultGroupLog2 = 11;
+constexpr int kMaxGroupLog2 = 13;
 constexpr int kGroupThreads = 256;
-constexpr int kGroupSlotBytes = 20;
+constexpr int kGroupSlotBytes = 22;
 
 constexpr int kWaveHist = 64;
 
@@ -135,6 +137,7 @@ struct RoundArgs {
   uint32_t m, L, B, nb, P, np, max_waves;
   uint32_t group_log2;  // shared-memory grouping table: 2^group_log2 slots
   uint32_t capt;        // tuple capacity of a partition
+  uint32_t group_grid;  // CTAs of the persistent grouping kernel
   uint32_t apply;  // 1 if status[] holds the last round's decisions (apply them when reading)
 };
 
@@ -154,8 +157,10 @@ enum Stage {
 
 // Dynamic shared memory of the grouping kernel, and the one-time opt-in to
 // more than 48 KB of it (call before the first round on a device).
+// prepare_kernels also returns the persistent grouping grid for this table
+// size (CTAs that fit on the device at once).
 size_t group_smem_bytes(uint32_t group_log2);
-cudaError_t prepare_kernels(uint32_t group_log2);
+cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_grid);
 
 // Host-side launchers (round.cu).  launch_round records kNumStages + 1
 // events into ev (if not null) around the stages and adds the number of

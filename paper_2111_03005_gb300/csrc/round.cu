@@ -557,29 +557,165 @@ __global__ void k_boundary(RoundArgs a) {
   }
 }
 
-// Group one tuple partition by edge id and decide wave 1 for its targets.
-// The shared-memory table holds the partition's distinct edge ids (key, p,
-// smallest inserter q, number of inserters c).  If the partition has more
-// distinct ids than slots, it is processed in sub-passes that each take the
-// ids whose hash bits 32.. select them (split further until they fit).
+// Grouping of one tuple partition by edge id (Algorithm 1's table T for the
+// partition's edge ids) in a shared-memory table of S slots: key, p (the
+// eraser, from the source tuple), q (smallest inserter), c (number of
+// inserters).  Then wave 1 for every target: present when k runs (p >= k),
+// dependent on an undecided switch (p < k, or an earlier inserter q < k),
+// or free.  Edge ids with a dependency get an entry {p, q} for the later
+// waves.
+struct GroupSmem {
+  unsigned long long *gk;
+  uint32_t *gp, *gq, *gc;
+  uint16_t *used;  // slots claimed in the current partition
+};
+
+__device__ __forceinline__ GroupSmem group_smem(uint32_t S) {
+  extern __shared__ unsigned long long group_dyn[];
+  GroupSmem g;
+  g.gk = group_dyn;
+  g.gp = reinterpret_cast<uint32_t *>(g.gk + S);
+  g.gq = g.gp + S;
+  g.gc = g.gq + S;
+  g.used = reinterpret_cast<uint16_t *>(g.gc + S);
+  return g;
+}
+
+__device__ __forceinline__ void group_reset_slot(const GroupSmem &g, uint32_t s) {
+  g.gk[s] = kEmptyKey;
+  g.gp[s] = kPNone;
+  g.gq[s] = kQNone;
+  g.gc[s] = 0;
+}
+
+// Insert one tuple; returns its slot, or S if the table is full.  A slot
+// claimed here is appended to the used list.
+__device__ __forceinline__ uint32_t group_insert(const GroupSmem &g, uint32_t S, unsigned long long key,
+                                                 unsigned long long h, uint32_t v, uint32_t *nused) {
+  uint32_t s = (uint32_t)h & (S - 1), n = 0;
+  for (; n < S; ++n) {
+    const unsigned long long cur = g.gk[s];
+    if (cur == key) break;
+    if (cur == kEmptyKey) {
+      const unsigned long long prev = atomicCAS(&g.gk[s], kEmptyKey, key);
+      if (prev == kEmptyKey) {
+        g.used[atomicAdd(nused, 1u)] = (uint16_t)s;
+        break;
+      }
+      if (prev == key) break;
+    }
+    s = (s + 1) & (S - 1);
+  }
+  if (n == S) return S;
+  if (v & kTupleSource) {
+    const uint32_t kk = v & kTupleK;
+    g.gp[s] = kk == kKeepK ? kPKeep : kk;  // one source per edge id (Obs. 2)
+  } else {
+    atomicMin(&g.gq[s], v & kTupleK);
+    atomicAdd(&g.gc[s], 1u);
+  }
+  return s;
+}
+
+// One dependency entry per edge id that some target depends on: an id
+// inserted more than once, or inserted while in E at the round start.
+// gc[s] is replaced by the entry index (kTrivial if none).
+__device__ __forceinline__ void group_alloc(const RoundArgs &a, const GroupSmem &g, uint32_t s) {
+  const bool need = g.gc[s] >= 2 || (g.gc[s] >= 1 && g.gp[s] != kPNone);
+  uint32_t idx = kTrivial;
+  if (need) {
+    idx = atomicAdd(&a.ctl->dep_count, 1u);
+    if (idx <= 2 * a.L) {
+      a.dep[idx] = make_uint2(g.gp[s], g.gq[s]);
+    } else {
+      idx = kTrivial;
+      atomicOr(&a.ctl->err, kErrRecord);
+    }
+  }
+  g.gc[s] = idx;
+}
+
+// Wave 1 for target tuple v in slot s.
+__device__ __forceinline__ void group_decide(const RoundArgs &a, const GroupSmem &g, uint32_t s, uint32_t v) {
+  const uint32_t k = v & kTupleK;
+  const uint32_t p = g.gp[s], q = g.gq[s];
+  if (p != kPNone && p >= k) atomicOr(&a.word[k], kFlagBad);       // present when k runs
+  else if (p != kPNone || q != k) atomicOr(&a.word[k], kFlagDep);  // erased or inserted earlier, maybe
+  const uint32_t d = g.gc[s];
+  if (d != kTrivial) {
+    if (v & kTupleWhich) a.sw[k].y = d;
+    else a.sw[k].x = d;
+  }
+}
+
+constexpr int kGroupR = 8;  // tuples a thread holds in registers on the fast path
+
+// Persistent CTAs over the partitions.  Fast path: the partition's tuples
+// stay in registers and only the claimed slots are visited and cleared.
+// Partitions with more tuples than fit, or more distinct ids than slots,
+// take the sub-pass path: the ids whose hash bits 32.. select them, split
+// further until each sub-pass fits.
 __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
-  extern __shared__ unsigned long long group_smem[];
   const uint32_t S = 1u << a.group_log2;
-  unsigned long long *gk = group_smem;
-  uint32_t *gp = reinterpret_cast<uint32_t *>(gk + S);
-  uint32_t *gq = gp + S;
-  uint32_t *gc = gq + S;
+  const GroupSmem g = group_smem(S);
   __shared__ uint32_t stk_sub[64], stk_n[64];
   __shared__ int stk_top;
-  __shared__ uint32_t overflow;
+  __shared__ uint32_t overflow, nused;
   const int tid = threadIdx.x;
   const bool ovf = a.ctl->ovf_count != 0;
+  for (uint32_t s = tid; s < S; s += kGroupThreads) group_reset_slot(g, s);
+  if (tid == 0) {
+    nused = 0;
+    overflow = 0;
+  }
+  __syncthreads();
   for (uint32_t part = blockIdx.x; part < a.np; part += gridDim.x) {
     // the partition's tuples: its own region, then its overflow tuples
     const uint4 *prim = a.ptup + (size_t)part * a.capt;
     const uint32_t nprim = min(a.tcount[part], a.capt);
     const uint32_t obeg = ovf ? a.ooff[part] : 0, oend = ovf ? a.ooff[part + 1] : 0;
     const uint32_t ntup = nprim + (oend - obeg);
+    if (ntup <= (uint32_t)(kGroupR * kGroupThreads)) {
+      uint4 r[kGroupR];
+      uint32_t slot[kGroupR];
+#pragma unroll
+      for (int j = 0; j < kGroupR; ++j) {
+        const uint32_t t = tid + j * kGroupThreads;
+        r[j] = make_uint4(0, 0, 0, 0);
+        if (t < ntup) r[j] = t < nprim ? __ldcs(&prim[t]) : a.stup[obeg + (t - nprim)];
+      }
+#pragma unroll
+      for (int j = 0; j < kGroupR; ++j) {
+        const uint32_t t = tid + j * kGroupThreads;
+        slot[j] = S;
+        if (t < ntup) {
+          const unsigned long long key = ((unsigned long long)r[j].y << 32) | r[j].x;
+          slot[j] = group_insert(g, S, key, mix64(key), r[j].z, &nused);
+          if (slot[j] == S) overflow = 1;
+        }
+      }
+      __syncthreads();
+      const bool full = overflow != 0;
+      if (!full) {
+        for (uint32_t u = tid; u < nused; u += kGroupThreads) group_alloc(a, g, g.used[u]);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kGroupR; ++j) {
+          const uint32_t t = tid + j * kGroupThreads;
+          if (t < ntup && !(r[j].z & kTupleSource)) group_decide(a, g, slot[j], r[j].z);
+        }
+      }
+      __syncthreads();
+      for (uint32_t u = tid; u < nused; u += kGroupThreads) group_reset_slot(g, g.used[u]);
+      __syncthreads();
+      if (tid == 0) {
+        nused = 0;
+        overflow = 0;
+      }
+      __syncthreads();
+      if (!full) continue;
+    }
+    // sub-pass path
     if (tid == 0) {
       stk_top = 1;
       stk_sub[0] = 0;
@@ -592,42 +728,16 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
       if (tid == 0) {
         --stk_top;
         overflow = 0;
+        nused = 0;
       }
-      for (uint32_t s = tid; s < S; s += kGroupThreads) {
-        gk[s] = kEmptyKey;
-        gp[s] = kPNone;
-        gq[s] = kQNone;
-        gc[s] = 0;
-      }
+      for (uint32_t s = tid; s < S; s += kGroupThreads) group_reset_slot(g, s);
       __syncthreads();
-      // insert every tuple of this sub-pass
       for (uint32_t t = tid; t < ntup; t += kGroupThreads) {
         const uint4 r = t < nprim ? prim[t] : a.stup[obeg + (t - nprim)];
         const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
         const unsigned long long h = mix64(key);
         if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
-        const uint32_t v = r.z;
-        uint32_t s = (uint32_t)h & (S - 1), n = 0;
-        for (; n < (uint32_t)S; ++n) {
-          const unsigned long long cur = gk[s];
-          if (cur == key) break;
-          if (cur == kEmptyKey) {
-            const unsigned long long prev = atomicCAS(&gk[s], kEmptyKey, key);
-            if (prev == kEmptyKey || prev == key) break;
-          }
-          s = (s + 1) & (S - 1);
-        }
-        if (n == (uint32_t)S) {
-          overflow = 1;
-          continue;
-        }
-        if (v & kTupleSource) {
-          const uint32_t kk = v & kTupleK;
-          gp[s] = kk == kKeepK ? kPKeep : kk;  // one source per edge id (Obs. 2)
-        } else {
-          atomicMin(&gq[s], v & kTupleK);
-          atomicAdd(&gc[s], 1u);
-        }
+        if (group_insert(g, S, key, h, r.z, &nused) == S) overflow = 1;
       }
       __syncthreads();
       if (overflow) {
@@ -645,45 +755,28 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
         __syncthreads();
         continue;
       }
-      // one dependency entry per edge id that some target depends on: an id
-      // inserted more than once, or inserted while in E at the round start
-      for (uint32_t s = tid; s < S; s += kGroupThreads) {
-        const bool need = gk[s] != kEmptyKey && (gc[s] >= 2 || (gc[s] >= 1 && gp[s] != kPNone));
-        uint32_t idx = kTrivial;
-        if (need) {
-          idx = atomicAdd(&a.ctl->dep_count, 1u);
-          if (idx <= 2 * a.L) {
-            a.dep[idx] = make_uint2(gp[s], gq[s]);
-          } else {
-            idx = kTrivial;
-            atomicOr(&a.ctl->err, kErrRecord);
-          }
-        }
-        gc[s] = idx;  // gc now holds the entry index
-      }
+      for (uint32_t u = tid; u < nused; u += kGroupThreads) group_alloc(a, g, g.used[u]);
       __syncthreads();
-      // wave 1 for every target of this sub-pass
       for (uint32_t t = tid; t < ntup; t += kGroupThreads) {
         const uint4 r = t < nprim ? prim[t] : a.stup[obeg + (t - nprim)];
-        const uint32_t v = r.z;
-        if (v & kTupleSource) continue;
+        if (r.z & kTupleSource) continue;
         const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
         const unsigned long long h = mix64(key);
         if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
         uint32_t s = (uint32_t)h & (S - 1);
-        for (uint32_t n = 0; n < (uint32_t)S && gk[s] != key; ++n) s = (s + 1) & (S - 1);
-        const uint32_t k = v & kTupleK;
-        const uint32_t p = gp[s], q = gq[s];
-        if (p != kPNone && p >= k) atomicOr(&a.word[k], kFlagBad);       // present when k runs
-        else if (p != kPNone || q != k) atomicOr(&a.word[k], kFlagDep);  // erased or inserted earlier, maybe
-        const uint32_t d = gc[s];
-        if (d != kTrivial) {
-          if (v & kTupleWhich) a.sw[k].y = d;
-          else a.sw[k].x = d;
-        }
+        for (uint32_t n = 0; n < S && g.gk[s] != key; ++n) s = (s + 1) & (S - 1);
+        group_decide(a, g, s, r.z);
       }
       __syncthreads();
     }
+    // leave the table empty for the next partition
+    for (uint32_t s = tid; s < S; s += kGroupThreads) group_reset_slot(g, s);
+    __syncthreads();
+    if (tid == 0) {
+      nused = 0;
+      overflow = 0;
+    }
+    __syncthreads();
   }
 }
 
@@ -871,9 +964,17 @@ inline int grid_for(unsigned long long work, int threads, int num_sms, int per_s
 
 size_t group_smem_bytes(uint32_t group_log2) { return (size_t)kGroupSlotBytes << group_log2; }
 
-cudaError_t prepare_kernels(uint32_t group_log2) {
-  return cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)group_smem_bytes(group_log2));
+cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_grid) {
+  // opt in to the largest table any handle may use, so that handles with
+  // different table sizes never lower each other's limit
+  cudaError_t e = cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)group_smem_bytes(kMaxGroupLog2));
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group, kGroupThreads, group_smem_bytes(group_log2));
+  if (e != cudaSuccess) return e;
+  *group_grid = (uint32_t)(num_sms * (per_sm > 0 ? per_sm : 1));
+  return cudaSuccess;
 }
 
 cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEvent_t *ev, uint32_t *launches) {
@@ -906,7 +1007,11 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
     n += 3;
   }
   mark(kStageGroup);
-  if (work) { k_group<<<a.np, kGroupThreads, group_smem_bytes(a.group_log2), s>>>(a); ++n; }
+  if (work) {
+    const uint32_t ctas = a.group_grid ? a.group_grid : (uint32_t)num_sms;
+    k_group<<<ctas < a.np ? ctas : a.np, kGroupThreads, group_smem_bytes(a.group_log2), s>>>(a);
+    ++n;
+  }
   mark(kStageWave1);
   if (work) { k_wave1<<<grid_for(a.L, 256, num_sms, 16), 256, 0, s>>>(a); ++n; }
   mark(kStageTail);
