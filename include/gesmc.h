@@ -89,8 +89,8 @@ typedef struct gesmc_stats_s {
   uint64_t rejected_loop;   /* a new edge would be a loop (Def. 1)                */
   uint64_t rejected_exists; /* a new edge is in E when the switch runs (Def. 1)   */
   uint64_t kernel_launches; /* CUDA kernels gesmc_run launched                     */
-  uint64_t perm_buckets;    /* permutation buckets per round                      */
-  uint64_t tuple_partitions; /* hash partitions of the dependency tuples per round */
+  uint64_t perm_buckets;    /* permutation buckets in use (all chains)            */
+  uint64_t tuple_partitions; /* dependency-tuple hash partitions in use             */
   uint64_t waves_total;     /* resolution waves summed over rounds (Algorithm 1's
                                rounds of decide/delay)                            */
   uint64_t waves_max;       /* largest wave count of one round                    */
@@ -180,12 +180,77 @@ size_t gesmc_device_bytes(uint64_t m);
  * Returns GESMC_OK, GESMC_E_INVALID, GESMC_E_TOO_LARGE, GESMC_E_LOOP,
  * GESMC_E_RANGE, GESMC_E_MULTI, GESMC_E_CUDA or a round error of gesmc_run. */
 #define GESMC_NOALLOC_MAX_EDGES 65536
-#define GESMC_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define GESMC_NOALLOC_SCRATCH_BYTES (20u << 20)
 int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64_t global_switches, uint64_t seed,
                       uint64_t start_round, void *stream);
 
 /* Release the handle and its device memory (NULL is ignored). */
 void gesmc_destroy(gesmc_t h);
+
+/* ------------------------------------------------------------------------
+ * Pools: many independent chains advanced together, one set of kernels per
+ * round for all of them (an ensemble of null-model samples, or the chains
+ * of a sampling service).  Each chain has its own edge list, seed, round
+ * numbering and laziness; its result is bit for bit the one it would have
+ * alone (gesmc_create + gesmc_run with the same seed and start round), since
+ * every chain draws its permutation and its dependency partitions from its
+ * own counters and index ranges.  Chains join and leave between rounds
+ * without moving other chains' data (continuous batching).
+ *
+ * A pool allocates its device memory once, sized for max_edges edges in at
+ * most max_chains chains (gesmc_pool_device_bytes tells how much).  Adding a
+ * chain fails with GESMC_E_NOMEM when the edges or the chain slots are used
+ * up, or when the free index ranges are too fragmented for it.  Threading
+ * and errors as for single chains; all device work is on opts.stream.
+ */
+typedef struct gesmc_pool_ctx *gesmc_pool_t;
+
+typedef struct gesmc_pool_opts {
+  uint64_t max_edges;      /* edges of all chains at once                    */
+  uint32_t max_chains;     /* chains at once (>= 1)                          */
+  uint32_t max_waves;      /* as gesmc_opts.max_waves                        */
+  uint32_t tuple_log2;     /* as gesmc_opts.tuple_log2                       */
+  uint32_t group_log2;     /* as gesmc_opts.group_log2                       */
+  void *stream;            /* cudaStream_t; NULL: the legacy default stream  */
+  gesmc_alloc_fn alloc;    /* optional device allocator (as gesmc_opts)      */
+  gesmc_free_fn free;
+  void *alloc_ctx;
+} gesmc_pool_opts;
+
+typedef struct gesmc_chain_info_s {
+  uint64_t m, n;           /* edges; node bound                               */
+  uint64_t seed;
+  uint64_t rounds;         /* rounds run since the chain was added            */
+  uint64_t next_round;     /* number of the chain's next round                */
+  uint64_t switches;       /* floor(m/2) per round run                        */
+  uint64_t accepted;       /* switches that rewired (since added)             */
+} gesmc_chain_info_t;
+
+void gesmc_pool_opts_default(gesmc_pool_opts *o);
+size_t gesmc_pool_device_bytes(uint64_t max_edges, uint32_t max_chains, uint32_t tuple_log2);
+int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out);
+void gesmc_pool_destroy(gesmc_pool_t p);
+
+/* Add a chain (a simple graph, validated as in gesmc_create; host or device
+ * memory, copied).  Its first round is numbered start_round; *chain_out
+ * receives its id (ids of removed chains are reused). */
+int gesmc_pool_add(gesmc_pool_t p, const uint64_t *edges, uint64_t m, int edges_on_device, uint64_t n,
+                   uint64_t seed, uint64_t start_round, uint64_t lazy_threshold, uint32_t *chain_out);
+/* Remove a chain (its result should be read first with gesmc_pool_edges). */
+int gesmc_pool_remove(gesmc_pool_t p, uint32_t chain);
+/* Advance every chain of the pool by `global_switches` rounds. */
+int gesmc_pool_run(gesmc_pool_t p, uint64_t global_switches);
+/* Copy a chain's edge list, in position order, as gesmc_edges does. */
+int gesmc_pool_edges(gesmc_pool_t p, uint32_t chain, uint64_t *out, uint64_t capacity, int out_on_device,
+                     uint64_t *m_out);
+int gesmc_pool_chain_info(gesmc_pool_t p, uint32_t chain, gesmc_chain_info_t *out);
+uint32_t gesmc_pool_num_chains(gesmc_pool_t p);
+uint64_t gesmc_pool_free_edges(gesmc_pool_t p);
+/* Counters over all chains, stage timing: as for single chains. */
+int gesmc_pool_stats(gesmc_pool_t p, gesmc_stats_t *out);
+int gesmc_pool_reset_stats(gesmc_pool_t p);
+int gesmc_pool_set_profiling(gesmc_pool_t p, int enable);
+int gesmc_pool_stage_times(gesmc_pool_t p, double *ms, int n_stages, uint64_t *rounds);
 
 /* Static description of an error code. */
 const char *gesmc_strerror(int code);

@@ -1,8 +1,10 @@
-// C ABI of libgesmc (declared in include/gesmc.h): handle life cycle, device
-// memory plan, create-time validation and the round loop of Algorithm 3
-// (ParGlobalES) of arXiv 2111.03005.
+// C ABI of libgesmc (declared in include/gesmc.h): pools of chains, the
+// single-chain handle built on a one-chain pool, the allocation-free entry
+// point, and the round loop of Algorithm 3 (ParGlobalES) of arXiv 2111.03005.
 #include <cstdlib>
 #include <cstring>
+#include <iterator>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -15,75 +17,103 @@ using namespace gesmc;
 namespace {
 
 constexpr size_t kAlign = 256;
-
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Sizes of the pieces of one handle's single device allocation.
-struct Plan {
-  uint64_t m = 0;
-  uint32_t L = 0, B = 0, nb = 1, P = 0, np = 1, group_log2 = 0;
-  size_t off_E, off_cpos, off_cedge, off_prec, off_pcount, off_poff, off_pib_pos, off_pib_edge, off_bnd, off_word,
-      off_sw, off_status, off_list0, off_list1, off_ptup, off_otup, off_stup, off_tcount, off_ocount, off_ooff,
-      off_ocursor, off_dep, off_ctl, off_st, off_scratch, total;
-  uint32_t capt = 0;
-};
-
-// Largest m: switch indices must fit the 30 bits a tuple gives them.
+// Largest m: switch indices must fit the 30 bits a tuple gives them
+// (pool-wide), so a pool's edges are bounded the same way.
 constexpr uint64_t kMaxEdges = (1ull << 31) - 1;
 
-bool make_plan(uint64_t m, Plan *p, uint32_t tuple_log2 = 0, uint32_t group_log2 = 0) {
+// Shape of one chain in the index spaces.
+struct ChainShape {
+  uint32_t m, L, B, nb, P, np, capt;
+  uint32_t slots() const { return (m + 1) & ~1u; }  // slot ranges start on even slots
+  uint64_t tuples() const { return (uint64_t)np * capt; }
+};
+
+bool chain_shape(uint64_t m, uint32_t tuple_log2, ChainShape *s) {
   if (m > kMaxEdges) return false;
-  if (!tuple_log2) tuple_log2 = kDefaultTupleLog2;
-  if (!group_log2) group_log2 = kDefaultGroupLog2;
-  if (tuple_log2 < 8 || tuple_log2 > 16 || group_log2 < 10 || group_log2 > (uint32_t)kMaxGroupLog2) return false;
-  p->group_log2 = group_log2;
-  p->m = m;
-  p->L = (uint32_t)(m / 2);
+  s->m = (uint32_t)m;
+  s->L = (uint32_t)(m / 2);
   uint32_t B = 0;  // permutation buckets of about 2^kPermAvgLog2 positions
   while ((m >> B) > (1ull << kPermAvgLog2)) ++B;
-  p->B = B;
-  p->nb = 1u << B;
-  const uint64_t ntuple = 4ull * p->L + 1;
+  s->B = B;
+  s->nb = 1u << B;
+  const uint64_t ntuple = 4ull * s->L + 1;
   uint32_t P = 0;  // tuple partitions of about 2^tuple_log2 tuples
   while ((ntuple >> P) > (1ull << tuple_log2)) ++P;
-  p->P = P;
-  p->np = 1u << P;
+  s->P = P;
+  s->np = 1u << P;
+  s->capt = (uint32_t)((ntuple >> P) * 2 + 64);  // room for twice the mean
+  return true;
+}
+
+// Capacities of a pool's index spaces for at most M edges in at most C
+// chains; each bound holds for any split of the edges into chains.
+struct Capacity {
+  uint64_t slots, switches, buckets, parts, tuples, ovf, dep;
+};
+
+Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
+  Capacity c;
+  c.slots = M + C;
+  c.switches = M / 2 + C;
+  c.buckets = 2 * (M >> kPermAvgLog2) + 2 * C;
+  const uint64_t ntuple = 2 * M + C;  // bounds the sum over chains of 4L + 1
+  c.parts = 2 * (ntuple >> tuple_log2) + 4 * C;
+  c.tuples = 2 * ntuple + 64 * c.parts;
+  c.ovf = ntuple;
+  c.dep = M + 1;
+  return c;
+}
+
+// Offsets of the pieces of a pool's single device allocation.
+struct Layout {
+  size_t chains, chain_acc, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
+      pib_pos, pib_edge, bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
+      E, ctl, st, scratch, total;
+};
+
+Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
+  Layout l;
   size_t o = 0;
   auto take = [&o](size_t bytes) {
     const size_t at = o;
     o = align_up(o + (bytes ? bytes : 1));
     return at;
   };
-  const size_t L = p->L;
-  p->off_E = take(8 * m);
-  p->off_cpos = take(4 * m);
-  p->off_cedge = take(8 * m);
-  p->off_prec = take(16ull * p->nb * kPermBucketCap);
-  p->off_pcount = take(4ull * p->nb);
-  p->off_poff = take(4ull * (p->nb + 1));
-  p->off_pib_pos = take(4 * m);
-  p->off_pib_edge = take(8 * m);
-  p->off_bnd = take(4ull * (p->nb + 1));
-  p->off_word = take(4 * L);
-  p->off_sw = take(8 * L);
-  p->off_status = take(4 * L);
-  p->off_list0 = take(4 * L);
-  p->off_list1 = take(4 * L);
-  // a partition has room for twice its mean (at least 64 tuples)
-  p->capt = (uint32_t)((ntuple >> P) * 2 + 64);
-  p->off_ptup = take(16ull * p->np * p->capt);
-  p->off_otup = take(16 * ntuple);
-  p->off_stup = take(16 * ntuple);
-  p->off_tcount = take(4ull * p->np);
-  p->off_ocount = take(4ull * p->np);
-  p->off_ooff = take(4ull * (p->np + 1));
-  p->off_ocursor = take(4ull * p->np);
-  p->off_dep = take(8 * (2 * L + 1));
-  p->off_ctl = take(sizeof(Counters));
-  p->off_st = take(sizeof(StatsDev));
-  p->off_scratch = take(64);
-  p->total = o;
-  return true;
+  l.chains = take(sizeof(ChainDesc) * C);
+  l.chain_acc = take(8 * C);
+  l.owner_slot = take(4 * c.slots);
+  l.owner_switch = take(4 * c.switches);
+  l.owner_bucket = take(4 * c.buckets);
+  l.owner_part = take(4 * c.parts);
+  l.cpos = take(4 * c.slots);
+  l.cedge = take(8 * c.slots);
+  l.prec = take(16ull * kPermBucketCap * c.buckets);
+  l.pcount = take(4 * c.buckets);
+  l.poff = take(4 * (c.buckets + 1));
+  l.pib_pos = take(4 * c.slots);
+  l.pib_edge = take(8 * c.slots);
+  l.bnd = take(4 * (c.buckets + 1));
+  l.word = take(4 * c.switches);
+  l.sw = take(8 * c.switches);
+  l.status = take(4 * c.switches);
+  l.list0 = take(4 * c.switches);
+  l.list1 = take(4 * c.switches);
+  l.ptup = take(16 * c.tuples);
+  l.otup = take(16 * c.ovf);
+  l.stup = take(16 * c.ovf);
+  l.tcount = take(4 * c.parts);
+  l.ocount = take(4 * c.parts);
+  l.ooff = take(4 * (c.parts + 1));
+  l.ocursor = take(4 * c.parts);
+  l.dep = take(8 * c.dep);
+  l.E = take(8 * M);
+  l.ctl = take(sizeof(Counters));
+  l.st = take(sizeof(StatsDev));
+  l.scratch = take(64);
+  l.total = o;
+  return l;
 }
 
 template <class T>
@@ -91,81 +121,57 @@ T *at(void *base, size_t off) {
   return reinterpret_cast<T *>(static_cast<char *>(base) + off);
 }
 
-// Round arguments for a plan laid out at `base` (the edge list E is the
-// plan's own piece unless `E` is given).
-RoundArgs args_for(const Plan &p, void *base) {
-  RoundArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.cpos = at<uint32_t>(base, p.off_cpos);
-  a.cedge = at<unsigned long long>(base, p.off_cedge);
-  a.prec = at<uint4>(base, p.off_prec);
-  a.pcount = at<uint32_t>(base, p.off_pcount);
-  a.poff = at<uint32_t>(base, p.off_poff);
-  a.pib_pos = at<uint32_t>(base, p.off_pib_pos);
-  a.pib_edge = at<unsigned long long>(base, p.off_pib_edge);
-  a.bnd = at<uint32_t>(base, p.off_bnd);
-  a.word = at<uint32_t>(base, p.off_word);
-  a.sw = at<uint2>(base, p.off_sw);
-  a.status = at<uint32_t>(base, p.off_status);
-  a.list0 = at<uint32_t>(base, p.off_list0);
-  a.list1 = at<uint32_t>(base, p.off_list1);
-  a.ptup = at<uint4>(base, p.off_ptup);
-  a.otup = at<uint4>(base, p.off_otup);
-  a.stup = at<uint4>(base, p.off_stup);
-  a.tcount = at<uint32_t>(base, p.off_tcount);
-  a.ocount = at<uint32_t>(base, p.off_ocount);
-  a.ooff = at<uint32_t>(base, p.off_ooff);
-  a.ocursor = at<uint32_t>(base, p.off_ocursor);
-  a.capt = p.capt;
-  a.dep = at<uint2>(base, p.off_dep);
-  a.ctl = at<Counters>(base, p.off_ctl);
-  a.st = at<StatsDev>(base, p.off_st);
-  a.m = (uint32_t)p.m;
-  a.L = p.L;
-  a.B = p.B;
-  a.nb = p.nb;
-  a.P = p.P;
-  a.np = p.np;
-  a.group_log2 = p.group_log2;
-  a.apply = 0;
-  return a;
-}
+// First-fit allocator of ranges of one index space.
+class RangeSet {
+ public:
+  void reset(uint64_t capacity) {
+    cap_ = capacity;
+    free_.clear();
+    if (capacity) free_[0] = capacity;
+  }
+  bool alloc(uint64_t len, uint64_t *start) {
+    if (len == 0) {
+      *start = 0;
+      return true;
+    }
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= len) {
+        *start = it->first;
+        const uint64_t rest = it->second - len, next = it->first + len;
+        free_.erase(it);
+        if (rest) free_[next] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t start, uint64_t len) {
+    if (len == 0) return;
+    auto it = free_.emplace(start, len).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  // Smallest index above every allocated range.
+  uint64_t high_water() const {
+    if (free_.empty()) return cap_;
+    auto last = std::prev(free_.end());
+    return last->first + last->second == cap_ ? last->first : cap_;
+  }
 
-// Validate and canonicalise E in place (loops, ids >= n_bound, repeated
-// edges, in that precedence), then load it as the slot-order state of `a`.
-// *n_out receives n_bound, or largest id + 1 if n_bound is 0.  Synchronises
-// the stream.
-int validate_and_load(const RoundArgs &a, unsigned long long *E, uint64_t m, uint64_t n_bound, uint32_t *flags,
-                      cudaStream_t s, int sms, uint64_t *n_out) {
-  uint32_t host_flags[2] = {0, 0};
-  bool ok = cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
-  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
-  ok &= cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
-  if (ok && m > 0) ok &= launch_canonicalise(E, (uint32_t)m, n_bound, flags, flags + 1, s, sms) == cudaSuccess;
-  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok &= cudaStreamSynchronize(s) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return GESMC_E_CUDA;
-  }
-  if (host_flags[0] & kFlagLoop) return GESMC_E_LOOP;
-  if (host_flags[0] & kFlagRange) return GESMC_E_RANGE;
-  *n_out = n_bound ? n_bound : (m ? (uint64_t)host_flags[1] + 1 : 0);
-  if (m == 0) return GESMC_OK;
-  // the overflow-tuple array (16 bytes x (4L + 1)) serves as the duplicate set's slots
-  ok &= launch_duplicate_check(E, (uint32_t)m, reinterpret_cast<unsigned long long *>(a.otup), 2 * (4ull * a.L + 1),
-                               flags, s, sms) == cudaSuccess;
-  ok &= launch_load_state(a, E, s, sms) == cudaSuccess;
-  ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
-  ok &= cudaStreamSynchronize(s) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return GESMC_E_CUDA;
-  }
-  if (host_flags[0] & kFlagMulti) return GESMC_E_MULTI;
-  if (host_flags[0] & kFlagTableFull) return GESMC_E_INTERNAL;
-  return GESMC_OK;
-}
+ private:
+  uint64_t cap_ = 0;
+  std::map<uint64_t, uint64_t> free_;
+};
 
 struct DeviceGuard {
   int prev = -1;
@@ -179,49 +185,12 @@ struct DeviceGuard {
   }
 };
 
-}  // namespace
-
-struct gesmc_ctx {
-  int device = 0;
-  int num_sms = 1;
-  cudaStream_t stream = nullptr;
-  gesmc_alloc_fn alloc = nullptr;
-  gesmc_free_fn free_fn = nullptr;
-  void *alloc_ctx = nullptr;
-  void *base = nullptr;
-  Plan plan;
+struct HostChain {
+  bool live = false;
+  ChainDesc d;
+  ChainShape shape;
   uint64_t n = 0;
-  uint64_t next_round = 0;
-  uint64_t lazy_threshold = 0;
-  uint32_t max_waves = 0;
-  uint64_t rounds = 0;
-  uint64_t launches = 0;
-  int broken = 0;
-  RoundArgs args;
-  // stage timing (gesmc_set_profiling): kNumStages + 1 events per round
-  int profiling = 0;
-  std::vector<cudaEvent_t> events;
-  double stage_ms[kNumStages] = {};
-  uint64_t stage_rounds = 0;
 };
-
-namespace {
-
-void *dev_alloc(gesmc_ctx *h, size_t bytes) {
-  if (h->alloc) return h->alloc(bytes, (void *)h->stream, h->alloc_ctx);
-  void *p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
-  }
-  return p;
-}
-
-void dev_free(gesmc_ctx *h, void *p) {
-  if (!p) return;
-  if (h->free_fn) h->free_fn(p, h->alloc_ctx);
-  else cudaFree(p);
-}
 
 int map_device_errors(uint32_t err) {
   if (err & kErrTableFull) return GESMC_E_TABLE_FULL;
@@ -232,18 +201,571 @@ int map_device_errors(uint32_t err) {
 
 }  // namespace
 
+// A pool: device state for up to max_chains chains with max_edges edges in
+// total, and the host bookkeeping of its index spaces.
+struct gesmc_pool_ctx {
+  int device = 0;
+  int num_sms = 1;
+  cudaStream_t stream = nullptr;
+  gesmc_alloc_fn alloc = nullptr;
+  gesmc_free_fn free_fn = nullptr;
+  void *alloc_ctx = nullptr;
+  bool owns_memory = true;
+  void *base = nullptr;
+  uint64_t max_edges = 0;
+  uint32_t max_chains = 0;
+  uint32_t tuple_log2 = kDefaultTupleLog2;
+  Capacity cap;
+  Layout lay;
+  RangeSet slots, switches, buckets, parts, tuples;
+  std::vector<HostChain> chains;
+  uint32_t live_chains = 0, working_chains = 0;
+  uint64_t live_edges = 0;
+  uint64_t pool_round = 0;  // rounds completed (host copy of the device counter)
+  uint64_t rounds = 0, switches_run = 0, launches = 0;
+  int broken = 0;
+  RoundArgs args;
+  int profiling = 0;
+  std::vector<cudaEvent_t> events;
+  double stage_ms[kNumStages] = {};
+  uint64_t stage_rounds = 0;
+};
+
+struct gesmc_ctx {
+  gesmc_pool_t pool = nullptr;
+  uint32_t chain = 0;
+};
+
+namespace {
+
+void *dev_alloc(gesmc_pool_t p, size_t bytes) {
+  if (p->alloc) return p->alloc(bytes, (void *)p->stream, p->alloc_ctx);
+  void *ptr = nullptr;
+  if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return ptr;
+}
+
+void dev_free(gesmc_pool_t p, void *ptr) {
+  if (!ptr || !p->owns_memory) return;
+  if (p->free_fn) p->free_fn(ptr, p->alloc_ctx);
+  else cudaFree(ptr);
+}
+
+void refresh_args(gesmc_pool_t p) {
+  RoundArgs &a = p->args;
+  a.slot_hw = (uint32_t)p->slots.high_water();
+  a.switch_hw = (uint32_t)p->switches.high_water();
+  a.bucket_hw = (uint32_t)p->buckets.high_water();
+  a.part_hw = (uint32_t)p->parts.high_water();
+  a.any_work = p->working_chains > 0;
+}
+
+// Point the round arguments at the pieces of the pool's memory.
+void pool_bind(gesmc_pool_t p) {
+  void *b = p->base;
+  const Layout &l = p->lay;
+  RoundArgs &a = p->args;
+  std::memset(&a, 0, sizeof(a));
+  a.chains = at<ChainDesc>(b, l.chains);
+  a.chain_accepted = at<unsigned long long>(b, l.chain_acc);
+  a.owner_slot = at<uint32_t>(b, l.owner_slot);
+  a.owner_switch = at<uint32_t>(b, l.owner_switch);
+  a.owner_bucket = at<uint32_t>(b, l.owner_bucket);
+  a.owner_part = at<uint32_t>(b, l.owner_part);
+  a.cpos = at<uint32_t>(b, l.cpos);
+  a.cedge = at<unsigned long long>(b, l.cedge);
+  a.prec = at<uint4>(b, l.prec);
+  a.pcount = at<uint32_t>(b, l.pcount);
+  a.poff = at<uint32_t>(b, l.poff);
+  a.pib_pos = at<uint32_t>(b, l.pib_pos);
+  a.pib_edge = at<unsigned long long>(b, l.pib_edge);
+  a.bnd = at<uint32_t>(b, l.bnd);
+  a.word = at<uint32_t>(b, l.word);
+  a.sw = at<uint2>(b, l.sw);
+  a.status = at<uint32_t>(b, l.status);
+  a.list0 = at<uint32_t>(b, l.list0);
+  a.list1 = at<uint32_t>(b, l.list1);
+  a.ptup = at<uint4>(b, l.ptup);
+  a.otup = at<uint4>(b, l.otup);
+  a.stup = at<uint4>(b, l.stup);
+  a.tcount = at<uint32_t>(b, l.tcount);
+  a.ocount = at<uint32_t>(b, l.ocount);
+  a.ooff = at<uint32_t>(b, l.ooff);
+  a.ocursor = at<uint32_t>(b, l.ocursor);
+  a.dep = at<uint2>(b, l.dep);
+  a.ctl = at<Counters>(b, l.ctl);
+  a.st = at<StatsDev>(b, l.st);
+  a.ovf_cap = (uint32_t)p->cap.ovf;
+  a.dep_cap = (uint32_t)p->cap.dep;
+}
+
+bool valid_opts(const gesmc_pool_opts &o) {
+  if (o.max_edges > kMaxEdges || o.max_chains == 0 || o.max_chains > (1u << 20)) return false;
+  if (o.tuple_log2 && (o.tuple_log2 < 8 || o.tuple_log2 > 16)) return false;
+  if (o.group_log2 && (o.group_log2 < 10 || o.group_log2 > (uint32_t)kMaxGroupLog2)) return false;
+  if ((o.alloc == nullptr) != (o.free == nullptr)) return false;
+  return true;
+}
+
+// Host state and device memory (owner maps, counters) of an empty pool whose
+// memory is bound at p->base.
+int pool_init(gesmc_pool_t p, const gesmc_pool_opts &o) {
+  p->slots.reset(p->cap.slots);
+  p->switches.reset(p->cap.switches);
+  p->buckets.reset(p->cap.buckets);
+  p->parts.reset(p->cap.parts);
+  p->tuples.reset(p->cap.tuples);
+  p->chains.assign(p->max_chains, HostChain());
+  pool_bind(p);
+  RoundArgs &a = p->args;
+  a.max_waves = o.max_waves;
+  a.group_log2 = o.group_log2 ? o.group_log2 : kDefaultGroupLog2;
+  uint32_t grid = 0;
+  if (prepare_kernels(a.group_log2, p->num_sms, &grid) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  a.group_grid = grid;
+  cudaStream_t s = p->stream;
+  const int sms = p->num_sms;
+  bool ok = launch_fill_u32(const_cast<uint32_t *>(a.owner_slot), (uint32_t)p->cap.slots, kNoChain, s, sms) ==
+            cudaSuccess;
+  ok &= launch_fill_u32(const_cast<uint32_t *>(a.owner_switch), (uint32_t)p->cap.switches, kNoChain, s, sms) ==
+        cudaSuccess;
+  ok &= launch_fill_u32(const_cast<uint32_t *>(a.owner_bucket), (uint32_t)p->cap.buckets, kNoChain, s, sms) ==
+        cudaSuccess;
+  ok &= launch_fill_u32(const_cast<uint32_t *>(a.owner_part), (uint32_t)p->cap.parts, kNoChain, s, sms) ==
+        cudaSuccess;
+  ok &= cudaMemsetAsync(a.ctl, 0, sizeof(Counters), s) == cudaSuccess;
+  ok &= cudaMemsetAsync(a.st, 0, sizeof(StatsDev), s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  refresh_args(p);
+  return GESMC_OK;
+}
+
+// Validate and canonicalise the list at E (device, m edges) in place: loops,
+// ids >= n_bound, repeated edges, in that precedence.  *n_out receives
+// n_bound, or largest id + 1 if n_bound is 0.  Synchronises the stream.
+int validate_list(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t n_bound, uint64_t *n_out) {
+  cudaStream_t s = p->stream;
+  uint32_t *flags = at<uint32_t>(p->base, p->lay.scratch);
+  uint32_t host_flags[2] = {0, 0};
+  bool ok = cudaMemsetAsync(flags, 0, 8, s) == cudaSuccess;
+  if (ok && m > 0) ok &= launch_canonicalise(E, (uint32_t)m, n_bound, flags, flags + 1, s, p->num_sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host_flags, flags, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  if (host_flags[0] & kFlagLoop) return GESMC_E_LOOP;
+  if (host_flags[0] & kFlagRange) return GESMC_E_RANGE;
+  *n_out = n_bound ? n_bound : (m ? (uint64_t)host_flags[1] + 1 : 0);
+  if (m == 0) return GESMC_OK;
+  // between rounds the overflow-tuple array is free: it holds the set
+  ok &= launch_duplicate_check(E, (uint32_t)m, reinterpret_cast<unsigned long long *>(p->args.otup), 2 * p->cap.ovf,
+                               flags, s, p->num_sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host_flags, flags, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  if (host_flags[0] & kFlagMulti) return GESMC_E_MULTI;
+  if (host_flags[0] & kFlagTableFull) return GESMC_E_INTERNAL;
+  return GESMC_OK;
+}
+
+void release_ranges(gesmc_pool_t p, const HostChain &hc) {
+  p->slots.release(hc.d.slot_base, hc.shape.slots());
+  p->switches.release(hc.d.switch_base, hc.shape.L);
+  p->buckets.release(hc.d.bucket_base, hc.shape.nb);
+  p->parts.release(hc.d.part_base, hc.shape.np);
+  p->tuples.release(hc.d.tuple_base, hc.shape.tuples());
+}
+
+// Ranges for a chain of this shape, all or none.
+bool alloc_ranges(gesmc_pool_t p, HostChain &hc) {
+  uint64_t sb = 0, wb = 0, bb = 0, pb = 0, tb = 0;
+  const ChainShape &sh = hc.shape;
+  if (!p->slots.alloc(sh.slots(), &sb)) return false;
+  if (!p->switches.alloc(sh.L, &wb)) {
+    p->slots.release(sb, sh.slots());
+    return false;
+  }
+  if (!p->buckets.alloc(sh.nb, &bb)) {
+    p->slots.release(sb, sh.slots());
+    p->switches.release(wb, sh.L);
+    return false;
+  }
+  if (!p->parts.alloc(sh.np, &pb)) {
+    p->slots.release(sb, sh.slots());
+    p->switches.release(wb, sh.L);
+    p->buckets.release(bb, sh.nb);
+    return false;
+  }
+  if (!p->tuples.alloc(sh.tuples(), &tb)) {
+    p->slots.release(sb, sh.slots());
+    p->switches.release(wb, sh.L);
+    p->buckets.release(bb, sh.nb);
+    p->parts.release(pb, sh.np);
+    return false;
+  }
+  hc.d.slot_base = (uint32_t)sb;
+  hc.d.switch_base = (uint32_t)wb;
+  hc.d.bucket_base = (uint32_t)bb;
+  hc.d.part_base = (uint32_t)pb;
+  hc.d.tuple_base = (uint32_t)tb;
+  return true;
+}
+
+// Set the owner maps of a chain's ranges to `c` (kNoChain to remove it).
+bool set_owners(gesmc_pool_t p, const HostChain &hc, uint32_t c) {
+  RoundArgs &a = p->args;
+  cudaStream_t s = p->stream;
+  const int sms = p->num_sms;
+  bool ok = launch_fill_u32(const_cast<uint32_t *>(a.owner_slot) + hc.d.slot_base, hc.shape.slots(), c, s, sms) ==
+            cudaSuccess;
+  ok &= launch_fill_u32(const_cast<uint32_t *>(a.owner_switch) + hc.d.switch_base, hc.shape.L, c, s, sms) ==
+        cudaSuccess;
+  ok &= launch_fill_u32(const_cast<uint32_t *>(a.owner_bucket) + hc.d.bucket_base, hc.shape.nb, c, s, sms) ==
+        cudaSuccess;
+  ok &= launch_fill_u32(const_cast<uint32_t *>(a.owner_part) + hc.d.part_base, hc.shape.np, c, s, sms) ==
+        cudaSuccess;
+  return ok;
+}
+
+// Add a chain whose list is already on the device at E (the pool's staging
+// buffer, or the caller's buffer for the allocation-free path).
+int pool_add_device(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t n, uint64_t seed,
+                    uint64_t start_round, uint64_t lazy_threshold, uint32_t *chain_out) {
+  if (m > p->max_edges - p->live_edges) return GESMC_E_NOMEM;
+  uint32_t c = 0;
+  while (c < p->max_chains && p->chains[c].live) ++c;
+  if (c == p->max_chains) return GESMC_E_NOMEM;
+  HostChain hc;
+  std::memset(&hc.d, 0, sizeof(hc.d));
+  if (!chain_shape(m, p->tuple_log2, &hc.shape)) return GESMC_E_INVALID;
+  uint64_t n_eff = 0;
+  int rc = validate_list(p, E, m, n, &n_eff);
+  if (rc != GESMC_OK) return rc;
+  if (!alloc_ranges(p, hc)) return GESMC_E_NOMEM;
+  ChainDesc &d = hc.d;
+  d.m = hc.shape.m;
+  d.L = hc.shape.L;
+  d.B = hc.shape.B;
+  d.P = hc.shape.P;
+  d.capt = hc.shape.capt;
+  d.seed = seed;
+  d.start_round = start_round;
+  d.join = p->pool_round;
+  d.added = p->pool_round;
+  d.lazy_threshold = lazy_threshold;
+  hc.live = true;
+  hc.n = n_eff;
+  cudaStream_t s = p->stream;
+  RoundArgs &a = p->args;
+  bool ok = cudaMemcpyAsync(const_cast<ChainDesc *>(a.chains) + c, &d, sizeof(d), cudaMemcpyHostToDevice, s) ==
+            cudaSuccess;
+  ok &= cudaMemsetAsync(a.chain_accepted + c, 0, 8, s) == cudaSuccess;
+  ok &= set_owners(p, hc, c);
+  ok &= launch_load_chain(a, d, E, s, p->num_sms) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    release_ranges(p, hc);
+    return GESMC_E_CUDA;
+  }
+  p->chains[c] = hc;
+  ++p->live_chains;
+  if (m >= 2) ++p->working_chains;
+  p->live_edges += m;
+  refresh_args(p);
+  *chain_out = c;
+  return GESMC_OK;
+}
+
+int pool_run(gesmc_pool_t p, uint64_t rounds) {
+  if (p->broken) return p->broken;
+  DeviceGuard g(p->device);
+  cudaStream_t s = p->stream;
+  const RoundArgs a = p->args;
+  if (cudaMemsetAsync(&a.ctl->err, 0, sizeof(uint32_t), s) != cudaSuccess) return GESMC_E_CUDA;
+  const size_t per_round = kNumStages + 1;
+  if (p->profiling) {
+    const size_t need = per_round * (size_t)rounds;
+    while (p->events.size() < need) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return GESMC_E_CUDA;
+      }
+      p->events.push_back(e);
+    }
+  }
+  uint32_t launches = 0;
+  for (uint64_t r = 0; r < rounds; ++r) {
+    cudaEvent_t *ev = p->profiling ? &p->events[per_round * r] : nullptr;
+    if (launch_round(a, s, p->num_sms, ev, &launches) != cudaSuccess) {
+      p->broken = GESMC_E_CUDA;
+      return GESMC_E_CUDA;
+    }
+  }
+  Counters ctl;
+  if (cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    p->broken = GESMC_E_CUDA;
+    return GESMC_E_CUDA;
+  }
+  if (p->profiling) {
+    for (uint64_t r = 0; r < rounds; ++r)
+      for (int st = 0; st < kNumStages; ++st) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->events[per_round * r + st], p->events[per_round * r + st + 1]) ==
+            cudaSuccess)
+          p->stage_ms[st] += ms;
+      }
+    p->stage_rounds += rounds;
+  }
+  p->pool_round += rounds;
+  p->rounds += rounds;
+  p->launches += launches;
+  uint64_t sw = 0;
+  for (const HostChain &hc : p->chains)
+    if (hc.live) sw += hc.shape.L;
+  p->switches_run += rounds * sw;
+  const int rc = map_device_errors(ctl.err);
+  if (rc != GESMC_OK) p->broken = rc;
+  return rc;
+}
+
+}  // namespace
+
 extern "C" {
+
+// ---------------------------------------------------------------- pools
+
+void gesmc_pool_opts_default(gesmc_pool_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_chains = 1;
+}
+
+size_t gesmc_pool_device_bytes(uint64_t max_edges, uint32_t max_chains, uint32_t tuple_log2) {
+  if (max_edges > kMaxEdges || max_chains == 0) return 0;
+  if (!tuple_log2) tuple_log2 = kDefaultTupleLog2;
+  return pool_layout(pool_capacity(max_edges, max_chains, tuple_log2), max_edges, max_chains).total;
+}
+
+void gesmc_pool_destroy(gesmc_pool_t p) {
+  if (!p) return;
+  {
+    DeviceGuard g(p->device);
+    if (p->base) {
+      cudaStreamSynchronize(p->stream);
+      dev_free(p, p->base);
+    }
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  }
+  delete p;
+}
+
+int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out) {
+  if (!out || !opts) return GESMC_E_INVALID;
+  *out = nullptr;
+  const gesmc_pool_opts o = *opts;
+  if (!valid_opts(o)) return GESMC_E_INVALID;
+  gesmc_pool_t p = new (std::nothrow) gesmc_pool_ctx();
+  if (!p) return GESMC_E_NOMEM;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return GESMC_E_CUDA;
+  }
+  cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (p->num_sms < 1) p->num_sms = 1;
+  p->stream = (cudaStream_t)o.stream;
+  p->alloc = o.alloc;
+  p->free_fn = o.free;
+  p->alloc_ctx = o.alloc_ctx;
+  p->max_edges = o.max_edges;
+  p->max_chains = o.max_chains;
+  p->tuple_log2 = o.tuple_log2 ? o.tuple_log2 : kDefaultTupleLog2;
+  p->cap = pool_capacity(p->max_edges, p->max_chains, p->tuple_log2);
+  p->lay = pool_layout(p->cap, p->max_edges, p->max_chains);
+  p->base = dev_alloc(p, p->lay.total);
+  if (!p->base) {
+    delete p;
+    return GESMC_E_NOMEM;
+  }
+  const int rc = pool_init(p, o);
+  if (rc != GESMC_OK) {
+    gesmc_pool_destroy(p);
+    return rc;
+  }
+  *out = p;
+  return GESMC_OK;
+}
+
+int gesmc_pool_add(gesmc_pool_t p, const uint64_t *edges, uint64_t m, int edges_on_device, uint64_t n,
+                   uint64_t seed, uint64_t start_round, uint64_t lazy_threshold, uint32_t *chain_out) {
+  if (!p || !chain_out || (m > 0 && !edges) || m > kMaxEdges || n > (1ull << 32)) return GESMC_E_INVALID;
+  if (p->broken) return p->broken;
+  if (m > p->max_edges - p->live_edges) return GESMC_E_NOMEM;
+  DeviceGuard g(p->device);
+  unsigned long long *E = at<unsigned long long>(p->base, p->lay.E);
+  if (m > 0 && cudaMemcpyAsync(E, edges, 8 * m, edges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  return pool_add_device(p, E, m, n, seed, start_round, lazy_threshold, chain_out);
+}
+
+int gesmc_pool_remove(gesmc_pool_t p, uint32_t chain) {
+  if (!p || chain >= p->max_chains || !p->chains[chain].live) return GESMC_E_INVALID;
+  DeviceGuard g(p->device);
+  HostChain &hc = p->chains[chain];
+  bool ok = set_owners(p, hc, kNoChain);
+  ok &= cudaStreamSynchronize(p->stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  release_ranges(p, hc);
+  --p->live_chains;
+  if (hc.shape.m >= 2) --p->working_chains;
+  p->live_edges -= hc.shape.m;
+  hc.live = false;
+  refresh_args(p);
+  return GESMC_OK;
+}
+
+int gesmc_pool_run(gesmc_pool_t p, uint64_t global_switches) {
+  if (!p) return GESMC_E_INVALID;
+  return pool_run(p, global_switches);
+}
+
+int gesmc_pool_edges(gesmc_pool_t p, uint32_t chain, uint64_t *out, uint64_t capacity, int out_on_device,
+                     uint64_t *m_out) {
+  if (!p || chain >= p->max_chains || !p->chains[chain].live) return GESMC_E_INVALID;
+  const uint64_t m = p->chains[chain].shape.m;
+  if (m_out) *m_out = m;
+  if (capacity < m) return GESMC_E_CAPACITY;
+  if (m == 0) return GESMC_OK;
+  if (!out) return GESMC_E_INVALID;
+  DeviceGuard g(p->device);
+  // the list is kept in the last round's slot order: write it by position
+  unsigned long long *E = out_on_device ? reinterpret_cast<unsigned long long *>(out)
+                                        : at<unsigned long long>(p->base, p->lay.E);
+  bool ok = launch_store_chain(p->args, p->chains[chain].d, E, p->stream, p->num_sms) == cudaSuccess;
+  if (ok && !out_on_device) ok = cudaMemcpyAsync(out, E, 8 * m, cudaMemcpyDeviceToHost, p->stream) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(p->stream) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  return GESMC_OK;
+}
+
+int gesmc_pool_chain_info(gesmc_pool_t p, uint32_t chain, gesmc_chain_info_t *out) {
+  if (!p || !out || chain >= p->max_chains || !p->chains[chain].live) return GESMC_E_INVALID;
+  DeviceGuard g(p->device);
+  const HostChain &hc = p->chains[chain];
+  unsigned long long acc = 0;
+  if (cudaMemcpyAsync(&acc, p->args.chain_accepted + chain, 8, cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->m = hc.shape.m;
+  out->n = hc.n;
+  out->seed = hc.d.seed;
+  out->rounds = p->pool_round - hc.d.added;
+  out->next_round = hc.d.start_round + (p->pool_round - hc.d.join);
+  out->switches = out->rounds * hc.shape.L;
+  out->accepted = acc;
+  return GESMC_OK;
+}
+
+uint32_t gesmc_pool_num_chains(gesmc_pool_t p) { return p ? p->live_chains : 0; }
+
+uint64_t gesmc_pool_free_edges(gesmc_pool_t p) { return p ? p->max_edges - p->live_edges : 0; }
+
+int gesmc_pool_stats(gesmc_pool_t p, gesmc_stats_t *out) {
+  if (!p || !out) return GESMC_E_INVALID;
+  DeviceGuard g(p->device);
+  StatsDev st;
+  if (cudaMemcpyAsync(&st, p->args.st, sizeof(StatsDev), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->rounds = p->rounds;
+  out->switches = p->switches_run;
+  out->lazy = st.lazy;
+  out->accepted = st.accepted;
+  out->rejected_loop = st.rej_loop;
+  out->rejected_exists = st.rej_exists;
+  out->kernel_launches = p->launches;
+  out->perm_buckets = p->args.bucket_hw;
+  out->tuple_partitions = p->args.part_hw;
+  out->waves_total = st.waves_total;
+  out->waves_max = st.waves_max;
+  for (int w = 0; w < GESMC_WAVE_HIST && w < kWaveHist; ++w) {
+    out->wave_hist[w] = st.wave_hist[w];
+    out->last_round_pending[w] = st.last_pending[w];
+  }
+  return GESMC_OK;
+}
+
+int gesmc_pool_reset_stats(gesmc_pool_t p) {
+  if (!p) return GESMC_E_INVALID;
+  DeviceGuard g(p->device);
+  if (cudaMemsetAsync(p->args.st, 0, sizeof(StatsDev), p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  p->rounds = 0;
+  p->switches_run = 0;
+  p->launches = 0;
+  for (double &x : p->stage_ms) x = 0.0;
+  p->stage_rounds = 0;
+  return GESMC_OK;
+}
+
+int gesmc_pool_set_profiling(gesmc_pool_t p, int enable) {
+  if (!p) return GESMC_E_INVALID;
+  p->profiling = enable ? 1 : 0;
+  return GESMC_OK;
+}
+
+int gesmc_pool_stage_times(gesmc_pool_t p, double *ms, int n_stages, uint64_t *rounds) {
+  if (!p || (n_stages > 0 && !ms)) return GESMC_E_INVALID;
+  for (int st = 0; st < n_stages; ++st) ms[st] = st < kNumStages ? p->stage_ms[st] : 0.0;
+  if (rounds) *rounds = p->stage_rounds;
+  return GESMC_OK;
+}
+
+// ---------------------------------------------------------------- single chain
 
 void gesmc_opts_default(gesmc_opts *o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
 }
 
-size_t gesmc_device_bytes(uint64_t m) {
-  Plan p;
-  if (!make_plan(m, &p)) return 0;
-  return p.total;
-}
+size_t gesmc_device_bytes(uint64_t m) { return gesmc_pool_device_bytes(m, 1, 0); }
 
 const char *gesmc_strerror(int code) {
   switch (code) {
@@ -252,11 +774,11 @@ const char *gesmc_strerror(int code) {
     case GESMC_E_LOOP: return "edge list contains a loop";
     case GESMC_E_MULTI: return "edge list contains a repeated edge";
     case GESMC_E_RANGE: return "node id out of range";
-    case GESMC_E_NOMEM: return "device allocation failed";
+    case GESMC_E_NOMEM: return "device allocation failed, or the pool has no room";
     case GESMC_E_CUDA: return "CUDA runtime error";
     case GESMC_E_TABLE_FULL: return "dependency table full";
     case GESMC_E_WAVE_CAP: return "wave cap exceeded";
-    case GESMC_E_INTERNAL: return "internal error (permutation bucket overflow)";
+    case GESMC_E_INTERNAL: return "internal error (bucket overflow or stalled waves)";
     case GESMC_E_CAPACITY: return "output buffer too small";
     case GESMC_E_TOO_LARGE: return "edge list larger than the no-alloc scratch allows (GESMC_NOALLOC_MAX_EDGES)";
     default: return "unknown error";
@@ -265,14 +787,7 @@ const char *gesmc_strerror(int code) {
 
 void gesmc_destroy(gesmc_t h) {
   if (!h) return;
-  {
-    DeviceGuard g(h->device);
-    if (h->base) {
-      cudaStreamSynchronize(h->stream);
-      dev_free(h, h->base);
-    }
-    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
-  }
+  gesmc_pool_destroy(h->pool);
   delete h;
 }
 
@@ -282,54 +797,24 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   gesmc_opts o;
   gesmc_opts_default(&o);
   if (opts) o = *opts;
-  if (m > kMaxEdges || (m > 0 && !edges)) return GESMC_E_INVALID;
-  if (o.n > (1ull << 32)) return GESMC_E_INVALID;
-  if ((o.alloc == nullptr) != (o.free == nullptr)) return GESMC_E_INVALID;
-
+  if (m > kMaxEdges || (m > 0 && !edges) || o.n > (1ull << 32)) return GESMC_E_INVALID;
+  gesmc_pool_opts po;
+  gesmc_pool_opts_default(&po);
+  po.max_edges = m;
+  po.max_chains = 1;
+  po.max_waves = o.max_waves;
+  po.tuple_log2 = o.tuple_log2;
+  po.group_log2 = o.group_log2;
+  po.stream = o.stream;
+  po.alloc = o.alloc;
+  po.free = o.free;
+  po.alloc_ctx = o.alloc_ctx;
   gesmc_ctx *h = new (std::nothrow) gesmc_ctx();
   if (!h) return GESMC_E_NOMEM;
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
-    delete h;
-    return GESMC_E_CUDA;
-  }
-  cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-  if (h->num_sms < 1) h->num_sms = 1;
-  h->stream = (cudaStream_t)o.stream;
-  h->alloc = o.alloc;
-  h->free_fn = o.free;
-  h->alloc_ctx = o.alloc_ctx;
-  h->next_round = o.start_round;
-  h->lazy_threshold = o.lazy_threshold;
-  h->max_waves = o.max_waves;
-  if (!make_plan(m, &h->plan, o.tuple_log2, o.group_log2)) {
-    delete h;
-    return GESMC_E_INVALID;
-  }
-  uint32_t group_grid = 0;
-  if (prepare_kernels(h->plan.group_log2, h->num_sms, &group_grid) != cudaSuccess) {
-    cudaGetLastError();
-    delete h;
-    return GESMC_E_CUDA;
-  }
-  const Plan &p = h->plan;
-  h->base = dev_alloc(h, p.total);
-  if (!h->base) {
-    delete h;
-    return GESMC_E_NOMEM;
-  }
-  h->args = args_for(p, h->base);
-  h->args.group_grid = group_grid;
-  h->args.lazy_threshold = o.lazy_threshold;
-  h->args.max_waves = o.max_waves;
-  unsigned long long *E = at<unsigned long long>(h->base, p.off_E);
-  int rc = GESMC_OK;
-  if (m > 0 && cudaMemcpyAsync(E, edges, 8 * m, edges_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                               h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    rc = GESMC_E_CUDA;
-  }
+  int rc = gesmc_pool_create(&po, &h->pool);
+  // the seed is given to gesmc_run; the chain starts with seed 0
   if (rc == GESMC_OK)
-    rc = validate_and_load(h->args, E, m, o.n, at<uint32_t>(h->base, p.off_scratch), h->stream, h->num_sms, &h->n);
+    rc = gesmc_pool_add(h->pool, edges, m, edges_on_device, o.n, 0, o.start_round, o.lazy_threshold, &h->chain);
   if (rc != GESMC_OK) {
     gesmc_destroy(h);
     return rc;
@@ -340,136 +825,36 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
 
 int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed) {
   if (!h) return GESMC_E_INVALID;
-  if (h->broken) return h->broken;
-  DeviceGuard g(h->device);
-  cudaStream_t s = h->stream;
-  RoundArgs a = h->args;
-  a.seed = seed;
-  if (cudaMemsetAsync(&a.ctl->err, 0, sizeof(uint32_t), s) != cudaSuccess) return GESMC_E_CUDA;
-  const size_t per_round = kNumStages + 1;
-  if (h->profiling) {
-    const size_t need = per_round * (size_t)global_switches;
-    while (h->events.size() < need) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) {
-        cudaGetLastError();
-        return GESMC_E_CUDA;
-      }
-      h->events.push_back(e);
-    }
-  }
-  uint32_t launches = 0;
-  for (uint64_t r = 0; r < global_switches; ++r) {
-    a.round = h->next_round + r;
-    cudaEvent_t *ev = h->profiling ? &h->events[per_round * r] : nullptr;
-    if (launch_round(a, s, h->num_sms, ev, &launches) != cudaSuccess) {
-      h->broken = GESMC_E_CUDA;
+  gesmc_pool_t p = h->pool;
+  if (p->broken) return p->broken;
+  HostChain &hc = p->chains[h->chain];
+  if (seed != hc.d.seed) {
+    // a new seed continues the chain's round numbering
+    DeviceGuard g(p->device);
+    hc.d.start_round += p->pool_round - hc.d.join;
+    hc.d.join = p->pool_round;
+    hc.d.seed = seed;
+    if (cudaMemcpyAsync(const_cast<ChainDesc *>(p->args.chains) + h->chain, &hc.d, sizeof(ChainDesc),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess) {
+      cudaGetLastError();
       return GESMC_E_CUDA;
     }
-    a.apply = 1;  // status[] now holds this round's decisions
-    h->args.apply = 1;
   }
-  Counters ctl;
-  if (cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    h->broken = GESMC_E_CUDA;
-    return GESMC_E_CUDA;
-  }
-  if (h->profiling) {
-    for (uint64_t r = 0; r < global_switches; ++r) {
-      for (int st = 0; st < kNumStages; ++st) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, h->events[per_round * r + st], h->events[per_round * r + st + 1]) ==
-            cudaSuccess)
-          h->stage_ms[st] += ms;
-      }
-    }
-    h->stage_rounds += global_switches;
-  }
-  h->next_round += global_switches;
-  h->rounds += global_switches;
-  h->launches += launches;
-  const int rc = map_device_errors(ctl.err);
-  if (rc != GESMC_OK) h->broken = rc;
-  return rc;
+  return pool_run(p, global_switches);
 }
 
 int gesmc_edges(gesmc_t h, uint64_t *out, uint64_t capacity, int out_on_device, uint64_t *m_out) {
   if (!h) return GESMC_E_INVALID;
-  if (m_out) *m_out = h->plan.m;
-  if (capacity < h->plan.m) return GESMC_E_CAPACITY;
-  if (h->plan.m == 0) return GESMC_OK;
-  if (!out) return GESMC_E_INVALID;
-  DeviceGuard g(h->device);
-  // the list is kept in the last round's slot order: write it by position
-  unsigned long long *E = out_on_device ? reinterpret_cast<unsigned long long *>(out)
-                                        : at<unsigned long long>(h->base, h->plan.off_E);
-  bool ok = launch_store_state(h->args, E, h->stream, h->num_sms) == cudaSuccess;
-  if (ok && !out_on_device)
-    ok = cudaMemcpyAsync(out, E, 8 * h->plan.m, cudaMemcpyDeviceToHost, h->stream) == cudaSuccess;
-  ok = ok && cudaStreamSynchronize(h->stream) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return GESMC_E_CUDA;
-  }
-  return GESMC_OK;
+  return gesmc_pool_edges(h->pool, h->chain, out, capacity, out_on_device, m_out);
 }
 
-int gesmc_stats(gesmc_t h, gesmc_stats_t *out) {
-  if (!h || !out) return GESMC_E_INVALID;
-  DeviceGuard g(h->device);
-  StatsDev st;
-  if (cudaMemcpyAsync(&st, h->args.st, sizeof(StatsDev), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return GESMC_E_CUDA;
-  }
-  std::memset(out, 0, sizeof(*out));
-  out->rounds = h->rounds;
-  out->switches = h->rounds * (uint64_t)h->plan.L;
-  out->lazy = st.lazy;
-  out->accepted = st.accepted;
-  out->rejected_loop = st.rej_loop;
-  out->rejected_exists = st.rej_exists;
-  out->kernel_launches = h->launches;
-  out->perm_buckets = h->plan.nb;
-  out->tuple_partitions = h->plan.np;
-  out->waves_total = st.waves_total;
-  out->waves_max = st.waves_max;
-  for (int w = 0; w < GESMC_WAVE_HIST && w < kWaveHist; ++w) {
-    out->wave_hist[w] = st.wave_hist[w];
-    out->last_round_pending[w] = st.last_pending[w];
-  }
-  return GESMC_OK;
-}
-
-int gesmc_reset_stats(gesmc_t h) {
-  if (!h) return GESMC_E_INVALID;
-  DeviceGuard g(h->device);
-  if (cudaMemsetAsync(h->args.st, 0, sizeof(StatsDev), h->stream) != cudaSuccess ||
-      cudaStreamSynchronize(h->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return GESMC_E_CUDA;
-  }
-  h->rounds = 0;
-  h->launches = 0;
-  for (double &x : h->stage_ms) x = 0.0;
-  h->stage_rounds = 0;
-  return GESMC_OK;
-}
-
+int gesmc_stats(gesmc_t h, gesmc_stats_t *out) { return h ? gesmc_pool_stats(h->pool, out) : GESMC_E_INVALID; }
+int gesmc_reset_stats(gesmc_t h) { return h ? gesmc_pool_reset_stats(h->pool) : GESMC_E_INVALID; }
 int gesmc_set_profiling(gesmc_t h, int enable) {
-  if (!h) return GESMC_E_INVALID;
-  h->profiling = enable ? 1 : 0;
-  return GESMC_OK;
+  return h ? gesmc_pool_set_profiling(h->pool, enable) : GESMC_E_INVALID;
 }
-
 int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
-  if (!h || (n_stages > 0 && !ms)) return GESMC_E_INVALID;
-  for (int st = 0; st < n_stages; ++st) ms[st] = st < kNumStages ? h->stage_ms[st] : 0.0;
-  if (rounds) *rounds = h->stage_rounds;
-  return GESMC_OK;
+  return h ? gesmc_pool_stage_times(h->pool, ms, n_stages, rounds) : GESMC_E_INVALID;
 }
 
 const char *gesmc_stage_name(int stage) {
@@ -478,9 +863,13 @@ const char *gesmc_stage_name(int stage) {
   return (stage >= 0 && stage < kNumStages) ? names[stage] : "";
 }
 
-uint64_t gesmc_next_round(gesmc_t h) { return h ? h->next_round : 0; }
-uint64_t gesmc_num_edges(gesmc_t h) { return h ? h->plan.m : 0; }
-uint64_t gesmc_num_nodes(gesmc_t h) { return h ? h->n : 0; }
+uint64_t gesmc_next_round(gesmc_t h) {
+  if (!h) return 0;
+  const HostChain &hc = h->pool->chains[h->chain];
+  return hc.d.start_round + (h->pool->pool_round - hc.d.join);
+}
+uint64_t gesmc_num_edges(gesmc_t h) { return h ? h->pool->chains[h->chain].shape.m : 0; }
+uint64_t gesmc_num_nodes(gesmc_t h) { return h ? h->pool->chains[h->chain].n : 0; }
 
 }  // extern "C"
 
@@ -518,48 +907,38 @@ extern "C" int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64
                                  uint64_t start_round, void *stream) {
   if (m > GESMC_NOALLOC_MAX_EDGES) return GESMC_E_TOO_LARGE;
   if ((m > 0 && !edges) || n > (1ull << 32)) return GESMC_E_INVALID;
-  int dev = 0, sms = 1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  gesmc_pool_ctx p;  // host bookkeeping only; the device state lives in the scratch array
+  if (cudaGetDevice(&p.device) != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms < 1) sms = 1;
-  void *base = nullptr;
-  int rc = noalloc_scratch(dev, &base);
+  cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device);
+  if (p.num_sms < 1) p.num_sms = 1;
+  int rc = noalloc_scratch(p.device, &p.base);
   if (rc != GESMC_OK) return rc;
-  Plan p;
-  if (!make_plan(m, &p) || p.total > GESMC_NOALLOC_SCRATCH_BYTES) return GESMC_E_INTERNAL;
-  uint32_t group_grid = 0;
-  if (prepare_kernels(p.group_log2, sms, &group_grid) != cudaSuccess) {
+  p.owns_memory = false;
+  p.stream = (cudaStream_t)stream;
+  p.max_edges = GESMC_NOALLOC_MAX_EDGES;
+  p.max_chains = 1;
+  p.tuple_log2 = kDefaultTupleLog2;
+  p.cap = pool_capacity(p.max_edges, 1, p.tuple_log2);
+  p.lay = pool_layout(p.cap, p.max_edges, 1);
+  if (p.lay.total > GESMC_NOALLOC_SCRATCH_BYTES) return GESMC_E_INTERNAL;
+  gesmc_pool_opts o;
+  gesmc_pool_opts_default(&o);
+  // the array keeps the previous call's contents: pool_init resets the owner
+  // maps and counters, and adding the chain rebuilds all of its state
+  rc = pool_init(&p, o);
+  uint32_t chain = 0;
+  if (rc == GESMC_OK)
+    rc = pool_add_device(&p, reinterpret_cast<unsigned long long *>(edges), m, n, seed, start_round, 0, &chain);
+  if (rc == GESMC_OK) rc = pool_run(&p, global_switches);
+  if (rc == GESMC_OK &&
+      (launch_store_chain(p.args, p.chains[chain].d, reinterpret_cast<unsigned long long *>(edges), p.stream,
+                          p.num_sms) != cudaSuccess ||
+       cudaStreamSynchronize(p.stream) != cudaSuccess)) {
     cudaGetLastError();
-    return GESMC_E_CUDA;
+    rc = GESMC_E_CUDA;
   }
-
-  cudaStream_t s = (cudaStream_t)stream;
-  RoundArgs a = args_for(p, base);
-  a.group_grid = group_grid;
-  a.seed = seed;
-  unsigned long long *E = reinterpret_cast<unsigned long long *>(edges);  // in place on the caller's list
-  uint64_t n_eff = 0;
-  // the array keeps the previous call's contents: validate_and_load zeroes
-  // the counters and rebuilds all state from the caller's list
-  rc = validate_and_load(a, E, m, n, at<uint32_t>(base, p.off_scratch), s, sms, &n_eff);
-  if (rc != GESMC_OK) return rc;
-  for (uint64_t r = 0; r < global_switches; ++r) {
-    a.round = start_round + r;
-    if (launch_round(a, s, sms, nullptr, nullptr) != cudaSuccess) {
-      cudaGetLastError();
-      return GESMC_E_CUDA;
-    }
-    a.apply = 1;
-  }
-  Counters ctl;
-  if (launch_store_state(a, E, s, sms) != cudaSuccess ||
-      cudaMemcpyAsync(&ctl, a.ctl, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    return GESMC_E_CUDA;
-  }
-  return map_device_errors(ctl.err);
+  return rc;
 }

@@ -1,25 +1,36 @@
 // Internal declarations shared by the CUDA translation units of libgesmc.
 //
-// Device state of one chain, for m edges and L = floor(m/2) switches a round.
-// The list E is kept in the slot order of the last round, as (position,
-// edge) pairs: cpos[s], cedge[s] hold the position and the edge that slot s
-// of the last round's permutation had when that round started; status[k]
-// says whether switch k (slots 2k, 2k+1) was legal.  The rewiring of a legal
-// switch (Def. 1, E[i] <- e3, E[j] <- e4) is applied on the fly by the next
-// pass that reads the pair, so no round writes E at random positions.
+// A pool holds any number of independent chains (G-ES-MC runs on their own
+// graphs, seeds and round counters).  Each chain owns contiguous ranges of
+// five index spaces: slots (one per edge), switches (one per pair of slots),
+// permutation buckets, tuple partitions and tuple storage.  Small owner
+// arrays map an index back to its chain (kNoChain for an unused index).
+// Every round runs the same kernels over all chains at once; a chain's
+// randomness, buckets and partitions are its own, so its result does not
+// depend on the other chains.
 //
-//   cpos/cedge   u32[m] / u64[m]   list in last-round slot order (see above)
-//   prec         uint4[nb * cap]   permutation buckets: {32 key bits,
-//                                  position, edge lo, edge hi}
-//   word         u32[L]            per switch: outright-reject code | flags
-//   sw           uint2[L]          per switch: dependency entry of e3, e4
-//   status       u32[L]            (wave << 2) | state of each switch
-//   ptup         uint4[np * capt]  Algorithm 1's tuples (four per switch),
-//                                  appended to fixed-capacity hash partitions
-//   otup/stup    uint4[4L+1]       tuples beyond a partition's capacity, and
-//                                  the same grouped by partition (rare)
-//   dep          uint2[2L+1]       {p, q} of every edge id with a dependency
-//   E            u64[m]            position-order copy (input / output only)
+// Per chain, the edge list is kept in the slot order of its last round, as
+// (position, edge) pairs: cpos[s], cedge[s] hold the position and the edge
+// that slot s had when that round started; status[k] says whether switch k
+// (slots 2k, 2k+1 of the chain) was legal.  The rewiring of a legal switch
+// (Def. 1, E[i] <- e3, E[j] <- e4) is applied on the fly by the next pass
+// that reads the pair, so no round writes edges at random positions.
+//
+//   cpos/cedge   u32 / u64 [slots]        list in last-round slot order
+//   prec         uint4[buckets * cap]     permutation bucket records:
+//                                         {32 key bits, position, edge lo, hi}
+//   word         u32[switches]            outright-reject code | flags
+//   sw           uint2[switches]          dependency entries of e3, e4
+//   status       u32[switches]            (wave << 2) | state
+//   ptup         uint4[tuple storage]     Algorithm 1's tuples (four per
+//                                         switch) in fixed-capacity hash
+//                                         partitions: {id lo, id hi, value,
+//                                         partition}
+//   otup/stup    uint4[overflow cap]      tuples beyond a partition's
+//                                         capacity, and the same grouped by
+//                                         partition (rare)
+//   dep          uint2[dep cap]           {p, q} of every edge id with a
+//                                         dependency
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,10 +39,12 @@
 namespace gesmc {
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // would be the loop {2^32-1, 2^32-1}: never an edge
+constexpr uint32_t kNoChain = 0xFFFFFFFFu;
 
 // Tuple value (Algorithm 1's (e, k, type)): bit 31 = the edge is a source
 // (ERASE) of switch k, else a target (INSERT); bit 30 = which target (e3: 0,
-// e4: 1); bits 29..0 = k, or kKeepK for a source that no switch erases.
+// e4: 1); bits 29..0 = k (pool-wide switch index), or kKeepK for a source
+// that no switch erases.
 constexpr uint32_t kTupleSource = 0x80000000u;
 constexpr uint32_t kTupleWhich = 0x40000000u;
 constexpr uint32_t kTupleK = 0x3FFFFFFFu;
@@ -42,7 +55,9 @@ constexpr uint32_t kKeepK = 0x3FFFFFFFu;
 //      round but no switch erases it, kPNone if it is not in E then;
 //   q  smallest switch that inserts it and is not known to be illegal,
 //      kQNone if none is left.
-// Obs. 2 makes p unique per edge id, so one field suffices.
+// Obs. 2 makes p unique per edge id, so one field suffices.  Switch indices
+// of one chain are contiguous and in the chain's own order, so comparing
+// pool-wide indices compares positions in the chain's global switch.
 constexpr uint32_t kPNone = 0xFFFFFFFFu;
 constexpr uint32_t kPKeep = 0xFFFFFFFEu;
 constexpr uint32_t kQNone = 0xFFFFFFFFu;
@@ -62,25 +77,24 @@ constexpr uint32_t kErrTableFull = 1u, kErrBucket = 2u, kErrWaveCap = 4u, kErrNo
                    kErrGroup = 32u;
 
 // Wave cap used when the caller passes max_waves = 0.  Every wave decides at
-// least the smallest undecided switch, so a round needs at most L + 1 waves;
-// rounds observed in practice need a handful.  The cap bounds the time a
-// faulty input or build can spend in one round.
+// least the smallest undecided switch of some chain, so a round needs at
+// most (largest L) + 1 waves; rounds observed in practice need a handful.
+// The cap bounds the time a faulty input or build can spend in one round.
 constexpr uint32_t kDefaultWaveCap = 10000;
 
-// Permutation buckets: positions go to 2^B buckets by the top B bits of
-// their key (about 2^kPermAvgLog2 per bucket, at most kPermBucketCap), and
-// each bucket is sorted in shared memory by one CTA.
+// Permutation buckets: a chain's positions go to 2^B buckets by the top B
+// bits of their key (about 2^kPermAvgLog2 per bucket, at most
+// kPermBucketCap), and each bucket is sorted in shared memory by one CTA.
 constexpr int kSortThreads = 256;
 constexpr int kPermBucketCap = 2048;
 constexpr int kPermAvgLog2 = 10;
 constexpr int kPerThread = kPermBucketCap / kSortThreads;
 constexpr int kSubBits = 11;
 
-// Tuple partitions: 2^P partitions by the top P bits of the hash of the
-// edge id (about 2^tuple_log2 tuples each, room for twice that); one CTA
-// groups a partition by edge id in a shared-memory table of 2^group_log2
-// slots (22 bytes each, with the used-slot list).  A tuple is {edge id lo,
-// edge id hi, value, 0}.
+// Tuple partitions: a chain's tuples go to 2^P partitions by the top P bits
+// of the hash of the edge id (about 2^tuple_log2 tuples each, room for
+// twice that); one CTA groups a partition by edge id in a shared-memory
+// table of 2^group_log2 slots (22 bytes each, with the used-slot list).
 constexpr int kDefaultTupleLog2 = 10;
 constexpr int kDefaultGroupLog2 = 11;
 constexpr int kMaxGroupLog2 = 13;
@@ -88,6 +102,19 @@ constexpr int kGroupThreads = 256;
 constexpr int kGroupSlotBytes = 22;
 
 constexpr int kWaveHist = 64;
+
+// One chain of the pool.  Its round number in pool round R (R rounds
+// completed) is start_round + (R - join); its last round's decisions are
+// pending in status[] once R > added, the pool round at which the chain was
+// added.  (join and start_round move together when the seed changes.)
+struct ChainDesc {
+  uint32_t slot_base, m;      // slots [slot_base, slot_base + m); slot_base even
+  uint32_t switch_base, L;    // switches [switch_base, switch_base + L), L = floor(m/2)
+  uint32_t bucket_base, B;    // 2^B permutation buckets from bucket_base
+  uint32_t part_base, P;      // 2^P tuple partitions from part_base
+  uint32_t tuple_base, capt;  // partition j of the chain holds capt tuples from tuple_base + j * capt
+  unsigned long long seed, start_round, join, added, lazy_threshold;
+};
 
 // Device-resident counters of the round in flight.
 struct Counters {
@@ -98,9 +125,10 @@ struct Counters {
   uint32_t dep_count;   // dependency entries allocated this round
   uint32_t ovf_count;   // tuples that did not fit their partition
   uint32_t pad;
+  unsigned long long pool_round;  // rounds the pool has completed
 };
 
-// Device-resident statistics, accumulated over rounds.
+// Device-resident statistics, accumulated over rounds (all chains).
 struct StatsDev {
   unsigned long long lazy, accepted, rej_loop, rej_exists;
   unsigned long long waves_total, waves_max;
@@ -108,13 +136,17 @@ struct StatsDev {
   unsigned long long last_pending[kWaveHist];
 };
 
-// Everything a round kernel needs; passed by value.
+// Everything a round kernel needs; passed by value.  The *_hw fields are
+// high-water marks of the index spaces (kernels visit [0, hw)).
 struct RoundArgs {
+  const ChainDesc *chains;
+  const uint32_t *owner_slot, *owner_switch, *owner_bucket, *owner_part;
+  unsigned long long *chain_accepted;  // per chain
   uint32_t *cpos;
   unsigned long long *cedge;
   uint4 *prec;
-  uint32_t *pcount;  // nb: records per permutation bucket
-  uint32_t *poff;    // nb + 1: slot offset of each bucket
+  uint32_t *pcount;  // per bucket: records appended
+  uint32_t *poff;    // per bucket + 1: exclusive scan of pcount
   uint32_t *pib_pos;
   unsigned long long *pib_edge;
   uint32_t *bnd;
@@ -123,25 +155,25 @@ struct RoundArgs {
   uint32_t *status;
   uint32_t *list0;
   uint32_t *list1;
-  uint4 *ptup;        // np * capt
-  uint4 *otup;        // 4L + 1
-  uint4 *stup;        // 4L + 1
-  uint32_t *tcount;   // np: tuples appended per partition (may exceed capt)
-  uint32_t *ocount;   // np: overflow tuples per partition
-  uint32_t *ooff;     // np + 1
-  uint32_t *ocursor;  // np
+  uint4 *ptup;
+  uint4 *otup;
+  uint4 *stup;
+  uint32_t *tcount;   // per partition: tuples appended (may exceed capt)
+  uint32_t *ocount;   // per partition: overflow tuples
+  uint32_t *ooff;     // per partition + 1
+  uint32_t *ocursor;  // per partition
   uint2 *dep;
   Counters *ctl;
   StatsDev *st;
-  unsigned long long seed, round, lazy_threshold;
-  uint32_t m, L, B, nb, P, np, max_waves;
+  uint32_t slot_hw, switch_hw, bucket_hw, part_hw;
+  uint32_t ovf_cap, dep_cap;
+  uint32_t max_waves;
   uint32_t group_log2;  // shared-memory grouping table: 2^group_log2 slots
-  uint32_t capt;        // tuple capacity of a partition
   uint32_t group_grid;  // CTAs of the persistent grouping kernel
-  uint32_t apply;  // 1 if status[] holds the last round's decisions (apply them when reading)
+  uint32_t any_work;    // some chain has m >= 2
 };
 
-// Stages of a round, in launch order (one kernel each).
+// Stages of a round, in launch order.
 enum Stage {
   kStageClear = 0,
   kStagePermute,
@@ -155,21 +187,23 @@ enum Stage {
   kNumStages
 };
 
-// Dynamic shared memory of the grouping kernel, and the one-time opt-in to
-// more than 48 KB of it (call before the first round on a device).
-// prepare_kernels also returns the persistent grouping grid for this table
+// Dynamic shared memory of the grouping kernel; prepare_kernels opts in to
+// the largest table once and returns the persistent grid for this table
 // size (CTAs that fit on the device at once).
 size_t group_smem_bytes(uint32_t group_log2);
 cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_grid);
 
-// Host-side launchers (round.cu).  launch_round records kNumStages + 1
-// events into ev (if not null) around the stages and adds the number of
-// kernels it launched to *launches (if not null).
+// One pool round.  ev (optional) receives kNumStages + 1 events around the
+// stages; *launches (optional) counts the kernels launched.
 cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEvent_t *ev, uint32_t *launches);
-// Position-order list -> slot-order state (cpos[s] = s, cedge[s] = E[s]).
-cudaError_t launch_load_state(const RoundArgs &a, const unsigned long long *E, cudaStream_t s, int num_sms);
-// Slot-order state (with the last round's decisions applied) -> E by position.
-cudaError_t launch_store_state(const RoundArgs &a, unsigned long long *E, cudaStream_t s, int num_sms);
+// One chain (host copy of its descriptor): load a position-order list into
+// its slots, and write its current list by position.
+cudaError_t launch_load_chain(const RoundArgs &a, const ChainDesc &ch, const unsigned long long *E, cudaStream_t s,
+                              int num_sms);
+cudaError_t launch_store_chain(const RoundArgs &a, const ChainDesc &ch, unsigned long long *E, cudaStream_t s,
+                               int num_sms);
+// Fill n u32 words with v.
+cudaError_t launch_fill_u32(uint32_t *p, uint32_t n, uint32_t v, cudaStream_t s, int num_sms);
 cudaError_t launch_canonicalise(unsigned long long *E, uint32_t m, unsigned long long n_bound, uint32_t *flags,
                                 uint32_t *max_id, cudaStream_t s, int num_sms);
 // Repeated edges, with an open-addressing set of `cap` u64 slots as scratch.

@@ -1,6 +1,6 @@
-// One global switch round (Def. 2 of arXiv 2111.03005) on one GB300, laid
-// out as streaming passes so that no step needs a random DRAM access per
-// switch.
+// One global switch round (Def. 2 of arXiv 2111.03005) of every chain of a
+// pool, on one GB300, laid out as streaming passes so that no step needs a
+// random DRAM access per switch.
 //
 //   k_clear          zero the per-round counters
 //   k_permute        read the list in last-round slot order (applying the
@@ -81,11 +81,6 @@ __device__ __forceinline__ unsigned long long perm_key(unsigned long long seed, 
   return word_of(philox(i >> 2, round, 0, 0, seed, 0), i & 3);
 }
 
-__device__ __forceinline__ bool is_lazy(const RoundArgs &a, uint32_t k) {
-  if (a.lazy_threshold == 0) return false;
-  return word_of(philox(k >> 2, a.round, 1, 0, a.seed, 0), k & 3) < a.lazy_threshold;
-}
-
 __device__ __forceinline__ uint32_t bucket_of(unsigned long long key, uint32_t B) {
   return B ? (uint32_t)(key >> (64 - B)) : 0u;
 }
@@ -137,11 +132,29 @@ __device__ __forceinline__ uint32_t tau(uint32_t i, uint32_t j, unsigned long lo
   return 0;
 }
 
-// The values of slots 2k, 2k+1 at the start of this round: the last round's
-// switch k rewired them if it was legal.
-__device__ __forceinline__ void apply_last(const RoundArgs &a, uint32_t k, uint32_t i, uint32_t j,
-                                           unsigned long long &e1, unsigned long long &e2) {
-  if (a.apply && k < a.L && (__ldcs(&a.status[k]) & 3u) == kLegal) {
+
+// ---------------------------------------------------------------- chains
+// Round number of a chain in the current pool round, and whether status[]
+// holds decisions of the chain's last round that still have to be applied.
+__device__ __forceinline__ unsigned long long chain_round(const ChainDesc &ch, unsigned long long pool_round) {
+  return ch.start_round + (pool_round - ch.join);
+}
+__device__ __forceinline__ bool chain_apply(const ChainDesc &ch, unsigned long long pool_round) {
+  return pool_round > ch.added;
+}
+
+// Laziness (Def. 2, P_L): switch k (the chain's own index) is skipped iff
+// its Philox word (purpose 1) is below the chain's threshold.
+__device__ __forceinline__ bool is_lazy(const ChainDesc &ch, unsigned long long round, uint32_t k) {
+  if (ch.lazy_threshold == 0) return false;
+  return word_of(philox(k >> 2, round, 1, 0, ch.seed, 0), k & 3) < ch.lazy_threshold;
+}
+
+// The values of slots 2k, 2k+1 of a chain at the start of this round: the
+// chain's last-round switch k rewired them if it was legal.
+__device__ __forceinline__ void apply_last(const RoundArgs &a, const ChainDesc &ch, bool apply, uint32_t k,
+                                           uint32_t i, uint32_t j, unsigned long long &e1, unsigned long long &e2) {
+  if (apply && k < ch.L && (__ldcs(&a.status[ch.switch_base + k]) & 3u) == kLegal) {
     unsigned long long e3, e4;
     tau(i, j, e1, e2, e3, e4);
     e1 = e3;
@@ -154,49 +167,53 @@ __device__ __forceinline__ void apply_last(const RoundArgs &a, uint32_t k, uint3
 // first (independent, in flight together), then the 16-byte stores.  A
 // tuple that finds its partition full goes to the overflow list.
 template <int N>
-__device__ __forceinline__ void emit_tuples(const RoundArgs &a, const unsigned long long (&key)[N],
-                                            const uint32_t (&val)[N]) {
+__device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc &ch,
+                                            const unsigned long long (&key)[N], const uint32_t (&val)[N]) {
   uint32_t part[N], idx[N];
 #pragma unroll
   for (int t = 0; t < N; ++t) {
-    part[t] = partition_of(mix64(key[t]), a.P);
-    idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[part[t]], 1u) : 0u;
+    part[t] = partition_of(mix64(key[t]), ch.P);
+    idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[ch.part_base + part[t]], 1u) : 0u;
   }
 #pragma unroll
   for (int t = 0; t < N; ++t) {
     if (key[t] == kEmptyKey) continue;
-    const uint4 rec = make_uint4((uint32_t)key[t], (uint32_t)(key[t] >> 32), val[t], 0u);
-    if (idx[t] < a.capt) {
-      a.ptup[(size_t)part[t] * a.capt + idx[t]] = rec;
+    const uint4 rec = make_uint4((uint32_t)key[t], (uint32_t)(key[t] >> 32), val[t], ch.part_base + part[t]);
+    if (idx[t] < ch.capt) {
+      a.ptup[ch.tuple_base + (size_t)part[t] * ch.capt + idx[t]] = rec;
     } else {
       const uint32_t o = atomicAdd(&a.ctl->ovf_count, 1u);
-      if (o <= 4 * a.L) a.otup[o] = rec;  // at most 4L + 1 tuples exist
+      if (o < a.ovf_cap) a.otup[o] = rec;
+      else atomicOr(&a.ctl->err, kErrRecord);
     }
   }
 }
 
-// Switch k = (i, j, g) of this round with sources e1, e2: record its reject
-// code and Algorithm 1's four tuples (e1, k, ERASE), (e2, k, ERASE),
-// (e3, k, INSERT), (e4, k, INSERT).  A switch rejected outright stores its
-// sources as never erased and no targets.
-__device__ __forceinline__ void build_switch(const RoundArgs &a, uint32_t k, uint32_t i, unsigned long long e1,
-                                             uint32_t j, unsigned long long e2) {
+// Switch k (the chain's own index) = (i, j, g) with sources e1, e2: record
+// its reject code and Algorithm 1's four tuples (e1, k, ERASE), (e2, k,
+// ERASE), (e3, k, INSERT), (e4, k, INSERT), with k made pool-wide.  A
+// switch rejected outright stores its sources as never erased and no
+// targets.
+__device__ __forceinline__ void build_switch(const RoundArgs &a, const ChainDesc &ch, unsigned long long round,
+                                             uint32_t k, uint32_t i, unsigned long long e1, uint32_t j,
+                                             unsigned long long e2) {
   unsigned long long e3 = kEmptyKey, e4 = kEmptyKey;
-  const uint32_t code = is_lazy(a, k) ? kCodeLazy : tau(i, j, e1, e2, e3, e4);
-  a.word[k] = code;
-  a.sw[k] = make_uint2(kTrivial, kTrivial);
-  const uint32_t src = kTupleSource | (code ? kKeepK : k);
+  const uint32_t code = is_lazy(ch, round, k) ? kCodeLazy : tau(i, j, e1, e2, e3, e4);
+  const uint32_t kg = ch.switch_base + k;
+  a.word[kg] = code;
+  a.sw[kg] = make_uint2(kTrivial, kTrivial);
+  const uint32_t src = kTupleSource | (code ? kKeepK : kg);
   if (code) e3 = e4 = kEmptyKey;
   const unsigned long long key[4] = {e1, e2, e3, e4};
-  const uint32_t val[4] = {src, src, k, k | kTupleWhich};
-  emit_tuples<4>(a, key, val);
+  const uint32_t val[4] = {src, src, kg, kg | kTupleWhich};
+  emit_tuples<4>(a, ch, key, val);
 }
 
 // The unpaired last position of an odd list: a source no switch erases.
-__device__ __forceinline__ void keep_source(const RoundArgs &a, unsigned long long e) {
+__device__ __forceinline__ void keep_source(const RoundArgs &a, const ChainDesc &ch, unsigned long long e) {
   const unsigned long long key[1] = {e};
   const uint32_t val[1] = {kTupleSource | kKeepK};
-  emit_tuples<1>(a, key, val);
+  emit_tuples<1>(a, ch, key, val);
 }
 
 // ---------------------------------------------------------------- decide
@@ -261,6 +278,32 @@ __device__ __forceinline__ void flush_tally(const RoundArgs &a, Tally t) {
   }
 }
 
+// Per-chain count of accepted switches: each thread keeps a running count
+// for the chain it last saw and hands it on when the chain changes; at the
+// end, lanes of a warp holding the same chain add once (all lanes call).
+struct ChainCount {
+  uint32_t chain = kNoChain, n = 0;
+};
+
+__device__ __forceinline__ void count_accepted(const RoundArgs &a, ChainCount &cc, uint32_t chain) {
+  if (chain != cc.chain) {
+    if (cc.n) atomicAdd(&a.chain_accepted[cc.chain], (unsigned long long)cc.n);
+    cc.chain = chain;
+    cc.n = 0;
+  }
+  ++cc.n;
+}
+
+__device__ __forceinline__ void flush_count(const RoundArgs &a, const ChainCount &cc) {
+  const unsigned same = __match_any_sync(0xffffffffu, cc.n ? cc.chain : kNoChain);
+  unsigned long long n = cc.n;
+  // sum n over the lanes of this group, result at its first lane
+  const int lane = threadIdx.x & 31;
+  unsigned long long total = 0;
+  for (unsigned rest = same; rest; rest &= rest - 1) total += __shfl_sync(same, n, __ffs(rest) - 1);
+  if (cc.n && (__ffs(same) - 1) == lane) atomicAdd(&a.chain_accepted[cc.chain], total);
+}
+
 // Warp-aggregated append of k to a list (all lanes of the warp must call).
 __device__ __forceinline__ void append_if(bool take, uint32_t k, uint32_t *list, uint32_t *count) {
   const unsigned mask = __ballot_sync(0xffffffffu, take);
@@ -277,8 +320,8 @@ __device__ __forceinline__ void append_if(bool take, uint32_t k, uint32_t *list,
 
 __global__ void k_clear(RoundArgs a) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-  for (uint32_t b = tid; b < a.nb; b += nth) a.pcount[b] = 0;
-  for (uint32_t p = tid; p < a.np; p += nth) {
+  for (uint32_t b = tid; b < a.bucket_hw; b += nth) a.pcount[b] = 0;
+  for (uint32_t p = tid; p < a.part_hw; p += nth) {
     a.tcount[p] = 0;
     a.ocount[p] = 0;
   }
@@ -292,38 +335,44 @@ __global__ void k_clear(RoundArgs a) {
   }
 }
 
-__device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uint32_t idx, unsigned long long K,
+__device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uint32_t idx, uint32_t keybits,
                                              uint32_t pos, unsigned long long e) {
   if (idx < (uint32_t)kPermBucketCap)
-    a.prec[(size_t)b * kPermBucketCap + idx] = make_uint4(mid_of(K, a.B), pos, (uint32_t)e, (uint32_t)(e >> 32));
+    a.prec[(size_t)b * kPermBucketCap + idx] = make_uint4(keybits, pos, (uint32_t)e, (uint32_t)(e >> 32));
   else
     atomicOr(&a.ctl->err, kErrBucket);
 }
 
-// Append every position, with its current edge, to its permutation bucket.
+// Append every position, with its current edge, to its chain's bucket.
 __global__ void k_permute(RoundArgs a) {
-  const uint32_t npair = (a.m + 1) >> 1;
+  const unsigned long long R = a.ctl->pool_round;
+  const uint32_t npair = (a.slot_hw + 1) >> 1;
   const uint32_t nth = gridDim.x * blockDim.x;
-  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < npair; k += nth) {
-    const uint32_t s0 = 2 * k;
-    if (s0 + 1 < a.m) {
-      const uint2 ij = __ldcs(reinterpret_cast<const uint2 *>(a.cpos) + k);
-      const ulonglong2 ee = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + k);
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += nth) {
+    const uint32_t s0 = 2 * x;
+    const uint32_t c = a.owner_slot[s0];
+    if (c == kNoChain) continue;
+    const ChainDesc ch = a.chains[c];
+    const unsigned long long round = chain_round(ch, R);
+    const uint32_t ls = s0 - ch.slot_base;
+    if (ls + 1 < ch.m) {
+      const uint2 ij = __ldcs(reinterpret_cast<const uint2 *>(a.cpos) + x);
+      const ulonglong2 ee = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
       unsigned long long e1 = ee.x, e2 = ee.y;
-      apply_last(a, k, ij.x, ij.y, e1, e2);
+      apply_last(a, ch, chain_apply(ch, R), ls >> 1, ij.x, ij.y, e1, e2);
       // both keys and both atomics before the two stores
-      const unsigned long long K1 = perm_key(a.seed, a.round, ij.x);
-      const unsigned long long K2 = perm_key(a.seed, a.round, ij.y);
-      const uint32_t b1 = bucket_of(K1, a.B), b2 = bucket_of(K2, a.B);
+      const unsigned long long K1 = perm_key(ch.seed, round, ij.x);
+      const unsigned long long K2 = perm_key(ch.seed, round, ij.y);
+      const uint32_t b1 = ch.bucket_base + bucket_of(K1, ch.B), b2 = ch.bucket_base + bucket_of(K2, ch.B);
       const uint32_t x1 = atomicAdd(&a.pcount[b1], 1u);
       const uint32_t x2 = atomicAdd(&a.pcount[b2], 1u);
-      store_record(a, b1, x1, K1, ij.x, e1);
-      store_record(a, b2, x2, K2, ij.y, e2);
-    } else {  // odd m: the last slot has no partner
+      store_record(a, b1, x1, mid_of(K1, ch.B), ij.x, e1);
+      store_record(a, b2, x2, mid_of(K2, ch.B), ij.y, e2);
+    } else {  // odd m: the chain's last slot has no partner
       const uint32_t pos = a.cpos[s0];
-      const unsigned long long K = perm_key(a.seed, a.round, pos);
-      const uint32_t b = bucket_of(K, a.B);
-      store_record(a, b, atomicAdd(&a.pcount[b], 1u), K, pos, a.cedge[s0]);
+      const unsigned long long K = perm_key(ch.seed, round, pos);
+      const uint32_t b = ch.bucket_base + bucket_of(K, ch.B);
+      store_record(a, b, atomicAdd(&a.pcount[b], 1u), mid_of(K, ch.B), pos, a.cedge[s0]);
     }
   }
 }
@@ -356,31 +405,28 @@ __device__ __forceinline__ void cta_scan_1024(const uint32_t *count, uint32_t *o
 }
 
 __global__ void __launch_bounds__(1024) k_scan_perm(RoundArgs a) {
-  cta_scan_1024(a.pcount, a.poff, nullptr, a.nb, kPermBucketCap);
+  cta_scan_1024(a.pcount, a.poff, nullptr, a.bucket_hw, kPermBucketCap);
 }
 
 // Overflow tuples (those that found their partition full), grouped by
-// partition with exact counts.  All three kernels return at once when there
-// is no overflow, which is the normal case.
+// partition with exact counts.  All three kernels do nothing when there is
+// no overflow, which is the normal case.
 __global__ void k_overflow_count(RoundArgs a) {
-  const uint32_t n = min(a.ctl->ovf_count, 4 * a.L + 1);
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const uint4 r = a.otup[t];
-    atomicAdd(&a.ocount[partition_of(mix64(((unsigned long long)r.y << 32) | r.x), a.P)], 1u);
-  }
+  const uint32_t n = min(a.ctl->ovf_count, a.ovf_cap);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    atomicAdd(&a.ocount[a.otup[t].w], 1u);
 }
 
 __global__ void __launch_bounds__(1024) k_overflow_scan(RoundArgs a) {
   if (a.ctl->ovf_count == 0) return;
-  cta_scan_1024(a.ocount, a.ooff, a.ocursor, a.np, 0xFFFFFFFFu);
+  cta_scan_1024(a.ocount, a.ooff, a.ocursor, a.part_hw, 0xFFFFFFFFu);
 }
 
 __global__ void k_overflow_scatter(RoundArgs a) {
-  const uint32_t n = min(a.ctl->ovf_count, 4 * a.L + 1);
+  const uint32_t n = min(a.ctl->ovf_count, a.ovf_cap);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const uint4 r = a.otup[t];
-    const uint32_t part = partition_of(mix64(((unsigned long long)r.y << 32) | r.x), a.P);
-    const uint32_t dst = atomicAdd(&a.ocursor[part], 1u);
+    const uint32_t dst = atomicAdd(&a.ocursor[r.w], 1u);
     if (dst < n) a.stup[dst] = r;
   }
 }
@@ -423,8 +469,9 @@ __device__ __forceinline__ void cta_exclusive_scan(uint32_t *h, uint32_t *warp_t
   }
 }
 
-__device__ __forceinline__ bool full_key_less(const RoundArgs &a, uint32_t i, uint32_t j) {
-  const unsigned long long ki = perm_key(a.seed, a.round, i), kj = perm_key(a.seed, a.round, j);
+__device__ __forceinline__ bool full_key_less(unsigned long long seed, unsigned long long round, uint32_t i,
+                                              uint32_t j) {
+  const unsigned long long ki = perm_key(seed, round, i), kj = perm_key(seed, round, j);
   return ki < kj || (ki == kj && i < j);
 }
 
@@ -439,8 +486,14 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
   __shared__ uint32_t warp_tot[kSortThreads / 32];
   const int tid = threadIdx.x;
   constexpr int nsub = 1 << kSubBits;
-  for (uint32_t b = blockIdx.x; b < a.nb; b += gridDim.x) {
-    const uint32_t off = a.poff[b];
+  const unsigned long long R = a.ctl->pool_round;
+  for (uint32_t b = blockIdx.x; b < a.bucket_hw; b += gridDim.x) {
+    const uint32_t c = a.owner_bucket[b];
+    if (c == kNoChain) continue;
+    const ChainDesc ch = a.chains[c];
+    const unsigned long long round = chain_round(ch, R);
+    const uint32_t loff = a.poff[b] - a.poff[ch.bucket_base];  // chain-local slot offset
+    const uint32_t goff = ch.slot_base + loff;
     const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
     const uint4 *rec = a.prec + (size_t)b * kPermBucketCap;
     for (int s = tid; s < nsub; s += kSortThreads) hist[s] = 0;
@@ -498,7 +551,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
           const unsigned long long val = scomp[x];
           const uint16_t li = slidx[x];
           uint32_t y = x;
-          while (y > t && full_key_less(a, (uint32_t)val, (uint32_t)scomp[y - 1])) {
+          while (y > t && full_key_less(ch.seed, round, (uint32_t)val, (uint32_t)scomp[y - 1])) {
             scomp[y] = scomp[y - 1];
             slidx[y] = slidx[y - 1];
             --y;
@@ -509,35 +562,36 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
       }
     }
     __syncthreads();
-    // slots off .. off+cnt-1 hold pi in order: write the list in slot order
+    // slots of the bucket hold pi in order: write the list in slot order
     for (uint32_t t = tid; t < cnt; t += kSortThreads) {
       const uint2 eh = *reinterpret_cast<const uint2 *>(&rec[slidx[t]].z);  // edge lo, hi
       const unsigned long long e = ((unsigned long long)eh.y << 32) | eh.x;
       sedge[t] = e;
-      a.cpos[off + t] = (uint32_t)scomp[t];
-      a.cedge[off + t] = e;
+      a.cpos[goff + t] = (uint32_t)scomp[t];
+      a.cedge[goff + t] = e;
     }
     __syncthreads();
-    const uint32_t t0 = off & 1u;
+    const uint32_t t0 = loff & 1u;
     const uint32_t npairs = cnt > t0 ? (cnt - t0) >> 1 : 0;
     for (uint32_t p = tid; p < npairs; p += kSortThreads) {
       const uint32_t t = t0 + 2 * p;
-      build_switch(a, (off + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1], sedge[t + 1]);
+      build_switch(a, ch, round, (loff + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1],
+                   sedge[t + 1]);
     }
     if (tid == 0 && cnt > 0) {
-      if (t0 == 1) {  // slot off is the second of a pair started in an earlier bucket
-        a.pib_pos[off] = (uint32_t)scomp[0];
-        a.pib_edge[off] = sedge[0];
+      if (t0 == 1) {  // this bucket's first slot is the second of a pair started in an earlier bucket
+        a.pib_pos[goff] = (uint32_t)scomp[0];
+        a.pib_edge[goff] = sedge[0];
         const uint32_t idx = atomicAdd(&a.ctl->boundary, 1u);
-        a.bnd[idx] = (off - 1) >> 1;
+        a.bnd[idx] = goff - 1;  // the pair's first slot
       }
-      const uint32_t last = off + cnt - 1;
+      const uint32_t last = loff + cnt - 1;
       if ((last & 1u) == 0) {  // first of a pair whose partner is in a later bucket
-        if (last + 1 == a.m) {
-          keep_source(a, sedge[cnt - 1]);  // odd m: unpaired
+        if (last + 1 == ch.m) {
+          keep_source(a, ch, sedge[cnt - 1]);  // odd m: unpaired
         } else {
-          a.pib_pos[last] = (uint32_t)scomp[cnt - 1];
-          a.pib_edge[last] = sedge[cnt - 1];
+          a.pib_pos[goff + cnt - 1] = (uint32_t)scomp[cnt - 1];
+          a.pib_edge[goff + cnt - 1] = sedge[cnt - 1];
         }
       }
     }
@@ -547,16 +601,24 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
 
 __global__ void k_boundary(RoundArgs a) {
   const uint32_t n = a.ctl->boundary;
+  const unsigned long long R = a.ctl->pool_round;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-    const uint32_t k = a.bnd[idx];
-    if (k >= a.L) {  // cannot happen unless a bucket overflowed (reported)
+    const uint32_t g = a.bnd[idx];  // first slot of the pair
+    const uint32_t c = g < a.slot_hw ? a.owner_slot[g] : kNoChain;
+    if (c == kNoChain) {  // cannot happen unless a bucket overflowed (reported)
       atomicOr(&a.ctl->err, kErrRecord);
       continue;
     }
-    build_switch(a, k, a.pib_pos[2 * k], a.pib_edge[2 * k], a.pib_pos[2 * k + 1], a.pib_edge[2 * k + 1]);
+    const ChainDesc ch = a.chains[c];
+    const uint32_t k = (g - ch.slot_base) >> 1;
+    if (k >= ch.L) {
+      atomicOr(&a.ctl->err, kErrRecord);
+      continue;
+    }
+    build_switch(a, ch, chain_round(ch, R), k, a.pib_pos[g], a.pib_edge[g], a.pib_pos[g + 1],
+                 a.pib_edge[g + 1]);
   }
 }
-
 // Grouping of one tuple partition by edge id (Algorithm 1's table T for the
 // partition's edge ids) in a shared-memory table of S slots: key, p (the
 // eraser, from the source tuple), q (smallest inserter), c (number of
@@ -625,7 +687,7 @@ __device__ __forceinline__ void group_alloc(const RoundArgs &a, const GroupSmem 
   uint32_t idx = kTrivial;
   if (need) {
     idx = atomicAdd(&a.ctl->dep_count, 1u);
-    if (idx <= 2 * a.L) {
+    if (idx < a.dep_cap) {
       a.dep[idx] = make_uint2(g.gp[s], g.gq[s]);
     } else {
       idx = kTrivial;
@@ -669,10 +731,13 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
     overflow = 0;
   }
   __syncthreads();
-  for (uint32_t part = blockIdx.x; part < a.np; part += gridDim.x) {
+  for (uint32_t part = blockIdx.x; part < a.part_hw; part += gridDim.x) {
+    const uint32_t c = a.owner_part[part];
+    if (c == kNoChain) continue;
+    const uint32_t pbase = a.chains[c].part_base, tbase = a.chains[c].tuple_base, capt = a.chains[c].capt;
     // the partition's tuples: its own region, then its overflow tuples
-    const uint4 *prim = a.ptup + (size_t)part * a.capt;
-    const uint32_t nprim = min(a.tcount[part], a.capt);
+    const uint4 *prim = a.ptup + tbase + (size_t)(part - pbase) * capt;
+    const uint32_t nprim = min(a.tcount[part], capt);
     const uint32_t obeg = ovf ? a.ooff[part] : 0, oend = ovf ? a.ooff[part + 1] : 0;
     const uint32_t ntup = nprim + (oend - obeg);
     if (ntup <= (uint32_t)(kGroupR * kGroupThreads)) {
@@ -782,11 +847,14 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
 
 __global__ void k_wave1(RoundArgs a) {
   Tally t;
+  ChainCount cc;
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < a.L; base += stride) {
+  for (uint32_t base = blockIdx.x * blockDim.x; base < a.switch_hw; base += stride) {
     const uint32_t k = base + threadIdx.x;
     bool wait = false;
-    if (k < a.L) {
+    uint32_t c = kNoChain;
+    if (k < a.switch_hw) c = a.owner_switch[k];
+    if (c != kNoChain) {
       const uint32_t w = __ldcs(&a.word[k]);
       const uint32_t code = w & kCodeMask;
       uint32_t state = kLegal;
@@ -804,20 +872,25 @@ __global__ void k_wave1(RoundArgs a) {
         wait = true;
       } else {
         ++t.accepted;
+        count_accepted(a, cc, c);
       }
       a.status[k] = state == kUndecided ? 0u : ((1u << 2) | state);
     }
     append_if(wait, k, a.list0, &a.ctl->pending[0]);
   }
   flush_tally(a, t);
+  flush_count(a, cc);
 }
 
 // Waves 2, 3, ... on one CTA: undecided switches re-register as inserters
-// (the q fields of illegal minima were cleared), then decide.
+// (the q fields of illegal minima were cleared), then decide.  The kernel
+// also closes the pool round (the round counter every chain derives its own
+// round number from).
 __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
   __shared__ uint32_t s_n;
   Tally t;
-  uint32_t cur = 0, wave = 2, prev_n = a.L + 1;
+  ChainCount cc;
+  uint32_t cur = 0, wave = 2, prev_n = a.switch_hw + 1;
   volatile uint32_t *pend = a.ctl->pending;
   for (;;) {
     __syncthreads();
@@ -865,6 +938,7 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
         } else {
           a.status[k] = (wave << 2) | kLegal;
           ++t.accepted;
+          count_accepted(a, cc, a.owner_switch[k]);
         }
       }
       append_if(wait, k, out, (uint32_t *)&pend[cur ^ 1]);
@@ -873,40 +947,49 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
     ++wave;
   }
   flush_tally(a, t);
+  flush_count(a, cc);
   if (threadIdx.x == 0) {
-    const uint32_t waves = a.L ? wave - 1 : 0;
+    const uint32_t waves = a.any_work ? wave - 1 : 0;
     a.ctl->waves = waves;
-    a.st->waves_total += waves;
-    if (waves > a.st->waves_max) a.st->waves_max = waves;
-    a.st->wave_hist[waves < kWaveHist ? waves : kWaveHist - 1] += 1;
-    a.st->last_pending[1] = a.L;
+    if (a.any_work) {
+      a.st->waves_total += waves;
+      if (waves > a.st->waves_max) a.st->waves_max = waves;
+      a.st->wave_hist[waves < kWaveHist ? waves : kWaveHist - 1] += 1;
+    }
+    a.st->last_pending[1] = a.switch_hw;
     for (uint32_t w = wave; w < kWaveHist; ++w) a.st->last_pending[w] = 0;
+    a.ctl->pool_round += 1;
   }
 }
 
 // ---------------------------------------------------------------- state in / out
 
-__global__ void k_load_state(RoundArgs a, const unsigned long long *E) {
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.m; s += gridDim.x * blockDim.x) {
-    a.cpos[s] = s;
-    a.cedge[s] = E[s];
+__global__ void k_load_chain(RoundArgs a, ChainDesc ch, const unsigned long long *E) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < ch.m; s += gridDim.x * blockDim.x) {
+    a.cpos[ch.slot_base + s] = s;
+    a.cedge[ch.slot_base + s] = E[s];
   }
 }
 
-__global__ void k_store_state(RoundArgs a, unsigned long long *E) {
-  const uint32_t npair = (a.m + 1) >> 1;
+__global__ void k_store_chain(RoundArgs a, ChainDesc ch, unsigned long long *E) {
+  const bool apply = chain_apply(ch, a.ctl->pool_round);
+  const uint32_t npair = (ch.m + 1) >> 1;
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < npair; k += gridDim.x * blockDim.x) {
-    const uint32_t s0 = 2 * k;
-    if (s0 + 1 < a.m) {
+    const uint32_t s0 = ch.slot_base + 2 * k;
+    if (2 * k + 1 < ch.m) {
       const uint32_t i = a.cpos[s0], j = a.cpos[s0 + 1];
       unsigned long long e1 = a.cedge[s0], e2 = a.cedge[s0 + 1];
-      apply_last(a, k, i, j, e1, e2);
+      apply_last(a, ch, apply, k, i, j, e1, e2);
       E[i] = e1;
       E[j] = e2;
     } else {
       E[a.cpos[s0]] = a.cedge[s0];
     }
   }
+}
+
+__global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
 
 // ---------------------------------------------------------------- create-time checks
@@ -965,7 +1048,7 @@ inline int grid_for(unsigned long long work, int threads, int num_sms, int per_s
 size_t group_smem_bytes(uint32_t group_log2) { return (size_t)kGroupSlotBytes << group_log2; }
 
 cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_grid) {
-  // opt in to the largest table any handle may use, so that handles with
+  // opt in to the largest table any pool may use, so that pools with
   // different table sizes never lower each other's limit
   cudaError_t e = cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)group_smem_bytes(kMaxGroupLog2));
@@ -979,28 +1062,26 @@ cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_gr
 
 cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEvent_t *ev, uint32_t *launches) {
   // ev (optional) receives kNumStages + 1 stage boundaries; stages that do
-  // not run for tiny m still get both of their events (zero duration).
+  // not run (no chain with two edges) still get both events (zero duration)
   auto mark = [&](int stage) {
     if (ev) cudaEventRecord(ev[stage], s);
   };
   uint32_t n = 0;
-  const bool work = a.m >= 2;
-  const uint32_t npair = (a.m + 1) / 2;
-  const unsigned long long ntuple = 4ull * a.L + 1;
+  const bool work = a.any_work != 0;
   mark(kStageClear);
-  k_clear<<<grid_for(a.nb > a.np ? a.nb : a.np, 256, num_sms, 4), 256, 0, s>>>(a);
+  k_clear<<<grid_for(a.bucket_hw > a.part_hw ? a.bucket_hw : a.part_hw, 256, num_sms, 4), 256, 0, s>>>(a);
   ++n;
   mark(kStagePermute);
-  if (work) { k_permute<<<grid_for(npair, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  if (work) { k_permute<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStageScanPerm);
   if (work) { k_scan_perm<<<1, 1024, 0, s>>>(a); ++n; }
   mark(kStageSortPair);
-  if (work) { k_sortpair<<<a.nb, kSortThreads, 0, s>>>(a); ++n; }
+  if (work) { k_sortpair<<<a.bucket_hw, kSortThreads, 0, s>>>(a); ++n; }
   mark(kStageBoundary);
-  if (work) { k_boundary<<<grid_for(a.nb, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
+  if (work) { k_boundary<<<grid_for(a.bucket_hw, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
   mark(kStageOverflow);
   if (work) {
-    const int g = grid_for(ntuple, 256, num_sms, 2);
+    const int g = grid_for(a.ovf_cap, 256, num_sms, 2);
     k_overflow_count<<<g, 256, 0, s>>>(a);
     k_overflow_scan<<<1, 1024, 0, s>>>(a);
     k_overflow_scatter<<<g, 256, 0, s>>>(a);
@@ -1009,27 +1090,36 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   mark(kStageGroup);
   if (work) {
     const uint32_t ctas = a.group_grid ? a.group_grid : (uint32_t)num_sms;
-    k_group<<<ctas < a.np ? ctas : a.np, kGroupThreads, group_smem_bytes(a.group_log2), s>>>(a);
+    k_group<<<ctas < a.part_hw ? ctas : a.part_hw, kGroupThreads, group_smem_bytes(a.group_log2), s>>>(a);
     ++n;
   }
   mark(kStageWave1);
-  if (work) { k_wave1<<<grid_for(a.L, 256, num_sms, 16), 256, 0, s>>>(a); ++n; }
+  if (work) { k_wave1<<<grid_for(a.switch_hw, 256, num_sms, 16), 256, 0, s>>>(a); ++n; }
   mark(kStageTail);
-  if (work) { k_tail<<<1, 1024, 0, s>>>(a); ++n; }
+  k_tail<<<1, 1024, 0, s>>>(a);
+  ++n;
   mark(kNumStages);
   if (launches) *launches += n;
   return cudaGetLastError();
 }
 
-cudaError_t launch_load_state(const RoundArgs &a, const unsigned long long *E, cudaStream_t s, int num_sms) {
-  if (a.m == 0) return cudaSuccess;
-  k_load_state<<<grid_for(a.m, 256, num_sms, 8), 256, 0, s>>>(a, E);
+cudaError_t launch_load_chain(const RoundArgs &a, const ChainDesc &ch, const unsigned long long *E, cudaStream_t s,
+                              int num_sms) {
+  if (ch.m == 0) return cudaSuccess;
+  k_load_chain<<<grid_for(ch.m, 256, num_sms, 8), 256, 0, s>>>(a, ch, E);
   return cudaGetLastError();
 }
 
-cudaError_t launch_store_state(const RoundArgs &a, unsigned long long *E, cudaStream_t s, int num_sms) {
-  if (a.m == 0) return cudaSuccess;
-  k_store_state<<<grid_for((a.m + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a, E);
+cudaError_t launch_store_chain(const RoundArgs &a, const ChainDesc &ch, unsigned long long *E, cudaStream_t s,
+                               int num_sms) {
+  if (ch.m == 0) return cudaSuccess;
+  k_store_chain<<<grid_for((ch.m + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a, ch, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u32(uint32_t *p, uint32_t n, uint32_t v, cudaStream_t s, int num_sms) {
+  if (n == 0) return cudaSuccess;
+  k_fill_u32<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(p, n, v);
   return cudaGetLastError();
 }
 

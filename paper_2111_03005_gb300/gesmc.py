@@ -77,6 +77,28 @@ class GesmcStats(ctypes.Structure):
         return d
 
 
+class GesmcPoolOpts(ctypes.Structure):
+    _fields_ = [
+        ("max_edges", ctypes.c_uint64),
+        ("max_chains", ctypes.c_uint32),
+        ("max_waves", ctypes.c_uint32),
+        ("tuple_log2", ctypes.c_uint32),
+        ("group_log2", ctypes.c_uint32),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class GesmcChainInfo(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in ("m", "n", "seed", "rounds", "next_round", "switches",
+                                                      "accepted")]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class GesmcError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -108,6 +130,25 @@ _SIGNATURES = [
     ("gesmc_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("gesmc_run_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p]),
+    ("gesmc_pool_opts_default", None, [ctypes.POINTER(GesmcPoolOpts)]),
+    ("gesmc_pool_device_bytes", ctypes.c_size_t, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]),
+    ("gesmc_pool_create", ctypes.c_int, [ctypes.POINTER(GesmcPoolOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    ("gesmc_pool_destroy", None, [ctypes.c_void_p]),
+    ("gesmc_pool_add", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.POINTER(ctypes.c_uint32)]),
+    ("gesmc_pool_remove", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    ("gesmc_pool_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("gesmc_pool_edges", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
+    ("gesmc_pool_chain_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(GesmcChainInfo)]),
+    ("gesmc_pool_num_chains", ctypes.c_uint32, [ctypes.c_void_p]),
+    ("gesmc_pool_free_edges", ctypes.c_uint64, [ctypes.c_void_p]),
+    ("gesmc_pool_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GesmcStats)]),
+    ("gesmc_pool_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
+    ("gesmc_pool_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("gesmc_pool_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_uint64)]),
     # include/gesmc_microbench.h
     ("gesmc_probe_random_access", ctypes.c_int, [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint64,
                                                  ctypes.POINTER(ctypes.c_double)]),
@@ -341,6 +382,110 @@ class Chain:
         if self._h:
             gesmc_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Pool:
+    """Many independent chains on the current CUDA device, advanced together.
+
+    Each chain's result equals what a single-chain ``Chain`` with the same
+    list, seed and start round gives; chains join and leave between rounds."""
+
+    def __init__(self, max_edges: int, max_chains: int, max_waves: int = 0, tuple_log2: int = 0,
+                 group_log2: int = 0, stream=None, torch_allocator: bool = True):
+        import torch
+
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libgesmc needs a CUDA device")
+        o = GesmcPoolOpts()
+        lib.gesmc_pool_opts_default(ctypes.byref(o))
+        o.max_edges, o.max_chains, o.max_waves = max_edges, max_chains, max_waves
+        o.tuple_log2, o.group_log2 = tuple_log2, group_log2
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
+        self._hooks = None
+        if torch_allocator:
+            self._hooks = _TorchAllocator(torch.cuda.current_device())
+            o.alloc, o.free = self._hooks.alloc, self._hooks.free
+        self._p = ctypes.c_void_p()
+        _check(lib.gesmc_pool_create(ctypes.byref(o), ctypes.byref(self._p)), "gesmc_pool_create")
+
+    @staticmethod
+    def device_bytes(max_edges: int, max_chains: int, tuple_log2: int = 0) -> int:
+        return int(load_library().gesmc_pool_device_bytes(max_edges, max_chains, tuple_log2))
+
+    def add(self, edges, n: int = 0, seed: int = 0, start_round: int = 0, lazy_threshold: int = 0) -> int:
+        ptr, m, on_dev, _keep = _as_edge_buffer(edges)
+        cid = ctypes.c_uint32()
+        _check(load_library().gesmc_pool_add(self._p, ctypes.c_void_p(ptr), m, on_dev, n, seed, start_round,
+                                             lazy_threshold, ctypes.byref(cid)), "gesmc_pool_add")
+        return int(cid.value)
+
+    def remove(self, chain: int):
+        _check(load_library().gesmc_pool_remove(self._p, chain), "gesmc_pool_remove")
+
+    def run(self, global_switches: int):
+        _check(load_library().gesmc_pool_run(self._p, global_switches), "gesmc_pool_run")
+        return self
+
+    def edges(self, chain: int, out=None):
+        lib = load_library()
+        if out is None:
+            out = np.empty(self.chain_info(chain)["m"], dtype=np.uint64)
+        ptr, cap, on_dev, _keep = _as_edge_buffer(out)
+        m_out = ctypes.c_uint64()
+        _check(lib.gesmc_pool_edges(self._p, chain, ctypes.c_void_p(ptr), cap, on_dev, ctypes.byref(m_out)),
+               "gesmc_pool_edges")
+        return out
+
+    def chain_info(self, chain: int) -> dict:
+        info = GesmcChainInfo()
+        _check(load_library().gesmc_pool_chain_info(self._p, chain, ctypes.byref(info)), "gesmc_pool_chain_info")
+        return info.as_dict()
+
+    @property
+    def num_chains(self) -> int:
+        return int(load_library().gesmc_pool_num_chains(self._p))
+
+    @property
+    def free_edges(self) -> int:
+        return int(load_library().gesmc_pool_free_edges(self._p))
+
+    def stats(self) -> dict:
+        st = GesmcStats()
+        _check(load_library().gesmc_pool_stats(self._p, ctypes.byref(st)), "gesmc_pool_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        _check(load_library().gesmc_pool_reset_stats(self._p), "gesmc_pool_reset_stats")
+
+    def set_profiling(self, enable: bool = True):
+        _check(load_library().gesmc_pool_set_profiling(self._p, int(enable)), "gesmc_pool_set_profiling")
+
+    def stage_times(self) -> tuple[dict, int]:
+        ms = (ctypes.c_double * NUM_STAGES)()
+        rounds = ctypes.c_uint64()
+        _check(load_library().gesmc_pool_stage_times(self._p, ms, NUM_STAGES, ctypes.byref(rounds)),
+               "gesmc_pool_stage_times")
+        return {gesmc_stage_name(i): float(ms[i]) for i in range(NUM_STAGES)}, int(rounds.value)
+
+    def close(self):
+        if self._p:
+            load_library().gesmc_pool_destroy(self._p)
+            self._p = None
 
     def __enter__(self):
         return self

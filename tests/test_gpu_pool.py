@@ -1,0 +1,124 @@
+"""Pools: many chains advanced by one set of kernels per round.  Every chain's
+edge list must equal, bit for bit, the sequential oracle run on that chain
+alone (its own seed, start round and laziness), whatever else is in the pool
+and whenever the chain joined."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_03005_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2111_03005_gb300 import gesmc  # noqa: E402
+
+
+def mixed_graphs(seed=0):
+    rng = np.random.default_rng(seed)
+    graphs = []
+    for t in range(12):
+        n = int(rng.integers(20, 3000))
+        m = int(rng.integers(1, min(4 * n, n * (n - 1) // 2)))
+        graphs.append((inputs.random_simple_graph(n, m, seed=100 + t), n))
+    graphs.append((inputs.pld_graph(4000, 2.1, 1, 300, seed=5), 4000))
+    graphs.append((inputs.workload_gnp_small(seed=2)[0], 1000))
+    for lst in ([], [(0, 1)], [(0, 1), (2, 3)], [(0, 1), (2, 3), (4, 5)]):
+        e = oracle.pack([a for a, _ in lst], [b for _, b in lst]) if lst else np.zeros(0, np.uint64)
+        graphs.append((e, 6))
+    return graphs
+
+
+def test_every_chain_matches_its_oracle_alone():
+    graphs = mixed_graphs()
+    total = sum(len(e) for e, _ in graphs)
+    with gesmc.Pool(max_edges=total, max_chains=len(graphs)) as pool:
+        ids, expect, meta = [], [], []
+        for t, (e, n) in enumerate(graphs):
+            seed, start, lazy = 1000 + 7 * t, 3 * t, (1 << 61) if t % 5 == 0 else 0
+            ids.append(pool.add(e, n=n, seed=seed, start_round=start, lazy_threshold=lazy))
+            expect.append(oracle.validate(e, n)[1])
+            meta.append((seed, start, lazy))
+        done = 0
+        for rounds in (1, 3, 2):
+            pool.run(rounds)
+            for t, c in enumerate(ids):
+                seed, start, lazy = meta[t]
+                expect[t], st = oracle.run(expect[t], seed=seed, rounds=rounds, start_round=start + done,
+                                           lazy_threshold=lazy)
+                got = pool.edges(c)
+                assert np.array_equal(got, expect[t]), (t, rounds)
+            done += rounds
+        for t, c in enumerate(ids):
+            info = pool.chain_info(c)
+            assert info["rounds"] == done and info["next_round"] == meta[t][1] + done
+            assert info["m"] == len(graphs[t][0])
+        total_acc = sum(pool.chain_info(c)["accepted"] for c in ids)
+        assert total_acc == pool.stats()["accepted"]
+
+
+def test_chains_join_and_leave_between_rounds():
+    graphs = mixed_graphs(seed=1)
+    cap = sum(len(e) for e, _ in graphs[:8])
+    with gesmc.Pool(max_edges=cap, max_chains=6) as pool:
+        live = {}   # chain id -> (graph index, seed, rounds run, expected list)
+        queue = list(range(len(graphs)))
+        step = 0
+        while queue or live:
+            # admit while there is room; "no room" (edges, chain slots or a
+            # free range long enough) means: wait until a chain leaves
+            while queue:
+                g = queue[0]
+                e, n = graphs[g]
+                try:
+                    c = pool.add(e, n=n, seed=50 + g, start_round=g)
+                except gesmc.GesmcError as err:
+                    assert err.code == gesmc.GESMC_E_NOMEM and live, "an empty pool must admit"
+                    break
+                queue.pop(0)
+                live[c] = [g, 50 + g, 0, oracle.validate(e, n)[1]]
+            if not live:
+                break
+            pool.run(1)
+            step += 1
+            for c, rec in list(live.items()):
+                g, seed, done, exp = rec
+                rec[3], _ = oracle.run(exp, seed=seed, rounds=1, start_round=g + done)
+                rec[2] = done + 1
+                assert np.array_equal(pool.edges(c), rec[3]), (c, g, rec[2])
+                if rec[2] == 2 + g % 3:      # each request asks for its own number of rounds
+                    pool.remove(c)
+                    del live[c]
+        assert step > 0 and pool.num_chains == 0
+
+
+def test_pool_full_and_bad_chain_ids():
+    e = inputs.random_simple_graph(50, 100, seed=3)
+    with gesmc.Pool(max_edges=150, max_chains=2) as pool:
+        a = pool.add(e, n=50, seed=1)
+        with pytest.raises(gesmc.GesmcError) as ei:
+            pool.add(e, n=50, seed=2)            # 200 edges > 150
+        assert ei.value.code == gesmc.GESMC_E_NOMEM
+        pool.add(e[:40], n=50, seed=2)
+        with pytest.raises(gesmc.GesmcError):
+            pool.add(e[:5], n=50, seed=3)         # no chain slot left
+        pool.remove(a)
+        with pytest.raises(gesmc.GesmcError):
+            pool.edges(a)
+        pool.add(e[:100], n=50, seed=4)           # the freed room is reused
+
+
+def test_invalid_chain_does_not_disturb_the_pool():
+    e = inputs.random_simple_graph(40, 80, seed=4)
+    with gesmc.Pool(max_edges=200, max_chains=3) as pool:
+        c = pool.add(e, n=40, seed=9)
+        bad = np.array([(1 << 32) | 1], dtype=np.uint64)
+        with pytest.raises(gesmc.GesmcError) as ei:
+            pool.add(bad, n=40, seed=1)
+        assert ei.value.code == gesmc.GESMC_E_LOOP
+        pool.run(3)
+        expect, _ = oracle.run(e, seed=9, rounds=3)
+        assert np.array_equal(pool.edges(c), expect)
