@@ -237,7 +237,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload]["desc"], "sample": WORKLOADS[CPU_SAMPLE]["desc"],
+        "config": {"workload": WORKLOADS.get(args.workload, {"desc": args.workload})["desc"],
+                   "sample": WORKLOADS[CPU_SAMPLE]["desc"],
                    "parallelism": "none (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -366,6 +367,151 @@ def run_gesmc(args):
     return 0
 
 
+# --------------------------------------------------------------------- ensemble and serving
+
+def run_ensemble(args):
+    """4096 chains on graphs of uneven size in one pool, 50 rounds per step,
+    against one single-chain handle per graph (a sample) on the same GPU."""
+    import numpy as np
+    import torch
+
+    from paper_2111_03005_gb300 import ensemble, gesmc, inputs
+
+    torch.cuda.set_device(0)
+    count, rounds = args.chains, 50
+    graphs = inputs.ensemble_graphs(count, seed=41)
+    seeds = [5000 + t for t in range(count)]
+    total = sum(len(e) for e, _ in graphs)
+    L_total = sum(len(e) // 2 for e, _ in graphs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream), gesmc.Pool(max_edges=total, max_chains=count, stream=stream) as pool:
+        t0 = time.perf_counter()
+        ids = [pool.add(e, n=n, seed=s) for (e, n), s in zip(graphs, seeds)]
+        add_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            pool.run(rounds)
+        pool.reset_stats()
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clocks:
+            start.record(stream)
+            for _ in range(args.steps):
+                pool.run(rounds)
+            stop.record(stream)
+            torch.cuda.synchronize()
+        ms = start.elapsed_time(stop)
+        st = pool.stats()
+        del ids
+    value = args.steps * rounds * L_total / (ms / 1e3)
+    # the per-graph alternative on a sample, and bit-exactness of the two
+    rng = np.random.default_rng(3)
+    sample = sorted(rng.choice(count, size=min(args.sample, count), replace=False).tolist())
+    sub = [graphs[t] for t in sample]
+    sub_seeds = [seeds[t] for t in sample]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    alone = ensemble.run_one_by_one(sub, sub_seeds, rounds)
+    torch.cuda.synchronize()
+    one_by_one_s = time.perf_counter() - t0
+    pooled = ensemble.run_pool(sub, sub_seeds, rounds)
+    L_sub = sum(len(e) // 2 for e, _ in sub)
+    per_graph = rounds * L_sub / one_by_one_s
+    line = {
+        "metric": "edge switches/sec, batched ensemble of chains (one pool, bit-exact per chain)",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{count} chains, n log-uniform in [100, 1e5], half G(n, 8/(n-1)), half "
+                               f"Pld([1..n^(1/(gamma-1))], gamma ~ U[2.2, 3.0]) by Havel-Hakimi; "
+                               f"{rounds} global switches per step", "chains": count, "edges": total,
+                   "parallelism": "single GPU"},
+        "per_graph_handles": {"value": per_graph, "unit": UNIT, "sample_chains": len(sample),
+                              "includes": "create + run + edges per graph, one after another"},
+        "speedup_vs_per_graph": value / per_graph,
+        "identical_results_on_sample": ensemble.same_results(pooled, alone),
+        "pool_add_s": add_s,
+        "gpu_launches": st["kernel_launches"],
+        "waves": {"max": st["waves_max"], "mean": st["waves_total"] / max(st["rounds"], 1)},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """A Poisson stream of sampling requests served by continuous batching."""
+    import numpy as np
+    import torch
+
+    from paper_2111_03005_gb300 import gesmc, inputs, serve
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(17)
+    reqs = []
+    for rid in range(args.requests):
+        m_target = int(np.exp(rng.uniform(np.log(1e3), np.log(1e7))))
+        e, n = inputs.request_graph(m_target, seed=rid)
+        reqs.append(serve.Request(rid=rid, edges=e, n=n, seed=100 + rid, rounds=int(rng.integers(10, 101))))
+    gaps = rng.exponential(1.0 / args.rate, size=len(reqs))
+    offsets = np.cumsum(gaps) - gaps[0]
+    work = sum(r.rounds * (len(r.edges) // 2) for r in reqs)
+    cap = max(args.pool_edges, max(len(r.edges) for r in reqs))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains, stream=stream) as srv:
+        # warm the kernels once (a small request, not counted)
+        w = serve.Request(rid=-1, edges=reqs[0].edges, n=reqs[0].n, seed=1, rounds=3)
+        srv.submit(w)
+        while not srv.idle():
+            srv.step()
+        srv.done.clear()
+        t0 = time.perf_counter()
+        nxt = 0
+        while nxt < len(reqs) or not srv.idle():
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and offsets[nxt] <= now:
+                srv.submit(reqs[nxt], now=t0 + offsets[nxt])
+                nxt += 1
+            if srv.idle():
+                time.sleep(max(0.0, min(0.01, offsets[nxt] - now)) if nxt < len(reqs) else 0)
+                continue
+            srv.step()
+        wall = time.perf_counter() - t0
+    lat = np.array([r.finished - r.arrival for r in reqs])
+    # the plain alternative: one handle per request, first come first served
+    svc = []
+    for r in reqs:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        with gesmc.Chain(r.edges, n=r.n) as c:
+            c.run(r.rounds, r.seed)
+            out = c.edges()
+        svc.append(time.perf_counter() - t1)
+        assert np.array_equal(out, r.result), f"request {r.rid}: served result differs from its single run"
+    finish, free_at = [], 0.0
+    for off, d in zip(offsets, svc):
+        free_at = max(free_at, off) + d
+        finish.append(free_at - off)
+    fifo = np.array(finish)
+    line = {
+        "metric": "sampling service: aggregate edge switches/sec with continuous batching",
+        "value": work / wall, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 1,
+        "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, power-law graphs with "
+                               f"m log-uniform in [1e3, 1e7], 10-100 global switches each",
+                   "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "per_request_handles_fifo": {"value": work / (max(o + f for o, f in zip(offsets, finish))),
+                                     "latency_s": {"p50": float(np.percentile(fifo, 50)),
+                                                   "p99": float(np.percentile(fifo, 99))}},
+        "identical_to_single_runs": True,
+        "rounds_run": srv.rounds_run,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     global CPU_SAMPLE
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -373,7 +519,13 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gesmc", "reference"], default="gesmc")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="gnp_2p24")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve"], default="gnp_2p24")
+    ap.add_argument("--chains", type=int, default=4096, help="ensemble: chains")
+    ap.add_argument("--sample", type=int, default=256, help="ensemble: chains run one by one for comparison")
+    ap.add_argument("--requests", type=int, default=128, help="serve: requests")
+    ap.add_argument("--rate", type=float, default=400.0, help="serve: arrivals per second")
+    ap.add_argument("--pool-edges", type=int, default=40_000_000, help="serve: pool capacity in edges")
+    ap.add_argument("--pool-chains", type=int, default=256, help="serve: pool capacity in chains")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")
@@ -387,6 +539,10 @@ def main(argv=None):
     CPU_SAMPLE = args.cpu_sample
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gesmc(args)
 
 

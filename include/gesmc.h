@@ -58,6 +58,12 @@ enum {
   GESMC_E_TOO_LARGE = -11  /* m above GESMC_NOALLOC_MAX_EDGES (no-alloc call) */
 };
 
+/* Rounds are replayed from a captured CUDA graph of one round (launched on
+ * a private stream ordered after and before the caller's stream); this flag
+ * launches the kernels one by one instead.  Stage timing always launches
+ * them one by one. */
+#define GESMC_FLAG_NO_GRAPHS 1u
+
 /* Device allocation hooks: alloc returns device memory usable on `stream`
  * (or NULL on failure); free releases it.  Both NULL: cudaMalloc/cudaFree. */
 typedef void *(*gesmc_alloc_fn)(size_t bytes, void *stream, void *ctx);
@@ -72,7 +78,7 @@ typedef struct gesmc_opts {
                               partition, 8..16; 0: default                      */
   uint32_t group_log2;     /* tuning: log2 of the shared-memory grouping table
                               slots, 10..13; 0: default                          */
-  uint32_t reserved;
+  uint32_t flags;          /* GESMC_FLAG_* bits                                 */
   void *stream;            /* cudaStream_t for all device work; NULL: default  */
   gesmc_alloc_fn alloc;    /* optional device allocator                        */
   gesmc_free_fn free;
@@ -211,6 +217,7 @@ typedef struct gesmc_pool_opts {
   uint32_t max_waves;      /* as gesmc_opts.max_waves                        */
   uint32_t tuple_log2;     /* as gesmc_opts.tuple_log2                       */
   uint32_t group_log2;     /* as gesmc_opts.group_log2                       */
+  uint32_t flags;          /* GESMC_FLAG_* bits                              */
   void *stream;            /* cudaStream_t; NULL: the legacy default stream  */
   gesmc_alloc_fn alloc;    /* optional device allocator (as gesmc_opts)      */
   gesmc_free_fn free;

@@ -225,6 +225,14 @@ struct gesmc_pool_ctx {
   uint64_t rounds = 0, switches_run = 0, launches = 0;
   int broken = 0;
   RoundArgs args;
+  uint64_t args_version = 1;  // bumped whenever args change (invalidates the graph)
+  // captured round (CUDA graph), replayed on gstream
+  bool use_graphs = true;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t graph_version = 0;
+  uint32_t graph_launches = 0;
   int profiling = 0;
   std::vector<cudaEvent_t> events;
   double stage_ms[kNumStages] = {};
@@ -255,6 +263,7 @@ void dev_free(gesmc_pool_t p, void *ptr) {
 }
 
 void refresh_args(gesmc_pool_t p) {
+  ++p->args_version;
   RoundArgs &a = p->args;
   a.slot_hw = (uint32_t)p->slots.high_water();
   a.switch_hw = (uint32_t)p->switches.high_water();
@@ -511,11 +520,45 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
     }
   }
   uint32_t launches = 0;
-  for (uint64_t r = 0; r < rounds; ++r) {
-    cudaEvent_t *ev = p->profiling ? &p->events[per_round * r] : nullptr;
-    if (launch_round(a, s, p->num_sms, ev, &launches) != cudaSuccess) {
+  if (p->use_graphs && !p->profiling && rounds > 0) {
+    if (!p->gexec || p->graph_version != p->args_version) {
+      if (p->gexec) cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+      cudaGraph_t graph = nullptr;
+      uint32_t n = 0;
+      bool ok = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bool launched = launch_round(a, p->gstream, p->num_sms, nullptr, &n) == cudaSuccess;
+        ok = cudaStreamEndCapture(p->gstream, &graph) == cudaSuccess && launched;
+      }
+      ok = ok && cudaGraphInstantiate(&p->gexec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      if (!ok) {
+        cudaGetLastError();
+        p->gexec = nullptr;
+        p->broken = GESMC_E_CUDA;
+        return GESMC_E_CUDA;
+      }
+      p->graph_version = p->args_version;
+      p->graph_launches = n;
+    }
+    bool ok = cudaEventRecord(p->ev_in, s) == cudaSuccess && cudaStreamWaitEvent(p->gstream, p->ev_in, 0) == cudaSuccess;
+    for (uint64_t r = 0; r < rounds && ok; ++r) ok = cudaGraphLaunch(p->gexec, p->gstream) == cudaSuccess;
+    ok = ok && cudaEventRecord(p->ev_out, p->gstream) == cudaSuccess &&
+         cudaStreamWaitEvent(s, p->ev_out, 0) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
       p->broken = GESMC_E_CUDA;
       return GESMC_E_CUDA;
+    }
+    launches = (uint32_t)(rounds * p->graph_launches);
+  } else {
+    for (uint64_t r = 0; r < rounds; ++r) {
+      cudaEvent_t *ev = p->profiling ? &p->events[per_round * r] : nullptr;
+      if (launch_round(a, s, p->num_sms, ev, &launches) != cudaSuccess) {
+        p->broken = GESMC_E_CUDA;
+        return GESMC_E_CUDA;
+      }
     }
   }
   Counters ctl;
@@ -571,9 +614,14 @@ void gesmc_pool_destroy(gesmc_pool_t p) {
     DeviceGuard g(p->device);
     if (p->base) {
       cudaStreamSynchronize(p->stream);
+      if (p->gstream) cudaStreamSynchronize(p->gstream);
       dev_free(p, p->base);
     }
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
   }
   delete p;
 }
@@ -599,11 +647,20 @@ int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out) {
   p->max_edges = o.max_edges;
   p->max_chains = o.max_chains;
   p->tuple_log2 = o.tuple_log2 ? o.tuple_log2 : kDefaultTupleLog2;
+  p->use_graphs = !(o.flags & GESMC_FLAG_NO_GRAPHS);
   p->cap = pool_capacity(p->max_edges, p->max_chains, p->tuple_log2);
   p->lay = pool_layout(p->cap, p->max_edges, p->max_chains);
+  if (p->use_graphs &&
+      (cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    gesmc_pool_destroy(p);
+    return GESMC_E_CUDA;
+  }
   p->base = dev_alloc(p, p->lay.total);
   if (!p->base) {
-    delete p;
+    gesmc_pool_destroy(p);
     return GESMC_E_NOMEM;
   }
   const int rc = pool_init(p, o);
@@ -805,6 +862,7 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   po.max_waves = o.max_waves;
   po.tuple_log2 = o.tuple_log2;
   po.group_log2 = o.group_log2;
+  po.flags = o.flags;
   po.stream = o.stream;
   po.alloc = o.alloc;
   po.free = o.free;
@@ -917,6 +975,7 @@ extern "C" int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64
   int rc = noalloc_scratch(p.device, &p.base);
   if (rc != GESMC_OK) return rc;
   p.owns_memory = false;
+  p.use_graphs = false;
   p.stream = (cudaStream_t)stream;
   p.max_edges = GESMC_NOALLOC_MAX_EDGES;
   p.max_chains = 1;

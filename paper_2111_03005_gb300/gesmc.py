@@ -30,6 +30,7 @@ GESMC_E_WAVE_CAP = -8
 GESMC_E_INTERNAL = -9
 GESMC_E_CAPACITY = -10
 GESMC_E_TOO_LARGE = -11
+FLAG_NO_GRAPHS = 1
 NOALLOC_MAX_EDGES = 65536
 WAVE_HIST = 64
 
@@ -45,7 +46,7 @@ class GesmcOpts(ctypes.Structure):
         ("max_waves", ctypes.c_uint32),
         ("tuple_log2", ctypes.c_uint32),
         ("group_log2", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -84,6 +85,7 @@ class GesmcPoolOpts(ctypes.Structure):
         ("max_waves", ctypes.c_uint32),
         ("tuple_log2", ctypes.c_uint32),
         ("group_log2", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -226,7 +228,7 @@ def _as_edge_buffer(edges):
 
 
 def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 0, max_waves: int = 0, stream=None,
-                 torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0):
+                 torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0, graphs: bool = True):
     """Create a chain handle; returns (handle, keepalive).  Raises GesmcError."""
     import torch
 
@@ -241,6 +243,7 @@ def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 
     opts.max_waves = max_waves
     opts.tuple_log2 = tuple_log2
     opts.group_log2 = group_log2
+    opts.flags = 0 if graphs else FLAG_NO_GRAPHS
     if stream is None:
         stream = torch.cuda.current_stream()
     opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
@@ -403,7 +406,7 @@ class Pool:
     list, seed and start round gives; chains join and leave between rounds."""
 
     def __init__(self, max_edges: int, max_chains: int, max_waves: int = 0, tuple_log2: int = 0,
-                 group_log2: int = 0, stream=None, torch_allocator: bool = True):
+                 group_log2: int = 0, stream=None, torch_allocator: bool = True, graphs: bool = True):
         import torch
 
         lib = load_library()
@@ -413,6 +416,7 @@ class Pool:
         lib.gesmc_pool_opts_default(ctypes.byref(o))
         o.max_edges, o.max_chains, o.max_waves = max_edges, max_chains, max_waves
         o.tuple_log2, o.group_log2 = tuple_log2, group_log2
+        o.flags = 0 if graphs else FLAG_NO_GRAPHS
         if stream is None:
             stream = torch.cuda.current_stream()
         o.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))

@@ -163,3 +163,52 @@ def workload_gnp_2p24(seed: int = 3) -> tuple[np.ndarray, int]:
     """G(n=2^24, p=16/(n-1)): about 1.34e8 edges."""
     n = 1 << 24
     return gnp(n, 16.0 / (n - 1), seed), n
+
+
+def pld_mean_degree(gamma: float, dmin: int, dmax: int) -> float:
+    k = np.arange(dmin, dmax + 1, dtype=np.float64)
+    w = k ** -gamma
+    return float((k * w).sum() / w.sum())
+
+
+def graphical_pld_graph(n: int, gamma: float, dmax: int, seed: int, tries: int = 8) -> np.ndarray:
+    """pld_graph, redrawing the degrees (seed + 1, ...) until they are graphical."""
+    for t in range(tries):
+        try:
+            return pld_graph(n, gamma, 1, dmax, seed + t)
+        except ValueError:
+            continue
+    raise ValueError("no graphical power-law sequence drawn")
+
+
+def ensemble_graphs(count: int, seed: int, n_lo: int = 100, n_hi: int = 100_000) -> list[tuple[np.ndarray, int]]:
+    """A null-model ensemble of graphs of uneven size: n log-uniform in
+    [n_lo, n_hi]; half G(n, 8/(n-1)), half Pld([1..Delta], gamma) with gamma
+    uniform in [2.2, 3.0] and Delta = n^(1/(gamma-1)) (the paper's SynPld
+    choice, Sec. 6), realised by Havel-Hakimi."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for t in range(count):
+        n = int(round(float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))))
+        s = int(rng.integers(0, 2**62))
+        if t % 2 == 0:
+            out.append((gnp(n, 8.0 / (n - 1), s), n))
+        else:
+            gamma = float(rng.uniform(2.2, 3.0))
+            dmax = max(1, min(n - 1, int(n ** (1.0 / (gamma - 1.0)))))
+            out.append((graphical_pld_graph(n, gamma, dmax, s), n))
+    return out
+
+
+def request_graph(m_target: int, seed: int) -> tuple[np.ndarray, int]:
+    """A sampling request's starting graph: a power-law degree sequence
+    (gamma uniform in [2.2, 3.0], Delta = n^(1/(gamma-1))) with n chosen so
+    that the graph has about m_target edges, realised by Havel-Hakimi."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    gamma = float(rng.uniform(2.2, 3.0))
+    n = max(16, int(m_target))
+    for _ in range(4):  # Delta depends on n: settle n by fixed-point steps
+        dmax = max(1, min(n - 1, int(n ** (1.0 / (gamma - 1.0)))))
+        n = max(16, int(round(2.0 * m_target / pld_mean_degree(gamma, 1, dmax))))
+    dmax = max(1, min(n - 1, int(n ** (1.0 / (gamma - 1.0)))))
+    return graphical_pld_graph(n, gamma, dmax, int(rng.integers(0, 2**62))), n

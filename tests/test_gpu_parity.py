@@ -210,3 +210,17 @@ def test_gnp_2p24_full_size_round():
     pos = first_diff(got, expect)
     assert pos < 0, f"position {pos}"
     assert st["accepted"] == ost["accepted"] and st["rejected_exists"] == ost["rejected_exists"]
+
+
+def test_graph_replay_equals_direct_launches():
+    edges, n = inputs.workload_gnp_small(seed=7)
+    with gesmc.Chain(edges, n=n) as a, gesmc.Chain(edges, n=n, graphs=False) as b:
+        for rounds in (1, 4, 2, 5):
+            a.run(rounds, 77)
+            b.run(rounds, 77)
+            assert np.array_equal(a.edges(), b.edges())
+        assert a.stats()["kernel_launches"] == b.stats()["kernel_launches"] == 12 * 11
+    expect, _ = oracle.run(edges, seed=77, rounds=12)
+    with gesmc.Chain(edges, n=n) as c:
+        c.run(12, 77)
+        assert np.array_equal(c.edges(), expect)
