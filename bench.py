@@ -457,7 +457,8 @@ def run_serve(args):
     work = sum(r.rounds * (len(r.edges) // 2) for r in reqs)
     cap = max(args.pool_edges, max(len(r.edges) for r in reqs))
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains, stream=stream) as srv:
+    with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
+                                                     max_rounds_per_step=args.rounds_per_step, stream=stream) as srv:
         # warm the kernels once (a small request, not counted)
         w = serve.Request(rid=-1, edges=reqs[0].edges, n=reqs[0].n, seed=1, rounds=3)
         srv.submit(w)
@@ -499,7 +500,8 @@ def run_serve(args):
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, power-law graphs with "
                                f"m log-uniform in [1e3, 1e7], 10-100 global switches each",
-                   "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work},
+                   "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work,
+                   "max_rounds_per_step": args.rounds_per_step},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "max": float(lat.max())},
         "per_request_handles_fifo": {"value": work / (max(o + f for o, f in zip(offsets, finish))),
@@ -526,6 +528,7 @@ def main(argv=None):
     ap.add_argument("--rate", type=float, default=400.0, help="serve: arrivals per second")
     ap.add_argument("--pool-edges", type=int, default=40_000_000, help="serve: pool capacity in edges")
     ap.add_argument("--pool-chains", type=int, default=256, help="serve: pool capacity in chains")
+    ap.add_argument("--rounds-per-step", type=int, default=8, help="serve: most rounds between admissions")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")

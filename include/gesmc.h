@@ -103,6 +103,11 @@ typedef struct gesmc_stats_s {
   uint64_t wave_hist[GESMC_WAVE_HIST]; /* rounds that needed w waves (w >= 63: last) */
   uint64_t last_round_pending[GESMC_WAVE_HIST]; /* undecided switches entering wave
                                w (index w, w >= 1) in the most recent round       */
+  uint64_t overflow_tuples; /* dependency tuples that found their hash partition
+                               full and took the exact overflow path (a graph
+                               with an edge id proposed by many switches)         */
+  uint64_t subpass_partitions; /* partitions grouped in several passes (more
+                               tuples or distinct ids than one pass holds)        */
 } gesmc_stats_t;
 
 /* Fill *o with the defaults named above. */

@@ -15,7 +15,10 @@ extern "C" {
 
 /* Time `accesses` uniformly random 8-byte accesses of one kind over a
  * freshly allocated device buffer of `bytes` bytes on the current device:
- * kind 0 = loads, 1 = stores, 2 = 64-bit atomicCAS.  Best of three timed
+ * kind 0 = loads, 1 = stores, 2 = 64-bit atomicCAS, 3 = 32-bit atomicAdd with
+ * its result used (a cursor), 4 = the same without result (a count).  With a
+ * small buffer (a few MB) kinds 3 and 4 measure the L2 atomic rate that
+ * bucket cursors and histograms see.  Best of three timed
  * repetitions (after one warm-up), each after a refill of the buffer.
  * Writes accesses per second to *accesses_per_s.  Allocates and frees the
  * buffer itself (cudaMalloc).  Returns 0, -1 (bad argument), -5 (allocation

@@ -783,6 +783,8 @@ int gesmc_pool_stats(gesmc_pool_t p, gesmc_stats_t *out) {
     out->wave_hist[w] = st.wave_hist[w];
     out->last_round_pending[w] = st.last_pending[w];
   }
+  out->overflow_tuples = st.overflow_tuples;
+  out->subpass_partitions = st.subpass_partitions;
   return GESMC_OK;
 }
 

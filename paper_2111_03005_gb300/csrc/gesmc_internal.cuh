@@ -25,10 +25,11 @@
 //   ptup         uint4[tuple storage]     Algorithm 1's tuples (four per
 //                                         switch) in fixed-capacity hash
 //                                         partitions: {id lo, id hi, value,
-//                                         partition}
+//                                         low 32 bits of the id's hash}
 //   otup/stup    uint4[overflow cap]      tuples beyond a partition's
-//                                         capacity, and the same grouped by
-//                                         partition (rare)
+//                                         capacity ({.., partition}), and
+//                                         the same grouped by partition in
+//                                         the ptup format (rare)
 //   dep          uint2[dep cap]           {p, q} of every edge id with a
 //                                         dependency
 #pragma once
@@ -94,12 +95,12 @@ constexpr int kSubBits = 11;
 // Tuple partitions: a chain's tuples go to 2^P partitions by the top P bits
 // of the hash of the edge id (about 2^tuple_log2 tuples each, room for
 // twice that); one CTA groups a partition by edge id in a shared-memory
-// table of 2^group_log2 slots (22 bytes each, with the used-slot list).
+// table of 2^group_log2 slots of 20 bytes.
 constexpr int kDefaultTupleLog2 = 10;
 constexpr int kDefaultGroupLog2 = 11;
 constexpr int kMaxGroupLog2 = 13;
-constexpr int kGroupThreads = 256;
-constexpr int kGroupSlotBytes = 22;
+constexpr int kGroupThreads = 512;
+constexpr int kGroupSlotBytes = 20;
 
 constexpr int kWaveHist = 64;
 
@@ -134,6 +135,7 @@ struct StatsDev {
   unsigned long long waves_total, waves_max;
   unsigned long long wave_hist[kWaveHist];
   unsigned long long last_pending[kWaveHist];
+  unsigned long long overflow_tuples, subpass_partitions;
 };
 
 // Everything a round kernel needs; passed by value.  The *_hw fields are

@@ -27,7 +27,8 @@ __global__ void k_fill(unsigned long long *buf, unsigned long long words, unsign
     buf[i] = value;
 }
 
-// kind 0: loads, 1: stores, 2: CAS.  Each thread issues `per_thread` accesses
+// kind 0: loads, 1: stores, 2: CAS, 3: 32-bit atomic add with return, 4: the
+// same without return.  Each thread issues `per_thread` accesses
 // in groups of kIlp independent ones.
 __global__ void k_random(unsigned long long *buf, unsigned long long words, int kind, uint32_t per_thread,
                          unsigned long long salt, unsigned long long *sink) {
@@ -43,9 +44,15 @@ __global__ void k_random(unsigned long long *buf, unsigned long long words, int 
     } else if (kind == 1) {
 #pragma unroll
       for (int u = 0; u < kIlp; ++u) __stcg(&buf[idx[u]], idx[u]);
-    } else {
+    } else if (kind == 2) {
 #pragma unroll
       for (int u = 0; u < kIlp; ++u) acc += atomicCAS(&buf[idx[u]], ~0ull, idx[u]);
+    } else if (kind == 3) {  // 32-bit add with return (a cursor), counters at 8-byte spacing
+#pragma unroll
+      for (int u = 0; u < kIlp; ++u) acc += atomicAdd(reinterpret_cast<unsigned int *>(&buf[idx[u]]), 1u);
+    } else {  // 32-bit add without return (a histogram count)
+#pragma unroll
+      for (int u = 0; u < kIlp; ++u) atomicAdd(reinterpret_cast<unsigned int *>(&buf[idx[u]]), 1u);
     }
   }
   if (acc == 0x123456789ull) *sink = acc;  // keeps the loads alive
@@ -54,7 +61,7 @@ __global__ void k_random(unsigned long long *buf, unsigned long long words, int 
 }  // namespace
 
 extern "C" int gesmc_probe_random_access(uint64_t bytes, int kind, uint64_t accesses, double *accesses_per_s) {
-  if (!accesses_per_s || kind < 0 || kind > 2 || bytes < 4096 || accesses == 0) return -1;
+  if (!accesses_per_s || kind < 0 || kind > 4 || bytes < 4096 || accesses == 0) return -1;
   int dev = 0, sms = 1;
   if (cudaGetDevice(&dev) != cudaSuccess) return -6;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

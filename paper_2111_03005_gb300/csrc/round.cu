@@ -165,26 +165,33 @@ __device__ __forceinline__ void apply_last(const RoundArgs &a, const ChainDesc &
 // ---------------------------------------------------------------- build
 // Append tuples to their hash partitions: partition ids and cursor atomics
 // first (independent, in flight together), then the 16-byte stores.  A
-// tuple that finds its partition full goes to the overflow list.
+// tuple in its partition is {id lo, id hi, value, low 32 bits of the id's
+// hash} (the grouping kernel probes its table with those bits); one that
+// finds its partition full goes to the overflow list with its partition id
+// in place of the hash bits.
 template <int N>
 __device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc &ch,
                                             const unsigned long long (&key)[N], const uint32_t (&val)[N]) {
-  uint32_t part[N], idx[N];
+  uint32_t part[N], hlo[N], idx[N];
 #pragma unroll
   for (int t = 0; t < N; ++t) {
-    part[t] = partition_of(mix64(key[t]), ch.P);
+    const unsigned long long h = mix64(key[t]);
+    part[t] = partition_of(h, ch.P);
+    hlo[t] = (uint32_t)h;
     idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[ch.part_base + part[t]], 1u) : 0u;
   }
 #pragma unroll
   for (int t = 0; t < N; ++t) {
     if (key[t] == kEmptyKey) continue;
-    const uint4 rec = make_uint4((uint32_t)key[t], (uint32_t)(key[t] >> 32), val[t], ch.part_base + part[t]);
     if (idx[t] < ch.capt) {
-      a.ptup[ch.tuple_base + (size_t)part[t] * ch.capt + idx[t]] = rec;
+      a.ptup[ch.tuple_base + (size_t)part[t] * ch.capt + idx[t]] =
+          make_uint4((uint32_t)key[t], (uint32_t)(key[t] >> 32), val[t], hlo[t]);
     } else {
       const uint32_t o = atomicAdd(&a.ctl->ovf_count, 1u);
-      if (o < a.ovf_cap) a.otup[o] = rec;
-      else atomicOr(&a.ctl->err, kErrRecord);
+      if (o < a.ovf_cap)
+        a.otup[o] = make_uint4((uint32_t)key[t], (uint32_t)(key[t] >> 32), val[t], ch.part_base + part[t]);
+      else
+        atomicOr(&a.ctl->err, kErrRecord);
     }
   }
 }
@@ -344,7 +351,9 @@ __device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uin
 }
 
 // Append every position, with its current edge, to its chain's bucket.
-__global__ void k_permute(RoundArgs a) {
+// Capped at 40 registers (6 CTAs of 256 per SM): more warps in flight hide
+// the latency of the record loads and of the bucket cursor atomics.
+__global__ void __launch_bounds__(256, 6) k_permute(RoundArgs a) {
   const unsigned long long R = a.ctl->pool_round;
   const uint32_t npair = (a.slot_hw + 1) >> 1;
   const uint32_t nth = gridDim.x * blockDim.x;
@@ -427,7 +436,7 @@ __global__ void k_overflow_scatter(RoundArgs a) {
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const uint4 r = a.otup[t];
     const uint32_t dst = atomicAdd(&a.ocursor[r.w], 1u);
-    if (dst < n) a.stup[dst] = r;
+    if (dst < n) a.stup[dst] = make_uint4(r.x, r.y, r.z, (uint32_t)mix64(((unsigned long long)r.y << 32) | r.x));
   }
 }
 
@@ -620,48 +629,50 @@ __global__ void k_boundary(RoundArgs a) {
   }
 }
 // Grouping of one tuple partition by edge id (Algorithm 1's table T for the
-// partition's edge ids) in a shared-memory table of S slots: key, p (the
-// eraser, from the source tuple), q (smallest inserter), c (number of
-// inserters).  Then wave 1 for every target: present when k runs (p >= k),
-// dependent on an undecided switch (p < k, or an earlier inserter q < k),
-// or free.  Edge ids with a dependency get an entry {p, q} for the later
-// waves.
+// partition's edge ids) in a shared-memory table of S slots: slot[s] =
+// {key lo, key hi, p, q} with p the eraser (from the source tuple) and q
+// the smallest inserter, and aux[s] = 1 once a second inserter arrives.
+// Then wave 1 for every target: present when k runs (p >= k), dependent on
+// an undecided switch (p < k, or an earlier inserter q < k), or free.  Edge
+// ids with a dependency get an entry {p, q} for the later waves, whose index
+// replaces aux[s].  Slots are probed from the low bits of the id's hash,
+// which the tuple carries.
 struct GroupSmem {
-  unsigned long long *gk;
-  uint32_t *gp, *gq, *gc;
-  uint16_t *used;  // slots claimed in the current partition
+  uint4 *slot;
+  uint32_t *aux;
 };
 
 __device__ __forceinline__ GroupSmem group_smem(uint32_t S) {
-  extern __shared__ unsigned long long group_dyn[];
+  extern __shared__ uint4 group_dyn[];
   GroupSmem g;
-  g.gk = group_dyn;
-  g.gp = reinterpret_cast<uint32_t *>(g.gk + S);
-  g.gq = g.gp + S;
-  g.gc = g.gq + S;
-  g.used = reinterpret_cast<uint16_t *>(g.gc + S);
+  g.slot = group_dyn;
+  g.aux = reinterpret_cast<uint32_t *>(group_dyn + S);
   return g;
 }
 
-__device__ __forceinline__ void group_reset_slot(const GroupSmem &g, uint32_t s) {
-  g.gk[s] = kEmptyKey;
-  g.gp[s] = kPNone;
-  g.gq[s] = kQNone;
-  g.gc[s] = 0;
+__device__ __forceinline__ unsigned long long *slot_key(const GroupSmem &g, uint32_t s) {
+  return reinterpret_cast<unsigned long long *>(&g.slot[s]);
 }
 
-// Insert one tuple; returns its slot, or S if the table is full.  A slot
-// claimed here is appended to the used list.
-__device__ __forceinline__ uint32_t group_insert(const GroupSmem &g, uint32_t S, unsigned long long key,
-                                                 unsigned long long h, uint32_t v, uint32_t *nused) {
-  uint32_t s = (uint32_t)h & (S - 1), n = 0;
+__device__ __forceinline__ void group_reset_slot(const GroupSmem &g, uint32_t s) {
+  g.slot[s] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, kPNone, kQNone);
+  g.aux[s] = 0;
+}
+
+constexpr uint32_t kClaimed = 0x80000000u;  // slot result: this thread took the slot
+
+// Insert one tuple; returns its slot (| kClaimed if this thread took the
+// empty slot), or S if the table is full.
+__device__ __forceinline__ uint32_t group_insert(const GroupSmem &g, uint32_t S, unsigned long long key, uint32_t h,
+                                                 uint32_t v) {
+  uint32_t s = h & (S - 1), n = 0, claimed = 0;
   for (; n < S; ++n) {
-    const unsigned long long cur = g.gk[s];
+    const unsigned long long cur = *slot_key(g, s);
     if (cur == key) break;
     if (cur == kEmptyKey) {
-      const unsigned long long prev = atomicCAS(&g.gk[s], kEmptyKey, key);
+      const unsigned long long prev = atomicCAS(slot_key(g, s), kEmptyKey, key);
       if (prev == kEmptyKey) {
-        g.used[atomicAdd(nused, 1u)] = (uint16_t)s;
+        claimed = kClaimed;
         break;
       }
       if (prev == key) break;
@@ -671,65 +682,62 @@ __device__ __forceinline__ uint32_t group_insert(const GroupSmem &g, uint32_t S,
   if (n == S) return S;
   if (v & kTupleSource) {
     const uint32_t kk = v & kTupleK;
-    g.gp[s] = kk == kKeepK ? kPKeep : kk;  // one source per edge id (Obs. 2)
-  } else {
-    atomicMin(&g.gq[s], v & kTupleK);
-    atomicAdd(&g.gc[s], 1u);
+    g.slot[s].z = kk == kKeepK ? kPKeep : kk;  // one source per edge id (Obs. 2)
+  } else if (atomicMin(&g.slot[s].w, v & kTupleK) != kQNone) {
+    g.aux[s] = 1;  // a second inserter
   }
-  return s;
+  return s | claimed;
 }
 
 // One dependency entry per edge id that some target depends on: an id
 // inserted more than once, or inserted while in E at the round start.
-// gc[s] is replaced by the entry index (kTrivial if none).
+// aux[s] is replaced by the entry index (kTrivial if none).
 __device__ __forceinline__ void group_alloc(const RoundArgs &a, const GroupSmem &g, uint32_t s) {
-  const bool need = g.gc[s] >= 2 || (g.gc[s] >= 1 && g.gp[s] != kPNone);
+  const uint32_t p = g.slot[s].z, q = g.slot[s].w;
+  const bool need = q != kQNone && (g.aux[s] != 0 || p != kPNone);
   uint32_t idx = kTrivial;
   if (need) {
     idx = atomicAdd(&a.ctl->dep_count, 1u);
     if (idx < a.dep_cap) {
-      a.dep[idx] = make_uint2(g.gp[s], g.gq[s]);
+      a.dep[idx] = make_uint2(p, q);
     } else {
       idx = kTrivial;
       atomicOr(&a.ctl->err, kErrRecord);
     }
   }
-  g.gc[s] = idx;
+  g.aux[s] = idx;
 }
 
 // Wave 1 for target tuple v in slot s.
 __device__ __forceinline__ void group_decide(const RoundArgs &a, const GroupSmem &g, uint32_t s, uint32_t v) {
   const uint32_t k = v & kTupleK;
-  const uint32_t p = g.gp[s], q = g.gq[s];
+  const uint32_t p = g.slot[s].z, q = g.slot[s].w;
   if (p != kPNone && p >= k) atomicOr(&a.word[k], kFlagBad);       // present when k runs
   else if (p != kPNone || q != k) atomicOr(&a.word[k], kFlagDep);  // erased or inserted earlier, maybe
-  const uint32_t d = g.gc[s];
+  const uint32_t d = g.aux[s];
   if (d != kTrivial) {
     if (v & kTupleWhich) a.sw[k].y = d;
     else a.sw[k].x = d;
   }
 }
 
-constexpr int kGroupR = 8;  // tuples a thread holds in registers on the fast path
+constexpr int kGroupR = 4;  // tuples a thread holds in registers on the fast path
 
 // Persistent CTAs over the partitions.  Fast path: the partition's tuples
-// stay in registers and only the claimed slots are visited and cleared.
-// Partitions with more tuples than fit, or more distinct ids than slots,
-// take the sub-pass path: the ids whose hash bits 32.. select them, split
-// further until each sub-pass fits.
-__global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
+// stay in registers, and each thread later visits and clears the slots it
+// claimed.  Partitions with more tuples than fit, or more distinct ids than
+// slots, take the sub-pass path: the ids whose hash bits 16.. select them,
+// split further until each sub-pass fits.
+__global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) {
   const uint32_t S = 1u << a.group_log2;
   const GroupSmem g = group_smem(S);
   __shared__ uint32_t stk_sub[64], stk_n[64];
   __shared__ int stk_top;
-  __shared__ uint32_t overflow, nused;
+  __shared__ uint32_t overflow;
   const int tid = threadIdx.x;
   const bool ovf = a.ctl->ovf_count != 0;
   for (uint32_t s = tid; s < S; s += kGroupThreads) group_reset_slot(g, s);
-  if (tid == 0) {
-    nused = 0;
-    overflow = 0;
-  }
+  if (tid == 0) overflow = 0;
   __syncthreads();
   for (uint32_t part = blockIdx.x; part < a.part_hw; part += gridDim.x) {
     const uint32_t c = a.owner_part[part];
@@ -754,34 +762,32 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
         const uint32_t t = tid + j * kGroupThreads;
         slot[j] = S;
         if (t < ntup) {
-          const unsigned long long key = ((unsigned long long)r[j].y << 32) | r[j].x;
-          slot[j] = group_insert(g, S, key, mix64(key), r[j].z, &nused);
+          slot[j] = group_insert(g, S, ((unsigned long long)r[j].y << 32) | r[j].x, r[j].w, r[j].z);
           if (slot[j] == S) overflow = 1;
         }
       }
       __syncthreads();
       const bool full = overflow != 0;
       if (!full) {
-        for (uint32_t u = tid; u < nused; u += kGroupThreads) group_alloc(a, g, g.used[u]);
+#pragma unroll
+        for (int j = 0; j < kGroupR; ++j)
+          if (slot[j] != S && (slot[j] & kClaimed)) group_alloc(a, g, slot[j] & ~kClaimed);
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kGroupR; ++j) {
-          const uint32_t t = tid + j * kGroupThreads;
-          if (t < ntup && !(r[j].z & kTupleSource)) group_decide(a, g, slot[j], r[j].z);
-        }
+        for (int j = 0; j < kGroupR; ++j)
+          if (slot[j] != S && !(r[j].z & kTupleSource)) group_decide(a, g, slot[j] & ~kClaimed, r[j].z);
       }
       __syncthreads();
-      for (uint32_t u = tid; u < nused; u += kGroupThreads) group_reset_slot(g, g.used[u]);
-      __syncthreads();
-      if (tid == 0) {
-        nused = 0;
-        overflow = 0;
-      }
+#pragma unroll
+      for (int j = 0; j < kGroupR; ++j)
+        if (slot[j] != S && (slot[j] & kClaimed)) group_reset_slot(g, slot[j] & ~kClaimed);
+      if (tid == 0) overflow = 0;
       __syncthreads();
       if (!full) continue;
     }
     // sub-pass path
     if (tid == 0) {
+      atomicAdd(&a.st->subpass_partitions, 1ull);
       stk_top = 1;
       stk_sub[0] = 0;
       stk_n[0] = 1;
@@ -793,16 +799,13 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
       if (tid == 0) {
         --stk_top;
         overflow = 0;
-        nused = 0;
       }
       for (uint32_t s = tid; s < S; s += kGroupThreads) group_reset_slot(g, s);
       __syncthreads();
       for (uint32_t t = tid; t < ntup; t += kGroupThreads) {
         const uint4 r = t < nprim ? prim[t] : a.stup[obeg + (t - nprim)];
-        const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
-        const unsigned long long h = mix64(key);
-        if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
-        if (group_insert(g, S, key, h, r.z, &nused) == S) overflow = 1;
+        if (ns > 1 && ((r.w >> 16) & (ns - 1)) != sub) continue;
+        if (group_insert(g, S, ((unsigned long long)r.y << 32) | r.x, r.w, r.z) == S) overflow = 1;
       }
       __syncthreads();
       if (overflow) {
@@ -820,27 +823,23 @@ __global__ void __launch_bounds__(kGroupThreads) k_group(RoundArgs a) {
         __syncthreads();
         continue;
       }
-      for (uint32_t u = tid; u < nused; u += kGroupThreads) group_alloc(a, g, g.used[u]);
+      for (uint32_t s = tid; s < S; s += kGroupThreads)
+        if (*slot_key(g, s) != kEmptyKey) group_alloc(a, g, s);
       __syncthreads();
       for (uint32_t t = tid; t < ntup; t += kGroupThreads) {
         const uint4 r = t < nprim ? prim[t] : a.stup[obeg + (t - nprim)];
         if (r.z & kTupleSource) continue;
+        if (ns > 1 && ((r.w >> 16) & (ns - 1)) != sub) continue;
         const unsigned long long key = ((unsigned long long)r.y << 32) | r.x;
-        const unsigned long long h = mix64(key);
-        if (ns > 1 && (uint32_t)((h >> 32) & (ns - 1)) != sub) continue;
-        uint32_t s = (uint32_t)h & (S - 1);
-        for (uint32_t n = 0; n < S && g.gk[s] != key; ++n) s = (s + 1) & (S - 1);
+        uint32_t s = r.w & (S - 1);
+        for (uint32_t n = 0; n < S && *slot_key(g, s) != key; ++n) s = (s + 1) & (S - 1);
         group_decide(a, g, s, r.z);
       }
       __syncthreads();
     }
     // leave the table empty for the next partition
     for (uint32_t s = tid; s < S; s += kGroupThreads) group_reset_slot(g, s);
-    __syncthreads();
-    if (tid == 0) {
-      nused = 0;
-      overflow = 0;
-    }
+    if (tid == 0) overflow = 0;
     __syncthreads();
   }
 }
@@ -957,6 +956,7 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
       a.st->wave_hist[waves < kWaveHist ? waves : kWaveHist - 1] += 1;
     }
     a.st->last_pending[1] = a.switch_hw;
+    a.st->overflow_tuples += a.ctl->ovf_count;
     for (uint32_t w = wave; w < kWaveHist; ++w) a.st->last_pending[w] = 0;
     a.ctl->pool_round += 1;
   }

@@ -69,12 +69,16 @@ class GesmcStats(ctypes.Structure):
         ("waves_max", ctypes.c_uint64),
         ("wave_hist", ctypes.c_uint64 * WAVE_HIST),
         ("last_round_pending", ctypes.c_uint64 * WAVE_HIST),
+        ("overflow_tuples", ctypes.c_uint64),
+        ("subpass_partitions", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
         d = {f: int(getattr(self, f)) for f, _ in self._fields_[:11]}
         d["wave_hist"] = [int(x) for x in self.wave_hist]
         d["last_round_pending"] = [int(x) for x in self.last_round_pending]
+        d["overflow_tuples"] = int(self.overflow_tuples)
+        d["subpass_partitions"] = int(self.subpass_partitions)
         return d
 
 
@@ -329,7 +333,7 @@ def gesmc_run_noalloc(edges, n: int, global_switches: int, seed: int, start_roun
     return edges
 
 
-RANDOM_LOAD, RANDOM_STORE, RANDOM_CAS = 0, 1, 2
+RANDOM_LOAD, RANDOM_STORE, RANDOM_CAS, RANDOM_ATOMIC_ADD, RANDOM_RED = 0, 1, 2, 3, 4
 
 
 def gesmc_probe_random_access(nbytes: int, kind: int, accesses: int) -> float:

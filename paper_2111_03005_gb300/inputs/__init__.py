@@ -212,3 +212,14 @@ def request_graph(m_target: int, seed: int) -> tuple[np.ndarray, int]:
         n = max(16, int(round(2.0 * m_target / pld_mean_degree(gamma, 1, dmax))))
     dmax = max(1, min(n - 1, int(n ** (1.0 / (gamma - 1.0)))))
     return graphical_pld_graph(n, gamma, dmax, int(rng.integers(0, 2**62))), n
+
+
+def double_star(k: int, seed: int) -> tuple[np.ndarray, int]:
+    """Hubs 0 and 1 with k leaves each (leaves 2..k+1 on hub 0, k+2..2k+1 on
+    hub 1), in a seeded random list order.  About a quarter of the switches
+    of a round pair a hub-0 edge with a hub-1 edge in the orientation that
+    proposes the edge {0, 1}, so that one edge id collects thousands of
+    insert tuples: the case that fills a dependency partition."""
+    a = np.concatenate([np.zeros(k, np.uint64), np.ones(k, np.uint64)])
+    b = np.arange(2, 2 + 2 * k, dtype=np.uint64)
+    return shuffle_edges((a << np.uint64(32)) | b, seed), 2 + 2 * k

@@ -12,6 +12,12 @@ between rounds
   for them (edges, chain slots and contiguous index ranges: the admission is
   by device-memory footprint, since the pool's memory is fixed).
 
+A step runs as many rounds as every admitted request still needs, at most
+``max_rounds_per_step``: no request leaves earlier, so no queued request
+could have been admitted earlier, and the cap bounds how long a request that
+arrives during a step waits for its admission.  Fewer steps mean fewer host
+synchronisations and longer runs of replayed round graphs.
+
 A request's result does not depend on what else is in the pool: each chain
 draws its permutations from its own seed and round numbers and owns its own
 index ranges, so the result equals a single-chain run with the same inputs.
@@ -44,9 +50,12 @@ class Request:
 
 
 class Server:
-    def __init__(self, max_edges: int, max_chains: int, **pool_opts):
+    def __init__(self, max_edges: int, max_chains: int, max_rounds_per_step: int = 8, **pool_opts):
+        if max_rounds_per_step < 1:
+            raise ValueError("max_rounds_per_step must be at least 1")
         self.pool = gesmc.Pool(max_edges=max_edges, max_chains=max_chains, **pool_opts)
         self._max_edges = max_edges
+        self.max_rounds_per_step = max_rounds_per_step
         self.queue: deque[Request] = deque()
         self.live: dict[int, tuple[Request, int]] = {}  # chain id -> (request, rounds run)
         self.done: list[Request] = []
@@ -88,20 +97,22 @@ class Server:
         self.done.append(req)
 
     def step(self) -> list[Request]:
-        """Admit what fits, run one round for every admitted request, retire
-        the finished ones.  Returns the requests finished in this step."""
+        """Admit what fits, run the same number of rounds (at least one) for
+        every admitted request, retire the finished ones.  Returns the
+        requests finished in this step."""
         before = len(self.done)
         self._admit()
         if self.live:
-            self.pool.run(1)
-            self.rounds_run += 1
+            k = min(self.max_rounds_per_step, min(req.rounds - done for req, done in self.live.values()))
+            self.pool.run(k)
+            self.rounds_run += k
             for cid, (req, done) in list(self.live.items()):
-                self.switches_run += len(req.edges) // 2
-                if done + 1 == req.rounds:
+                self.switches_run += k * (len(req.edges) // 2)
+                if done + k == req.rounds:
                     del self.live[cid]
                     self._retire(cid, req)
                 else:
-                    self.live[cid] = (req, done + 1)
+                    self.live[cid] = (req, done + k)
         return self.done[before:]
 
     def idle(self) -> bool:

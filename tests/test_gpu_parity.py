@@ -102,6 +102,23 @@ def test_perfect_matchings_many_seeds():
         run_and_compare(edges, 2000, seed=seed, rounds=2)
 
 
+def test_one_edge_id_proposed_thousands_of_times():
+    # {0, 1} gets about L/4 insert tuples per round: its partition overflows
+    # (exact overflow path) and holds more tuples than one grouping pass
+    edges, n = inputs.double_star(10000, seed=5)
+    _, st = run_and_compare(edges, n, seed=21, rounds=3)
+    assert st["overflow_tuples"] > 0 and st["subpass_partitions"] > 0
+
+
+@pytest.mark.parametrize("tuple_log2,group_log2", [(8, 10), (10, 11), (12, 10), (13, 13), (16, 12)])
+def test_tuning_does_not_change_the_result(tuple_log2, group_log2):
+    n = 20_000
+    edges = inputs.random_simple_graph(n, 120_001, seed=12)
+    _, st = run_and_compare(edges, n, seed=8, rounds=2, tuple_log2=tuple_log2, group_log2=group_log2)
+    if tuple_log2 - group_log2 >= 2:  # more distinct ids per partition than table slots
+        assert st["subpass_partitions"] > 0
+
+
 def test_laziness():
     edges, n = inputs.workload_gnp_small(seed=2)
     _, st = run_and_compare(edges, n, seed=9, rounds=4, lazy_threshold=1 << 62)

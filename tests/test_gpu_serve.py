@@ -15,7 +15,8 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2111_03005_gb300 import ensemble, gesmc, serve  # noqa: E402
 
 
-def test_served_requests_equal_their_oracle_runs():
+@pytest.mark.parametrize("rounds_per_step", [1, 8])
+def test_served_requests_equal_their_oracle_runs(rounds_per_step):
     rng = np.random.default_rng(3)
     reqs = []
     for rid in range(24):
@@ -25,7 +26,7 @@ def test_served_requests_equal_their_oracle_runs():
                                   start_round=int(rng.integers(0, 5))))
     cap = sum(len(r.edges) for r in reqs) // 3          # not everything fits at once
     cap = max(cap, max(len(r.edges) for r in reqs))
-    with serve.Server(max_edges=cap, max_chains=8) as srv:
+    with serve.Server(max_edges=cap, max_chains=8, max_rounds_per_step=rounds_per_step) as srv:
         arrivals = sorted(rng.integers(0, 30, size=len(reqs)))
         step, nxt = 0, 0
         while nxt < len(reqs) or not srv.idle():
