@@ -337,6 +337,17 @@ def run_gesmc(args):
             "ceiling_per_s": {k: v for k, v in rates.items()},
             "ceiling_sector_GBps": {k: 32 * v / 1e9 for k, v in rates.items()},
         }
+        # the random-access roofline of a global switch: what one round costs a design that
+        # gathers the sources and probes an edge hash set at random, per switch 8 random loads
+        # (2 source gathers, 2 set probes, 2 slot reads, 2 table reads), 2 table atomics,
+        # 6a random writes for an accepted switch (2 set erases, 2 set inserts, 2 list writes)
+        # and about 130 streaming bytes, at this GPU's measured rates
+        a = line["waves"]["accept_rate"]
+        t_switch = (8 / rates["load"] + 2 / rates["cas"] + 6 * a / rates["store"] + 130.0 / (peak * 1e9))
+        line["random_access_roofline"] = {
+            "switches_per_s": 1.0 / t_switch, "frac": value * t_switch,
+            "model": "per switch: 8 random loads + 2 random atomics + 6a random writes + 130 streaming bytes",
+        }
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
@@ -375,7 +386,7 @@ def run_ensemble(args):
     import numpy as np
     import torch
 
-    from paper_2111_03005_gb300 import ensemble, gesmc, inputs
+    from paper_2111_03005_gb300 import autotune, ensemble, gesmc, inputs
 
     torch.cuda.set_device(0)
     count, rounds = args.chains, 50
@@ -383,8 +394,16 @@ def run_ensemble(args):
     seeds = [5000 + t for t in range(count)]
     total = sum(len(e) for e, _ in graphs)
     L_total = sum(len(e) // 2 for e, _ in graphs)
+    layout, tuning = {}, None
+    if not args.no_autotune:
+        # partition size and table load factor timed on a sample of the ensemble itself
+        t_tune = time.perf_counter()
+        tuning = autotune.tune(graphs, seeds, rounds=3, cache=autotune.TuneCache(args.tune_cache),
+                               problem=(total, count), sample_chains=512)
+        tuning["tuning_s"] = time.perf_counter() - t_tune
+        layout = {"tuple_log2": tuning["tuple_log2"], "group_log2": tuning["group_log2"]}
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream), gesmc.Pool(max_edges=total, max_chains=count, stream=stream) as pool:
+    with torch.cuda.stream(stream), gesmc.Pool(max_edges=total, max_chains=count, stream=stream, **layout) as pool:
         t0 = time.perf_counter()
         ids = [pool.add(e, n=n, seed=s) for (e, n), s in zip(graphs, seeds)]
         add_s = time.perf_counter() - t0
@@ -401,6 +420,11 @@ def run_ensemble(args):
             torch.cuda.synchronize()
         ms = start.elapsed_time(stop)
         st = pool.stats()
+        # one more step, untimed, with CUDA events between the stages of every round
+        pool.set_profiling(True)
+        pool.run(rounds)
+        stage_ms, prof_rounds = pool.stage_times()
+        pool.set_profiling(False)
         del ids
     value = args.steps * rounds * L_total / (ms / 1e3)
     # the per-graph alternative on a sample, and bit-exactness of the two
@@ -413,7 +437,7 @@ def run_ensemble(args):
     alone = ensemble.run_one_by_one(sub, sub_seeds, rounds)
     torch.cuda.synchronize()
     one_by_one_s = time.perf_counter() - t0
-    pooled = ensemble.run_pool(sub, sub_seeds, rounds)
+    pooled = ensemble.run_pool(sub, sub_seeds, rounds, **layout)
     L_sub = sum(len(e) // 2 for e, _ in sub)
     per_graph = rounds * L_sub / one_by_one_s
     line = {
@@ -427,6 +451,8 @@ def run_ensemble(args):
                    "parallelism": "single GPU"},
         "per_graph_handles": {"value": per_graph, "unit": UNIT, "sample_chains": len(sample),
                               "includes": "create + run + edges per graph, one after another"},
+        "autotune": tuning,
+        "stages_ms_per_round": {k: round(v / max(prof_rounds, 1), 4) for k, v in stage_ms.items()},
         "speedup_vs_per_graph": value / per_graph,
         "identical_results_on_sample": ensemble.same_results(pooled, alone),
         "pool_add_s": add_s,
@@ -439,7 +465,11 @@ def run_ensemble(args):
 
 
 def run_serve(args):
-    """A Poisson stream of sampling requests served by continuous batching."""
+    """A Poisson stream of sampling requests served by continuous batching,
+    at each arrival rate of --rates (requests/s), one JSON line per rate.
+    The mean request is about 1.9e7 switches, so about 95 requests/s
+    saturate the GPU; the defaults are 0.5x and 0.8x of that and an
+    overload burst."""
     import numpy as np
     import torch
 
@@ -447,70 +477,79 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     rng = np.random.default_rng(17)
-    reqs = []
+    base = []
     for rid in range(args.requests):
         m_target = int(np.exp(rng.uniform(np.log(1e3), np.log(1e7))))
         e, n = inputs.request_graph(m_target, seed=rid)
-        reqs.append(serve.Request(rid=rid, edges=e, n=n, seed=100 + rid, rounds=int(rng.integers(10, 101))))
-    gaps = rng.exponential(1.0 / args.rate, size=len(reqs))
-    offsets = np.cumsum(gaps) - gaps[0]
-    work = sum(r.rounds * (len(r.edges) // 2) for r in reqs)
-    cap = max(args.pool_edges, max(len(r.edges) for r in reqs))
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
-                                                     max_rounds_per_step=args.rounds_per_step, stream=stream) as srv:
-        # warm the kernels once (a small request, not counted)
-        w = serve.Request(rid=-1, edges=reqs[0].edges, n=reqs[0].n, seed=1, rounds=3)
-        srv.submit(w)
-        while not srv.idle():
-            srv.step()
-        srv.done.clear()
-        t0 = time.perf_counter()
-        nxt = 0
-        while nxt < len(reqs) or not srv.idle():
-            now = time.perf_counter() - t0
-            while nxt < len(reqs) and offsets[nxt] <= now:
-                srv.submit(reqs[nxt], now=t0 + offsets[nxt])
-                nxt += 1
-            if srv.idle():
-                time.sleep(max(0.0, min(0.01, offsets[nxt] - now)) if nxt < len(reqs) else 0)
-                continue
-            srv.step()
-        wall = time.perf_counter() - t0
-    lat = np.array([r.finished - r.arrival for r in reqs])
-    # the plain alternative: one handle per request, first come first served
-    svc = []
-    for r in reqs:
+        base.append((e, n, 100 + rid, int(rng.integers(10, 101))))
+    unit_gaps = rng.exponential(1.0, size=len(base))
+    work = sum(r * (len(e) // 2) for e, _, _, r in base)
+    cap = max(args.pool_edges, max(len(e) for e, _, _, _ in base))
+    # the plain alternative: one handle per request, first come first served (service times
+    # do not depend on the arrival rate)
+    svc, alone = [], []
+    for e, n, seed, rounds in base:
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        with gesmc.Chain(r.edges, n=r.n) as c:
-            c.run(r.rounds, r.seed)
-            out = c.edges()
+        with gesmc.Chain(e, n=n) as c:
+            c.run(rounds, seed)
+            alone.append(c.edges())
         svc.append(time.perf_counter() - t1)
-        assert np.array_equal(out, r.result), f"request {r.rid}: served result differs from its single run"
-    finish, free_at = [], 0.0
-    for off, d in zip(offsets, svc):
-        free_at = max(free_at, off) + d
-        finish.append(free_at - off)
-    fifo = np.array(finish)
-    line = {
-        "metric": "sampling service: aggregate edge switches/sec with continuous batching",
-        "value": work / wall, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 1,
-        "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {args.rate}/s, power-law graphs with "
-                               f"m log-uniform in [1e3, 1e7], 10-100 global switches each",
-                   "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work,
-                   "max_rounds_per_step": args.rounds_per_step},
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "max": float(lat.max())},
-        "per_request_handles_fifo": {"value": work / (max(o + f for o, f in zip(offsets, finish))),
-                                     "latency_s": {"p50": float(np.percentile(fifo, 50)),
-                                                   "p99": float(np.percentile(fifo, 99))}},
-        "identical_to_single_runs": True,
-        "rounds_run": srv.rounds_run,
-    }
-    print(json.dumps(line), flush=True)
+    stream = torch.cuda.Stream()
+    for rate in [float(x) for x in args.rates.split(",")]:
+        reqs = [serve.Request(rid=rid, edges=e, n=n, seed=seed, rounds=rounds)
+                for rid, (e, n, seed, rounds) in enumerate(base)]
+        offsets = (np.cumsum(unit_gaps) - unit_gaps[0]) / rate
+        with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
+                                                     max_rounds_per_step=args.rounds_per_step,
+                                                     stream=stream) as srv:
+            # warm the kernels once (a small request, not counted)
+            srv.submit(serve.Request(rid=-1, edges=reqs[0].edges, n=reqs[0].n, seed=1, rounds=3))
+            while not srv.idle():
+                srv.step()
+            srv.done.clear()
+            t0 = time.perf_counter()
+            nxt = 0
+            while nxt < len(reqs) or not srv.idle():
+                now = time.perf_counter() - t0
+                while nxt < len(reqs) and offsets[nxt] <= now:
+                    srv.submit(reqs[nxt], now=t0 + offsets[nxt])
+                    nxt += 1
+                if srv.idle():
+                    time.sleep(max(0.0, min(0.01, offsets[nxt] - now)) if nxt < len(reqs) else 0)
+                    continue
+                srv.step()
+            wall = time.perf_counter() - t0
+            rounds_run = srv.rounds_run
+        for r, out in zip(reqs, alone):
+            assert np.array_equal(out, r.result), f"request {r.rid}: served result differs from its single run"
+        lat = np.array([r.finished - r.arrival for r in reqs])
+        small = np.array([len(r.edges) <= 100_000 for r in reqs])
+        finish, free_at = [], 0.0
+        for off, d in zip(offsets, svc):
+            free_at = max(free_at, off) + d
+            finish.append(free_at - off)
+        fifo = np.array(finish)
+        line = {
+            "metric": "sampling service: aggregate edge switches/sec with continuous batching",
+            "value": work / wall, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 1,
+            "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {rate}/s, power-law graphs with "
+                                   f"m log-uniform in [1e3, 1e7], 10-100 global switches each",
+                       "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work,
+                       "max_rounds_per_step": args.rounds_per_step},
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max()),
+                          "p50_small_requests": float(np.percentile(lat[small], 50)) if small.any() else None},
+            "per_request_handles_fifo": {
+                "value": work / (max(o + f for o, f in zip(offsets, finish))),
+                "latency_s": {"p50": float(np.percentile(fifo, 50)), "p99": float(np.percentile(fifo, 99)),
+                              "p50_small_requests": float(np.percentile(fifo[small], 50)) if small.any() else None}},
+            "identical_to_single_runs": True,
+            "rounds_run": rounds_run,
+        }
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -525,7 +564,7 @@ def main(argv=None):
     ap.add_argument("--chains", type=int, default=4096, help="ensemble: chains")
     ap.add_argument("--sample", type=int, default=256, help="ensemble: chains run one by one for comparison")
     ap.add_argument("--requests", type=int, default=128, help="serve: requests")
-    ap.add_argument("--rate", type=float, default=400.0, help="serve: arrivals per second")
+    ap.add_argument("--rates", default="48,76,400", help="serve: arrival rates (requests/s), comma-separated")
     ap.add_argument("--pool-edges", type=int, default=40_000_000, help="serve: pool capacity in edges")
     ap.add_argument("--pool-chains", type=int, default=256, help="serve: pool capacity in chains")
     ap.add_argument("--rounds-per-step", type=int, default=8, help="serve: most rounds between admissions")
@@ -533,6 +572,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")
     ap.add_argument("--tuple-log2", type=int, default=0, help="tuning: mean tuples per partition (log2)")
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble: default layout, no tuning")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file")
     ap.add_argument("--group-log2", type=int, default=0, help="tuning: grouping table slots (log2)")
     ap.add_argument("--cpu-sample", choices=sorted(WORKLOADS), default=CPU_SAMPLE,
                     help="workload of the CPU (oracle) legs")

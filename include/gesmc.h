@@ -147,8 +147,12 @@ int gesmc_reset_stats(gesmc_t h);
  * gesmc_reset_stats) of the first n_stages stages into ms and the number of
  * profiled rounds into *rounds.  Stage i is named by gesmc_stage_name(i);
  * GESMC_NUM_STAGES stages exist, in launch order, each one kernel except
- * "overflow" (three kernels that return at once when nothing overflowed). */
-#define GESMC_NUM_STAGES 9
+ * "overflow" (three kernels that return at once when nothing overflowed)
+ * and "waves" (a pair of kernels per wave after the first, run on the whole
+ * GPU; as many pairs as the handle's rounds have needed extra waves so far,
+ * at most 8, none while every round needed one wave; "tail" runs any waves
+ * beyond those on one CTA). */
+#define GESMC_NUM_STAGES 10
 int gesmc_set_profiling(gesmc_t h, int enable);
 int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds);
 const char *gesmc_stage_name(int stage);

@@ -1,6 +1,7 @@
 // C ABI of libgesmc (declared in include/gesmc.h): pools of chains, the
 // single-chain handle built on a one-chain pool, the allocation-free entry
 // point, and the round loop of Algorithm 3 (ParGlobalES) of arXiv 2111.03005.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <iterator>
@@ -226,6 +227,7 @@ struct gesmc_pool_ctx {
   int broken = 0;
   RoundArgs args;
   uint64_t args_version = 1;  // bumped whenever args change (invalidates the graph)
+  uint32_t wave_kernels = 0;  // whole-GPU wave kernel pairs per round (grows with the waves seen)
   // captured round (CUDA graph), replayed on gstream
   bool use_graphs = true;
   cudaStream_t gstream = nullptr;
@@ -270,6 +272,7 @@ void refresh_args(gesmc_pool_t p) {
   a.bucket_hw = (uint32_t)p->buckets.high_water();
   a.part_hw = (uint32_t)p->parts.high_water();
   a.any_work = p->working_chains > 0;
+  a.wave_kernels = p->wave_kernels;
 }
 
 // Point the round arguments at the pieces of the pool's memory.
@@ -587,6 +590,12 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
   p->switches_run += rounds * sw;
   const int rc = map_device_errors(ctl.err);
   if (rc != GESMC_OK) p->broken = rc;
+  // rounds that needed more than one wave: run that many on the whole GPU from now on
+  const uint32_t want = ctl.waves > 1 ? std::min<uint32_t>(ctl.waves - 1, kMaxWaveKernels) : 0u;
+  if (rc == GESMC_OK && want > p->wave_kernels) {
+    p->wave_kernels = want;
+    refresh_args(p);
+  }
   return rc;
 }
 
@@ -919,7 +928,7 @@ int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
 
 const char *gesmc_stage_name(int stage) {
   static const char *names[kNumStages] = {"clear",    "permute", "scan_perm", "sortpair", "boundary",
-                                          "overflow", "group",   "wave1",     "tail"};
+                                          "overflow", "group",   "wave1", "waves",     "tail"};
   return (stage >= 0 && stage < kNumStages) ? names[stage] : "";
 }
 

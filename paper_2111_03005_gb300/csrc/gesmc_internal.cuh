@@ -83,6 +83,11 @@ constexpr uint32_t kErrTableFull = 1u, kErrBucket = 2u, kErrWaveCap = 4u, kErrNo
 // The cap bounds the time a faulty input or build can spend in one round.
 constexpr uint32_t kDefaultWaveCap = 10000;
 
+// Waves after the first run on the whole GPU as pairs of kernels (register,
+// decide), as many pairs as the pool's rounds have needed so far, at most
+// kMaxWaveKernels; k_tail runs any remaining waves on one CTA.
+constexpr uint32_t kMaxWaveKernels = 8;
+
 // Permutation buckets: a chain's positions go to 2^B buckets by the top B
 // bits of their key (about 2^kPermAvgLog2 per bucket, at most
 // kPermBucketCap), and each bucket is sorted in shared memory by one CTA.
@@ -125,7 +130,9 @@ struct Counters {
   uint32_t waves;       // waves the last round needed
   uint32_t dep_count;   // dependency entries allocated this round
   uint32_t ovf_count;   // tuples that did not fit their partition
-  uint32_t pad;
+  uint32_t cur;         // list (0 or 1) holding the undecided switches of the next wave
+  uint32_t wave_next;   // number of the next wave
+  uint32_t wave_blocks; // CTAs of the running wave kernel that have finished
   unsigned long long pool_round;  // rounds the pool has completed
 };
 
@@ -173,6 +180,7 @@ struct RoundArgs {
   uint32_t group_log2;  // shared-memory grouping table: 2^group_log2 slots
   uint32_t group_grid;  // CTAs of the persistent grouping kernel
   uint32_t any_work;    // some chain has m >= 2
+  uint32_t wave_kernels;  // pairs of whole-GPU wave kernels per round
 };
 
 // Stages of a round, in launch order.
@@ -185,6 +193,7 @@ enum Stage {
   kStageOverflow,
   kStageGroup,
   kStageWave1,
+  kStageWaves,
   kStageTail,
   kNumStages
 };

@@ -24,7 +24,9 @@
 //                    an undecided switch; edge ids with a dependency get an
 //                    entry {p, q} for the later waves
 //   k_wave1          per switch: legal, illegal or pending
-//   k_tail           waves 2, 3, ... over the pending switches
+//   k_wave_register  waves 2, 3, ... over the pending switches on the whole
+//   k_wave_decide    GPU, one pair of kernels per wave
+//   k_tail           any remaining waves, on one CTA
 //
 // The waves are Jacobi steps: a switch decided in wave w only uses decisions
 // of waves < w (status words carry their wave), so the result and the wave
@@ -339,6 +341,9 @@ __global__ void k_clear(RoundArgs a) {
     a.ctl->waves = 0;
     a.ctl->dep_count = 0;
     a.ctl->ovf_count = 0;
+    a.ctl->cur = 0;
+    a.ctl->wave_next = 2;
+    a.ctl->wave_blocks = 0;
   }
 }
 
@@ -844,11 +849,15 @@ __global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) {
   }
 }
 
+// Each CTA takes a contiguous range of switches, so that a thread's running
+// per-chain count changes chain only at chain boundaries.
 __global__ void k_wave1(RoundArgs a) {
   Tally t;
   ChainCount cc;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < a.switch_hw; base += stride) {
+  const uint32_t per = (a.switch_hw + gridDim.x - 1) / gridDim.x;
+  const uint32_t chunk = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const uint32_t beg = min(blockIdx.x * chunk, a.switch_hw), end = min(beg + chunk, a.switch_hw);
+  for (uint32_t base = beg; base < end; base += blockDim.x) {
     const uint32_t k = base + threadIdx.x;
     bool wait = false;
     uint32_t c = kNoChain;
@@ -881,6 +890,81 @@ __global__ void k_wave1(RoundArgs a) {
   flush_count(a, cc);
 }
 
+__device__ __forceinline__ uint32_t wave_cap(const RoundArgs &a) {
+  return a.max_waves ? a.max_waves : kDefaultWaveCap;
+}
+
+// One wave after the first, on the whole GPU.  Registration: every
+// undecided switch becomes an inserter of its targets again (the q fields
+// of illegal minima were cleared); also empties the list of the next wave.
+// Nothing to do once no switch is undecided, or past the wave cap (k_tail
+// reports that).
+__global__ void k_wave_register(RoundArgs a) {
+  const uint32_t cur = a.ctl->cur, wave = a.ctl->wave_next;
+  const uint32_t n = a.ctl->pending[cur];
+  if (n == 0 || wave > wave_cap(a)) return;
+  const uint32_t *in = cur ? a.list1 : a.list0;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+    const uint32_t k = in[idx];
+    const uint2 s = __ldcg(&a.sw[k]);
+    if (s.x != kTrivial) atomicMin(&a.dep[s.x].y, k);
+    if (s.y != kTrivial) atomicMin(&a.dep[s.y].y, k);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl->pending[cur ^ 1] = 0;
+    if (wave < kWaveHist) a.st->last_pending[wave] = n;
+  }
+}
+
+// Decision of the same wave: legal, illegal (dropping it as an inserter),
+// or undecided again (appended to the next wave's list).  The last CTA to
+// finish moves the wave number on and switches lists.
+__global__ void k_wave_decide(RoundArgs a) {
+  __shared__ bool last;
+  const uint32_t cur = a.ctl->cur, wave = a.ctl->wave_next;
+  const uint32_t n = a.ctl->pending[cur];
+  if (n == 0 || wave > wave_cap(a)) return;
+  Tally t;
+  ChainCount cc;
+  const uint32_t *in = cur ? a.list1 : a.list0;
+  uint32_t *out = cur ? a.list0 : a.list1;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const uint32_t idx = base + threadIdx.x;
+    bool wait = false;
+    uint32_t k = 0;
+    if (idx < n) {
+      k = in[idx];
+      const uint2 s = __ldcg(&a.sw[k]);
+      const int r3 = check_target(a, k, s.x, wave);
+      const int r4 = check_target(a, k, s.y, wave);
+      if (r3 == kBad || r4 == kBad) {
+        a.status[k] = (wave << 2) | kIllegal;
+        drop_inserter(a, k, s);
+        ++t.rej_exists;
+      } else if (r3 == kWait || r4 == kWait) {
+        wait = true;
+      } else {
+        a.status[k] = (wave << 2) | kLegal;
+        ++t.accepted;
+        count_accepted(a, cc, a.owner_switch[k]);
+      }
+    }
+    append_if(wait, k, out, &a.ctl->pending[cur ^ 1]);
+  }
+  flush_tally(a, t);
+  flush_count(a, cc);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&a.ctl->wave_blocks, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    a.ctl->wave_blocks = 0;
+    a.ctl->cur = cur ^ 1;
+    a.ctl->wave_next = wave + 1;
+  }
+}
+
 // Waves 2, 3, ... on one CTA: undecided switches re-register as inserters
 // (the q fields of illegal minima were cleared), then decide.  The kernel
 // also closes the pool round (the round counter every chain derives its own
@@ -889,7 +973,7 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
   __shared__ uint32_t s_n;
   Tally t;
   ChainCount cc;
-  uint32_t cur = 0, wave = 2, prev_n = a.switch_hw + 1;
+  uint32_t cur = a.ctl->cur, wave = a.ctl->wave_next, prev_n = a.switch_hw + 1;
   volatile uint32_t *pend = a.ctl->pending;
   for (;;) {
     __syncthreads();
@@ -897,7 +981,7 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
     __syncthreads();
     const uint32_t n = s_n;
     if (n == 0) break;
-    if (wave > (a.max_waves ? a.max_waves : kDefaultWaveCap)) {
+    if (wave > wave_cap(a)) {
       if (threadIdx.x == 0) atomicOr(&a.ctl->err, kErrWaveCap);
       break;
     }
@@ -1095,6 +1179,14 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   }
   mark(kStageWave1);
   if (work) { k_wave1<<<grid_for(a.switch_hw, 256, num_sms, 16), 256, 0, s>>>(a); ++n; }
+  mark(kStageWaves);
+  if (work) {
+    for (uint32_t w = 0; w < a.wave_kernels && w < kMaxWaveKernels; ++w) {
+      k_wave_register<<<num_sms * 4, 256, 0, s>>>(a);
+      k_wave_decide<<<num_sms * 4, 256, 0, s>>>(a);
+      n += 2;
+    }
+  }
   mark(kStageTail);
   k_tail<<<1, 1024, 0, s>>>(a);
   ++n;

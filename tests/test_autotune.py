@@ -1,0 +1,67 @@
+"""Autotuner logic on the CPU: choice, cache, sampling and the agreement check
+(with a fake timer; the GPU timer is exercised in the GPU tests)."""
+import numpy as np
+import pytest
+
+from paper_2111_03005_gb300 import autotune
+
+
+def fake_graphs(k):
+    return [(np.arange(t + 2, dtype=np.uint64), t + 10) for t in range(k)], list(range(100, 100 + k))
+
+
+def test_pick_is_the_fastest_and_ties_keep_candidate_order():
+    assert autotune.pick({(9, 10): 3.0, (10, 11): 1.0, (11, 12): 2.0}) == (10, 11)
+    assert autotune.pick({(9, 10): 1.0, (10, 11): 1.0}) == (9, 10)
+    with pytest.raises(ValueError):
+        autotune.pick({})
+
+
+def test_tune_times_every_candidate_once_and_caches(tmp_path):
+    graphs, seeds = fake_graphs(5)
+    times = {(9, 10): 5.0, (9, 11): 4.0, (10, 11): 2.5, (10, 12): 3.0, (11, 12): 9.0}
+    calls = []
+
+    def timer(g, s, rounds, cand):
+        calls.append(cand)
+        assert rounds == 2 and len(g) == len(s) == 5
+        return times[cand], np.array([1, 2, 3], dtype=np.uint64)
+
+    cache = autotune.TuneCache(str(tmp_path / "tune.json"))
+    got = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=cache, device="dev")
+    assert (got["tuple_log2"], got["group_log2"]) == (10, 11) and not got["cached"]
+    assert calls == list(autotune.CANDIDATES)
+    # a second tuner over the same problem class reads the file and times nothing
+    again = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=autotune.TuneCache(str(tmp_path / "tune.json")),
+                          device="dev")
+    assert again["cached"] and (again["tuple_log2"], again["group_log2"]) == (10, 11)
+    assert len(calls) == len(autotune.CANDIDATES)
+    # another device is another problem class
+    other = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=cache, device="other")
+    assert not other["cached"]
+
+
+def test_tune_rejects_a_candidate_that_changes_the_result():
+    graphs, seeds = fake_graphs(3)
+
+    def timer(g, s, rounds, cand):
+        return 1.0, np.array([0 if cand == (10, 12) else 1], dtype=np.uint64)
+
+    with pytest.raises(RuntimeError):
+        autotune.tune(graphs, seeds, timer=timer, cache=None, device="dev")
+
+
+def test_sample_keeps_order_and_pairs():
+    graphs, seeds = fake_graphs(50)
+    g, s = autotune.sample_graphs(graphs, seeds, 8, rng_seed=1)
+    assert len(g) == len(s) == 8
+    idx = [seeds.index(x) for x in s]
+    assert idx == sorted(idx)
+    assert all(g[k] is graphs[i] for k, i in enumerate(idx))
+    g2, s2 = autotune.sample_graphs(graphs, seeds, 100)
+    assert len(g2) == 50
+
+
+def test_problem_key_rounds_sizes():
+    assert autotune.problem_key("d", 1000, 4096) == autotune.problem_key("d", 1100, 4000)
+    assert autotune.problem_key("d", 1000, 4096) != autotune.problem_key("d", 4000, 4096)

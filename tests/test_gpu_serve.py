@@ -53,3 +53,19 @@ def test_pooled_ensemble_equals_one_handle_per_graph():
     for t in range(0, len(graphs), 7):
         expect, _ = oracle.run(graphs[t][0], seed=seeds[t], rounds=4)
         assert np.array_equal(pooled[t], expect)
+
+
+def test_autotuned_layout_keeps_every_result(tmp_path):
+    from paper_2111_03005_gb300 import autotune
+
+    graphs = inputs.ensemble_graphs(40, seed=12, n_lo=100, n_hi=5000)
+    seeds = [8000 + t for t in range(len(graphs))]
+    cache = autotune.TuneCache(str(tmp_path / "tune.json"))
+    choice = autotune.tune(graphs, seeds, rounds=2, cache=cache)
+    assert (choice["tuple_log2"], choice["group_log2"]) in autotune.CANDIDATES and not choice["cached"]
+    assert autotune.tune(graphs, seeds, rounds=2, cache=cache)["cached"]
+    pooled = ensemble.run_pool(graphs, seeds, rounds=3, tuple_log2=choice["tuple_log2"],
+                               group_log2=choice["group_log2"])
+    for t in range(0, len(graphs), 9):
+        expect, _ = oracle.run(graphs[t][0], seed=seeds[t], rounds=3)
+        assert np.array_equal(pooled[t], expect)
