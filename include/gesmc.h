@@ -63,6 +63,12 @@ enum {
  * launches the kernels one by one instead.  Stage timing always launches
  * them one by one. */
 #define GESMC_FLAG_NO_GRAPHS 1u
+/* Def. 2 as printed: each round draws l ~ Binom(floor(m/2), 1 - P_L) and
+ * runs only its first l switches, l = the number of switches whose laziness
+ * word is >= lazy_threshold.  Without it, each switch is skipped on its own
+ * (word < lazy_threshold), the equivalent per-switch form.  No effect when
+ * lazy_threshold is 0. */
+#define GESMC_FLAG_EXACT_ELL 2u
 
 /* Device allocation hooks: alloc returns device memory usable on `stream`
  * (or NULL on failure); free releases it.  Both NULL: cudaMalloc/cudaFree. */
@@ -248,10 +254,13 @@ int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out);
 void gesmc_pool_destroy(gesmc_pool_t p);
 
 /* Add a chain (a simple graph, validated as in gesmc_create; host or device
- * memory, copied).  Its first round is numbered start_round; *chain_out
- * receives its id (ids of removed chains are reused). */
+ * memory, copied).  Its first round is numbered start_round; flags is 0 or
+ * GESMC_CHAIN_EXACT_ELL (laziness as GESMC_FLAG_EXACT_ELL describes);
+ * *chain_out receives its id (ids of removed chains are reused). */
+#define GESMC_CHAIN_EXACT_ELL 1u
 int gesmc_pool_add(gesmc_pool_t p, const uint64_t *edges, uint64_t m, int edges_on_device, uint64_t n,
-                   uint64_t seed, uint64_t start_round, uint64_t lazy_threshold, uint32_t *chain_out);
+                   uint64_t seed, uint64_t start_round, uint64_t lazy_threshold, uint32_t flags,
+                   uint32_t *chain_out);
 /* Remove a chain (its result should be read first with gesmc_pool_edges). */
 int gesmc_pool_remove(gesmc_pool_t p, uint32_t chain);
 /* Advance every chain of the pool by `global_switches` rounds. */

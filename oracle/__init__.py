@@ -76,7 +76,7 @@ def _load():
     lib.orc_edge_switch.restype = ctypes.c_int
     lib.orc_global_switch.argtypes = [u64p, u64, u32p, u64, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(Stats)]
     lib.orc_global_switch.restype = ctypes.c_int
-    lib.orc_run.argtypes = [u64p, u64, u64, u64, u64, u64, ctypes.c_int, ctypes.POINTER(Stats), u64p]
+    lib.orc_run.argtypes = [u64p, u64, u64, u64, u64, u64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Stats), u64p]
     lib.orc_run.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -161,13 +161,14 @@ def global_switch(edges, pi, ell: int | None = None, skip=None) -> tuple[np.ndar
 
 
 def run(edges, seed: int, rounds: int, start_round: int = 0, lazy_threshold: int = 0,
-        check_every_switch: bool = False, snapshots: bool = False):
+        check_every_switch: bool = False, snapshots: bool = False, exact_ell: bool = False):
     """Algorithm 3, sequentially.  Returns (final list, stats[, per-round lists])."""
     e = _u64(edges)
     m = len(e)
     st = Stats()
     snap = np.zeros((rounds, m), dtype=np.uint64) if snapshots else None
-    code = _load().orc_run(_p64(e), m, seed, start_round, rounds, lazy_threshold, int(check_every_switch),
+    code = _load().orc_run(_p64(e), m, seed, start_round, rounds, lazy_threshold, int(exact_ell),
+                           int(check_every_switch),
                            ctypes.byref(st), _p64(snap) if snap is not None else None)
     if code != 0:
         raise ValueError(f"orc_run failed: {code}")

@@ -29,6 +29,11 @@
 //   * Laziness (Def. 2, P_L): switch k of round r is skipped iff
 //     Philox4x64-10(counter = (k >> 2, r, 1, 0), key = (seed, 0))[k & 3]
 //     < lazy_threshold; the default threshold 0 never skips (P_L = 0).
+//   * Exact l (Def. 2 as printed, optional): the global switch draws
+//     l ~ Binom(floor(m/2), 1 - P_L) and runs its first l switches only.
+//     l is the number of k < floor(m/2) whose laziness word is
+//     >= lazy_threshold (floor(m/2) independent trials, each passing with
+//     probability 1 - P_L), so both implementations draw the same l.
 //   * Rounds are numbered cumulatively, so run(a) then run(b) equals run(a+b).
 //
 // Parity pins live in tests/test_oracle_pins.py (worked example of Fig. 1,
@@ -245,7 +250,7 @@ int orc_global_switch(uint64_t* E, uint64_t m, const uint32_t* pi, uint64_t ell,
 // check_every_switch re-verifies simplicity, |E| = m and the degree sequence
 // after every single switch (slow; for small graphs).
 int orc_run(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_round, uint64_t rounds,
-            uint64_t lazy_threshold, int check_every_switch, orc_stats* st, uint64_t* snapshots) {
+            uint64_t lazy_threshold, int exact_ell, int check_every_switch, orc_stats* st, uint64_t* snapshots) {
   if (E == nullptr && m > 0) return ORC_E_INVALID;
   std::unordered_set<uint64_t> S;
   S.reserve(m * 2 + 1);
@@ -258,9 +263,16 @@ int orc_run(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_round, uint64
   for (uint64_t t = 0; t < rounds; ++t) {
     const uint64_t r = start_round + t;
     orc_permutation(seed, r, m, pi.data());
+    uint64_t ell = L;  // exact l: the number of trials that pass
+    if (exact_ell && lazy_threshold != 0) {
+      ell = 0;
+      for (uint64_t k = 0; k < L; ++k) ell += orc_lazy_word(seed, r, k) >= lazy_threshold ? 1 : 0;
+    }
     for (uint64_t k = 0; k < L; ++k) {
       if (st) ++st->switches;
-      if (lazy_threshold != 0 && orc_lazy_word(seed, r, k) < lazy_threshold) {
+      const bool skipped = exact_ell ? k >= ell
+                                     : lazy_threshold != 0 && orc_lazy_word(seed, r, k) < lazy_threshold;
+      if (skipped) {
         if (st) ++st->lazy;
         continue;
       }

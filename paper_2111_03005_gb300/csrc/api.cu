@@ -69,7 +69,7 @@ Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
 
 // Offsets of the pieces of a pool's single device allocation.
 struct Layout {
-  size_t chains, chain_acc, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
+  size_t chains, chain_acc, chain_ell, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
       pib_pos, pib_edge, bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
       E, ctl, st, scratch, total;
 };
@@ -84,6 +84,7 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   };
   l.chains = take(sizeof(ChainDesc) * C);
   l.chain_acc = take(8 * C);
+  l.chain_ell = take(4 * C);
   l.owner_slot = take(4 * c.slots);
   l.owner_switch = take(4 * c.switches);
   l.owner_bucket = take(4 * c.buckets);
@@ -273,6 +274,14 @@ void refresh_args(gesmc_pool_t p) {
   a.part_hw = (uint32_t)p->parts.high_water();
   a.any_work = p->working_chains > 0;
   a.wave_kernels = p->wave_kernels;
+  a.chain_hw = 0;
+  a.any_exact = 0;
+  for (uint32_t c = 0; c < p->max_chains; ++c) {
+    const HostChain &hc = p->chains[c];
+    if (!hc.live) continue;
+    a.chain_hw = c + 1;
+    if (hc.d.exact_ell && hc.d.lazy_threshold != 0 && hc.d.L > 0) a.any_exact = 1;
+  }
 }
 
 // Point the round arguments at the pieces of the pool's memory.
@@ -283,6 +292,7 @@ void pool_bind(gesmc_pool_t p) {
   std::memset(&a, 0, sizeof(a));
   a.chains = at<ChainDesc>(b, l.chains);
   a.chain_accepted = at<unsigned long long>(b, l.chain_acc);
+  a.chain_ell = at<uint32_t>(b, l.chain_ell);
   a.owner_slot = at<uint32_t>(b, l.owner_slot);
   a.owner_switch = at<uint32_t>(b, l.owner_switch);
   a.owner_bucket = at<uint32_t>(b, l.owner_bucket);
@@ -457,7 +467,8 @@ bool set_owners(gesmc_pool_t p, const HostChain &hc, uint32_t c) {
 // Add a chain whose list is already on the device at E (the pool's staging
 // buffer, or the caller's buffer for the allocation-free path).
 int pool_add_device(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t n, uint64_t seed,
-                    uint64_t start_round, uint64_t lazy_threshold, uint32_t *chain_out) {
+                    uint64_t start_round, uint64_t lazy_threshold, uint32_t flags, uint32_t *chain_out) {
+  if (flags & ~GESMC_CHAIN_EXACT_ELL) return GESMC_E_INVALID;
   if (m > p->max_edges - p->live_edges) return GESMC_E_NOMEM;
   uint32_t c = 0;
   while (c < p->max_chains && p->chains[c].live) ++c;
@@ -480,6 +491,7 @@ int pool_add_device(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t 
   d.join = p->pool_round;
   d.added = p->pool_round;
   d.lazy_threshold = lazy_threshold;
+  d.exact_ell = (flags & GESMC_CHAIN_EXACT_ELL) ? 1u : 0u;
   hc.live = true;
   hc.n = n_eff;
   cudaStream_t s = p->stream;
@@ -682,7 +694,8 @@ int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out) {
 }
 
 int gesmc_pool_add(gesmc_pool_t p, const uint64_t *edges, uint64_t m, int edges_on_device, uint64_t n,
-                   uint64_t seed, uint64_t start_round, uint64_t lazy_threshold, uint32_t *chain_out) {
+                   uint64_t seed, uint64_t start_round, uint64_t lazy_threshold, uint32_t flags,
+                   uint32_t *chain_out) {
   if (!p || !chain_out || (m > 0 && !edges) || m > kMaxEdges || n > (1ull << 32)) return GESMC_E_INVALID;
   if (p->broken) return p->broken;
   if (m > p->max_edges - p->live_edges) return GESMC_E_NOMEM;
@@ -693,7 +706,7 @@ int gesmc_pool_add(gesmc_pool_t p, const uint64_t *edges, uint64_t m, int edges_
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
-  return pool_add_device(p, E, m, n, seed, start_round, lazy_threshold, chain_out);
+  return pool_add_device(p, E, m, n, seed, start_round, lazy_threshold, flags, chain_out);
 }
 
 int gesmc_pool_remove(gesmc_pool_t p, uint32_t chain) {
@@ -873,7 +886,7 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   po.max_waves = o.max_waves;
   po.tuple_log2 = o.tuple_log2;
   po.group_log2 = o.group_log2;
-  po.flags = o.flags;
+  po.flags = o.flags & GESMC_FLAG_NO_GRAPHS;
   po.stream = o.stream;
   po.alloc = o.alloc;
   po.free = o.free;
@@ -883,7 +896,8 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   int rc = gesmc_pool_create(&po, &h->pool);
   // the seed is given to gesmc_run; the chain starts with seed 0
   if (rc == GESMC_OK)
-    rc = gesmc_pool_add(h->pool, edges, m, edges_on_device, o.n, 0, o.start_round, o.lazy_threshold, &h->chain);
+    rc = gesmc_pool_add(h->pool, edges, m, edges_on_device, o.n, 0, o.start_round, o.lazy_threshold,
+                        (o.flags & GESMC_FLAG_EXACT_ELL) ? GESMC_CHAIN_EXACT_ELL : 0u, &h->chain);
   if (rc != GESMC_OK) {
     gesmc_destroy(h);
     return rc;
@@ -1001,7 +1015,7 @@ extern "C" int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64
   rc = pool_init(&p, o);
   uint32_t chain = 0;
   if (rc == GESMC_OK)
-    rc = pool_add_device(&p, reinterpret_cast<unsigned long long *>(edges), m, n, seed, start_round, 0, &chain);
+    rc = pool_add_device(&p, reinterpret_cast<unsigned long long *>(edges), m, n, seed, start_round, 0, 0u, &chain);
   if (rc == GESMC_OK) rc = pool_run(&p, global_switches);
   if (rc == GESMC_OK &&
       (launch_store_chain(p.args, p.chains[chain].d, reinterpret_cast<unsigned long long *>(edges), p.stream,

@@ -119,6 +119,7 @@ struct ChainDesc {
   uint32_t bucket_base, B;    // 2^B permutation buckets from bucket_base
   uint32_t part_base, P;      // 2^P tuple partitions from part_base
   uint32_t tuple_base, capt;  // partition j of the chain holds capt tuples from tuple_base + j * capt
+  uint32_t exact_ell, spare;  // exact l: run only the first l switches (l counted per round)
   unsigned long long seed, start_round, join, added, lazy_threshold;
 };
 
@@ -151,6 +152,7 @@ struct RoundArgs {
   const ChainDesc *chains;
   const uint32_t *owner_slot, *owner_switch, *owner_bucket, *owner_part;
   unsigned long long *chain_accepted;  // per chain
+  uint32_t *chain_ell;                 // per chain: switches that run this round (exact-l chains)
   uint32_t *cpos;
   unsigned long long *cedge;
   uint4 *prec;
@@ -181,6 +183,8 @@ struct RoundArgs {
   uint32_t group_grid;  // CTAs of the persistent grouping kernel
   uint32_t any_work;    // some chain has m >= 2
   uint32_t wave_kernels;  // pairs of whole-GPU wave kernels per round
+  uint32_t chain_hw;      // chain ids in use are below this
+  uint32_t any_exact;     // some chain uses exact l with a nonzero threshold
 };
 
 // Stages of a round, in launch order.

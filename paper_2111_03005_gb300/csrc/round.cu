@@ -145,11 +145,18 @@ __device__ __forceinline__ bool chain_apply(const ChainDesc &ch, unsigned long l
   return pool_round > ch.added;
 }
 
-// Laziness (Def. 2, P_L): switch k (the chain's own index) is skipped iff
-// its Philox word (purpose 1) is below the chain's threshold.
-__device__ __forceinline__ bool is_lazy(const ChainDesc &ch, unsigned long long round, uint32_t k) {
+// Laziness word of switch k (the chain's own index): Philox, purpose 1.
+__device__ __forceinline__ unsigned long long lazy_word(const ChainDesc &ch, unsigned long long round, uint32_t k) {
+  return word_of(philox(k >> 2, round, 1, 0, ch.seed, 0), k & 3);
+}
+
+// Laziness (Def. 2, P_L).  Per-switch form: switch k is skipped iff its word
+// is below the chain's threshold.  Exact l: the round runs its first ell
+// switches only, ell = the number of words that pass (counted beforehand).
+__device__ __forceinline__ bool is_lazy(const ChainDesc &ch, unsigned long long round, uint32_t k, uint32_t ell) {
   if (ch.lazy_threshold == 0) return false;
-  return word_of(philox(k >> 2, round, 1, 0, ch.seed, 0), k & 3) < ch.lazy_threshold;
+  if (ch.exact_ell) return k >= ell;
+  return lazy_word(ch, round, k) < ch.lazy_threshold;
 }
 
 // The values of slots 2k, 2k+1 of a chain at the start of this round: the
@@ -204,10 +211,10 @@ __device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc 
 // switch rejected outright stores its sources as never erased and no
 // targets.
 __device__ __forceinline__ void build_switch(const RoundArgs &a, const ChainDesc &ch, unsigned long long round,
-                                             uint32_t k, uint32_t i, unsigned long long e1, uint32_t j,
-                                             unsigned long long e2) {
+                                             uint32_t ell, uint32_t k, uint32_t i, unsigned long long e1,
+                                             uint32_t j, unsigned long long e2) {
   unsigned long long e3 = kEmptyKey, e4 = kEmptyKey;
-  const uint32_t code = is_lazy(ch, round, k) ? kCodeLazy : tau(i, j, e1, e2, e3, e4);
+  const uint32_t code = is_lazy(ch, round, k, ell) ? kCodeLazy : tau(i, j, e1, e2, e3, e4);
   const uint32_t kg = ch.switch_base + k;
   a.word[kg] = code;
   a.sw[kg] = make_uint2(kTrivial, kTrivial);
@@ -334,6 +341,7 @@ __global__ void k_clear(RoundArgs a) {
     a.tcount[p] = 0;
     a.ocount[p] = 0;
   }
+  for (uint32_t c = tid; c < a.chain_hw; c += nth) a.chain_ell[c] = 0;
   if (tid == 0) {
     a.ctl->pending[0] = 0;
     a.ctl->pending[1] = 0;
@@ -353,6 +361,31 @@ __device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uin
     a.prec[(size_t)b * kPermBucketCap + idx] = make_uint4(keybits, pos, (uint32_t)e, (uint32_t)(e >> 32));
   else
     atomicOr(&a.ctl->err, kErrBucket);
+}
+
+// Exact l (Def. 2 as printed): per chain in that mode, the number of its
+// switches whose laziness word passes (>= threshold); the round then runs
+// the chain's first l switches.  Each CTA takes a contiguous range of
+// switches and each thread keeps a running count for its current chain.
+__global__ void k_lazy_count(RoundArgs a) {
+  const unsigned long long R = a.ctl->pool_round;
+  const uint32_t per = (a.switch_hw + gridDim.x - 1) / gridDim.x;
+  const uint32_t chunk = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const uint32_t beg = min(blockIdx.x * chunk, a.switch_hw), end = min(beg + chunk, a.switch_hw);
+  uint32_t cur = kNoChain, n = 0;
+  for (uint32_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+    const uint32_t c = a.owner_switch[k];
+    if (c == kNoChain) continue;
+    const ChainDesc ch = a.chains[c];
+    if (!ch.exact_ell || ch.lazy_threshold == 0) continue;
+    if (c != cur) {
+      if (n) atomicAdd(&a.chain_ell[cur], n);
+      cur = c;
+      n = 0;
+    }
+    n += lazy_word(ch, chain_round(ch, R), k - ch.switch_base) >= ch.lazy_threshold ? 1u : 0u;
+  }
+  if (n) atomicAdd(&a.chain_ell[cur], n);
 }
 
 // Append every position, with its current edge, to its chain's bucket.
@@ -506,6 +539,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
     if (c == kNoChain) continue;
     const ChainDesc ch = a.chains[c];
     const unsigned long long round = chain_round(ch, R);
+    const uint32_t ell = ch.exact_ell ? a.chain_ell[c] : 0u;
     const uint32_t loff = a.poff[b] - a.poff[ch.bucket_base];  // chain-local slot offset
     const uint32_t goff = ch.slot_base + loff;
     const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
@@ -589,7 +623,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
     const uint32_t npairs = cnt > t0 ? (cnt - t0) >> 1 : 0;
     for (uint32_t p = tid; p < npairs; p += kSortThreads) {
       const uint32_t t = t0 + 2 * p;
-      build_switch(a, ch, round, (loff + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1],
+      build_switch(a, ch, round, ell, (loff + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1],
                    sedge[t + 1]);
     }
     if (tid == 0 && cnt > 0) {
@@ -629,8 +663,8 @@ __global__ void k_boundary(RoundArgs a) {
       atomicOr(&a.ctl->err, kErrRecord);
       continue;
     }
-    build_switch(a, ch, chain_round(ch, R), k, a.pib_pos[g], a.pib_edge[g], a.pib_pos[g + 1],
-                 a.pib_edge[g + 1]);
+    build_switch(a, ch, chain_round(ch, R), ch.exact_ell ? a.chain_ell[c] : 0u, k, a.pib_pos[g], a.pib_edge[g],
+                 a.pib_pos[g + 1], a.pib_edge[g + 1]);
   }
 }
 // Grouping of one tuple partition by edge id (Algorithm 1's table T for the
@@ -1155,6 +1189,7 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   mark(kStageClear);
   k_clear<<<grid_for(a.bucket_hw > a.part_hw ? a.bucket_hw : a.part_hw, 256, num_sms, 4), 256, 0, s>>>(a);
   ++n;
+  if (work && a.any_exact) { k_lazy_count<<<grid_for(a.switch_hw, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStagePermute);
   if (work) { k_permute<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStageScanPerm);

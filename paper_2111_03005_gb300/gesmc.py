@@ -31,6 +31,8 @@ GESMC_E_INTERNAL = -9
 GESMC_E_CAPACITY = -10
 GESMC_E_TOO_LARGE = -11
 FLAG_NO_GRAPHS = 1
+FLAG_EXACT_ELL = 2
+CHAIN_EXACT_ELL = 1
 NOALLOC_MAX_EDGES = 65536
 WAVE_HIST = 64
 
@@ -142,7 +144,7 @@ _SIGNATURES = [
     ("gesmc_pool_destroy", None, [ctypes.c_void_p]),
     ("gesmc_pool_add", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
                                       ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
-                                      ctypes.POINTER(ctypes.c_uint32)]),
+                                      ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     ("gesmc_pool_remove", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     ("gesmc_pool_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("gesmc_pool_edges", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
@@ -232,7 +234,8 @@ def _as_edge_buffer(edges):
 
 
 def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 0, max_waves: int = 0, stream=None,
-                 torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0, graphs: bool = True):
+                 torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0, graphs: bool = True,
+                 exact_ell: bool = False):
     """Create a chain handle; returns (handle, keepalive).  Raises GesmcError."""
     import torch
 
@@ -247,7 +250,7 @@ def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 
     opts.max_waves = max_waves
     opts.tuple_log2 = tuple_log2
     opts.group_log2 = group_log2
-    opts.flags = 0 if graphs else FLAG_NO_GRAPHS
+    opts.flags = (0 if graphs else FLAG_NO_GRAPHS) | (FLAG_EXACT_ELL if exact_ell else 0)
     if stream is None:
         stream = torch.cuda.current_stream()
     opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
@@ -435,11 +438,13 @@ class Pool:
     def device_bytes(max_edges: int, max_chains: int, tuple_log2: int = 0) -> int:
         return int(load_library().gesmc_pool_device_bytes(max_edges, max_chains, tuple_log2))
 
-    def add(self, edges, n: int = 0, seed: int = 0, start_round: int = 0, lazy_threshold: int = 0) -> int:
+    def add(self, edges, n: int = 0, seed: int = 0, start_round: int = 0, lazy_threshold: int = 0,
+            exact_ell: bool = False) -> int:
         ptr, m, on_dev, _keep = _as_edge_buffer(edges)
         cid = ctypes.c_uint32()
         _check(load_library().gesmc_pool_add(self._p, ctypes.c_void_p(ptr), m, on_dev, n, seed, start_round,
-                                             lazy_threshold, ctypes.byref(cid)), "gesmc_pool_add")
+                                             lazy_threshold, CHAIN_EXACT_ELL if exact_ell else 0,
+                                             ctypes.byref(cid)), "gesmc_pool_add")
         return int(cid.value)
 
     def remove(self, chain: int):

@@ -23,14 +23,16 @@ def first_diff(a, b):
     return int(d[0]) if len(d) else -1
 
 
-def run_and_compare(edges, n, seed, rounds, lazy_threshold=0, start_round=0, check_stats=True, **opts):
+def run_and_compare(edges, n, seed, rounds, lazy_threshold=0, start_round=0, check_stats=True, exact_ell=False,
+                    **opts):
     expect = oracle.validate(edges, n)[1]
     totals = {"accepted": 0, "rejected_loop": 0, "rejected_exists": 0, "lazy": 0}
-    with gesmc.Chain(edges, n=n, lazy_threshold=lazy_threshold, start_round=start_round, **opts) as chain:
+    with gesmc.Chain(edges, n=n, lazy_threshold=lazy_threshold, start_round=start_round, exact_ell=exact_ell,
+                     **opts) as chain:
         for r in range(rounds):
             chain.run(1, seed)
             expect, st = oracle.run(expect, seed=seed, rounds=1, start_round=start_round + r,
-                                    lazy_threshold=lazy_threshold)
+                                    lazy_threshold=lazy_threshold, exact_ell=exact_ell)
             for k in totals:
                 totals[k] += st[k]
             got = chain.edges()
@@ -142,6 +144,17 @@ def test_laziness():
     edges, n = inputs.workload_gnp_small(seed=2)
     _, st = run_and_compare(edges, n, seed=9, rounds=4, lazy_threshold=1 << 62)
     assert 0.2 < st["lazy"] / st["switches"] < 0.3
+
+
+@pytest.mark.parametrize("t", [1 << 62, 3 << 62, (1 << 64) - 1])
+def test_exact_ell(t):
+    # Def. 2 as printed: only the first l ~ Binom(L, 1 - P_L) switches run
+    edges = inputs.random_simple_graph(3000, 20_001, seed=14)
+    _, st = run_and_compare(edges, 3000, seed=10, rounds=4, lazy_threshold=t, exact_ell=True)
+    frac = st["lazy"] / st["switches"]
+    assert abs(frac - t / 2**64) < 0.02
+    edges, n = inputs.workload_gnp_small(seed=3)
+    run_and_compare(edges, n, seed=4, rounds=3, lazy_threshold=t, exact_ell=True, graphs=False)
 
 
 def test_input_orientation_is_canonicalised():

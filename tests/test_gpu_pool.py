@@ -41,16 +41,17 @@ def test_every_chain_matches_its_oracle_alone():
         ids, expect, meta = [], [], []
         for t, (e, n) in enumerate(graphs):
             seed, start, lazy = 1000 + 7 * t, 3 * t, (1 << 61) if t % 5 == 0 else 0
-            ids.append(pool.add(e, n=n, seed=seed, start_round=start, lazy_threshold=lazy))
+            exact = t % 10 == 0                   # exact l for half of the lazy chains
+            ids.append(pool.add(e, n=n, seed=seed, start_round=start, lazy_threshold=lazy, exact_ell=exact))
             expect.append(oracle.validate(e, n)[1])
-            meta.append((seed, start, lazy))
+            meta.append((seed, start, lazy, exact))
         done = 0
         for rounds in (1, 3, 2):
             pool.run(rounds)
             for t, c in enumerate(ids):
-                seed, start, lazy = meta[t]
+                seed, start, lazy, exact = meta[t]
                 expect[t], st = oracle.run(expect[t], seed=seed, rounds=rounds, start_round=start + done,
-                                           lazy_threshold=lazy)
+                                           lazy_threshold=lazy, exact_ell=exact)
                 got = pool.edges(c)
                 assert np.array_equal(got, expect[t]), (t, rounds)
             done += rounds

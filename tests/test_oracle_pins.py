@@ -276,3 +276,77 @@ def test_final_graph_uniform_on_gd_chi2():
         e, _ = oracle.run(start, seed=seed + 1000, rounds=rounds)
         counts[index[graph_key(e)]] += 1
     assert chisquare(counts).pvalue > 1e-4
+
+
+# ---------------------------------------------------------------- exact l (Def. 2 as printed)
+
+def _numpy_lazy_words(seed, rnd, L):
+    words = []
+    for b in range((L + 3) // 4):
+        words.extend(int(x) for x in _numpy_philox_block([b, rnd, 1, 0], [seed, 0]))
+    return words[:L]
+
+
+@pytest.mark.parametrize("t", [1 << 62, 1 << 63, (1 << 64) - (1 << 60)])
+def test_exact_ell_runs_the_first_ell_switches(t):
+    # l from numpy's Philox (an independent implementation) and the permutation
+    # from numpy keys; one exact-l round must equal the first l switches of pi
+    e0 = inputs.random_simple_graph(60, 171, seed=5)
+    m, L = len(e0), len(e0) // 2
+    canon = oracle.validate(e0, 60)[1]
+    for seed, rnd in ((3, 0), (11, 4)):
+        ell = sum(w >= t for w in _numpy_lazy_words(seed, rnd, L))
+        keys = np.empty(m, dtype=np.uint64)
+        for b in range((m + 3) // 4):
+            blk = _numpy_philox_block([b, rnd, 0, 0], [seed, 0])
+            for q in range(4):
+                if 4 * b + q < m:
+                    keys[4 * b + q] = blk[q]
+        pi = np.lexsort((np.arange(m), keys)).astype(np.uint32)
+        want, wst = oracle.global_switch(canon, pi, ell=ell)
+        got, st = oracle.run(canon, seed=seed, rounds=1, start_round=rnd, lazy_threshold=t, exact_ell=True)
+        assert np.array_equal(got, want)
+        assert st["lazy"] == L - ell and st["accepted"] == wst["accepted"]
+
+
+def test_exact_ell_without_laziness_is_the_plain_round():
+    e0 = inputs.random_simple_graph(40, 90, seed=2)
+    a, sa = oracle.run(e0, seed=5, rounds=4)
+    b, sb = oracle.run(e0, seed=5, rounds=4, exact_ell=True)
+    assert np.array_equal(a, b) and sa == sb
+
+
+def test_exact_ell_is_binomial():
+    from scipy.stats import binom, chisquare
+    # l over many rounds: Binom(L, 1 - P_L) with P_L = 3/8
+    e0 = inputs.random_simple_graph(30, 24, seed=8)
+    L, pl = 12, 3 / 8
+    t = int(pl * 2**64)
+    counts = np.zeros(L + 1, dtype=np.int64)
+    for seed in range(1500):
+        _, st = oracle.run(e0, seed=seed, rounds=1, lazy_threshold=t, exact_ell=True)
+        counts[L - st["lazy"]] += 1
+    expect = binom.pmf(np.arange(L + 1), L, 1 - pl) * counts.sum()
+    keep = expect >= 5
+    obs = np.append(counts[keep], counts[~keep].sum())
+    exp = np.append(expect[keep], expect[~keep].sum())
+    assert chisquare(obs, exp * obs.sum() / exp.sum()).pvalue > 1e-4
+
+
+def test_transition_matrix_symmetric_with_exact_ell():
+    # Def. 2 as printed: P = sum_l Binom(L, 1 - P_L)(l) * (1/m!) sum_pi T(pi, l); with P_L = 1/2 the
+    # weights are C(L, l) / 2^L, so integer counts weighted by C(L, l) must be symmetric
+    deg = (2, 2, 2, 2, 1, 1)
+    states = enumerate_gd(deg)
+    m = sum(deg) // 2
+    L = m // 2
+    index = {s: t for t, s in enumerate(states)}
+    C = np.zeros((len(states), len(states)), dtype=np.int64)
+    for a, s in enumerate(states):
+        e = P(list(s))
+        for pi in itertools.permutations(range(m)):
+            for ell in range(L + 1):
+                after, _ = oracle.global_switch(e, pi, ell=ell)
+                C[a, index[graph_key(after)]] += math.comb(L, ell)
+    assert (C.sum(axis=1) == math.factorial(m) * 2**L).all()
+    assert np.array_equal(C, C.T)
