@@ -78,6 +78,10 @@ def _load():
     lib.orc_global_switch.restype = ctypes.c_int
     lib.orc_run.argtypes = [u64p, u64, u64, u64, u64, u64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Stats), u64p]
     lib.orc_run.restype = ctypes.c_int
+    lib.orc_es_sample.argtypes = [u64, u64, u64, u64p]
+    lib.orc_es_sample.restype = None
+    lib.orc_es_run.argtypes = [u64p, u64, u64, u64, u64, ctypes.c_int, ctypes.POINTER(Stats)]
+    lib.orc_es_run.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -175,3 +179,22 @@ def run(edges, seed: int, rounds: int, start_round: int = 0, lazy_threshold: int
     if snapshots:
         return e, st.as_dict(), snap
     return e, st.as_dict()
+
+
+def es_sample(seed: int, k: int, m: int) -> tuple[int, int, int]:
+    """ES-MC switch k of a list of m >= 2 edges: (i, j, g)."""
+    out = np.zeros(3, dtype=np.uint64)
+    _load().orc_es_sample(seed, k, m, _p64(out))
+    return int(out[0]), int(out[1]), int(out[2])
+
+
+def es_run(edges, seed: int, switches: int, start_switch: int = 0, check_every_switch: bool = False):
+    """ES-MC sequentially (the chain ParES parallelises).  Returns (final list, stats)."""
+    e = _u64(edges)
+    st = Stats()
+    code = _load().orc_es_run(_p64(e), len(e), seed, start_switch, switches, int(check_every_switch),
+                              ctypes.byref(st))
+    if code != 0:
+        raise ValueError(f"orc_es_run failed: {code}")
+    return e, st.as_dict()
+

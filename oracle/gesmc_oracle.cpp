@@ -18,6 +18,9 @@
 //     sigma_k = (pi(2k-1), pi(2k), 1[pi(2k-1) < pi(2k)]) one after another
 //     (1-based in the paper; 0-based here: pi[2k], pi[2k+1]).
 //   * Algorithm 3 (ParGlobalES): one global switch per round, r rounds.
+//   * ES-MC (Def. 1's chain, the one Algorithm 2, ParES, parallelises): r
+//     independent switches sigma_k = (i, j, g), i != j uniform in [m] and g
+//     a fair bit, one after another.
 //
 // Readings where the paper leaves a choice open (each is listed in the design doc):
 //   * Edges are stored canonically, (min << 32) | max (Sec. 5.2 edge ids;
@@ -35,6 +38,12 @@
 //     >= lazy_threshold (floor(m/2) independent trials, each passing with
 //     probability 1 - P_L), so both implementations draw the same l.
 //   * Rounds are numbered cumulatively, so run(a) then run(b) equals run(a+b).
+//   * ES-MC switch k draws Philox4x64-10(counter = (k, 0, 2, 0),
+//     key = (seed, 0)) = (w0, w1, w2, w3): i = floor(w0 * m / 2^64),
+//     j = j' + [j' >= i] with j' = floor(w1 * (m - 1) / 2^64) (uniform over
+//     [m] minus i), g = the top bit of w2.  Switches are numbered
+//     cumulatively like rounds.  With m < 2 no switch exists; each requested
+//     switch is counted as skipped.
 //
 // Parity pins live in tests/test_oracle_pins.py (worked example of Fig. 1,
 // hand-worked global switches, special graphs, exact transition matrices
@@ -91,6 +100,19 @@ uint64_t philox_word(uint64_t seed, uint64_t round, uint64_t purpose, uint64_t i
 
 const uint64_t kPurposePermutation = 0;
 const uint64_t kPurposeLazy = 1;
+const uint64_t kPurposeEsSwitch = 2;
+
+// ES-MC switch k: (i, j, g) from one Philox block, as stated in the header.
+void es_sample(uint64_t seed, uint64_t k, uint64_t m, uint64_t* i, uint64_t* j, int* g) {
+  const uint64_t ctr[4] = {k, 0, kPurposeEsSwitch, 0};
+  const uint64_t key[2] = {seed, 0};
+  uint64_t w[4];
+  philox4x64_10(ctr, key, w);
+  *i = (uint64_t)(((unsigned __int128)w[0] * m) >> 64);
+  const uint64_t jj = (uint64_t)(((unsigned __int128)w[1] * (m - 1)) >> 64);
+  *j = jj + (jj >= *i ? 1 : 0);
+  *g = (int)(w[2] >> 63);
+}
 
 inline uint64_t pack(uint32_t a, uint32_t b) {
   // canonical id of the undirected edge {a, b}: smaller node in the high half
@@ -282,6 +304,42 @@ int orc_run(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_round, uint64
       if (check_every_switch && !degrees_and_set_ok(E, m, S, deg0)) return ORC_E_INVARIANT;
     }
     if (snapshots) std::memcpy(snapshots + t * m, E, m * sizeof(uint64_t));
+  }
+  return ORC_OK;
+}
+
+// ES-MC switch k of a list of m >= 2 edges: out = {i, j, g}.
+void orc_es_sample(uint64_t seed, uint64_t k, uint64_t m, uint64_t* out) {
+  int g = 0;
+  es_sample(seed, k, m, &out[0], &out[1], &g);
+  out[2] = (uint64_t)g;
+}
+
+// ES-MC run sequentially: switches start_switch, start_switch + 1, ... (the
+// result ParES must reproduce).  E must be a canonical simple edge list.
+int orc_es_run(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_switch, uint64_t switches,
+               int check_every_switch, orc_stats* st) {
+  if (E == nullptr && m > 0) return ORC_E_INVALID;
+  if (m < 2) {
+    if (st) {
+      st->switches += switches;
+      st->lazy += switches;
+    }
+    return ORC_OK;
+  }
+  std::unordered_set<uint64_t> S;
+  S.reserve(m * 2 + 1);
+  for (uint64_t i = 0; i < m; ++i) S.insert(E[i]);
+  if (S.size() != m) return ORC_E_MULTI;
+  std::unordered_map<uint32_t, uint64_t> deg0;
+  if (check_every_switch) deg0 = degree_map(E, m);
+  for (uint64_t k = start_switch; k < start_switch + switches; ++k) {
+    uint64_t i = 0, j = 0;
+    int g = 0;
+    es_sample(seed, k, m, &i, &j, &g);
+    if (st) ++st->switches;
+    count(st, edge_switch(E, S, i, j, g));
+    if (check_every_switch && !degrees_and_set_ok(E, m, S, deg0)) return ORC_E_INVARIANT;
   }
   return ORC_OK;
 }

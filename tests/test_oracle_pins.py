@@ -350,3 +350,86 @@ def test_transition_matrix_symmetric_with_exact_ell():
                 C[a, index[graph_key(after)]] += math.comb(L, ell)
     assert (C.sum(axis=1) == math.factorial(m) * 2**L).all()
     assert np.array_equal(C, C.T)
+
+
+# ---------------------------------------------------------------- ES-MC (the chain of Algorithm 2, ParES)
+
+def _numpy_es_sample(seed, k, m):
+    w = [int(x) for x in _numpy_philox_block([k, 0, 2, 0], [seed, 0])]
+    i = (w[0] * m) >> 64
+    jj = (w[1] * (m - 1)) >> 64
+    return i, jj + (1 if jj >= i else 0), w[2] >> 63
+
+
+def test_es_sample_matches_numpy_philox():
+    for seed, k, m in ((0, 0, 2), (7, 12345, 1000), (2**64 - 1, 2**40, 134198120), (5, 3, 3)):
+        assert oracle.es_sample(seed, k, m) == _numpy_es_sample(seed, k, m)
+        i, j, g = oracle.es_sample(seed, k, m)
+        assert 0 <= i < m and 0 <= j < m and i != j and g in (0, 1)
+
+
+def test_es_run_is_the_sampled_switches_in_order():
+    e0 = oracle.validate(inputs.random_simple_graph(40, 70, seed=6), 40)[1]
+    want = e0.copy()
+    acc = 0
+    for k in range(5, 5 + 300):
+        i, j, g = _numpy_es_sample(11, k, len(e0))
+        outcome, want = oracle.edge_switch(want, i, j, g)
+        acc += outcome == 0
+    got, st = oracle.es_run(e0, seed=11, switches=300, start_switch=5)
+    assert np.array_equal(got, want) and st["accepted"] == acc and st["switches"] == 300
+
+
+def test_es_run_resumes_and_keeps_invariants():
+    e0 = inputs.pld_graph(300, 2.2, 1, 40, seed=3)
+    a, _ = oracle.es_run(e0, seed=2, switches=500, check_every_switch=True)
+    a, _ = oracle.es_run(a, seed=2, switches=700, start_switch=500, check_every_switch=True)
+    b, _ = oracle.es_run(e0, seed=2, switches=1200)
+    assert np.array_equal(a, b)
+    assert oracle.es_run(np.zeros(1, np.uint64), seed=1, switches=5)[1]["lazy"] == 5
+
+
+def es_transition_counts(states, m):
+    index = {s: t for t, s in enumerate(states)}
+    C = np.zeros((len(states), len(states)), dtype=np.int64)
+    for a, s in enumerate(states):
+        e = P(list(s))
+        for i in range(m):
+            for j in range(m):
+                if i == j:
+                    continue
+                for g in (0, 1):
+                    _, after = oracle.edge_switch(e, i, j, g)
+                    C[a, index[graph_key(after)]] += 1
+    return C
+
+
+@pytest.mark.parametrize("deg", [(2, 2, 1, 1, 1, 1), (2, 2, 2, 2, 2, 2), (3, 2, 2, 2, 2, 1)])
+def test_es_transition_matrix_symmetric(deg):
+    # ES-MC picks (i, j, g) uniformly: the lumped matrix is symmetric (Obs. 1)
+    states = enumerate_gd(deg)
+    m = sum(deg) // 2
+    C = es_transition_counts(states, m)
+    assert (C.sum(axis=1) == m * (m - 1) * 2).all()
+    assert np.array_equal(C, C.T)
+
+
+def test_es_final_graph_uniform_on_gd_chi2():
+    from scipy.stats import chisquare
+    deg = (2, 2, 2, 2, 2, 2)
+    states = enumerate_gd(deg)
+    m = sum(deg) // 2
+    Pm = es_transition_counts(states, m) / (m * (m - 1) * 2)
+    start = inputs.havel_hakimi(np.array(deg, dtype=np.uint32))
+    x = np.zeros(len(states))
+    x[states.index(graph_key(start))] = 1.0
+    steps = 0
+    while 0.5 * np.abs(x - 1.0 / len(states)).sum() > 1e-4:
+        x = x @ Pm
+        steps += 1
+    index = {s: t for t, s in enumerate(states)}
+    counts = np.zeros(len(states), dtype=np.int64)
+    for seed in range(14000):
+        e, _ = oracle.es_run(start, seed=seed + 77, switches=steps)
+        counts[index[graph_key(e)]] += 1
+    assert chisquare(counts).pvalue > 1e-4
