@@ -137,6 +137,18 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
  * floor(m/2) edge switches with the sequential outcome (Algorithm 1). */
 int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed);
 
+/* ParES (Algorithm 2, Sec. 4): run `switches` switches of the plain Edge
+ * Switching Markov Chain (Def. 1's chain, ES-MC) on the handle's graph, with
+ * the sequential outcome.  Switch k draws Philox4x64-10(counter = (k, 0, 2,
+ * 0), key = (seed, 0)) = (w0, w1, w2, w3): i = floor(w0 m / 2^64),
+ * j = j' + [j' >= i] with j' = floor(w1 (m - 1) / 2^64), g = the top bit of
+ * w2; switches are numbered on from the handle's last ES-MC switch.  Runs
+ * in supersteps without source dependencies, one CTA per chain.  May be
+ * mixed with gesmc_run on the same handle.  A seed different from the
+ * handle's current one re-seeds it as gesmc_run does.  With m < 2 every
+ * switch is counted as skipped (stats.lazy).  Synchronises the stream. */
+int gesmc_es_run(gesmc_t h, uint64_t switches, uint64_t seed);
+
 /* Copy E, in position order, to `out` (host memory, or device memory if
  * out_on_device != 0); `capacity` is out's length in edges.  *m_out (if not
  * NULL) receives m.  Returns GESMC_E_CAPACITY if capacity < m. */
@@ -245,7 +257,8 @@ typedef struct gesmc_chain_info_s {
   uint64_t rounds;         /* rounds run since the chain was added            */
   uint64_t next_round;     /* number of the chain's next round                */
   uint64_t switches;       /* floor(m/2) per round run                        */
-  uint64_t accepted;       /* switches that rewired (since added)             */
+  uint64_t accepted;       /* switches that rewired (since added), both chains */
+  uint64_t es_switches;    /* ES-MC switches run (gesmc_pool_es_run)          */
 } gesmc_chain_info_t;
 
 void gesmc_pool_opts_default(gesmc_pool_opts *o);
@@ -265,6 +278,9 @@ int gesmc_pool_add(gesmc_pool_t p, const uint64_t *edges, uint64_t m, int edges_
 int gesmc_pool_remove(gesmc_pool_t p, uint32_t chain);
 /* Advance every chain of the pool by `global_switches` rounds. */
 int gesmc_pool_run(gesmc_pool_t p, uint64_t global_switches);
+/* Advance every chain of the pool by `switches` ES-MC switches (as
+ * gesmc_es_run, each chain with its own seed). */
+int gesmc_pool_es_run(gesmc_pool_t p, uint64_t switches);
 /* Copy a chain's edge list, in position order, as gesmc_edges does. */
 int gesmc_pool_edges(gesmc_pool_t p, uint32_t chain, uint64_t *out, uint64_t capacity, int out_on_device,
                      uint64_t *m_out);

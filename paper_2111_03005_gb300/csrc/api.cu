@@ -69,7 +69,7 @@ Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
 
 // Offsets of the pieces of a pool's single device allocation.
 struct Layout {
-  size_t chains, chain_acc, chain_ell, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
+  size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
       pib_pos, pib_edge, bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
       E, ctl, st, scratch, total;
 };
@@ -85,6 +85,8 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.chains = take(sizeof(ChainDesc) * C);
   l.chain_acc = take(8 * C);
   l.chain_ell = take(4 * C);
+  l.es_jobs = take(sizeof(EsJob) * C);
+  l.es_job_of = take(4 * C);
   l.owner_slot = take(4 * c.slots);
   l.owner_switch = take(4 * c.switches);
   l.owner_bucket = take(4 * c.buckets);
@@ -192,6 +194,7 @@ struct HostChain {
   ChainDesc d;
   ChainShape shape;
   uint64_t n = 0;
+  uint64_t es_next = 0;  // ES-MC switches run (numbering of the next one)
 };
 
 int map_device_errors(uint32_t err) {
@@ -351,6 +354,10 @@ int pool_init(gesmc_pool_t p, const gesmc_pool_opts &o) {
     return GESMC_E_CUDA;
   }
   a.group_grid = grid;
+  if (prepare_es_kernels() != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
   cudaStream_t s = p->stream;
   const int sms = p->num_sms;
   bool ok = launch_fill_u32(const_cast<uint32_t *>(a.owner_slot), (uint32_t)p->cap.slots, kNoChain, s, sms) ==
@@ -611,6 +618,95 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
   return rc;
 }
 
+// ParES (Algorithm 2) on the live chains of the pool (all of them, or only
+// `only`): each runs `switches` ES-MC switches with its own seed, numbered
+// on from its last ES-MC switch.  Each chain's list leaves its slots for
+// its tuple storage (position order), where its edge set and first-touch
+// table also live; the edge set is rebuilt between chunks of at most an
+// eighth of its slots in switches, so that tombstones stay below a quarter.
+int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
+  if (p->broken) return p->broken;
+  if (switches == 0) return GESMC_OK;
+  DeviceGuard g(p->device);
+  cudaStream_t s = p->stream;
+  const RoundArgs &a = p->args;
+  std::vector<EsJob> jobs;
+  std::vector<uint32_t> job_of(p->max_chains, kNoChain);
+  std::vector<uint64_t> chunk;
+  char *tup = reinterpret_cast<char *>(a.ptup);
+  for (uint32_t c = 0; c < p->max_chains; ++c) {
+    const HostChain &hc = p->chains[c];
+    if (!hc.live || (only != kNoChain && c != only)) continue;
+    EsJob jb;
+    std::memset(&jb, 0, sizeof(jb));
+    jb.m = hc.d.m;
+    jb.seed = hc.d.seed;
+    jb.k0 = hc.es_next;
+    jb.chain = c;
+    uint64_t per = switches;
+    if (jb.m >= 2) {
+      char *base = tup + 16ull * hc.d.tuple_base;
+      const uint64_t bytes = 16ull * hc.d.capt << hc.d.P;
+      const uint64_t first_off = align_up(8ull * jb.m), h_off = align_up(first_off + 4ull * jb.m);
+      if (h_off >= bytes) return GESMC_E_INTERNAL;
+      uint32_t hlog2 = 0;
+      while ((16ull << hlog2) <= bytes - h_off && hlog2 < 31) ++hlog2;  // largest 2^h with 8 * 2^h <= room
+      if ((1ull << hlog2) < 2ull * jb.m) return GESMC_E_INTERNAL;
+      jb.E = reinterpret_cast<unsigned long long *>(base);
+      jb.first = reinterpret_cast<uint32_t *>(base + first_off);
+      jb.H = reinterpret_cast<unsigned long long *>(base + h_off);
+      jb.hlog2 = hlog2;
+      per = std::max<uint64_t>(1, (1ull << hlog2) / 8);
+    }
+    // chains with m < 2 have no list to move (their switches are only counted)
+    if (jb.m >= 2) job_of[c] = (uint32_t)jobs.size();
+    jobs.push_back(jb);
+    chunk.push_back(per);
+  }
+  if (jobs.empty()) return GESMC_OK;
+  EsJob *djobs = at<EsJob>(p->base, p->lay.es_jobs);
+  uint32_t *djob_of = at<uint32_t>(p->base, p->lay.es_job_of);
+  uint32_t *err = &a.ctl->err;
+  const uint32_t nj = (uint32_t)jobs.size();
+  bool ok = cudaMemsetAsync(err, 0, sizeof(uint32_t), s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(djob_of, job_of.data(), 4ull * p->max_chains, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemcpyAsync(djobs, jobs.data(), sizeof(EsJob) * nj, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= launch_es_store(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
+  std::vector<EsJob> step(jobs);
+  std::vector<uint64_t> done(nj, 0);  // switches job t has run in this call
+  while (ok) {
+    // the next chunk: at most chunk[t] more switches of job t, numbered on
+    bool any = false;
+    for (uint32_t t = 0; t < nj; ++t) {
+      step[t].k0 = jobs[t].k0 + done[t];
+      step[t].count = std::min(switches - done[t], chunk[t]);
+      any |= step[t].count > 0;
+    }
+    if (!any) break;
+    ok &= cudaMemcpyAsync(djobs, step.data(), sizeof(EsJob) * nj, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok &= launch_es_set(djobs, nj, err, s, p->num_sms) == cudaSuccess;
+    ok &= launch_es_run(djobs, nj, a.st, a.chain_accepted, err, s) == cudaSuccess;
+    ok &= cudaStreamSynchronize(s) == cudaSuccess;  // step[] is rewritten for the next chunk
+    for (uint32_t t = 0; t < nj; ++t) done[t] += step[t].count;
+    p->launches += 3ull * ((nj + 65534) / 65535);
+  }
+  p->launches += 2;
+  ok &= launch_es_load(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
+  uint32_t host_err = 0;
+  ok &= cudaMemcpyAsync(&host_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    p->broken = GESMC_E_CUDA;
+    return GESMC_E_CUDA;
+  }
+  for (uint32_t t = 0; t < nj; ++t) p->chains[jobs[t].chain].es_next += switches;
+  p->switches_run += switches * nj;
+  const int rc = map_device_errors(host_err);
+  if (rc != GESMC_OK) p->broken = rc;
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -773,7 +869,12 @@ int gesmc_pool_chain_info(gesmc_pool_t p, uint32_t chain, gesmc_chain_info_t *ou
   out->next_round = hc.d.start_round + (p->pool_round - hc.d.join);
   out->switches = out->rounds * hc.shape.L;
   out->accepted = acc;
+  out->es_switches = hc.es_next;
   return GESMC_OK;
+}
+
+int gesmc_pool_es_run(gesmc_pool_t p, uint64_t switches) {
+  return p ? pool_es_run(p, switches, kNoChain) : GESMC_E_INVALID;
 }
 
 uint32_t gesmc_pool_num_chains(gesmc_pool_t p) { return p ? p->live_chains : 0; }
@@ -924,6 +1025,25 @@ int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed) {
     }
   }
   return pool_run(p, global_switches);
+}
+
+int gesmc_es_run(gesmc_t h, uint64_t switches, uint64_t seed) {
+  if (!h) return GESMC_E_INVALID;
+  gesmc_pool_t p = h->pool;
+  if (p->broken) return p->broken;
+  HostChain &hc = p->chains[h->chain];
+  if (seed != hc.d.seed) {  // as gesmc_run: the round numbering goes on
+    DeviceGuard g(p->device);
+    hc.d.start_round += p->pool_round - hc.d.join;
+    hc.d.join = p->pool_round;
+    hc.d.seed = seed;
+    if (cudaMemcpyAsync(const_cast<ChainDesc *>(p->args.chains) + h->chain, &hc.d, sizeof(ChainDesc),
+                        cudaMemcpyHostToDevice, p->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GESMC_E_CUDA;
+    }
+  }
+  return pool_es_run(p, switches, h->chain);
 }
 
 int gesmc_edges(gesmc_t h, uint64_t *out, uint64_t capacity, int out_on_device, uint64_t *m_out) {

@@ -40,6 +40,7 @@
 namespace gesmc {
 
 constexpr unsigned long long kEmptyKey = ~0ull;  // would be the loop {2^32-1, 2^32-1}: never an edge
+constexpr unsigned long long kTombKey = ~0ull - 1;  // {2^32-1, 2^32-2}: not canonical, never an edge
 constexpr uint32_t kNoChain = 0xFFFFFFFFu;
 
 // Tuple value (Algorithm 1's (e, k, type)): bit 31 = the edge is a source
@@ -224,6 +225,34 @@ cudaError_t launch_canonicalise(unsigned long long *E, uint32_t m, unsigned long
 // Repeated edges, with an open-addressing set of `cap` u64 slots as scratch.
 cudaError_t launch_duplicate_check(const unsigned long long *E, uint32_t m, unsigned long long *set,
                                    unsigned long long cap, uint32_t *flags, cudaStream_t s, int num_sms);
+
+// ParES (Algorithm 2) for one chain: its list in position order, its edge
+// set (open addressing, 2^hlog2 slots) and the first-touch table, all in
+// the chain's tuple storage, which no round uses between rounds; ES-MC
+// switches k0 .. k0 + count - 1 with the chain's seed.
+struct EsJob {
+  unsigned long long *E;
+  unsigned long long *H;
+  uint32_t *first;
+  unsigned long long seed, k0, count;
+  uint32_t m, hlog2, chain, pad;
+};
+
+// Shared memory of the ParES kernel; opt-in once per device.
+size_t es_smem_bytes();
+cudaError_t prepare_es_kernels();
+// Edge sets of all jobs rebuilt from their lists (first-touch tables cleared).
+cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms);
+// All jobs' switches, one CTA per job.
+cudaError_t launch_es_run(const EsJob *jobs, uint32_t njobs, StatsDev *stats, unsigned long long *chain_acc,
+                          uint32_t *err, cudaStream_t s);
+// Lists of the chains with a job (job_of[chain] != kNoChain) out of their
+// slots into the jobs' position-order lists, and back (slots in position
+// order, nothing pending).
+cudaError_t launch_es_store(const RoundArgs &a, const EsJob *jobs, const uint32_t *job_of, cudaStream_t s,
+                            int num_sms);
+cudaError_t launch_es_load(const RoundArgs &a, const EsJob *jobs, const uint32_t *job_of, cudaStream_t s,
+                           int num_sms);
 
 // Flags written by the create-time validation kernels.
 constexpr uint32_t kFlagLoop = 1u, kFlagRange = 2u, kFlagMulti = 4u, kFlagTableFull = 8u;

@@ -32,50 +32,11 @@
 // of waves < w (status words carry their wave), so the result and the wave
 // count do not depend on thread timing.  The list after the round is the one
 // the sequential loop of Def. 2 produces.
+#include "device_util.cuh"
 #include "gesmc_internal.cuh"
 
 namespace gesmc {
 namespace {
-
-// ---------------------------------------------------------------- Philox4x64-10
-// Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten
-// rounds, each multiplying counter words 0 and 2 by fixed 64-bit constants,
-// xor-ing the high halves into words 1 and 3 with the round key, and
-// permuting; the key is advanced by two Weyl increments between rounds.
-struct U64x4 {
-  unsigned long long w[4];
-};
-
-__device__ __forceinline__ U64x4 philox(unsigned long long c0, unsigned long long c1, unsigned long long c2,
-                                        unsigned long long c3, unsigned long long k0, unsigned long long k1) {
-  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
-    const unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
-    const unsigned long long n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = lo1;
-    c2 = n2;
-    c3 = lo0;
-    k0 += W0;
-    k1 += W1;
-  }
-  U64x4 out;
-  out.w[0] = c0;
-  out.w[1] = c1;
-  out.w[2] = c2;
-  out.w[3] = c3;
-  return out;
-}
-
-// Word t of a block, t in 0..3 (selects, so the block stays in registers).
-__device__ __forceinline__ unsigned long long word_of(const U64x4 &w, uint32_t t) {
-  const unsigned long long lo = (t & 1) ? w.w[1] : w.w[0];
-  const unsigned long long hi = (t & 1) ? w.w[3] : w.w[2];
-  return (t & 2) ? hi : lo;
-}
 
 // Permutation key K(i) of round `round` (purpose 0).
 __device__ __forceinline__ unsigned long long perm_key(unsigned long long seed, unsigned long long round,
@@ -93,45 +54,15 @@ __device__ __forceinline__ uint32_t mid_of(unsigned long long key, uint32_t B) {
 }
 
 // ---------------------------------------------------------------- edges
-__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
-  // MurmurHash3's 64-bit finaliser (Appleby): a bijective avalanche mixer
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
-}
-
 __device__ __forceinline__ uint32_t partition_of(unsigned long long h, uint32_t P) {
   return P ? (uint32_t)(h >> (64 - P)) : 0u;
 }
 
-__device__ __forceinline__ unsigned long long pack_edge(uint32_t a, uint32_t b) {
-  const uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
-  return ((unsigned long long)lo << 32) | hi;
-}
-
-// Edge switch (i, j, g = [i < j]) on e1 = E[i], e2 = E[j] (Def. 1 with the
-// direction bit of Def. 2): the canonical new edges e3 (for position i) and
-// e4 (for j), and the outright-reject code: a new edge is a loop, or the
-// sources share a node (then every outcome of tau is a loop or re-creates
-// the two source edges, which are in E when the switch runs).
+// Edge switch (i, j, g = [i < j]) of a global switch (Def. 2): tau with the
+// direction bit the permutation gives.
 __device__ __forceinline__ uint32_t tau(uint32_t i, uint32_t j, unsigned long long e1, unsigned long long e2,
                                         unsigned long long &e3, unsigned long long &e4) {
-  const uint32_t u = (uint32_t)(e1 >> 32), v = (uint32_t)e1;
-  const uint32_t x = (uint32_t)(e2 >> 32), y = (uint32_t)e2;
-  uint32_t a3, b3, a4, b4;
-  if (i < j) {  // g = 1: (u, y), (v, x)
-    a3 = u; b3 = y; a4 = v; b4 = x;
-  } else {      // g = 0: (u, x), (v, y)
-    a3 = u; b3 = x; a4 = v; b4 = y;
-  }
-  e3 = pack_edge(a3, b3);
-  e4 = pack_edge(a4, b4);
-  if (a3 == b3 || a4 == b4) return kCodeLoop;
-  if (u == x || u == y || v == x || v == y) return kCodeShared;
-  return 0;
+  return tau_g(i < j ? 1u : 0u, e1, e2, e3, e4);
 }
 
 
@@ -1106,6 +1037,43 @@ __global__ void k_store_chain(RoundArgs a, ChainDesc ch, unsigned long long *E) 
   }
 }
 
+// ParES: the lists of the chains with a job, by position, with the last
+// round's legal switches applied; and back into their slots (slot s holds
+// position s, nothing pending).
+__global__ void k_es_store(RoundArgs a, const EsJob *jobs, const uint32_t *job_of) {
+  const unsigned long long R = a.ctl->pool_round;
+  const uint32_t npair = (a.slot_hw + 1) >> 1;
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += gridDim.x * blockDim.x) {
+    const uint32_t s0 = 2 * x;
+    const uint32_t c = a.owner_slot[s0];
+    if (c == kNoChain || job_of[c] == kNoChain) continue;
+    const ChainDesc ch = a.chains[c];
+    unsigned long long *E = jobs[job_of[c]].E;
+    const uint32_t ls = s0 - ch.slot_base;
+    if (ls + 1 < ch.m) {
+      const uint32_t i = a.cpos[s0], j = a.cpos[s0 + 1];
+      unsigned long long e1 = a.cedge[s0], e2 = a.cedge[s0 + 1];
+      apply_last(a, ch, chain_apply(ch, R), ls >> 1, i, j, e1, e2);
+      E[i] = e1;
+      E[j] = e2;
+    } else {
+      E[a.cpos[s0]] = a.cedge[s0];
+    }
+  }
+}
+
+__global__ void k_es_load(RoundArgs a, const EsJob *jobs, const uint32_t *job_of) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.slot_hw; s += gridDim.x * blockDim.x) {
+    const uint32_t c = a.owner_slot[s];
+    if (c == kNoChain || job_of[c] == kNoChain) continue;
+    const ChainDesc ch = a.chains[c];
+    const uint32_t ls = s - ch.slot_base;
+    a.cpos[s] = ls;
+    a.cedge[s] = jobs[job_of[c]].E[ls];
+    if ((ls & 1u) == 0 && (ls >> 1) < ch.L) a.status[ch.switch_base + (ls >> 1)] = 0;  // nothing pending
+  }
+}
+
 __global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
 }
@@ -1241,6 +1209,20 @@ cudaError_t launch_store_chain(const RoundArgs &a, const ChainDesc &ch, unsigned
                                int num_sms) {
   if (ch.m == 0) return cudaSuccess;
   k_store_chain<<<grid_for((ch.m + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a, ch, E);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_es_store(const RoundArgs &a, const EsJob *jobs, const uint32_t *job_of, cudaStream_t s,
+                            int num_sms) {
+  if (a.slot_hw == 0) return cudaSuccess;
+  k_es_store<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a, jobs, job_of);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_es_load(const RoundArgs &a, const EsJob *jobs, const uint32_t *job_of, cudaStream_t s,
+                           int num_sms) {
+  if (a.slot_hw == 0) return cudaSuccess;
+  k_es_load<<<grid_for(a.slot_hw, 256, num_sms, 8), 256, 0, s>>>(a, jobs, job_of);
   return cudaGetLastError();
 }
 

@@ -101,7 +101,7 @@ class GesmcPoolOpts(ctypes.Structure):
 
 class GesmcChainInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in ("m", "n", "seed", "rounds", "next_round", "switches",
-                                                      "accepted")]
+                                                      "accepted", "es_switches")]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -122,6 +122,7 @@ _SIGNATURES = [
     ("gesmc_create", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(GesmcOpts),
                                     ctypes.POINTER(ctypes.c_void_p)]),
     ("gesmc_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]),
+    ("gesmc_es_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]),
     ("gesmc_edges", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_uint64)]),
     ("gesmc_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GesmcStats)]),
@@ -147,6 +148,7 @@ _SIGNATURES = [
                                       ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     ("gesmc_pool_remove", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     ("gesmc_pool_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("gesmc_pool_es_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("gesmc_pool_edges", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     ("gesmc_pool_chain_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(GesmcChainInfo)]),
@@ -373,6 +375,11 @@ class Chain:
         gesmc_run(self._h, global_switches, seed)
         return self
 
+    def es_run(self, switches: int, seed: int):
+        """ParES: `switches` ES-MC switches with the sequential outcome (Algorithm 2)."""
+        _check(load_library().gesmc_es_run(self._h, switches, seed), "gesmc_es_run")
+        return self
+
     def edges(self, out=None):
         return gesmc_edges(self._h, out)
 
@@ -452,6 +459,11 @@ class Pool:
 
     def run(self, global_switches: int):
         _check(load_library().gesmc_pool_run(self._p, global_switches), "gesmc_pool_run")
+        return self
+
+    def es_run(self, switches: int):
+        """ParES on every chain: `switches` ES-MC switches each, with its own seed."""
+        _check(load_library().gesmc_pool_es_run(self._p, switches), "gesmc_pool_es_run")
         return self
 
     def edges(self, chain: int, out=None):
