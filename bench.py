@@ -553,6 +553,79 @@ def run_serve(args):
     return 0
 
 
+def run_es(args):
+    """ParES (Algorithm 2): ES-MC switches with the sequential outcome, on one
+    chain (one CTA) and on a pool of chains (one CTA each), next to the
+    sequential oracle on one host core."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2111_03005_gb300 import gesmc, inputs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    # one chain: G(2^20, 16/(n-1)), m switches per step
+    edges, n = make_workload("gnp_2p20")
+    m = len(edges)
+    per_step = m
+    with gesmc.Chain(edges, n=n) as c:
+        for _ in range(args.warmup):
+            c.es_run(per_step // 16, 3)
+        c.reset_stats()
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as clocks:
+            start.record(stream)
+            for _ in range(args.steps):
+                c.es_run(per_step, 3)
+            stop.record(stream)
+            torch.cuda.synchronize()
+        ms = start.elapsed_time(stop)
+        st = c.stats()
+    single = args.steps * per_step / (ms / 1e3)
+    # a pool: 4096 chains of the ensemble recipe, m_t switches each per step
+    graphs = inputs.ensemble_graphs(args.chains, seed=41)
+    total = sum(len(e) for e, _ in graphs)
+    sw = 20_000
+    with gesmc.Pool(max_edges=total, max_chains=len(graphs)) as pool:
+        for t, (e, nn) in enumerate(graphs):
+            pool.add(e, n=nn, seed=9000 + t)
+        pool.es_run(1000)
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(args.steps):
+            pool.es_run(sw)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        pms = start.elapsed_time(stop)
+        pst = pool.stats()
+    pooled = args.steps * sw * len(graphs) / (pms / 1e3)
+    # the sequential oracle on a sample
+    oracle.build()
+    t0 = time.perf_counter()
+    _, ost = oracle.es_run(edges, seed=3, switches=2_000_000)
+    cpu = ost["switches"] / (time.perf_counter() - t0)
+    line = {
+        "metric": "ES-MC edge switches/sec (ParES, bit-exact vs sequential ES-MC)",
+        "value": single, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOADS['gnp_2p20']['desc']}, m switches per step, one chain",
+                   "m": m, "switches_per_step": per_step},
+        "accept_rate": st["accepted"] / max(st["switches"], 1),
+        "pool": {"value": pooled, "unit": UNIT, "chains": len(graphs), "edges": total,
+                 "switches_per_chain_per_step": sw, "ms_per_step": pms / args.steps,
+                 "accept_rate": pst["accepted"] / max(pst["switches"], 1)},
+        "cpu_baseline": {"value": cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"2e6 sequential ES-MC switches on {WORKLOADS['gnp_2p20']['desc']}"},
+        "clocks": clocks.summary(),
+        "gpu_launches": st["kernel_launches"],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     global CPU_SAMPLE
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
@@ -560,7 +633,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gesmc", "reference"], default="gesmc")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve"], default="gnp_2p24")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "es"], default="gnp_2p24")
     ap.add_argument("--chains", type=int, default=4096, help="ensemble: chains")
     ap.add_argument("--sample", type=int, default=256, help="ensemble: chains run one by one for comparison")
     ap.add_argument("--requests", type=int, default=128, help="serve: requests")
@@ -587,6 +660,8 @@ def main(argv=None):
         return run_ensemble(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "es":
+        return run_es(args)
     return run_gesmc(args)
 
 

@@ -622,8 +622,8 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
 // `only`): each runs `switches` ES-MC switches with its own seed, numbered
 // on from its last ES-MC switch.  Each chain's list leaves its slots for
 // its tuple storage (position order), where its edge set and first-touch
-// table also live; the edge set is rebuilt between chunks of at most an
-// eighth of its slots in switches, so that tombstones stay below a quarter.
+// table also live (the ParES kernel rebuilds the set when tombstones pass a
+// quarter of its slots).
 int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   if (p->broken) return p->broken;
   if (switches == 0) return GESMC_OK;
@@ -632,7 +632,6 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   const RoundArgs &a = p->args;
   std::vector<EsJob> jobs;
   std::vector<uint32_t> job_of(p->max_chains, kNoChain);
-  std::vector<uint64_t> chunk;
   char *tup = reinterpret_cast<char *>(a.ptup);
   for (uint32_t c = 0; c < p->max_chains; ++c) {
     const HostChain &hc = p->chains[c];
@@ -642,8 +641,8 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
     jb.m = hc.d.m;
     jb.seed = hc.d.seed;
     jb.k0 = hc.es_next;
+    jb.count = switches;
     jb.chain = c;
-    uint64_t per = switches;
     if (jb.m >= 2) {
       char *base = tup + 16ull * hc.d.tuple_base;
       const uint64_t bytes = 16ull * hc.d.capt << hc.d.P;
@@ -656,12 +655,10 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
       jb.first = reinterpret_cast<uint32_t *>(base + first_off);
       jb.H = reinterpret_cast<unsigned long long *>(base + h_off);
       jb.hlog2 = hlog2;
-      per = std::max<uint64_t>(1, (1ull << hlog2) / 8);
     }
     // chains with m < 2 have no list to move (their switches are only counted)
     if (jb.m >= 2) job_of[c] = (uint32_t)jobs.size();
     jobs.push_back(jb);
-    chunk.push_back(per);
   }
   if (jobs.empty()) return GESMC_OK;
   EsJob *djobs = at<EsJob>(p->base, p->lay.es_jobs);
@@ -672,25 +669,9 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   ok &= cudaMemcpyAsync(djob_of, job_of.data(), 4ull * p->max_chains, cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(djobs, jobs.data(), sizeof(EsJob) * nj, cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= launch_es_store(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
-  std::vector<EsJob> step(jobs);
-  std::vector<uint64_t> done(nj, 0);  // switches job t has run in this call
-  while (ok) {
-    // the next chunk: at most chunk[t] more switches of job t, numbered on
-    bool any = false;
-    for (uint32_t t = 0; t < nj; ++t) {
-      step[t].k0 = jobs[t].k0 + done[t];
-      step[t].count = std::min(switches - done[t], chunk[t]);
-      any |= step[t].count > 0;
-    }
-    if (!any) break;
-    ok &= cudaMemcpyAsync(djobs, step.data(), sizeof(EsJob) * nj, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok &= launch_es_set(djobs, nj, err, s, p->num_sms) == cudaSuccess;
-    ok &= launch_es_run(djobs, nj, a.st, a.chain_accepted, err, s) == cudaSuccess;
-    ok &= cudaStreamSynchronize(s) == cudaSuccess;  // step[] is rewritten for the next chunk
-    for (uint32_t t = 0; t < nj; ++t) done[t] += step[t].count;
-    p->launches += 3ull * ((nj + 65534) / 65535);
-  }
-  p->launches += 2;
+  ok &= launch_es_set(djobs, nj, err, s, p->num_sms) == cudaSuccess;
+  ok &= launch_es_run(djobs, nj, a.st, a.chain_accepted, err, s) == cudaSuccess;
+  p->launches += 3ull * ((nj + 65534) / 65535) + 2;
   ok &= launch_es_load(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
   uint32_t host_err = 0;
   ok &= cudaMemcpyAsync(&host_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;

@@ -20,6 +20,8 @@
 // tombstones on erase) live in HBM.  Many chains run as many CTAs of one
 // launch.  A superstep is also cut at kEsBatch switches; any cut into
 // consecutive runs without source dependencies gives the sequential result.
+// When tombstones pass a quarter of the set's slots, the CTA rebuilds the set
+// from the list between supersteps.
 #include "device_util.cuh"
 #include "gesmc_internal.cuh"
 
@@ -59,18 +61,19 @@ __device__ __forceinline__ void hset_erase(unsigned long long *H, uint32_t mask,
 }
 
 // Insert a key that is not in the set into the first empty or tombstone
-// slot of its probe sequence.  Returns false if the table is full.
-__device__ __forceinline__ bool hset_insert(unsigned long long *H, uint32_t mask, unsigned long long key) {
+// slot of its probe sequence.  Returns 0 (empty slot taken), 1 (tombstone
+// reused) or -1 (table full).
+__device__ __forceinline__ int hset_insert(unsigned long long *H, uint32_t mask, unsigned long long key) {
   uint32_t s = (uint32_t)mix64(key) & mask;
   for (uint32_t n = 0; n <= mask; ++n) {
     const unsigned long long cur = __ldcg(&H[s]);
     if (cur == kEmptyKey || cur == kTombKey) {
-      if (atomicCAS(&H[s], cur, key) == cur) return true;
+      if (atomicCAS(&H[s], cur, key) == cur) return cur == kTombKey ? 1 : 0;
       continue;  // taken meanwhile: look at the same slot again
     }
     s = (s + 1) & mask;
   }
-  return false;
+  return -1;
 }
 
 // ---------------------------------------------------------------- shared-memory tables
@@ -146,7 +149,7 @@ __global__ void k_es_fill(const EsJob *jobs, uint32_t job_off, uint32_t *err) {
   if (jb.m < 2) return;
   const uint32_t mask = (uint32_t)((1ull << jb.hlog2) - 1);
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < jb.m; s += gridDim.x * blockDim.x)
-    if (!hset_insert(jb.H, mask, jb.E[s])) atomicOr(err, kErrTableFull);
+    if (hset_insert(jb.H, mask, jb.E[s]) < 0) atomicOr(err, kErrTableFull);
 }
 
 // One CTA per job: switches k0 .. k0 + count - 1 of the job's chain.
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32
                                                        unsigned long long *chain_acc, uint32_t *err) {
   const EsJob jb = jobs[job_off + blockIdx.x];
   const EsSmem sm = es_smem();
-  __shared__ uint32_t s_cut;
+  __shared__ uint32_t s_cut, s_tombs;
   const uint32_t x = threadIdx.x;
   uint32_t acc = 0, rej_loop = 0, rej_exists = 0;
   if (jb.m < 2) {  // no pair of positions: every requested switch is skipped
@@ -162,6 +165,7 @@ __global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32
     return;
   }
   const uint32_t mask = (uint32_t)((1ull << jb.hlog2) - 1);
+  if (x == 0) s_tombs = 0;  // the set was built from the list just before
   for (unsigned long long s = 0; s < jb.count;) {
     const uint32_t win = (uint32_t)min((unsigned long long)kEsBatch, jb.count - s);
     // sample the window and mark first touches (Algorithm 2's insert_if_min)
@@ -267,15 +271,27 @@ __global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32
       jb.E[sm.sj[x]] = sm.e4[x];
       hset_erase(jb.H, mask, sm.e1[x]);
       hset_erase(jb.H, mask, sm.e2[x]);
+      atomicAdd(&s_tombs, 2u);
       ++acc;
     } else if (x < n && sm.code[x] == 0) {
       ++rej_exists;
     }
     __syncthreads();
     if (legal) {
-      if (!hset_insert(jb.H, mask, sm.e3[x]) || !hset_insert(jb.H, mask, sm.e4[x])) atomicOr(err, kErrTableFull);
+      const int r3 = hset_insert(jb.H, mask, sm.e3[x]), r4 = hset_insert(jb.H, mask, sm.e4[x]);
+      if (r3 < 0 || r4 < 0) atomicOr(err, kErrTableFull);
+      const uint32_t reused = (r3 > 0 ? 1u : 0u) + (r4 > 0 ? 1u : 0u);
+      if (reused) atomicSub(&s_tombs, reused);
     }
     __syncthreads();
+    if (s_tombs > (mask >> 2)) {  // rebuild the set from the list
+      for (uint32_t t = x; t <= mask; t += kEsThreads) jb.H[t] = kEmptyKey;
+      __syncthreads();
+      for (uint32_t t = x; t < jb.m; t += kEsThreads)
+        if (hset_insert(jb.H, mask, __ldcg(&jb.E[t])) < 0) atomicOr(err, kErrTableFull);
+      if (x == 0) s_tombs = 0;
+      __syncthreads();
+    }
     s += n;
   }
   // counts of this job
