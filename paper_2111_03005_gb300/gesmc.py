@@ -149,6 +149,8 @@ _SIGNATURES = [
     ("gesmc_pool_remove", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
     ("gesmc_pool_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("gesmc_pool_es_run", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("gesmc_generate_gnp", ctypes.c_int, [ctypes.c_uint64, ctypes.c_double, ctypes.c_uint64, ctypes.c_void_p,
+                                          ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p]),
     ("gesmc_pool_edges", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_uint64,
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]),
     ("gesmc_pool_chain_info", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(GesmcChainInfo)]),
@@ -523,3 +525,26 @@ class Pool:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+def generate_gnp(n: int, p: float, seed: int, stream=None):
+    """G(n, p) generated on the current CUDA device: a device tensor (int64
+    view of the packed uint64 edge ids, canonical, in pair order)."""
+    import torch
+
+    lib = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
+    m = ctypes.c_uint64()
+    rc = lib.gesmc_generate_gnp(n, p, seed, None, 0, ctypes.byref(m), sp)
+    if rc not in (0, -5):
+        raise GesmcError(rc, "gesmc_generate_gnp")
+    out = torch.empty(int(m.value), dtype=torch.int64, device=torch.device("cuda", torch.cuda.current_device()))
+    if m.value:
+        m2 = ctypes.c_uint64()
+        _check(lib.gesmc_generate_gnp(n, p, seed, ctypes.c_void_p(out.data_ptr()), int(m.value), ctypes.byref(m2), sp),
+               "gesmc_generate_gnp")
+        assert m2.value == m.value
+    return out
+
