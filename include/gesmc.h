@@ -170,7 +170,7 @@ int gesmc_reset_stats(gesmc_t h);
  * GPU; as many pairs as the handle's rounds have needed extra waves so far,
  * at most 8, none while every round needed one wave; "tail" runs any waves
  * beyond those on one CTA). */
-#define GESMC_NUM_STAGES 10
+#define GESMC_NUM_STAGES 11
 int gesmc_set_profiling(gesmc_t h, int enable);
 int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds);
 const char *gesmc_stage_name(int stage);

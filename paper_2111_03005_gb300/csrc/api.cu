@@ -67,9 +67,18 @@ Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
   return c;
 }
 
+// Bits of the target filter for at most M edges: about four per edge (so
+// that a source passes by a collision with probability about 1/5), a power
+// of two between 2^12 and 2^29 (at most 64 MB, which stays in L2).
+uint64_t filter_bits(uint64_t M) {
+  uint64_t b = 1ull << 12;
+  while (b < 4 * M && b < (1ull << 29)) b <<= 1;
+  return b;
+}
+
 // Offsets of the pieces of a pool's single device allocation.
 struct Layout {
-  size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
+  size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, tfilter, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
       pib_pos, pib_edge, bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
       E, ctl, st, scratch, total;
 };
@@ -112,6 +121,7 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.ooff = take(4 * (c.parts + 1));
   l.ocursor = take(4 * c.parts);
   l.dep = take(8 * c.dep);
+  l.tfilter = take(filter_bits(M) / 8);
   l.E = take(8 * M);
   l.ctl = take(sizeof(Counters));
   l.st = take(sizeof(StatsDev));
@@ -309,6 +319,8 @@ void pool_bind(gesmc_pool_t p) {
   a.pib_edge = at<unsigned long long>(b, l.pib_edge);
   a.bnd = at<uint32_t>(b, l.bnd);
   a.word = at<uint32_t>(b, l.word);
+  a.tfilter = at<uint32_t>(b, l.tfilter);
+  a.tfilter_mask = (uint32_t)(filter_bits(p->max_edges) - 1);
   a.sw = at<uint2>(b, l.sw);
   a.status = at<uint32_t>(b, l.status);
   a.list0 = at<uint32_t>(b, l.list0);
@@ -1042,7 +1054,7 @@ int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
 }
 
 const char *gesmc_stage_name(int stage) {
-  static const char *names[kNumStages] = {"clear",    "permute", "scan_perm", "sortpair", "boundary",
+  static const char *names[kNumStages] = {"clear",    "permute", "scan_perm", "sortpair", "boundary", "sources",
                                           "overflow", "group",   "wave1", "waves",     "tail"};
   return (stage >= 0 && stage < kNumStages) ? names[stage] : "";
 }

@@ -32,6 +32,8 @@
 //                                         the ptup format (rare)
 //   dep          uint2[dep cap]           {p, q} of every edge id with a
 //                                         dependency
+//   tfilter      u32[bits / 32]           target filter: the bit of every
+//                                         target id of the round is set
 #pragma once
 
 #include <cuda_runtime.h>
@@ -175,6 +177,8 @@ struct RoundArgs {
   uint32_t *ooff;     // per partition + 1
   uint32_t *ocursor;  // per partition
   uint2 *dep;
+  uint32_t *tfilter;      // target filter: one bit per hash of a target id (all chains)
+  uint32_t tfilter_mask;  // bits - 1
   Counters *ctl;
   StatsDev *st;
   uint32_t slot_hw, switch_hw, bucket_hw, part_hw;
@@ -195,6 +199,7 @@ enum Stage {
   kStageScanPerm,
   kStageSortPair,
   kStageBoundary,
+  kStageSources,
   kStageOverflow,
   kStageGroup,
   kStageWave1,

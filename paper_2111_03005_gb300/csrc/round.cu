@@ -17,6 +17,9 @@
 //                    (e2, k, ERASE), (e3, k, INSERT), (e4, k, INSERT) to
 //                    the hash partitions of their edge ids
 //   k_boundary       the same for pairs whose slots lie in two buckets
+//   k_sources        the sources (ERASE tuples) of all switches, from the
+//                    list in slot order, but only those whose edge id some
+//                    target of the round may equal (target filter)
 //   k_overflow_*     group the (rare) tuples that found their partition full
 //   k_group          per partition: group by edge id in a shared-memory
 //                    table and decide every target of wave 1 (Algorithm 1's
@@ -109,13 +112,19 @@ __device__ __forceinline__ void apply_last(const RoundArgs &a, const ChainDesc &
 // hash} (the grouping kernel probes its table with those bits); one that
 // finds its partition full goes to the overflow list with its partition id
 // in place of the hash bits.
+// The target filter's bit of an edge id with hash h.
+__device__ __forceinline__ uint32_t filter_bit(const RoundArgs &a, unsigned long long h) {
+  return (uint32_t)(h >> 24) & a.tfilter_mask;
+}
+
 template <int N>
 __device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc &ch,
-                                            const unsigned long long (&key)[N], const uint32_t (&val)[N]) {
+                                            const unsigned long long (&key)[N], const unsigned long long (&hash)[N],
+                                            const uint32_t (&val)[N]) {
   uint32_t part[N], hlo[N], idx[N];
 #pragma unroll
   for (int t = 0; t < N; ++t) {
-    const unsigned long long h = mix64(key[t]);
+    const unsigned long long h = hash[t];
     part[t] = partition_of(h, ch.P);
     hlo[t] = (uint32_t)h;
     idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[ch.part_base + part[t]], 1u) : 0u;
@@ -137,10 +146,10 @@ __device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc 
 }
 
 // Switch k (the chain's own index) = (i, j, g) with sources e1, e2: record
-// its reject code and Algorithm 1's four tuples (e1, k, ERASE), (e2, k,
-// ERASE), (e3, k, INSERT), (e4, k, INSERT), with k made pool-wide.  A
-// switch rejected outright stores its sources as never erased and no
-// targets.
+// its reject code, mark its targets in the target filter and emit Algorithm
+// 1's tuples (e3, k, INSERT), (e4, k, INSERT), with k made pool-wide.  Its
+// ERASE tuples (e1, k), (e2, k) follow from k_sources when the filter says
+// a target may need them.  A switch rejected outright has no targets.
 __device__ __forceinline__ void build_switch(const RoundArgs &a, const ChainDesc &ch, unsigned long long round,
                                              uint32_t ell, uint32_t k, uint32_t i, unsigned long long e1,
                                              uint32_t j, unsigned long long e2) {
@@ -149,18 +158,15 @@ __device__ __forceinline__ void build_switch(const RoundArgs &a, const ChainDesc
   const uint32_t kg = ch.switch_base + k;
   a.word[kg] = code;
   a.sw[kg] = make_uint2(kTrivial, kTrivial);
-  const uint32_t src = kTupleSource | (code ? kKeepK : kg);
-  if (code) e3 = e4 = kEmptyKey;
-  const unsigned long long key[4] = {e1, e2, e3, e4};
-  const uint32_t val[4] = {src, src, kg, kg | kTupleWhich};
-  emit_tuples<4>(a, ch, key, val);
-}
-
-// The unpaired last position of an odd list: a source no switch erases.
-__device__ __forceinline__ void keep_source(const RoundArgs &a, const ChainDesc &ch, unsigned long long e) {
-  const unsigned long long key[1] = {e};
-  const uint32_t val[1] = {kTupleSource | kKeepK};
-  emit_tuples<1>(a, ch, key, val);
+  if (code) return;
+  const unsigned long long key[2] = {e3, e4}, hash[2] = {mix64(e3), mix64(e4)};
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const uint32_t b = filter_bit(a, hash[t]);
+    atomicOr(&a.tfilter[b >> 5], 1u << (b & 31));
+  }
+  const uint32_t val[2] = {kg, kg | kTupleWhich};
+  emit_tuples<2>(a, ch, key, hash, val);
 }
 
 // ---------------------------------------------------------------- decide
@@ -565,13 +571,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
         a.bnd[idx] = goff - 1;  // the pair's first slot
       }
       const uint32_t last = loff + cnt - 1;
-      if ((last & 1u) == 0) {  // first of a pair whose partner is in a later bucket
-        if (last + 1 == ch.m) {
-          keep_source(a, ch, sedge[cnt - 1]);  // odd m: unpaired
-        } else {
-          a.pib_pos[goff + cnt - 1] = (uint32_t)scomp[cnt - 1];
-          a.pib_edge[goff + cnt - 1] = sedge[cnt - 1];
-        }
+      if ((last & 1u) == 0 && last + 1 < ch.m) {  // first of a pair whose partner is in a later bucket
+        a.pib_pos[goff + cnt - 1] = (uint32_t)scomp[cnt - 1];
+        a.pib_edge[goff + cnt - 1] = sedge[cnt - 1];
       }
     }
     __syncthreads();
@@ -598,6 +600,47 @@ __global__ void k_boundary(RoundArgs a) {
                  a.pib_pos[g + 1], a.pib_edge[g + 1]);
   }
 }
+// The sources of every switch (Algorithm 1's ERASE tuples) from the list in
+// this round's slot order, pair by pair.  Only an edge id that is some
+// switch's target needs one (the grouping only asks whether targets exist
+// and who erases them), so a source whose filter bit is clear is dropped; a
+// set bit can be a collision, which only adds a tuple nobody needs.  The
+// unpaired last slot of an odd list is a source no switch erases, and so are
+// the sources of a switch rejected outright.
+__global__ void __launch_bounds__(256, 8) k_sources(RoundArgs a) {
+  const uint32_t npair = (a.slot_hw + 1) >> 1;
+  const uint32_t nth = gridDim.x * blockDim.x;
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += nth) {
+    const uint32_t s0 = 2 * x;
+    const uint32_t c = a.owner_slot[s0];
+    if (c == kNoChain) continue;
+    const ChainDesc ch = a.chains[c];
+    const uint32_t ls = s0 - ch.slot_base;
+    unsigned long long key[2], hash[2];
+    uint32_t src;
+    if (ls + 1 < ch.m) {
+      const ulonglong2 ee = reinterpret_cast<const ulonglong2 *>(a.cedge)[x];
+      const uint32_t kg = ch.switch_base + (ls >> 1);
+      src = kTupleSource | ((__ldcs(&a.word[kg]) & kCodeMask) ? kKeepK : kg);
+      key[0] = ee.x;
+      key[1] = ee.y;
+    } else {
+      src = kTupleSource | kKeepK;
+      key[0] = a.cedge[s0];
+      key[1] = kEmptyKey;
+    }
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (key[t] == kEmptyKey) continue;
+      hash[t] = mix64(key[t]);
+      const uint32_t b = filter_bit(a, hash[t]);
+      if (!((__ldcg(&a.tfilter[b >> 5]) >> (b & 31)) & 1u)) key[t] = kEmptyKey;
+    }
+    const uint32_t val[2] = {src, src};
+    emit_tuples<2>(a, ch, key, hash, val);
+  }
+}
+
 // Grouping of one tuple partition by edge id (Algorithm 1's table T for the
 // partition's edge ids) in a shared-memory table of S slots: slot[s] =
 // {key lo, key hi, p, q} with p the eraser (from the source tuple) and q
@@ -1155,6 +1198,7 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   uint32_t n = 0;
   const bool work = a.any_work != 0;
   mark(kStageClear);
+  if (work) cudaMemsetAsync(a.tfilter, 0, 4ull * ((a.tfilter_mask >> 5) + 1), s);
   k_clear<<<grid_for(a.bucket_hw > a.part_hw ? a.bucket_hw : a.part_hw, 256, num_sms, 4), 256, 0, s>>>(a);
   ++n;
   if (work && a.any_exact) { k_lazy_count<<<grid_for(a.switch_hw, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
@@ -1166,6 +1210,8 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   if (work) { k_sortpair<<<a.bucket_hw, kSortThreads, 0, s>>>(a); ++n; }
   mark(kStageBoundary);
   if (work) { k_boundary<<<grid_for(a.bucket_hw, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
+  mark(kStageSources);
+  if (work) { k_sources<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStageOverflow);
   if (work) {
     const int g = grid_for(a.ovf_cap, 256, num_sms, 2);

@@ -297,7 +297,7 @@ def gesmc_reset_stats(h):
     _check(load_library().gesmc_reset_stats(h), "gesmc_reset_stats")
 
 
-NUM_STAGES = 10
+NUM_STAGES = 11
 
 
 def gesmc_set_profiling(h, enable: bool):

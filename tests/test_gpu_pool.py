@@ -26,8 +26,8 @@ def mixed_graphs(seed=0):
         graphs.append((inputs.random_simple_graph(n, m, seed=100 + t), n))
     graphs.append((inputs.pld_graph(4000, 2.1, 1, 300, seed=5), 4000))
     graphs.append((inputs.workload_gnp_small(seed=2)[0], 1000))
-    graphs.append(inputs.double_star(3000, seed=6))   # overflowing partitions
-    graphs.append(inputs.double_star(5000, seed=7))
+    graphs.append(inputs.double_star(12000, seed=6))   # overflowing partitions: {0, 1} gets ~3000 inserts
+    graphs.append(inputs.double_star(16000, seed=7))
     for lst in ([], [(0, 1)], [(0, 1), (2, 3)], [(0, 1), (2, 3), (4, 5)]):
         e = oracle.pack([a for a, _ in lst], [b for _, b in lst]) if lst else np.zeros(0, np.uint64)
         graphs.append((e, 6))
@@ -66,7 +66,7 @@ def test_every_chain_matches_its_oracle_alone():
 
 def test_chains_join_and_leave_between_rounds():
     graphs = mixed_graphs(seed=1)
-    cap = sum(len(e) for e, _ in graphs[:8])
+    cap = max(sum(len(e) for e, _ in graphs[:8]), max(len(e) for e, _ in graphs))
     with gesmc.Pool(max_edges=cap, max_chains=6) as pool:
         live = {}   # chain id -> (graph index, seed, rounds run, expected list)
         queue = list(range(len(graphs)))
