@@ -266,7 +266,17 @@ def run_gesmc(args):
     edges, n = make_workload(args.workload)
     m, L = len(edges), len(edges) // 2
     seed = 1000 + rank
-    chain = gesmc.Chain(edges, n=n, tuple_log2=args.tuple_log2, group_log2=args.group_log2)
+    layout = {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2}
+    tuning = None
+    if not args.no_autotune and not (args.tuple_log2 or args.group_log2):
+        # partition size and table load factor timed on this graph (3 rounds per candidate, untimed here)
+        from paper_2111_03005_gb300 import autotune
+
+        t_tune = time.perf_counter()
+        tuning = autotune.tune([(edges, n)], [seed], rounds=3, cache=autotune.TuneCache(args.tune_cache))
+        tuning["tuning_s"] = time.perf_counter() - t_tune
+        layout = {"tuple_log2": tuning["tuple_log2"], "group_log2": tuning["group_log2"]}
+    chain = gesmc.Chain(edges, n=n, **layout)
     for _ in range(args.warmup):
         chain.run(ROUNDS_PER_STEP, seed)
     chain.reset_stats()
@@ -316,7 +326,7 @@ def run_gesmc(args):
         "roofline": roofline,
         "round": {"ms": round_ms, "algorithmic_GBps": round_bytes / (round_ms / 1e3) / 1e9,
                   "stages_ms": {k: round(v, 4) for k, v in per_stage.items()}},
-        "tuning": {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2},
+        "tuning": dict(layout, autotune=tuning),
         "waves": {"max": st["waves_max"], "mean": st["waves_total"] / max(st["rounds"], 1),
                   "accept_rate": st["accepted"] / max(st["switches"], 1)},
         "gpu_launches": st["kernel_launches"],
@@ -645,7 +655,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")
     ap.add_argument("--tuple-log2", type=int, default=0, help="tuning: mean tuples per partition (log2)")
-    ap.add_argument("--no-autotune", action="store_true", help="ensemble: default layout, no tuning")
+    ap.add_argument("--no-autotune", action="store_true", help="default layout, no tuning")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file")
     ap.add_argument("--group-log2", type=int, default=0, help="tuning: grouping table slots (log2)")
     ap.add_argument("--cpu-sample", choices=sorted(WORKLOADS), default=CPU_SAMPLE,

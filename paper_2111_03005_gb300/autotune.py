@@ -25,7 +25,7 @@ import tempfile
 
 import numpy as np
 
-CANDIDATES = ((9, 10), (9, 11), (10, 11), (10, 12), (11, 12))
+CANDIDATES = ((9, 10), (9, 11), (10, 11), (10, 12), (11, 11), (11, 12))
 
 
 def problem_key(device: str, total_edges: int, chains: int) -> str:

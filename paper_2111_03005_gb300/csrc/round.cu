@@ -607,37 +607,48 @@ __global__ void k_boundary(RoundArgs a) {
 // set bit can be a collision, which only adds a tuple nobody needs.  The
 // unpaired last slot of an odd list is a source no switch erases, and so are
 // the sources of a switch rejected outright.
-__global__ void __launch_bounds__(256, 8) k_sources(RoundArgs a) {
+// Sources of one pair of slots x (u = 0, 1: slots 2x, 2x + 1) after the
+// filter test; the pair's list entries and owner are loaded by the caller.
+__device__ __forceinline__ void sources_of_pair(const RoundArgs &a, uint32_t x, uint32_t c, ulonglong2 ee) {
+  if (c == kNoChain) return;
+  const ChainDesc ch = a.chains[c];
+  const uint32_t ls = 2 * x - ch.slot_base;
+  unsigned long long key[2] = {ee.x, ee.y}, hash[2];
+  uint32_t src = kTupleSource | kKeepK;
+  if (ls + 1 < ch.m) {
+    const uint32_t kg = ch.switch_base + (ls >> 1);
+    if ((__ldcs(&a.word[kg]) & kCodeMask) == 0) src = kTupleSource | kg;
+  } else {
+    key[1] = kEmptyKey;  // odd m: the unpaired last slot
+  }
+  uint32_t bit[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    hash[t] = mix64(key[t]);
+    bit[t] = filter_bit(a, hash[t]);
+  }
+  uint32_t w[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) w[t] = key[t] == kEmptyKey ? 0u : __ldcg(&a.tfilter[bit[t] >> 5]);
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+    if (!((w[t] >> (bit[t] & 31)) & 1u)) key[t] = kEmptyKey;
+  const uint32_t val[2] = {src, src};
+  emit_tuples<2>(a, ch, key, hash, val);
+}
+
+__global__ void __launch_bounds__(256, 6) k_sources(RoundArgs a) {
   const uint32_t npair = (a.slot_hw + 1) >> 1;
   const uint32_t nth = gridDim.x * blockDim.x;
-  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += nth) {
-    const uint32_t s0 = 2 * x;
-    const uint32_t c = a.owner_slot[s0];
-    if (c == kNoChain) continue;
-    const ChainDesc ch = a.chains[c];
-    const uint32_t ls = s0 - ch.slot_base;
-    unsigned long long key[2], hash[2];
-    uint32_t src;
-    if (ls + 1 < ch.m) {
-      const ulonglong2 ee = reinterpret_cast<const ulonglong2 *>(a.cedge)[x];
-      const uint32_t kg = ch.switch_base + (ls >> 1);
-      src = kTupleSource | ((__ldcs(&a.word[kg]) & kCodeMask) ? kKeepK : kg);
-      key[0] = ee.x;
-      key[1] = ee.y;
-    } else {
-      src = kTupleSource | kKeepK;
-      key[0] = a.cedge[s0];
-      key[1] = kEmptyKey;
-    }
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      if (key[t] == kEmptyKey) continue;
-      hash[t] = mix64(key[t]);
-      const uint32_t b = filter_bit(a, hash[t]);
-      if (!((__ldcg(&a.tfilter[b >> 5]) >> (b & 31)) & 1u)) key[t] = kEmptyKey;
-    }
-    const uint32_t val[2] = {src, src};
-    emit_tuples<2>(a, ch, key, hash, val);
+  // two pairs per thread and step: their loads are in flight together
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += 2 * nth) {
+    const uint32_t y = x + nth;
+    const uint32_t cx = a.owner_slot[2 * x], cy = y < npair ? a.owner_slot[2 * y] : kNoChain;
+    const ulonglong2 ex = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
+    ulonglong2 ey = make_ulonglong2(kEmptyKey, kEmptyKey);
+    if (y < npair) ey = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + y);
+    sources_of_pair(a, x, cx, ex);
+    sources_of_pair(a, y, cy, ey);
   }
 }
 

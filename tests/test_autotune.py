@@ -19,7 +19,7 @@ def test_pick_is_the_fastest_and_ties_keep_candidate_order():
 
 def test_tune_times_every_candidate_once_and_caches(tmp_path):
     graphs, seeds = fake_graphs(5)
-    times = {(9, 10): 5.0, (9, 11): 4.0, (10, 11): 2.5, (10, 12): 3.0, (11, 12): 9.0}
+    times = {(9, 10): 5.0, (9, 11): 4.0, (10, 11): 2.5, (10, 12): 3.0, (11, 11): 2.7, (11, 12): 9.0}
     calls = []
 
     def timer(g, s, rounds, cand):
