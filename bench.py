@@ -159,22 +159,27 @@ def read_peaks():
 def algorithmic_bytes(stage: str, m: int, L: int, nb: int, npart: int, accepted: float) -> float:
     """DRAM bytes a stage must move per round (streaming reads + writes).
 
-    Per switch (two positions, four 16-byte dependency tuples):
+    Per switch (two positions):
       permute:   read the list in slot order (2 x 12 B) and the status word (4 B),
                  write two 16-byte bucket records (their write frontiers stay in L2)
       sortpair:  read the two records (32 B); write the list in slot order (24 B),
                  the reject word (4 B), the dependency-entry pair (8 B) and append
-                 four tuples to their hash partitions (64 B)
-      group:     read the four tuples of the partition (64 B)
+                 the two target tuples to their hash partitions (32 B)
+      sources:   read the two list edges (16 B) and the reject word (4 B); the
+                 source tuples a target needs are rare in a sparse graph, and the
+                 ones a filter collision lets through are not counted
+      group:     read the two target tuples of the partition (32 B)
       wave1:     read the reject word, write the status word (8 B)
     The scans, the clear and the (normally empty) overflow pass move a few
-    bytes per bucket or partition."""
+    bytes per bucket or partition; the target filter stays in L2."""
     if stage == "permute":
         return 12.0 * m + 4.0 * L + 16.0 * m
     if stage == "sortpair":
-        return 16.0 * m + 12.0 * m + L * (4.0 + 8.0 + 64.0)
+        return 16.0 * m + 12.0 * m + L * (4.0 + 8.0 + 32.0)
+    if stage == "sources":
+        return 8.0 * m + 4.0 * L
     if stage == "group":
-        return 64.0 * L
+        return 32.0 * L
     if stage == "wave1":
         return 8.0 * L
     if stage in ("scan_perm", "clear"):
