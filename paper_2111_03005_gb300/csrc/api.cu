@@ -78,7 +78,7 @@ uint64_t filter_bits(uint64_t M) {
 
 // Offsets of the pieces of a pool's single device allocation.
 struct Layout {
-  size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, tfilter, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff,
+  size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, tfilter, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff, pblk,
       pib_pos, pib_edge, bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
       E, ctl, st, scratch, total;
 };
@@ -105,6 +105,7 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.prec = take(16ull * kPermBucketCap * c.buckets);
   l.pcount = take(4 * c.buckets);
   l.poff = take(4 * (c.buckets + 1));
+  l.pblk = take(4 * (c.buckets / 1024 + 2));
   l.pib_pos = take(4 * c.slots);
   l.pib_edge = take(8 * c.slots);
   l.bnd = take(4 * (c.buckets + 1));
@@ -315,6 +316,7 @@ void pool_bind(gesmc_pool_t p) {
   a.prec = at<uint4>(b, l.prec);
   a.pcount = at<uint32_t>(b, l.pcount);
   a.poff = at<uint32_t>(b, l.poff);
+  a.pblk = at<uint32_t>(b, l.pblk);
   a.pib_pos = at<uint32_t>(b, l.pib_pos);
   a.pib_edge = at<unsigned long long>(b, l.pib_edge);
   a.bnd = at<uint32_t>(b, l.bnd);

@@ -160,7 +160,8 @@ struct RoundArgs {
   unsigned long long *cedge;
   uint4 *prec;
   uint32_t *pcount;  // per bucket: records appended
-  uint32_t *poff;    // per bucket + 1: exclusive scan of pcount
+  uint32_t *poff;    // per bucket: exclusive scan of pcount within its block of 1024 buckets
+  uint32_t *pblk;    // per block of 1024 buckets + 1: exclusive scan of the block sums
   uint32_t *pib_pos;
   unsigned long long *pib_edge;
   uint32_t *bnd;

@@ -361,8 +361,9 @@ __global__ void __launch_bounds__(256, 6) k_permute(RoundArgs a) {
   }
 }
 
-// Exclusive scan of n counters (n + 1 offsets) by one CTA of 1024 threads;
-// counts above `clamp` are clamped (their overflow was already reported).
+// Exclusive scan of n counters (n + 1 offsets) by one CTA of 1024 threads,
+// in place if off == count; counts above `clamp` are clamped (their
+// overflow was already reported).
 __device__ __forceinline__ void cta_scan_1024(const uint32_t *count, uint32_t *off, uint32_t *copy, uint32_t n,
                                               uint32_t clamp) {
   __shared__ uint32_t part[1024];
@@ -381,15 +382,52 @@ __device__ __forceinline__ void cta_scan_1024(const uint32_t *count, uint32_t *o
   }
   uint32_t run = part[tid] - sum;
   for (uint32_t b = beg; b < end; ++b) {
+    const uint32_t c = min(count[b], clamp);  // read before writing: count may be off itself
     off[b] = run;
     if (copy) copy[b] = run;
-    run += min(count[b], clamp);
+    run += c;
   }
   if (tid == 1023) off[n] = part[1023];
 }
 
+// Bucket slot offsets in two steps: each CTA scans a block of 1024 bucket
+// counts (clamped to the capacity; an overflow was reported) and records the
+// block's sum; one CTA then scans the block sums.  A bucket's offset is
+// pblk[b / 1024] + poff[b].
 __global__ void __launch_bounds__(1024) k_scan_perm(RoundArgs a) {
-  cta_scan_1024(a.pcount, a.poff, nullptr, a.bucket_hw, kPermBucketCap);
+  __shared__ uint32_t warp_tot[32];
+  const uint32_t b = blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t v = b < a.bucket_hw ? min(a.pcount[b], (uint32_t)kPermBucketCap) : 0u;
+  uint32_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += u;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= (uint32_t)d) t += u;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (b < a.bucket_hw) a.poff[b] = incl - v + (warp ? warp_tot[warp - 1] : 0u);
+  if (threadIdx.x == 1023) a.pblk[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(RoundArgs a) {
+  const uint32_t nblk = (a.bucket_hw + 1023) / 1024;
+  cta_scan_1024(a.pblk, a.pblk, nullptr, nblk, 0xFFFFFFFFu);
+}
+
+__device__ __forceinline__ uint32_t bucket_offset(const RoundArgs &a, uint32_t b) {
+  return a.pblk[b >> 10] + a.poff[b];
 }
 
 // Overflow tuples (those that found their partition full), grouped by
@@ -477,7 +515,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
     const ChainDesc ch = a.chains[c];
     const unsigned long long round = chain_round(ch, R);
     const uint32_t ell = ch.exact_ell ? a.chain_ell[c] : 0u;
-    const uint32_t loff = a.poff[b] - a.poff[ch.bucket_base];  // chain-local slot offset
+    const uint32_t loff = bucket_offset(a, b) - bucket_offset(a, ch.bucket_base);  // chain-local slot offset
     const uint32_t goff = ch.slot_base + loff;
     const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
     const uint4 *rec = a.prec + (size_t)b * kPermBucketCap;
@@ -1216,7 +1254,11 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   mark(kStagePermute);
   if (work) { k_permute<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStageScanPerm);
-  if (work) { k_scan_perm<<<1, 1024, 0, s>>>(a); ++n; }
+  if (work) {
+    k_scan_perm<<<a.bucket_hw ? (a.bucket_hw + 1023) / 1024 : 1, 1024, 0, s>>>(a);
+    k_scan_blocks<<<1, 1024, 0, s>>>(a);
+    n += 2;
+  }
   mark(kStageSortPair);
   if (work) { k_sortpair<<<a.bucket_hw, kSortThreads, 0, s>>>(a); ++n; }
   mark(kStageBoundary);

@@ -18,9 +18,9 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2111_03005_gb300 import gesmc  # noqa: E402
 
 
-# kernels of a round whose rounds need one wave (clear, permute, scan, sort, boundary, sources,
-# three overflow kernels, group, wave 1, tail)
-ROUND_LAUNCHES = 12
+# kernels of a round whose rounds need one wave (clear, permute, two scans, sort, boundary,
+# sources, three overflow kernels, group, wave 1, tail)
+ROUND_LAUNCHES = 13
 
 
 def first_diff(a, b):
