@@ -372,7 +372,7 @@ def run_gesmc(args):
         for step in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with gesmc.Chain(host_in, n=n) as c:
+            with gesmc.Chain(host_in, n=n, **layout) as c:
                 c.run(ROUNDS_PER_STEP, seed + 7)
                 c.edges(host_out)
             torch.cuda.synchronize()
@@ -380,7 +380,8 @@ def run_gesmc(args):
         e2e_t = max_over_ranks(statistics.median(e2e_times), dist, dev)
         line["e2e"] = {"value": world * ROUNDS_PER_STEP * L / e2e_t, "unit": UNIT,
                        "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * m,
-                       "includes": "gesmc_create (H2D copy, validation) + gesmc_run(20) + gesmc_edges (D2H) + destroy"}
+                       "includes": "gesmc_create (H2D copy, validation) + gesmc_run(20) + gesmc_edges (D2H) + destroy",
+                       "layout": layout}
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sw, dt = cpu_sample_switches_per_s()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
