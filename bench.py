@@ -411,7 +411,9 @@ def run_ensemble(args):
     total = sum(len(e) for e, _ in graphs)
     L_total = sum(len(e) // 2 for e, _ in graphs)
     layout, tuning = {}, None
-    if not args.no_autotune:
+    if args.tuple_log2 or args.group_log2:
+        layout = {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2}
+    elif not args.no_autotune:
         # partition size and table load factor timed on a sample of the ensemble itself
         t_tune = time.perf_counter()
         tuning = autotune.tune(graphs, seeds, rounds=3, cache=autotune.TuneCache(args.tune_cache),

@@ -29,6 +29,8 @@ struct ChainShape {
   uint32_t m, L, B, nb, P, np, capt;
   uint32_t slots() const { return (m + 1) & ~1u; }  // slot ranges start on even slots
   uint64_t tuples() const { return (uint64_t)np * capt; }
+  uint32_t tstride() const { return P <= kSpreadLog2 ? kSpreadStride : 1u; }
+  uint64_t tcounts() const { return (uint64_t)np * tstride(); }
 };
 
 bool chain_shape(uint64_t m, uint32_t tuple_log2, ChainShape *s) {
@@ -51,7 +53,7 @@ bool chain_shape(uint64_t m, uint32_t tuple_log2, ChainShape *s) {
 // Capacities of a pool's index spaces for at most M edges in at most C
 // chains; each bound holds for any split of the edges into chains.
 struct Capacity {
-  uint64_t slots, switches, buckets, parts, tuples, ovf, dep;
+  uint64_t slots, switches, buckets, parts, tuples, ovf, dep, tcounts;
 };
 
 Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
@@ -64,6 +66,7 @@ Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
   c.tuples = 2 * ntuple + 64 * c.parts;
   c.ovf = ntuple;
   c.dep = M + 1;
+  c.tcounts = kSpreadStride * c.parts;  // bounds the sum over chains of np * stride
   return c;
 }
 
@@ -117,7 +120,7 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.ptup = take(16 * c.tuples);
   l.otup = take(16 * c.ovf);
   l.stup = take(16 * c.ovf);
-  l.tcount = take(4 * c.parts);
+  l.tcount = take(4 * c.tcounts);
   l.ocount = take(4 * c.parts);
   l.ooff = take(4 * (c.parts + 1));
   l.ocursor = take(4 * c.parts);
@@ -233,7 +236,7 @@ struct gesmc_pool_ctx {
   uint32_t tuple_log2 = kDefaultTupleLog2;
   Capacity cap;
   Layout lay;
-  RangeSet slots, switches, buckets, parts, tuples;
+  RangeSet slots, switches, buckets, parts, tuples, tcounts;
   std::vector<HostChain> chains;
   uint32_t live_chains = 0, working_chains = 0;
   uint64_t live_edges = 0;
@@ -286,6 +289,7 @@ void refresh_args(gesmc_pool_t p) {
   a.switch_hw = (uint32_t)p->switches.high_water();
   a.bucket_hw = (uint32_t)p->buckets.high_water();
   a.part_hw = (uint32_t)p->parts.high_water();
+  a.tcount_hw = (uint32_t)p->tcounts.high_water();
   a.any_work = p->working_chains > 0;
   a.wave_kernels = p->wave_kernels;
   a.chain_hw = 0;
@@ -357,6 +361,7 @@ int pool_init(gesmc_pool_t p, const gesmc_pool_opts &o) {
   p->buckets.reset(p->cap.buckets);
   p->parts.reset(p->cap.parts);
   p->tuples.reset(p->cap.tuples);
+  p->tcounts.reset(p->cap.tcounts);
   p->chains.assign(p->max_chains, HostChain());
   pool_bind(p);
   RoundArgs &a = p->args;
@@ -432,6 +437,7 @@ void release_ranges(gesmc_pool_t p, const HostChain &hc) {
   p->buckets.release(hc.d.bucket_base, hc.shape.nb);
   p->parts.release(hc.d.part_base, hc.shape.np);
   p->tuples.release(hc.d.tuple_base, hc.shape.tuples());
+  p->tcounts.release(hc.d.tcount_base, hc.shape.tcounts());
 }
 
 // Ranges for a chain of this shape, all or none.
@@ -461,11 +467,22 @@ bool alloc_ranges(gesmc_pool_t p, HostChain &hc) {
     p->parts.release(pb, sh.np);
     return false;
   }
+  uint64_t cb = 0;
+  if (!p->tcounts.alloc(sh.tcounts(), &cb)) {
+    p->slots.release(sb, sh.slots());
+    p->switches.release(wb, sh.L);
+    p->buckets.release(bb, sh.nb);
+    p->parts.release(pb, sh.np);
+    p->tuples.release(tb, sh.tuples());
+    return false;
+  }
   hc.d.slot_base = (uint32_t)sb;
   hc.d.switch_base = (uint32_t)wb;
   hc.d.bucket_base = (uint32_t)bb;
   hc.d.part_base = (uint32_t)pb;
   hc.d.tuple_base = (uint32_t)tb;
+  hc.d.tcount_base = (uint32_t)cb;
+  hc.d.tstride = sh.tstride();
   return true;
 }
 

@@ -112,6 +112,13 @@ constexpr int kGroupSlotBytes = 20;
 
 constexpr int kWaveHist = 64;
 
+// A chain with at most 2^kSpreadLog2 partitions keeps its partition cursors
+// kSpreadStride words (one L2 line) apart: all its sort CTAs append to them
+// at once, and packed into a few lines they would contend for them.  Larger
+// chains keep them packed (their cursors are spread by number already).
+constexpr uint32_t kSpreadLog2 = 12;
+constexpr uint32_t kSpreadStride = 32;
+
 // One chain of the pool.  Its round number in pool round R (R rounds
 // completed) is start_round + (R - join); its last round's decisions are
 // pending in status[] once R > added, the pool round at which the chain was
@@ -122,7 +129,8 @@ struct ChainDesc {
   uint32_t bucket_base, B;    // 2^B permutation buckets from bucket_base
   uint32_t part_base, P;      // 2^P tuple partitions from part_base
   uint32_t tuple_base, capt;  // partition j of the chain holds capt tuples from tuple_base + j * capt
-  uint32_t exact_ell, spare;  // exact l: run only the first l switches (l counted per round)
+  uint32_t exact_ell, tstride;  // exact l; distance of the chain's partition cursors (words)
+  uint32_t tcount_base, pad;    // the chain's partition cursors start here
   unsigned long long seed, start_round, join, added, lazy_threshold;
 };
 
@@ -173,7 +181,7 @@ struct RoundArgs {
   uint4 *ptup;
   uint4 *otup;
   uint4 *stup;
-  uint32_t *tcount;   // per partition: tuples appended (may exceed capt)
+  uint32_t *tcount;   // partition cursors: chain c's partition j at tcount_base + j * tstride (may exceed capt)
   uint32_t *ocount;   // per partition: overflow tuples
   uint32_t *ooff;     // per partition + 1
   uint32_t *ocursor;  // per partition
@@ -182,7 +190,7 @@ struct RoundArgs {
   uint32_t tfilter_mask;  // bits - 1
   Counters *ctl;
   StatsDev *st;
-  uint32_t slot_hw, switch_hw, bucket_hw, part_hw;
+  uint32_t slot_hw, switch_hw, bucket_hw, part_hw, tcount_hw;
   uint32_t ovf_cap, dep_cap;
   uint32_t max_waves;
   uint32_t group_log2;  // shared-memory grouping table: 2^group_log2 slots

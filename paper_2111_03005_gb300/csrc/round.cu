@@ -127,7 +127,7 @@ __device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc 
     const unsigned long long h = hash[t];
     part[t] = partition_of(h, ch.P);
     hlo[t] = (uint32_t)h;
-    idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[ch.part_base + part[t]], 1u) : 0u;
+    idx[t] = key[t] != kEmptyKey ? atomicAdd(&a.tcount[ch.tcount_base + part[t] * ch.tstride], 1u) : 0u;
   }
 #pragma unroll
   for (int t = 0; t < N; ++t) {
@@ -274,10 +274,8 @@ __device__ __forceinline__ void append_if(bool take, uint32_t k, uint32_t *list,
 __global__ void k_clear(RoundArgs a) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (uint32_t b = tid; b < a.bucket_hw; b += nth) a.pcount[b] = 0;
-  for (uint32_t p = tid; p < a.part_hw; p += nth) {
-    a.tcount[p] = 0;
-    a.ocount[p] = 0;
-  }
+  for (uint32_t p = tid; p < a.part_hw; p += nth) a.ocount[p] = 0;
+  for (uint32_t p = tid; p < a.tcount_hw; p += nth) a.tcount[p] = 0;
   for (uint32_t c = tid; c < a.chain_hw; c += nth) a.chain_ell[c] = 0;
   if (tid == 0) {
     a.ctl->pending[0] = 0;
@@ -807,7 +805,8 @@ __global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) {
     const uint32_t pbase = a.chains[c].part_base, tbase = a.chains[c].tuple_base, capt = a.chains[c].capt;
     // the partition's tuples: its own region, then its overflow tuples
     const uint4 *prim = a.ptup + tbase + (size_t)(part - pbase) * capt;
-    const uint32_t nprim = min(a.tcount[part], capt);
+    const ChainDesc &cd = a.chains[c];
+    const uint32_t nprim = min(a.tcount[cd.tcount_base + (part - pbase) * cd.tstride], capt);
     const uint32_t obeg = ovf ? a.ooff[part] : 0, oend = ovf ? a.ooff[part + 1] : 0;
     const uint32_t ntup = nprim + (oend - obeg);
     if (ntup <= (uint32_t)(kGroupR * kGroupThreads)) {
@@ -1248,7 +1247,7 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   const bool work = a.any_work != 0;
   mark(kStageClear);
   if (work) cudaMemsetAsync(a.tfilter, 0, 4ull * ((a.tfilter_mask >> 5) + 1), s);
-  k_clear<<<grid_for(a.bucket_hw > a.part_hw ? a.bucket_hw : a.part_hw, 256, num_sms, 4), 256, 0, s>>>(a);
+  k_clear<<<grid_for(max(max(a.bucket_hw, a.part_hw), a.tcount_hw), 256, num_sms, 4), 256, 0, s>>>(a);
   ++n;
   if (work && a.any_exact) { k_lazy_count<<<grid_for(a.switch_hw, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStagePermute);
