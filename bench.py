@@ -363,6 +363,19 @@ def run_gesmc(args):
             "switches_per_s": 1.0 / t_switch, "frac": value * t_switch,
             "model": "per switch: 8 random loads + 2 random atomics + 6a random writes + 130 streaming bytes",
         }
+        # the L2-operation roofline of the permutation scatter: per position one cursor atomic
+        # with its result and one 16-byte record store, at the rates of L2-resident random
+        # atomics and stores (64 MB buffer); the kernel's live duration against that time
+        l2 = {name: gesmc.gesmc_probe_random_access(64 << 20, kind, 1 << 29)
+              for name, kind in (("atomic_add", gesmc.RANDOM_ATOMIC_ADD), ("store", gesmc.RANDOM_STORE),
+                                 ("red", gesmc.RANDOM_RED))}
+        t_perm = m * (1.0 / l2["atomic_add"] + 1.0 / l2["store"])
+        line["l2_op_roofline"] = {
+            "kernel": "k_permute", "ops_per_launch": 2 * m, "bound_ms": 1e3 * t_perm,
+            "achieved_ms": per_stage.get("permute"), "frac": 1e3 * t_perm / per_stage["permute"],
+            "rates_per_s": l2,
+            "model": "per position: one cursor atomic with return + one record store, L2-resident rates",
+        }
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
