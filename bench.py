@@ -527,15 +527,22 @@ def run_serve(args):
             alone.append(c.edges())
         svc.append(time.perf_counter() - t1)
     stream = torch.cuda.Stream()
+    classes = tuple(int(float(x)) for x in args.size_classes.split(",") if x.strip())
+    poll = 2e-4 if classes else None   # with several pools, admit to an idle one while another runs
     for rate in [float(x) for x in args.rates.split(",")]:
         reqs = [serve.Request(rid=rid, edges=e, n=n, seed=seed, rounds=rounds)
                 for rid, (e, n, seed, rounds) in enumerate(base)]
         offsets = (np.cumsum(unit_gaps) - unit_gaps[0]) / rate
         with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
                                                      max_rounds_per_step=args.rounds_per_step,
-                                                     stream=stream) as srv:
-            # warm the kernels once (a small request, not counted)
-            srv.submit(serve.Request(rid=-1, edges=reqs[0].edges, n=reqs[0].n, seed=1, rounds=3))
+                                                     size_classes=classes, stream=stream) as srv:
+            # warm the kernels of every pool once (one request each, not counted)
+            warmed = set()
+            for r in reqs:
+                lane = id(srv._lane_of(r))
+                if lane not in warmed:
+                    warmed.add(lane)
+                    srv.submit(serve.Request(rid=-1, edges=r.edges, n=r.n, seed=1, rounds=3))
             while not srv.idle():
                 srv.step()
             srv.done.clear()
@@ -549,7 +556,7 @@ def run_serve(args):
                 if srv.idle():
                     time.sleep(max(0.0, min(0.01, offsets[nxt] - now)) if nxt < len(reqs) else 0)
                     continue
-                srv.step()
+                srv.step(poll)
             wall = time.perf_counter() - t0
             rounds_run = srv.rounds_run
         for r, out in zip(reqs, alone):
@@ -569,7 +576,8 @@ def run_serve(args):
             "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {rate}/s, power-law graphs with "
                                    f"m log-uniform in [1e3, 1e7], 10-100 global switches each",
                        "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work,
-                       "max_rounds_per_step": args.rounds_per_step},
+                       "max_rounds_per_step": args.rounds_per_step,
+                       "size_classes": list(classes)},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max()),
                           "p50_small_requests": float(np.percentile(lat[small], 50)) if small.any() else None},
@@ -672,6 +680,8 @@ def main(argv=None):
     ap.add_argument("--pool-edges", type=int, default=40_000_000, help="serve: pool capacity in edges")
     ap.add_argument("--pool-chains", type=int, default=256, help="serve: pool capacity in chains")
     ap.add_argument("--rounds-per-step", type=int, default=8, help="serve: most rounds between admissions")
+    ap.add_argument("--size-classes", default="",
+                    help="serve: edge-count bounds of the size classes (one pool each), comma-separated")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")

@@ -15,8 +15,9 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2111_03005_gb300 import ensemble, gesmc, serve  # noqa: E402
 
 
-@pytest.mark.parametrize("rounds_per_step", [1, 8])
-def test_served_requests_equal_their_oracle_runs(rounds_per_step):
+@pytest.mark.parametrize("rounds_per_step,size_classes,timeout", [(1, (), None), (8, (), None),
+                                                                  (3, (2000,), None), (8, (1000, 5000), 0.0005)])
+def test_served_requests_equal_their_oracle_runs(rounds_per_step, size_classes, timeout):
     rng = np.random.default_rng(3)
     reqs = []
     for rid in range(24):
@@ -26,16 +27,18 @@ def test_served_requests_equal_their_oracle_runs(rounds_per_step):
                                   start_round=int(rng.integers(0, 5))))
     cap = sum(len(r.edges) for r in reqs) // 3          # not everything fits at once
     cap = max(cap, max(len(r.edges) for r in reqs))
-    with serve.Server(max_edges=cap, max_chains=8, max_rounds_per_step=rounds_per_step) as srv:
+    with serve.Server(max_edges=cap, max_chains=8, max_rounds_per_step=rounds_per_step,
+                      size_classes=size_classes) as srv:
+        assert len(srv.lanes) == len(size_classes) + 1
         arrivals = sorted(rng.integers(0, 30, size=len(reqs)))
         step, nxt = 0, 0
         while nxt < len(reqs) or not srv.idle():
             while nxt < len(reqs) and arrivals[nxt] <= step:   # requests arrive while others run
                 srv.submit(reqs[nxt])
                 nxt += 1
-            srv.step()
+            srv.step(timeout)
             step += 1
-            assert step < 10_000
+            assert step < 1_000_000
         assert len(srv.done) == len(reqs)
     for r in reqs:
         expect, st = oracle.run(r.edges, seed=r.seed, rounds=r.rounds, start_round=r.start_round)
