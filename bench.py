@@ -189,15 +189,17 @@ def algorithmic_bytes(stage: str, m: int, L: int, nb: int, npart: int, accepted:
 
 def traffic_from_profile(kernel: str, workload: str):
     """Measured DRAM bytes per launch of `kernel` from the committed ncu
-    summary, if the kernel's source has not changed since it was taken."""
+    summary, if neither the kernels nor the layout (round.cu, api.cu) have
+    changed since it was taken."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
     try:
         kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line)
-        src = open(os.path.join(ROOT, "paper_2111_03005_gb300", "csrc", "round.cu"), "rb").read()
-        if kv.get("round_cu_sha256", "").strip() != hashlib.sha256(src).hexdigest():
-            return None
+        for name in ("round.cu", "api.cu"):
+            src = open(os.path.join(ROOT, "paper_2111_03005_gb300", "csrc", name), "rb").read()
+            if kv.get(name.replace(".", "_") + "_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+                return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
@@ -281,6 +283,17 @@ def run_gesmc(args):
         tuning = autotune.tune([(edges, n)], [seed], rounds=3, cache=autotune.TuneCache(args.tune_cache))
         tuning["tuning_s"] = time.perf_counter() - t_tune
         layout = {"tuple_log2": tuning["tuple_log2"], "group_log2": tuning["group_log2"]}
+    # create time (the paper's timings include initialisation): validation, edge set and first layout from a
+    # device-resident list; the second of two creates (the first also pays one-time driver work)
+    d_edges = torch.from_numpy(edges.view(np.int64)).to(dev)
+    create_ms = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with gesmc.Chain(d_edges, n=n, **layout):
+            torch.cuda.synchronize()
+            create_ms.append(1e3 * (time.perf_counter() - t0))
+    del d_edges
     chain = gesmc.Chain(edges, n=n, **layout)
     for _ in range(args.warmup):
         chain.run(ROUNDS_PER_STEP, seed)
@@ -335,6 +348,7 @@ def run_gesmc(args):
         "waves": {"max": st["waves_max"], "mean": st["waves_total"] / max(st["rounds"], 1),
                   "accept_rate": st["accepted"] / max(st["switches"], 1)},
         "gpu_launches": st["kernel_launches"],
+        "create_ms": {"from_device": create_ms[-1]},
     }
     clk = clocks.summary()
     line["clocks"] = clk
@@ -381,11 +395,13 @@ def run_gesmc(args):
     if not args.no_e2e:
         host_in = torch.from_numpy(edges.view(np.int64)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        e2e_times = []
+        e2e_times, host_create = [], []
         for step in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with gesmc.Chain(host_in, n=n, **layout) as c:
+                torch.cuda.synchronize()
+                host_create.append(1e3 * (time.perf_counter() - t0))
                 c.run(ROUNDS_PER_STEP, seed + 7)
                 c.edges(host_out)
             torch.cuda.synchronize()
@@ -395,6 +411,7 @@ def run_gesmc(args):
                        "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * m,
                        "includes": "gesmc_create (H2D copy, validation) + gesmc_run(20) + gesmc_edges (D2H) + destroy",
                        "layout": layout}
+        line["create_ms"]["from_pinned_host"] = statistics.median(host_create)
     if rank == 0 and world == 1 and not args.no_cpu:
         v, sw, dt = cpu_sample_switches_per_s()
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -46,7 +46,10 @@ bool chain_shape(uint64_t m, uint32_t tuple_log2, ChainShape *s) {
   while ((ntuple >> P) > (1ull << tuple_log2)) ++P;
   s->P = P;
   s->np = 1u << P;
-  s->capt = (uint32_t)((ntuple >> P) * 2 + 64);  // room for twice the mean
+  // room for the mean at four tuples per switch (the target filter lets
+  // about 2.4 through) plus a margin; a partition that fills anyway spills
+  // to the overflow list, which has room for every tuple
+  s->capt = (uint32_t)((ntuple >> P) + 64);
   return true;
 }
 
@@ -58,12 +61,26 @@ struct Capacity {
 
 Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
   Capacity c;
+  ChainShape one;
+  if (C == 1 && chain_shape(M, tuple_log2, &one)) {
+    // one chain: its own shape, which also covers any smaller chain (every
+    // piece of a shape grows with m)
+    c.slots = one.slots();
+    c.switches = one.L + 1;
+    c.buckets = one.nb;
+    c.parts = one.np;
+    c.tuples = one.tuples();
+    c.ovf = 4ull * one.L + 1;
+    c.dep = M + 1;
+    c.tcounts = one.tcounts();
+    return c;
+  }
   c.slots = M + C;
   c.switches = M / 2 + C;
   c.buckets = 2 * (M >> kPermAvgLog2) + 2 * C;
   const uint64_t ntuple = 2 * M + C;  // bounds the sum over chains of 4L + 1
   c.parts = 2 * (ntuple >> tuple_log2) + 4 * C;
-  c.tuples = 2 * ntuple + 64 * c.parts;
+  c.tuples = ntuple + 64 * c.parts;  // bounds the sum over chains of np * capt
   c.ovf = ntuple;
   c.dep = M + 1;
   c.tcounts = kSpreadStride * c.parts;  // bounds the sum over chains of np * stride
@@ -82,7 +99,7 @@ uint64_t filter_bits(uint64_t M) {
 // Offsets of the pieces of a pool's single device allocation.
 struct Layout {
   size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, tfilter, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff, pblk,
-      pib_pos, pib_edge, bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
+      bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
       E, ctl, st, scratch, total;
 };
 
@@ -105,12 +122,14 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.owner_part = take(4 * c.parts);
   l.cpos = take(4 * c.slots);
   l.cedge = take(8 * c.slots);
-  l.prec = take(16ull * kPermBucketCap * c.buckets);
+  // the permutation records are dead once the sort has read them, so the
+  // overflow tuples sorted by partition (written after the sort, read by the
+  // grouping) share their bytes; so does ParES's edge set, between rounds
+  l.prec = take(std::max<uint64_t>(16ull * kPermBucketCap * c.buckets, 16ull * c.ovf));
+  l.stup = l.prec;
   l.pcount = take(4 * c.buckets);
   l.poff = take(4 * (c.buckets + 1));
   l.pblk = take(4 * (c.buckets / 1024 + 2));
-  l.pib_pos = take(4 * c.slots);
-  l.pib_edge = take(8 * c.slots);
   l.bnd = take(4 * (c.buckets + 1));
   l.word = take(4 * c.switches);
   l.sw = take(8 * c.switches);
@@ -119,7 +138,6 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.list1 = take(4 * c.switches);
   l.ptup = take(16 * c.tuples);
   l.otup = take(16 * c.ovf);
-  l.stup = take(16 * c.ovf);
   l.tcount = take(4 * c.tcounts);
   l.ocount = take(4 * c.parts);
   l.ooff = take(4 * (c.parts + 1));
@@ -321,8 +339,6 @@ void pool_bind(gesmc_pool_t p) {
   a.pcount = at<uint32_t>(b, l.pcount);
   a.poff = at<uint32_t>(b, l.poff);
   a.pblk = at<uint32_t>(b, l.pblk);
-  a.pib_pos = at<uint32_t>(b, l.pib_pos);
-  a.pib_edge = at<unsigned long long>(b, l.pib_edge);
   a.bnd = at<uint32_t>(b, l.bnd);
   a.word = at<uint32_t>(b, l.word);
   a.tfilter = at<uint32_t>(b, l.tfilter);
@@ -652,9 +668,9 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
 // ParES (Algorithm 2) on the live chains of the pool (all of them, or only
 // `only`): each runs `switches` ES-MC switches with its own seed, numbered
 // on from its last ES-MC switch.  Each chain's list leaves its slots for
-// its tuple storage (position order), where its edge set and first-touch
-// table also live (the ParES kernel rebuilds the set when tombstones pass a
-// quarter of its slots).
+// its tuple storage (position order), where its first-touch table also
+// lives; its edge set lives in its permutation records (the ParES kernel
+// rebuilds the set when tombstones pass a quarter of its slots).
 int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   if (p->broken) return p->broken;
   if (switches == 0) return GESMC_OK;
@@ -675,16 +691,21 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
     jb.count = switches;
     jb.chain = c;
     if (jb.m >= 2) {
+      // the list (position order) and the first-touch table in the chain's
+      // tuple storage (at least 32 bytes per edge), the edge set in its
+      // permutation records (at least 32 bytes per edge: 2^h >= 2m slots)
       char *base = tup + 16ull * hc.d.tuple_base;
       const uint64_t bytes = 16ull * hc.d.capt << hc.d.P;
-      const uint64_t first_off = align_up(8ull * jb.m), h_off = align_up(first_off + 4ull * jb.m);
-      if (h_off >= bytes) return GESMC_E_INTERNAL;
+      const uint64_t first_off = align_up(8ull * jb.m);
+      if (first_off + 4ull * jb.m > bytes) return GESMC_E_INTERNAL;
+      char *hbase = reinterpret_cast<char *>(a.prec) + 16ull * kPermBucketCap * hc.d.bucket_base;
+      const uint64_t hbytes = 16ull * kPermBucketCap * hc.shape.nb;
       uint32_t hlog2 = 0;
-      while ((16ull << hlog2) <= bytes - h_off && hlog2 < 31) ++hlog2;  // largest 2^h with 8 * 2^h <= room
+      while ((16ull << hlog2) <= hbytes && hlog2 < 31) ++hlog2;  // largest 2^h with 8 * 2^h <= room
       if ((1ull << hlog2) < 2ull * jb.m) return GESMC_E_INTERNAL;
       jb.E = reinterpret_cast<unsigned long long *>(base);
       jb.first = reinterpret_cast<uint32_t *>(base + first_off);
-      jb.H = reinterpret_cast<unsigned long long *>(base + h_off);
+      jb.H = reinterpret_cast<unsigned long long *>(hbase);
       jb.hlog2 = hlog2;
     }
     // chains with m < 2 have no list to move (their switches are only counted)

@@ -29,7 +29,9 @@
 //   otup/stup    uint4[overflow cap]      tuples beyond a partition's
 //                                         capacity ({.., partition}), and
 //                                         the same grouped by partition in
-//                                         the ptup format (rare)
+//                                         the ptup format (rare); stup
+//                                         shares prec's bytes (the records
+//                                         are dead after the sort)
 //   dep          uint2[dep cap]           {p, q} of every edge id with a
 //                                         dependency
 //   tfilter      u32[bits / 32]           target filter: the bit of every
@@ -170,8 +172,6 @@ struct RoundArgs {
   uint32_t *pcount;  // per bucket: records appended
   uint32_t *poff;    // per bucket: exclusive scan of pcount within its block of 1024 buckets
   uint32_t *pblk;    // per block of 1024 buckets + 1: exclusive scan of the block sums
-  uint32_t *pib_pos;
-  unsigned long long *pib_edge;
   uint32_t *bnd;
   uint32_t *word;
   uint2 *sw;

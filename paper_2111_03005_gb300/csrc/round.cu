@@ -599,18 +599,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
       build_switch(a, ch, round, ell, (loff + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1],
                    sedge[t + 1]);
     }
-    if (tid == 0 && cnt > 0) {
-      if (t0 == 1) {  // this bucket's first slot is the second of a pair started in an earlier bucket
-        a.pib_pos[goff] = (uint32_t)scomp[0];
-        a.pib_edge[goff] = sedge[0];
-        const uint32_t idx = atomicAdd(&a.ctl->boundary, 1u);
-        a.bnd[idx] = goff - 1;  // the pair's first slot
-      }
-      const uint32_t last = loff + cnt - 1;
-      if ((last & 1u) == 0 && last + 1 < ch.m) {  // first of a pair whose partner is in a later bucket
-        a.pib_pos[goff + cnt - 1] = (uint32_t)scomp[cnt - 1];
-        a.pib_edge[goff + cnt - 1] = sedge[cnt - 1];
-      }
+    if (tid == 0 && t0 == 1 && cnt > 0) {
+      // this bucket's first slot is the second of a pair started in an
+      // earlier bucket: k_boundary builds that switch from the list
+      const uint32_t idx = atomicAdd(&a.ctl->boundary, 1u);
+      a.bnd[idx] = goff - 1;  // the pair's first slot
     }
     __syncthreads();
   }
@@ -632,8 +625,9 @@ __global__ void k_boundary(RoundArgs a) {
       atomicOr(&a.ctl->err, kErrRecord);
       continue;
     }
-    build_switch(a, ch, chain_round(ch, R), ch.exact_ell ? a.chain_ell[c] : 0u, k, a.pib_pos[g], a.pib_edge[g],
-                 a.pib_pos[g + 1], a.pib_edge[g + 1]);
+    // both slots were written by the sort kernel (the list in this round's slot order)
+    build_switch(a, ch, chain_round(ch, R), ch.exact_ell ? a.chain_ell[c] : 0u, k, a.cpos[g], a.cedge[g],
+                 a.cpos[g + 1], a.cedge[g + 1]);
   }
 }
 // The sources of every switch (Algorithm 1's ERASE tuples) from the list in

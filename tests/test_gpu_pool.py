@@ -126,3 +126,34 @@ def test_invalid_chain_does_not_disturb_the_pool():
         pool.run(3)
         expect, _ = oracle.run(e, seed=9, rounds=3)
         assert np.array_equal(pool.edges(c), expect)
+
+
+@pytest.mark.slow
+def test_ensemble_4096_fifty_rounds_match_oracle_digests(golden_dir):
+    """The whole null-model ensemble (4096 graphs, 1.46e8 edges) in one pool
+    with the autotuner's layout, 50 global switches: every chain's final list
+    and accepted count against the sequential oracle run on that chain alone
+    (digests written by tests/golden/make_ensemble_digests.py)."""
+    import hashlib
+    import json
+    import os
+
+    with open(os.path.join(golden_dir, "ensemble_4096_digests.json")) as f:
+        gold = json.load(f)
+    graphs = inputs.ensemble_graphs(gold["count"], seed=gold["gen_seed"])
+    h = hashlib.sha256()
+    for e, n in graphs:
+        h.update(np.array([n, len(e)], dtype="<u8").tobytes())
+        h.update(np.ascontiguousarray(e, dtype="<u8").tobytes())
+    assert h.hexdigest() == gold["inputs_sha256"], "the generator gave other graphs on this machine"
+    total = sum(len(e) for e, _ in graphs)
+    with gesmc.Pool(max_edges=total, max_chains=len(graphs), tuple_log2=11, group_log2=11) as pool:
+        ids = [pool.add(e, n=n, seed=gold["seed0"] + t) for t, (e, n) in enumerate(graphs)]
+        pool.run(gold["rounds"])
+        bad = []
+        for t, c in enumerate(ids):
+            out = pool.edges(c)
+            d = hashlib.sha256(np.ascontiguousarray(out, dtype="<u8").tobytes()).hexdigest()[:16]
+            if d != gold["digests"][t] or pool.chain_info(c)["accepted"] != gold["accepted"][t]:
+                bad.append(t)
+    assert not bad, f"{len(bad)} chains differ, first {bad[:8]}"
