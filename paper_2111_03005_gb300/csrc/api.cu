@@ -668,9 +668,9 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
 // ParES (Algorithm 2) on the live chains of the pool (all of them, or only
 // `only`): each runs `switches` ES-MC switches with its own seed, numbered
 // on from its last ES-MC switch.  Each chain's list leaves its slots for
-// its tuple storage (position order), where its first-touch table also
-// lives; its edge set lives in its permutation records (the ParES kernel
-// rebuilds the set when tombstones pass a quarter of its slots).
+// its tuple storage (position order); its edge set lives in its
+// permutation records (the ParES kernel rebuilds the set when tombstones
+// pass a quarter of its slots).
 int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   if (p->broken) return p->broken;
   if (switches == 0) return GESMC_OK;
@@ -691,28 +691,33 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
     jb.count = switches;
     jb.chain = c;
     if (jb.m >= 2) {
-      // the list (position order) and the first-touch table in the chain's
-      // tuple storage (at least 32 bytes per edge), the edge set in its
-      // permutation records (at least 32 bytes per edge: 2^h >= 2m slots)
+      // the list (position order) in the chain's tuple storage (at least 32
+      // bytes per edge), the edge set in its permutation records (at least
+      // 32 bytes per edge: 2^h >= 2m slots)
       char *base = tup + 16ull * hc.d.tuple_base;
       const uint64_t bytes = 16ull * hc.d.capt << hc.d.P;
-      const uint64_t first_off = align_up(8ull * jb.m);
-      if (first_off + 4ull * jb.m > bytes) return GESMC_E_INTERNAL;
+      if (8ull * jb.m > bytes) return GESMC_E_INTERNAL;
       char *hbase = reinterpret_cast<char *>(a.prec) + 16ull * kPermBucketCap * hc.d.bucket_base;
       const uint64_t hbytes = 16ull * kPermBucketCap * hc.shape.nb;
       uint32_t hlog2 = 0;
       while ((16ull << hlog2) <= hbytes && hlog2 < 31) ++hlog2;  // largest 2^h with 8 * 2^h <= room
       if ((1ull << hlog2) < 2ull * jb.m) return GESMC_E_INTERNAL;
       jb.E = reinterpret_cast<unsigned long long *>(base);
-      jb.first = reinterpret_cast<uint32_t *>(base + first_off);
       jb.H = reinterpret_cast<unsigned long long *>(hbase);
       jb.hlog2 = hlog2;
     }
-    // chains with m < 2 have no list to move (their switches are only counted)
-    if (jb.m >= 2) job_of[c] = (uint32_t)jobs.size();
     jobs.push_back(jb);
   }
   if (jobs.empty()) return GESMC_OK;
+  // chains that run windows of 1024 switches first, then the rest (each
+  // group keeps chain order); chains with m < 2 have no list to move (their
+  // switches are only counted)
+  std::stable_partition(jobs.begin(), jobs.end(), [](const EsJob &jb) { return es_window(jb.m) == 1024u; });
+  uint32_t nbig = 0;
+  for (uint32_t t = 0; t < jobs.size(); ++t) {
+    if (jobs[t].m >= 2) job_of[jobs[t].chain] = t;
+    if (es_window(jobs[t].m) == 1024u) ++nbig;
+  }
   EsJob *djobs = at<EsJob>(p->base, p->lay.es_jobs);
   uint32_t *djob_of = at<uint32_t>(p->base, p->lay.es_job_of);
   uint32_t *err = &a.ctl->err;
@@ -722,8 +727,9 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   ok &= cudaMemcpyAsync(djobs, jobs.data(), sizeof(EsJob) * nj, cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= launch_es_store(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
   ok &= launch_es_set(djobs, nj, err, s, p->num_sms) == cudaSuccess;
-  ok &= launch_es_run(djobs, nj, a.st, a.chain_accepted, err, s) == cudaSuccess;
-  p->launches += 3ull * ((nj + 65534) / 65535) + 2;
+  uint32_t run_launches = 0;
+  ok &= launch_es_run(djobs, nbig, nj, a.st, a.chain_accepted, err, s, &run_launches) == cudaSuccess;
+  p->launches += 2ull * ((nj + 65534) / 65535) + run_launches + 2;
   ok &= launch_es_load(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
   uint32_t host_err = 0;
   ok &= cudaMemcpyAsync(&host_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;

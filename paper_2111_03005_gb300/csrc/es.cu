@@ -3,9 +3,10 @@
 // ES-MC runs independent edge switches sigma_k = (i, j, g) one after
 // another (Def. 1's chain).  Algorithm 2 cuts the sequence into supersteps:
 // maximal runs of consecutive switches of which no two share a source
-// position, found with a first-touch table (each switch writes its index
-// into the entries of its two positions with a minimum, and the first
-// switch that finds a smaller index there starts the next superstep).  A
+// position, found with a first-touch table (each switch of a window writes
+// its index into the entries of its two positions with a minimum, and the
+// first switch that finds a smaller index there starts the next superstep;
+// the table is a shared-memory hash table keyed by position).  A
 // superstep has no source dependencies, so ParallelSuperstep (Algorithm 1)
 // performs it with the sequential outcome: each target edge exists when its
 // switch runs iff it was in E at the superstep's start and its eraser (the
@@ -28,16 +29,21 @@
 namespace gesmc {
 namespace {
 
-constexpr int kEsThreads = 1024;
-constexpr int kEsBatch = kEsThreads;  // one switch per thread
-constexpr int kEsSlots = 4096;        // shared-memory table slots (>= 2 x 2 x kEsBatch keys at load <= 1/2)
 constexpr uint32_t kNil = 0xFFFFFFFFu;
 constexpr uint32_t kNoTouch = 0xFFFFFFFFu;
 constexpr uint8_t kEsUndecided = 0, kEsLegal = 1, kEsIllegal = 2;
+// Chains with at least this many edges run windows of 1024 switches (their
+// supersteps hold about 0.63 sqrt(m) switches: 450 at 2^19); smaller ones
+// run windows of 256 on CTAs of 256 threads, several per SM.
+constexpr uint32_t kEsBigChain = 1u << 19;
+
+__device__ __forceinline__ uint32_t hash32(unsigned long long key) { return (uint32_t)mix64(key); }
 
 // ---------------------------------------------------------------- the edge set H
-__device__ __forceinline__ bool hset_contains(const unsigned long long *H, uint32_t mask, unsigned long long key) {
-  uint32_t s = (uint32_t)mix64(key) & mask;
+// Open addressing with linear probing from h & mask (h = hash32(key)).
+__device__ __forceinline__ bool hset_contains(const unsigned long long *H, uint32_t mask, unsigned long long key,
+                                              uint32_t h) {
+  uint32_t s = h & mask;
   for (uint32_t n = 0; n <= mask; ++n) {
     const unsigned long long cur = __ldcg(&H[s]);
     if (cur == key) return true;
@@ -47,8 +53,8 @@ __device__ __forceinline__ bool hset_contains(const unsigned long long *H, uint3
   return false;
 }
 
-__device__ __forceinline__ void hset_erase(unsigned long long *H, uint32_t mask, unsigned long long key) {
-  uint32_t s = (uint32_t)mix64(key) & mask;
+__device__ __forceinline__ void hset_erase(unsigned long long *H, uint32_t mask, unsigned long long key, uint32_t h) {
+  uint32_t s = h & mask;
   for (uint32_t n = 0; n <= mask; ++n) {
     const unsigned long long cur = __ldcg(&H[s]);
     if (cur == key) {
@@ -63,8 +69,8 @@ __device__ __forceinline__ void hset_erase(unsigned long long *H, uint32_t mask,
 // Insert a key that is not in the set into the first empty or tombstone
 // slot of its probe sequence.  Returns 0 (empty slot taken), 1 (tombstone
 // reused) or -1 (table full).
-__device__ __forceinline__ int hset_insert(unsigned long long *H, uint32_t mask, unsigned long long key) {
-  uint32_t s = (uint32_t)mix64(key) & mask;
+__device__ __forceinline__ int hset_insert(unsigned long long *H, uint32_t mask, unsigned long long key, uint32_t h) {
+  uint32_t s = h & mask;
   for (uint32_t n = 0; n <= mask; ++n) {
     const unsigned long long cur = __ldcg(&H[s]);
     if (cur == kEmptyKey || cur == kTombKey) {
@@ -76,12 +82,54 @@ __device__ __forceinline__ int hset_insert(unsigned long long *H, uint32_t mask,
   return -1;
 }
 
-// ---------------------------------------------------------------- shared-memory tables
+// ---------------------------------------------------------------- shared memory
+// Per CTA, for windows of B switches (one per thread) and tables of S = 4B
+// slots: a region that holds the first-touch table while the window is cut
+// (position keys and minima, u32) and the erasers' and inserters' key tables
+// afterwards (u64), then the erasers' switches, the inserters' list heads and
+// links, and every switch's state.  Everything else a switch needs (its
+// positions, edges, hashes, outcome) stays in its thread's registers.
+template <int B>
+struct EsShape {
+  static constexpr int kSlots = 4 * B;
+  static constexpr int kSlotsLog2 = B == 1024 ? 12 : (B == 256 ? 10 : -1);
+  static constexpr size_t kRegion = 16ull * kSlots;
+  static constexpr size_t kBytes = kRegion + 4ull * (2 * kSlots + 2 * B) + B;
+  static_assert(kSlotsLog2 > 0, "window of 256 or 1024 switches");
+};
+
+template <int B>
+struct EsSmem {
+  unsigned long long *skey, *ikey;  // key tables (after the cut)
+  uint32_t *pkey, *pmin;            // first-touch table (until the cut); the same bytes
+  uint32_t *sval, *ihead, *tnext;
+  uint8_t *st;
+};
+
+template <int B>
+__device__ __forceinline__ EsSmem<B> es_smem() {
+  extern __shared__ unsigned long long es_dyn[];
+  constexpr int S = EsShape<B>::kSlots;
+  EsSmem<B> m;
+  m.skey = es_dyn;
+  m.ikey = es_dyn + S;
+  m.pkey = reinterpret_cast<uint32_t *>(es_dyn);
+  m.pmin = m.pkey + S;
+  uint32_t *q = reinterpret_cast<uint32_t *>(es_dyn + 2 * S);
+  m.sval = q;
+  m.ihead = q + S;
+  m.tnext = q + 2 * S;
+  m.st = reinterpret_cast<uint8_t *>(q + 2 * S + 2 * B);
+  return m;
+}
+
 // Sources of the superstep's switches (key -> switch) and its targets (key
-// -> list of (switch, which) entries through next[]).
-__device__ __forceinline__ uint32_t table_slot(unsigned long long *keys, unsigned long long key, bool claim) {
-  uint32_t s = (uint32_t)mix64(key) & (kEsSlots - 1);
-  for (int n = 0; n < kEsSlots; ++n) {
+// -> list of (switch, which) entries through next[]); h = hash32(key).
+template <int S>
+__device__ __forceinline__ uint32_t table_slot(unsigned long long *keys, unsigned long long key, uint32_t h,
+                                               bool claim) {
+  uint32_t s = h & (S - 1);
+  for (int n = 0; n < S; ++n) {
     const unsigned long long cur = keys[s];
     if (cur == key) return s;
     if (cur == kEmptyKey) {
@@ -89,49 +137,63 @@ __device__ __forceinline__ uint32_t table_slot(unsigned long long *keys, unsigne
       const unsigned long long prev = atomicCAS(&keys[s], kEmptyKey, key);
       if (prev == kEmptyKey || prev == key) return s;
     }
-    s = (s + 1) & (kEsSlots - 1);
+    s = (s + 1) & (S - 1);
   }
   return kNil;
 }
 
-struct EsSmem {
-  uint32_t *si, *sj;
-  unsigned long long *e1, *e2, *e3, *e4;
-  unsigned long long *skey, *ikey;
-  uint32_t *sval, *ihead, *tnext;
-  uint8_t *code, *st, *nx, *pres, *gb;
-};
-
-__device__ __forceinline__ EsSmem es_smem() {
-  extern __shared__ unsigned long long es_dyn[];
-  EsSmem m;
-  unsigned long long *p = es_dyn;
-  m.e1 = p;
-  m.e2 = p + kEsBatch;
-  m.e3 = p + 2 * kEsBatch;
-  m.e4 = p + 3 * kEsBatch;
-  m.skey = p + 4 * kEsBatch;
-  m.ikey = m.skey + kEsSlots;
-  uint32_t *q = reinterpret_cast<uint32_t *>(m.ikey + kEsSlots);
-  m.si = q;
-  m.sj = q + kEsBatch;
-  m.sval = q + 2 * kEsBatch;
-  m.ihead = m.sval + kEsSlots;
-  m.tnext = m.ihead + kEsSlots;
-  uint8_t *b = reinterpret_cast<uint8_t *>(m.tnext + 2 * kEsBatch);
-  m.code = b;
-  m.st = b + kEsBatch;
-  m.nx = b + 2 * kEsBatch;
-  m.pres = b + 3 * kEsBatch;
-  m.gb = b + 4 * kEsBatch;
-  return m;
+// First touches of a window (Algorithm 2's insert_if_min): position ->
+// smallest switch of the window that has it as a source position.  At most
+// 2B positions in S = 4B slots; a position is below 2^31, so never kNil.
+template <int S, int LOG2>
+__device__ __forceinline__ void touch_first(uint32_t *pkey, uint32_t *pmin, uint32_t pos, uint32_t x) {
+  uint32_t s = (pos * 0x9E3779B1u) >> (32 - LOG2);
+  for (int n = 0; n < S; ++n) {
+    uint32_t cur = pkey[s];
+    if (cur == kNil) {
+      cur = atomicCAS(&pkey[s], kNil, pos);
+      if (cur == kNil) cur = pos;
+    }
+    if (cur == pos) {
+      atomicMin(&pmin[s], x);
+      return;
+    }
+    s = (s + 1) & (S - 1);
+  }
 }
 
-constexpr size_t kEsSmemBytes = 8ull * (4 * kEsBatch + 2 * kEsSlots) + 4ull * (2 * kEsBatch + 2 * kEsSlots + 2 * kEsBatch) +
-                                5ull * kEsBatch;
+template <int S, int LOG2>
+__device__ __forceinline__ uint32_t first_touch(const uint32_t *pkey, const uint32_t *pmin, uint32_t pos) {
+  uint32_t s = (pos * 0x9E3779B1u) >> (32 - LOG2);
+  for (int n = 0; n < S; ++n) {
+    const uint32_t cur = pkey[s];
+    if (cur == pos) return pmin[s];
+    if (cur == kNil) break;
+    s = (s + 1) & (S - 1);
+  }
+  return kNoTouch;
+}
+
+// The region as the first-touch table / as the key tables (with the list heads).
+template <int B>
+__device__ __forceinline__ void clear_touch(const EsSmem<B> &sm) {
+  for (uint32_t t = threadIdx.x; t < (uint32_t)EsShape<B>::kSlots; t += B) {
+    sm.pkey[t] = kNil;
+    sm.pmin[t] = kNoTouch;
+  }
+}
+
+template <int B>
+__device__ __forceinline__ void clear_tables(const EsSmem<B> &sm) {
+  for (uint32_t t = threadIdx.x; t < (uint32_t)EsShape<B>::kSlots; t += B) {
+    sm.skey[t] = kEmptyKey;
+    sm.ikey[t] = kEmptyKey;
+    sm.ihead[t] = kNil;
+  }
+}
 
 // ---------------------------------------------------------------- kernels
-// H <- empty, first <- untouched, for every job (blockIdx.y = job).
+// H <- empty, for every job (blockIdx.y = job).
 __global__ void k_es_clear(const EsJob *jobs, uint32_t job_off) {
   const EsJob jb = jobs[job_off + blockIdx.y];
   if (jb.m < 2) return;  // no list, no set
@@ -139,8 +201,6 @@ __global__ void k_es_clear(const EsJob *jobs, uint32_t job_off) {
   const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < cap; s += nth)
     jb.H[s] = kEmptyKey;
-  for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < jb.m; s += nth)
-    jb.first[s] = kNoTouch;
 }
 
 // H <- the entries of E.
@@ -148,15 +208,20 @@ __global__ void k_es_fill(const EsJob *jobs, uint32_t job_off, uint32_t *err) {
   const EsJob jb = jobs[job_off + blockIdx.y];
   if (jb.m < 2) return;
   const uint32_t mask = (uint32_t)((1ull << jb.hlog2) - 1);
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < jb.m; s += gridDim.x * blockDim.x)
-    if (hset_insert(jb.H, mask, jb.E[s]) < 0) atomicOr(err, kErrTableFull);
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < jb.m; s += gridDim.x * blockDim.x) {
+    const unsigned long long e = jb.E[s];
+    if (hset_insert(jb.H, mask, e, hash32(e)) < 0) atomicOr(err, kErrTableFull);
+  }
 }
 
-// One CTA per job: switches k0 .. k0 + count - 1 of the job's chain.
-__global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32_t job_off, StatsDev *stats,
-                                                       unsigned long long *chain_acc, uint32_t *err) {
+// One CTA per job: switches k0 .. k0 + count - 1 of the job's chain, in
+// windows of B switches (thread x holds switch x of the window).
+template <int B, int MIN_BLOCKS>
+__global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uint32_t job_off, StatsDev *stats,
+                                                          unsigned long long *chain_acc, uint32_t *err) {
+  constexpr int S = EsShape<B>::kSlots, LOG2 = EsShape<B>::kSlotsLog2;
   const EsJob jb = jobs[job_off + blockIdx.x];
-  const EsSmem sm = es_smem();
+  const EsSmem<B> sm = es_smem<B>();
   __shared__ uint32_t s_cut, s_tombs;
   const uint32_t x = threadIdx.x;
   uint32_t acc = 0, rej_loop = 0, rej_exists = 0;
@@ -166,82 +231,80 @@ __global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32
   }
   const uint32_t mask = (uint32_t)((1ull << jb.hlog2) - 1);
   if (x == 0) s_tombs = 0;  // the set was built from the list just before
+  clear_touch(sm);
+  __syncthreads();
   for (unsigned long long s = 0; s < jb.count;) {
-    const uint32_t win = (uint32_t)min((unsigned long long)kEsBatch, jb.count - s);
+    const uint32_t win = (uint32_t)min((unsigned long long)B, jb.count - s);
     // sample the window and mark first touches (Algorithm 2's insert_if_min)
     if (x == 0) s_cut = win;
+    uint32_t i = 0, j = 0, g = 0;
     if (x < win) {
       const U64x4 w = philox(jb.k0 + s + x, 0, 2, 0, jb.seed, 0);
-      const uint32_t i = (uint32_t)__umul64hi(w.w[0], (unsigned long long)jb.m);
+      i = (uint32_t)__umul64hi(w.w[0], (unsigned long long)jb.m);
       const uint32_t jj = (uint32_t)__umul64hi(w.w[1], (unsigned long long)(jb.m - 1));
-      const uint32_t j = jj + (jj >= i ? 1u : 0u);
-      sm.si[x] = i;
-      sm.sj[x] = j;
-      sm.gb[x] = (uint8_t)(w.w[2] >> 63);
-      atomicMin(&jb.first[i], x);
-      atomicMin(&jb.first[j], x);
-    }
-    for (uint32_t t = x; t < kEsSlots; t += kEsThreads) {
-      sm.skey[t] = kEmptyKey;
-      sm.ikey[t] = kEmptyKey;
-      sm.ihead[t] = kNil;
+      j = jj + (jj >= i ? 1u : 0u);
+      g = (uint32_t)(w.w[2] >> 63);
+      touch_first<S, LOG2>(sm.pkey, sm.pmin, i, x);
+      touch_first<S, LOG2>(sm.pkey, sm.pmin, j, x);
     }
     __syncthreads();
     // the superstep ends before the first switch that shares a position with an earlier one
-    if (x < win && (__ldcg(&jb.first[sm.si[x]]) < x || __ldcg(&jb.first[sm.sj[x]]) < x)) atomicMin(&s_cut, x);
+    if (x < win && (first_touch<S, LOG2>(sm.pkey, sm.pmin, i) < x || first_touch<S, LOG2>(sm.pkey, sm.pmin, j) < x))
+      atomicMin(&s_cut, x);
     __syncthreads();
     const uint32_t n = s_cut;
-    if (x < win) {
-      atomicExch(&jb.first[sm.si[x]], kNoTouch);  // at L2, like the minima of the next window
-      atomicExch(&jb.first[sm.sj[x]], kNoTouch);
-    }
+    clear_tables(sm);  // the region becomes the key tables (the cut has read it)
     // sources, targets and the outright rules
+    unsigned long long e1 = 0, e2 = 0, e3 = 0, e4 = 0;
+    uint32_t h1 = 0, h2 = 0, h3 = 0, h4 = 0, code = 1;
     if (x < n) {
-      const unsigned long long e1 = __ldcg(&jb.E[sm.si[x]]), e2 = __ldcg(&jb.E[sm.sj[x]]);
-      unsigned long long e3, e4;
-      const uint32_t code = tau_g(sm.gb[x], e1, e2, e3, e4);
-      sm.e1[x] = e1;
-      sm.e2[x] = e2;
-      sm.e3[x] = e3;
-      sm.e4[x] = e4;
-      sm.code[x] = (uint8_t)code;
+      e1 = __ldcg(&jb.E[i]);
+      e2 = __ldcg(&jb.E[j]);
+      code = tau_g(g, e1, e2, e3, e4);
       sm.st[x] = code ? kEsIllegal : kEsUndecided;
       if (code == kCodeLoop) ++rej_loop;
       else if (code) ++rej_exists;  // shared node: the targets re-create the sources
+      if (!code) {
+        h1 = hash32(e1);
+        h2 = hash32(e2);
+        h3 = hash32(e3);
+        h4 = hash32(e4);
+      }
     }
     __syncthreads();
     // erasers and inserters of the superstep; presence of the targets in E at its start
-    if (x < n && sm.code[x] == 0) {
-      uint32_t t = table_slot(sm.skey, sm.e1[x], true);
+    uint32_t pres = 0;
+    if (x < n && code == 0) {
+      uint32_t t = table_slot<S>(sm.skey, e1, h1, true);
       if (t != kNil) sm.sval[t] = x;
-      t = table_slot(sm.skey, sm.e2[x], true);
+      t = table_slot<S>(sm.skey, e2, h2, true);
       if (t != kNil) sm.sval[t] = x;
-      uint8_t pres = 0;
-      for (uint32_t w = 0; w < 2; ++w) {
-        const unsigned long long e = w ? sm.e4[x] : sm.e3[x];
-        if (hset_contains(jb.H, mask, e)) pres |= (uint8_t)(1u << w);
-        t = table_slot(sm.ikey, e, true);
-        if (t != kNil) sm.tnext[2 * x + w] = atomicExch(&sm.ihead[t], 2 * x + w);
-        else atomicOr(err, kErrTableFull);
-      }
-      sm.pres[x] = pres;
+      if (hset_contains(jb.H, mask, e3, h3)) pres |= 1u;
+      if (hset_contains(jb.H, mask, e4, h4)) pres |= 2u;
+      t = table_slot<S>(sm.ikey, e3, h3, true);
+      if (t != kNil) sm.tnext[2 * x] = atomicExch(&sm.ihead[t], 2 * x);
+      else atomicOr(err, kErrTableFull);
+      t = table_slot<S>(sm.ikey, e4, h4, true);
+      if (t != kNil) sm.tnext[2 * x + 1] = atomicExch(&sm.ihead[t], 2 * x + 1);
+      else atomicOr(err, kErrTableFull);
     }
     __syncthreads();
     // waves (Algorithm 1): a switch decided in wave w only uses decisions of earlier waves
+    uint8_t dec = x < n ? sm.st[x] : kEsIllegal;
     for (uint32_t wave = 1;; ++wave) {
-      uint8_t dec = x < n ? sm.st[x] : kEsIllegal;
-      if (x < n && dec == kEsUndecided) {
+      if (dec == kEsUndecided) {
         bool bad = false, wait = false;
         for (uint32_t w = 0; w < 2 && !bad; ++w) {
-          const unsigned long long e = w ? sm.e4[x] : sm.e3[x];
-          if ((sm.pres[x] >> w) & 1u) {  // in E at the start: present unless an earlier legal switch erased it
-            const uint32_t t = table_slot(sm.skey, e, false);
+          const unsigned long long e = w ? e4 : e3;
+          const uint32_t h = w ? h4 : h3;
+          if ((pres >> w) & 1u) {  // in E at the start: present unless an earlier legal switch erased it
+            const uint32_t t = table_slot<S>(sm.skey, e, h, false);
             const uint32_t p = t == kNil ? kNil : sm.sval[t];
             if (p == kNil || p >= x || sm.st[p] == kEsIllegal) bad = true;
             else if (sm.st[p] == kEsUndecided) wait = true;
           }
           if (bad) break;
-          const uint32_t t = table_slot(sm.ikey, e, false);
+          const uint32_t t = table_slot<S>(sm.ikey, e, h, false);
           for (uint32_t q = t == kNil ? kNil : sm.ihead[t]; q != kNil; q = sm.tnext[q]) {
             const uint32_t k = q >> 1;  // an earlier switch that inserts e
             if (k >= x) continue;
@@ -254,41 +317,43 @@ __global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32
         }
         dec = bad ? kEsIllegal : (wait ? kEsUndecided : kEsLegal);
       }
-      if (x < n) sm.nx[x] = dec;
-      __syncthreads();
-      if (x < n) sm.st[x] = sm.nx[x];
-      const int left = __syncthreads_count(x < n && sm.st[x] == kEsUndecided);
+      __syncthreads();  // every read of this wave's states is done
+      if (x < n) sm.st[x] = dec;
+      const int left = __syncthreads_count(dec == kEsUndecided);
       if (left == 0) break;
-      if (wave > kEsBatch) {  // every wave decides the smallest undecided switch: cannot happen
+      if (wave > (uint32_t)B) {  // every wave decides the smallest undecided switch: cannot happen
         if (x == 0) atomicOr(err, kErrNoProgress);
         return;
       }
     }
     // apply: rewire, then erase the sources before inserting the targets
-    const bool legal = x < n && sm.st[x] == kEsLegal;
+    clear_touch(sm);  // the region becomes the next window's first-touch table (no table is read any more)
+    const bool legal = dec == kEsLegal;
     if (legal) {
-      jb.E[sm.si[x]] = sm.e3[x];
-      jb.E[sm.sj[x]] = sm.e4[x];
-      hset_erase(jb.H, mask, sm.e1[x]);
-      hset_erase(jb.H, mask, sm.e2[x]);
+      jb.E[i] = e3;
+      jb.E[j] = e4;
+      hset_erase(jb.H, mask, e1, h1);
+      hset_erase(jb.H, mask, e2, h2);
       atomicAdd(&s_tombs, 2u);
       ++acc;
-    } else if (x < n && sm.code[x] == 0) {
+    } else if (x < n && code == 0) {
       ++rej_exists;
     }
     __syncthreads();
     if (legal) {
-      const int r3 = hset_insert(jb.H, mask, sm.e3[x]), r4 = hset_insert(jb.H, mask, sm.e4[x]);
+      const int r3 = hset_insert(jb.H, mask, e3, h3), r4 = hset_insert(jb.H, mask, e4, h4);
       if (r3 < 0 || r4 < 0) atomicOr(err, kErrTableFull);
       const uint32_t reused = (r3 > 0 ? 1u : 0u) + (r4 > 0 ? 1u : 0u);
       if (reused) atomicSub(&s_tombs, reused);
     }
     __syncthreads();
     if (s_tombs > (mask >> 2)) {  // rebuild the set from the list
-      for (uint32_t t = x; t <= mask; t += kEsThreads) jb.H[t] = kEmptyKey;
+      for (uint32_t t = x; t <= mask; t += B) jb.H[t] = kEmptyKey;
       __syncthreads();
-      for (uint32_t t = x; t < jb.m; t += kEsThreads)
-        if (hset_insert(jb.H, mask, __ldcg(&jb.E[t])) < 0) atomicOr(err, kErrTableFull);
+      for (uint32_t t = x; t < jb.m; t += B) {
+        const unsigned long long e = __ldcg(&jb.E[t]);
+        if (hset_insert(jb.H, mask, e, hash32(e)) < 0) atomicOr(err, kErrTableFull);
+      }
       if (x == 0) s_tombs = 0;
       __syncthreads();
     }
@@ -310,10 +375,16 @@ __global__ void __launch_bounds__(kEsThreads) k_es_run(const EsJob *jobs, uint32
 
 }  // namespace
 
-size_t es_smem_bytes() { return kEsSmemBytes; }
+size_t es_smem_bytes() { return EsShape<1024>::kBytes; }
+
+uint32_t es_window(uint32_t m) { return m >= kEsBigChain ? 1024u : 256u; }
 
 cudaError_t prepare_es_kernels() {
-  return cudaFuncSetAttribute(k_es_run, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEsSmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k_es_run<1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)EsShape<1024>::kBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_es_run<256, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)EsShape<256>::kBytes);
 }
 
 cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms) {
@@ -327,12 +398,19 @@ cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_es_run(const EsJob *jobs, uint32_t njobs, StatsDev *stats, unsigned long long *chain_acc,
-                          uint32_t *err, cudaStream_t s) {
-  for (uint32_t off = 0; off < njobs; off += 65535u) {
-    const uint32_t nj = njobs - off < 65535u ? njobs - off : 65535u;
-    k_es_run<<<nj, kEsThreads, kEsSmemBytes, s>>>(jobs, off, stats, chain_acc, err);
+cudaError_t launch_es_run(const EsJob *jobs, uint32_t nbig, uint32_t njobs, StatsDev *stats,
+                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, uint32_t *launches) {
+  // jobs [0, nbig) run windows of 1024 switches, the rest windows of 256
+  uint32_t n = 0;
+  for (uint32_t off = 0; off < nbig; off += 65535u, ++n) {
+    const uint32_t nj = nbig - off < 65535u ? nbig - off : 65535u;
+    k_es_run<1024, 1><<<nj, 1024, EsShape<1024>::kBytes, s>>>(jobs, off, stats, chain_acc, err);
   }
+  for (uint32_t off = nbig; off < njobs; off += 65535u, ++n) {
+    const uint32_t nj = njobs - off < 65535u ? njobs - off : 65535u;
+    k_es_run<256, 6><<<nj, 256, EsShape<256>::kBytes, s>>>(jobs, off, stats, chain_acc, err);
+  }
+  if (launches) *launches = n;
   return cudaGetLastError();
 }
 

@@ -240,26 +240,29 @@ cudaError_t launch_canonicalise(unsigned long long *E, uint32_t m, unsigned long
 cudaError_t launch_duplicate_check(const unsigned long long *E, uint32_t m, unsigned long long *set,
                                    unsigned long long cap, uint32_t *flags, cudaStream_t s, int num_sms);
 
-// ParES (Algorithm 2) for one chain: its list in position order, its edge
-// set (open addressing, 2^hlog2 slots) and the first-touch table, all in
-// the chain's tuple storage, which no round uses between rounds; ES-MC
-// switches k0 .. k0 + count - 1 with the chain's seed.
+// ParES (Algorithm 2) for one chain: its list in position order (in the
+// chain's tuple storage) and its edge set (open addressing, 2^hlog2 slots,
+// in the chain's permutation records), neither of which a round uses
+// between rounds; ES-MC switches k0 .. k0 + count - 1 with the chain's seed.
 struct EsJob {
   unsigned long long *E;
   unsigned long long *H;
-  uint32_t *first;
   unsigned long long seed, k0, count;
   uint32_t m, hlog2, chain, pad;
 };
 
-// Shared memory of the ParES kernel; opt-in once per device.
+// Shared memory of the ParES kernel (its larger variant); opt-in once per device.
 size_t es_smem_bytes();
 cudaError_t prepare_es_kernels();
-// Edge sets of all jobs rebuilt from their lists (first-touch tables cleared).
+// Switches per window of the ParES kernel for a chain of m edges (1024 for
+// large chains, 256 otherwise).
+uint32_t es_window(uint32_t m);
+// Edge sets of all jobs rebuilt from their lists.
 cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms);
-// All jobs' switches, one CTA per job.
-cudaError_t launch_es_run(const EsJob *jobs, uint32_t njobs, StatsDev *stats, unsigned long long *chain_acc,
-                          uint32_t *err, cudaStream_t s);
+// All jobs' switches, one CTA per job: jobs [0, nbig) with windows of 1024,
+// the rest with windows of 256.  *launches receives the number of launches.
+cudaError_t launch_es_run(const EsJob *jobs, uint32_t nbig, uint32_t njobs, StatsDev *stats,
+                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, uint32_t *launches);
 // Lists of the chains with a job (job_of[chain] != kNoChain) out of their
 // slots into the jobs' position-order lists, and back (slots in position
 // order, nothing pending).

@@ -112,3 +112,37 @@ def test_pool_of_chains():
         x, _ = oracle.run(x, seed=300 + t, rounds=1, start_round=1)
         assert np.array_equal(outs[t], x), t
         assert infos[t]["es_switches"] == 2000
+
+
+def test_large_chain_wide_windows_and_rebuild():
+    """A chain above 2^19 edges runs windows of 1024 switches; 700,000
+    switches pass the edge set's rebuild threshold (a quarter of its slots
+    in tombstones) at least once."""
+    n = 1 << 17
+    edges = inputs.gnp(n, 10.0 / (n - 1), seed=21)
+    assert len(edges) >= 1 << 19
+    st = es_compare(edges, n, seed=6, calls=[1000, 700_000])
+    assert st["accepted"] > 600_000
+
+
+def test_pool_mixes_wide_and_narrow_windows():
+    """Large and small chains in one call (two kernel variants, jobs
+    reordered by window size): each equals its sequential run."""
+    n_big = 1 << 17
+    graphs = [(inputs.random_simple_graph(300, 900, seed=31), 300),
+              (inputs.gnp(n_big, 9.0 / (n_big - 1), seed=22), n_big),
+              (inputs.random_simple_graph(2000, 5000, seed=32), 2000),
+              (np.zeros(0, np.uint64), 4),
+              (inputs.gnp(n_big, 9.5 / (n_big - 1), seed=23), n_big)]
+    assert len(graphs[1][0]) >= 1 << 19 and len(graphs[4][0]) >= 1 << 19
+    total = sum(len(e) for e, _ in graphs)
+    with gesmc.Pool(max_edges=total, max_chains=len(graphs)) as pool:
+        ids = [pool.add(e, n=n, seed=500 + t) for t, (e, n) in enumerate(graphs)]
+        pool.es_run(30_000)
+        outs = [pool.edges(c) for c in ids]
+        infos = [pool.chain_info(c) for c in ids]
+    for t, (e, n) in enumerate(graphs):
+        x = oracle.validate(e, n)[1]
+        x, st = oracle.es_run(x, seed=500 + t, switches=30_000)
+        assert np.array_equal(outs[t], x), t
+        assert infos[t]["es_switches"] == 30_000

@@ -157,3 +157,23 @@ def test_ensemble_4096_fifty_rounds_match_oracle_digests(golden_dir):
             if d != gold["digests"][t] or pool.chain_info(c)["accepted"] != gold["accepted"][t]:
                 bad.append(t)
     assert not bad, f"{len(bad)} chains differ, first {bad[:8]}"
+
+
+@pytest.mark.parametrize("max_edges", [5000, 2 * 1024 + 1, 70_000])
+def test_one_chain_pool_holds_any_smaller_chain(max_edges):
+    """A one-chain pool is sized for its largest chain's own shape; every
+    smaller chain (sizes across the steps where the bucket and partition
+    counts double) fits in it, one after another, for rounds and for ParES."""
+    sizes = sorted({2, 3, 1023, 1024, 1025, 2048, 2049, max_edges // 3, max_edges - 1, max_edges} - {0})
+    with gesmc.Pool(max_edges=max_edges, max_chains=1) as pool:
+        for t, m in enumerate(s for s in sizes if s <= max_edges):
+            n = max(8, int(m ** 0.5 * 4))
+            edges = inputs.random_simple_graph(n, m, seed=300 + t)
+            c = pool.add(edges, n=n, seed=40 + t)
+            pool.run(3)
+            expect, _ = oracle.run(edges, seed=40 + t, rounds=3)
+            assert np.array_equal(pool.edges(c), expect), m
+            pool.es_run(500)
+            expect_es, _ = oracle.es_run(expect, seed=40 + t, switches=500)
+            assert np.array_equal(pool.edges(c), expect_es), m
+            pool.remove(c)
