@@ -235,6 +235,10 @@ void gesmc_destroy(gesmc_t h);
  * chain fails with GESMC_E_NOMEM when the edges or the chain slots are used
  * up, or when the free index ranges are too fragmented for it.  Threading
  * and errors as for single chains; all device work is on opts.stream.
+ * max_edges is at most 2^31 - 1, and every index space the pool sizes from
+ * it (tuple storage is the largest, about 2 max_edges) must fit 32 bits;
+ * gesmc_pool_create returns GESMC_E_INVALID otherwise, and
+ * gesmc_pool_device_bytes returns 0.
  */
 typedef struct gesmc_pool_ctx *gesmc_pool_t;
 

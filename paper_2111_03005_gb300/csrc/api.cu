@@ -87,6 +87,14 @@ Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
   return c;
 }
 
+// Every index space is addressed with 32-bit indices (chain ranges,
+// partition cursors, tuple positions).
+bool capacity_fits(const Capacity &c) {
+  const uint64_t lim = 0xFFFFFFFFull;
+  return c.slots < lim && c.switches < lim && c.buckets < lim && c.parts < lim && c.tuples < lim && c.ovf < lim &&
+         c.dep < lim && c.tcounts < lim;
+}
+
 // Bits of the target filter for at most M edges: about four per edge (so
 // that a source passes by a collision with probability about 1/5), a power
 // of two between 2^12 and 2^29 (at most 64 MB, which stays in L2).
@@ -761,7 +769,8 @@ void gesmc_pool_opts_default(gesmc_pool_opts *o) {
 size_t gesmc_pool_device_bytes(uint64_t max_edges, uint32_t max_chains, uint32_t tuple_log2) {
   if (max_edges > kMaxEdges || max_chains == 0) return 0;
   if (!tuple_log2) tuple_log2 = kDefaultTupleLog2;
-  return pool_layout(pool_capacity(max_edges, max_chains, tuple_log2), max_edges, max_chains).total;
+  const Capacity c = pool_capacity(max_edges, max_chains, tuple_log2);
+  return capacity_fits(c) ? pool_layout(c, max_edges, max_chains).total : 0;
 }
 
 void gesmc_pool_destroy(gesmc_pool_t p) {
@@ -805,6 +814,10 @@ int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out) {
   p->tuple_log2 = o.tuple_log2 ? o.tuple_log2 : kDefaultTupleLog2;
   p->use_graphs = !(o.flags & GESMC_FLAG_NO_GRAPHS);
   p->cap = pool_capacity(p->max_edges, p->max_chains, p->tuple_log2);
+  if (!capacity_fits(p->cap)) {
+    delete p;
+    return GESMC_E_INVALID;
+  }
   p->lay = pool_layout(p->cap, p->max_edges, p->max_chains);
   if (p->use_graphs &&
       (cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking) != cudaSuccess ||

@@ -630,55 +630,96 @@ __global__ void k_boundary(RoundArgs a) {
                  a.cpos[g + 1], a.cedge[g + 1]);
   }
 }
-// The sources of every switch (Algorithm 1's ERASE tuples) from the list in
-// this round's slot order, pair by pair.  Only an edge id that is some
-// switch's target needs one (the grouping only asks whether targets exist
-// and who erases them), so a source whose filter bit is clear is dropped; a
-// set bit can be a collision, which only adds a tuple nobody needs.  The
-// unpaired last slot of an odd list is a source no switch erases, and so are
-// the sources of a switch rejected outright.
-// Sources of one pair of slots x (u = 0, 1: slots 2x, 2x + 1) after the
-// filter test; the pair's list entries and owner are loaded by the caller.
-__device__ __forceinline__ void sources_of_pair(const RoundArgs &a, uint32_t x, uint32_t c, ulonglong2 ee) {
-  if (c == kNoChain) return;
+
+// One pair of slots: its two sources, the ERASE value they carry, and
+// where their tuples go (each key's partition cursor and storage, from its
+// chain).  A key that needs no tuple becomes kEmptyKey.
+struct SourcePair {
+  unsigned long long key[2], hash[2];
+  uint32_t val, cursor[2], capt, part[2];
+  size_t base[2];
+};
+
+__device__ __forceinline__ void load_source_pair(const RoundArgs &a, uint32_t x, uint32_t c, ulonglong2 ee,
+                                                 SourcePair &sp) {
+  sp.key[0] = ee.x;
+  sp.key[1] = ee.y;
+  sp.val = kTupleSource | kKeepK;
+  if (c == kNoChain) {
+    sp.key[0] = sp.key[1] = kEmptyKey;
+    return;
+  }
   const ChainDesc ch = a.chains[c];
   const uint32_t ls = 2 * x - ch.slot_base;
-  unsigned long long key[2] = {ee.x, ee.y}, hash[2];
-  uint32_t src = kTupleSource | kKeepK;
   if (ls + 1 < ch.m) {
     const uint32_t kg = ch.switch_base + (ls >> 1);
-    if ((__ldcs(&a.word[kg]) & kCodeMask) == 0) src = kTupleSource | kg;
+    if ((__ldcs(&a.word[kg]) & kCodeMask) == 0) sp.val = kTupleSource | kg;
   } else {
-    key[1] = kEmptyKey;  // odd m: the unpaired last slot
+    sp.key[1] = kEmptyKey;  // odd m: the unpaired last slot
   }
-  uint32_t bit[2];
+  sp.capt = ch.capt;
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
-    hash[t] = mix64(key[t]);
-    bit[t] = filter_bit(a, hash[t]);
+    sp.hash[t] = mix64(sp.key[t]);
+    const uint32_t p = partition_of(sp.hash[t], ch.P);
+    sp.cursor[t] = ch.tcount_base + p * ch.tstride;
+    sp.base[t] = ch.tuple_base + (size_t)p * ch.capt;
+    sp.part[t] = ch.part_base + p;
   }
-  uint32_t w[2];
-#pragma unroll
-  for (int t = 0; t < 2; ++t) w[t] = key[t] == kEmptyKey ? 0u : __ldcg(&a.tfilter[bit[t] >> 5]);
-#pragma unroll
-  for (int t = 0; t < 2; ++t)
-    if (!((w[t] >> (bit[t] & 31)) & 1u)) key[t] = kEmptyKey;
-  const uint32_t val[2] = {src, src};
-  emit_tuples<2>(a, ch, key, hash, val);
 }
 
-__global__ void __launch_bounds__(256, 6) k_sources(RoundArgs a) {
+// The sources of every switch (Algorithm 1's ERASE tuples) from the list in
+// this round's slot order, two pairs per thread: all loads first (slot
+// owners, list entries, chains, reject words, filter words), then the
+// cursor atomics of all four keys, then their stores.  Only an edge id
+// that is some switch's target needs a tuple (the grouping only asks
+// whether targets exist and who erases them), so a source whose filter bit
+// is clear is dropped; a set bit can be a collision, which only adds a
+// tuple nobody needs.  The unpaired last slot of an odd list is a source
+// no switch erases, and so are the sources of a switch rejected outright.
+__global__ void __launch_bounds__(256, 4) k_sources(RoundArgs a) {
   const uint32_t npair = (a.slot_hw + 1) >> 1;
   const uint32_t nth = gridDim.x * blockDim.x;
-  // two pairs per thread and step: their loads are in flight together
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += 2 * nth) {
     const uint32_t y = x + nth;
     const uint32_t cx = a.owner_slot[2 * x], cy = y < npair ? a.owner_slot[2 * y] : kNoChain;
     const ulonglong2 ex = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
     ulonglong2 ey = make_ulonglong2(kEmptyKey, kEmptyKey);
     if (y < npair) ey = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + y);
-    sources_of_pair(a, x, cx, ex);
-    sources_of_pair(a, y, cy, ey);
+    SourcePair sp[2];
+    load_source_pair(a, x, cx, ex, sp[0]);
+    load_source_pair(a, y, cy, ey, sp[1]);
+    uint32_t w[2][2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 2; ++t)
+        w[q][t] = sp[q].key[t] == kEmptyKey ? 0u : __ldcg(&a.tfilter[filter_bit(a, sp[q].hash[t]) >> 5]);
+    uint32_t idx[2][2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (!((w[q][t] >> (filter_bit(a, sp[q].hash[t]) & 31)) & 1u)) sp[q].key[t] = kEmptyKey;
+        idx[q][t] = sp[q].key[t] != kEmptyKey ? atomicAdd(&a.tcount[sp[q].cursor[t]], 1u) : 0u;
+      }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const unsigned long long k = sp[q].key[t];
+        if (k == kEmptyKey) continue;
+        if (idx[q][t] < sp[q].capt) {
+          a.ptup[sp[q].base[t] + idx[q][t]] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), sp[q].val,
+                                                         (uint32_t)sp[q].hash[t]);
+        } else {
+          const uint32_t o = atomicAdd(&a.ctl->ovf_count, 1u);
+          if (o < a.ovf_cap)
+            a.otup[o] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), sp[q].val, sp[q].part[t]);
+          else
+            atomicOr(&a.ctl->err, kErrRecord);
+        }
+      }
   }
 }
 

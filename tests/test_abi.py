@@ -49,11 +49,17 @@ def test_host_only_entry_points():
     opts = gesmc.GesmcOpts()
     lib.gesmc_opts_default(ctypes.byref(opts))
     assert opts.lazy_threshold == 0 and opts.n == 0 and opts.max_waves == 0
-    # memory plan: about 255 bytes per edge (tuple partitions with room for twice their mean)
+    # memory plan: about 145 bytes per edge for one chain (buckets of about 1024 positions with room for
+    # 2048, tuple partitions with room for their mean plus a margin, the overflow list for every tuple)
     m = 1 << 20
     b = gesmc.gesmc_device_bytes(m)
-    assert 100 * m <= b < 300 * m
+    assert 120 * m <= b < 180 * m
     assert gesmc.gesmc_device_bytes(1 << 31) == 0
+    # a 1.2e9-edge chain (the paper's largest graph) fits in 280 GB; near 2^31 edges the tuple storage
+    # would need more than 32-bit indices, and such a pool is refused
+    assert 0 < gesmc.gesmc_device_bytes(1_200_000_000) < 280e9
+    assert gesmc.Pool.device_bytes((1 << 31) - 1, 1, 9) == 0
+    assert gesmc.Pool.device_bytes(1 << 26, 4096, 0) > 0
     assert gesmc.gesmc_stage_name(0) == "clear" and gesmc.gesmc_stage_name(99) == ""
 
 

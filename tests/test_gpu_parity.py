@@ -266,6 +266,40 @@ def test_gnp_2p24_full_size_round():
     assert st["accepted"] == ost["accepted"] and st["rejected_exists"] == ost["rejected_exists"]
 
 
+@pytest.mark.slow
+def test_gnp_2p24_twenty_rounds_match_oracle_digests():
+    """G(2^24, 16/(n-1)): all 20 global switches at full size against the
+    sequential oracle's per-round SHA-256 digests of the list (written by
+    tests/golden/make_gnp_2p24_digests.py), one round per call and then as
+    one 20-round call, the configuration the benchmark times."""
+    import hashlib
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gnp_2p24_round_digests.json")) as f:
+        gold = json.load(f)
+
+    def digest(a):
+        return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
+
+    edges, n = inputs.workload_gnp_2p24(seed=gold["gen_seed"])
+    assert n == gold["n"] and len(edges) == gold["m"]
+    assert digest(edges) == gold["input_sha256"], "the generator gave another graph on this machine"
+    rounds = gold["rounds"]
+    assert len(rounds) == 20
+    with gesmc.Chain(edges, n=n) as c:
+        accepted = 0
+        for r, want in enumerate(rounds):
+            c.run(1, gold["chain_seed"])
+            accepted += want["accepted"]
+            assert digest(c.edges()) == want["sha256"], f"round {r}"
+            assert c.stats()["accepted"] == accepted, f"round {r}"   # counters run since create
+    with gesmc.Chain(edges, n=n) as c:
+        c.run(20, gold["chain_seed"])
+        assert digest(c.edges()) == rounds[-1]["sha256"]
+        assert c.stats()["accepted"] == sum(w["accepted"] for w in rounds)
+
+
 def test_graph_replay_equals_direct_launches():
     edges, n = inputs.workload_gnp_small(seed=7)
     with gesmc.Chain(edges, n=n) as a, gesmc.Chain(edges, n=n, graphs=False) as b:
