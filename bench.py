@@ -434,12 +434,19 @@ def run_ensemble(args):
 
     from paper_2111_03005_gb300 import autotune, ensemble, gesmc, inputs
 
-    torch.cuda.set_device(0)
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
     count, rounds = args.chains, 50
-    graphs = inputs.ensemble_graphs(count, seed=41)
-    seeds = [5000 + t for t in range(count)]
+    all_graphs = inputs.ensemble_graphs(count, seed=41)
+    L_all = sum(len(e) // 2 for e, _ in all_graphs)
+    # several GPUs: the chains are split by footprint, each GPU runs its share in its own pool (no exchange)
+    mine = ensemble.shard([len(e) for e, _ in all_graphs], world)[rank]
+    graphs = [all_graphs[t] for t in mine]
+    seeds = [5000 + t for t in mine]
+    count_mine = len(graphs)
     total = sum(len(e) for e, _ in graphs)
-    L_total = sum(len(e) // 2 for e, _ in graphs)
     layout, tuning = {}, None
     if args.tuple_log2 or args.group_log2:
         layout = {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2}
@@ -447,26 +454,29 @@ def run_ensemble(args):
         # partition size and table load factor timed on a sample of the ensemble itself
         t_tune = time.perf_counter()
         tuning = autotune.tune(graphs, seeds, rounds=3, cache=autotune.TuneCache(args.tune_cache),
-                               problem=(total, count), sample_chains=512)
+                               problem=(total, count_mine), sample_chains=512)
         tuning["tuning_s"] = time.perf_counter() - t_tune
         layout = {"tuple_log2": tuning["tuple_log2"], "group_log2": tuning["group_log2"]}
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream), gesmc.Pool(max_edges=total, max_chains=count, stream=stream, **layout) as pool:
+    with torch.cuda.stream(stream), gesmc.Pool(max_edges=max(total, 1), max_chains=max(count_mine, 1),
+                                                   stream=stream, **layout) as pool:
         t0 = time.perf_counter()
         ids = [pool.add(e, n=n, seed=s) for (e, n), s in zip(graphs, seeds)]
         add_s = time.perf_counter() - t0
         for _ in range(args.warmup):
             pool.run(rounds)
         pool.reset_stats()
+        barrier(dist)
         torch.cuda.synchronize()
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(0) as clocks:
+        with ClockSampler(local) as clocks:
             start.record(stream)
             for _ in range(args.steps):
                 pool.run(rounds)
             stop.record(stream)
             torch.cuda.synchronize()
-        ms = start.elapsed_time(stop)
+        barrier(dist)
+        ms = max_over_ranks(start.elapsed_time(stop), dist, dev)
         st = pool.stats()
         # one more step, untimed, with CUDA events between the stages of every round
         pool.set_profiling(True)
@@ -474,10 +484,14 @@ def run_ensemble(args):
         stage_ms, prof_rounds = pool.stage_times()
         pool.set_profiling(False)
         del ids
-    value = args.steps * rounds * L_total / (ms / 1e3)
-    # the per-graph alternative on a sample, and bit-exactness of the two
+    value = args.steps * rounds * L_all / (ms / 1e3)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    # the per-graph alternative on a sample of this GPU's chains, and bit-exactness of the two
     rng = np.random.default_rng(3)
-    sample = sorted(rng.choice(count, size=min(args.sample, count), replace=False).tolist())
+    sample = sorted(rng.choice(count_mine, size=min(args.sample, count_mine), replace=False).tolist())
     sub = [graphs[t] for t in sample]
     sub_seeds = [seeds[t] for t in sample]
     torch.cuda.synchronize()
@@ -490,13 +504,15 @@ def run_ensemble(args):
     per_graph = rounds * L_sub / one_by_one_s
     line = {
         "metric": "edge switches/sec, batched ensemble of chains (one pool, bit-exact per chain)",
-        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"{count} chains, n log-uniform in [100, 1e5], half G(n, 8/(n-1)), half "
                                f"Pld([1..n^(1/(gamma-1))], gamma ~ U[2.2, 3.0]) by Havel-Hakimi; "
-                               f"{rounds} global switches per step", "chains": count, "edges": total,
-                   "parallelism": "single GPU"},
+                               f"{rounds} global switches per step", "chains": count,
+                   "edges": sum(len(e) for e, _ in all_graphs),
+                   "parallelism": "single GPU" if world == 1 else
+                   f"chains split by footprint over {world} GPUs (rank 0: {count_mine} chains, {total} edges)"},
         "per_graph_handles": {"value": per_graph, "unit": UNIT, "sample_chains": len(sample),
                               "includes": "create + run + edges per graph, one after another"},
         "autotune": tuning,
@@ -509,6 +525,8 @@ def run_ensemble(args):
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -516,14 +534,17 @@ def run_serve(args):
     """A Poisson stream of sampling requests served by continuous batching,
     at each arrival rate of --rates (requests/s), one JSON line per rate.
     The mean request is about 1.9e7 switches, so about 95 requests/s
-    saturate the GPU; the defaults are 0.5x and 0.8x of that and an
-    overload burst."""
+    saturate one GPU; the defaults are 0.5x and 0.8x of that and an
+    overload burst.  On several GPUs each serves the requests the footprint
+    split gives it (edges x rounds), with no exchange."""
     import numpy as np
     import torch
 
-    from paper_2111_03005_gb300 import gesmc, inputs, serve
+    from paper_2111_03005_gb300 import ensemble, gesmc, inputs, serve
 
-    torch.cuda.set_device(0)
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
     rng = np.random.default_rng(17)
     base = []
     for rid in range(args.requests):
@@ -533,23 +554,26 @@ def run_serve(args):
     unit_gaps = rng.exponential(1.0, size=len(base))
     work = sum(r * (len(e) // 2) for e, _, _, r in base)
     cap = max(args.pool_edges, max(len(e) for e, _, _, _ in base))
-    # the plain alternative: one handle per request, first come first served (service times
+    mine = ensemble.shard([len(e) * r for e, _, _, r in base], world)[rank]
+    # the plain alternative: one handle per request, first come first served on this GPU (service times
     # do not depend on the arrival rate)
-    svc, alone = [], []
-    for e, n, seed, rounds in base:
+    svc, alone = {}, {}
+    for rid in mine:
+        e, n, seed, rounds = base[rid]
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         with gesmc.Chain(e, n=n) as c:
             c.run(rounds, seed)
-            alone.append(c.edges())
-        svc.append(time.perf_counter() - t1)
+            alone[rid] = c.edges()
+        svc[rid] = time.perf_counter() - t1
     stream = torch.cuda.Stream()
     classes = tuple(int(float(x)) for x in args.size_classes.split(",") if x.strip())
     poll = 2e-4 if classes else None   # with several pools, admit to an idle one while another runs
     for rate in [float(x) for x in args.rates.split(",")]:
-        reqs = [serve.Request(rid=rid, edges=e, n=n, seed=seed, rounds=rounds)
-                for rid, (e, n, seed, rounds) in enumerate(base)]
-        offsets = (np.cumsum(unit_gaps) - unit_gaps[0]) / rate
+        offsets_all = (np.cumsum(unit_gaps) - unit_gaps[0]) / rate
+        reqs = [serve.Request(rid=rid, edges=base[rid][0], n=base[rid][1], seed=base[rid][2], rounds=base[rid][3])
+                for rid in mine]
+        offsets = [offsets_all[rid] for rid in mine]
         with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
                                                      max_rounds_per_step=args.rounds_per_step,
                                                      size_classes=classes, stream=stream) as srv:
@@ -563,6 +587,7 @@ def run_serve(args):
             while not srv.idle():
                 srv.step()
             srv.done.clear()
+            barrier(dist)
             t0 = time.perf_counter()
             nxt = 0
             while nxt < len(reqs) or not srv.idle():
@@ -576,36 +601,55 @@ def run_serve(args):
                 srv.step(poll)
             wall = time.perf_counter() - t0
             rounds_run = srv.rounds_run
-        for r, out in zip(reqs, alone):
-            assert np.array_equal(out, r.result), f"request {r.rid}: served result differs from its single run"
-        lat = np.array([r.finished - r.arrival for r in reqs])
-        small = np.array([len(r.edges) <= 100_000 for r in reqs])
-        finish, free_at = [], 0.0
-        for off, d in zip(offsets, svc):
-            free_at = max(free_at, off) + d
-            finish.append(free_at - off)
-        fifo = np.array(finish)
+        for r in reqs:
+            assert np.array_equal(alone[r.rid], r.result), f"request {r.rid}: served result differs from its single run"
+        wall = max_over_ranks(wall, dist, torch.device("cuda", local))
+        # this GPU's first-come-first-served queue of single handles over its requests
+        fifo_mine, free_at = [], 0.0
+        for rid, off in zip(mine, offsets):
+            free_at = max(free_at, off) + svc[rid]
+            fifo_mine.append((rid, free_at - off, free_at))
+        mine_lat = [(r.rid, r.finished - r.arrival) for r in reqs]
+        if dist is not None:   # gathered for the report only
+            got_lat, got_fifo = [None] * world, [None] * world
+            dist.all_gather_object(got_lat, mine_lat)
+            dist.all_gather_object(got_fifo, fifo_mine)
+            mine_lat = [x for part in got_lat for x in part]
+            fifo_mine = [x for part in got_fifo for x in part]
+        if rank != 0:
+            continue
+        lat_by = dict(mine_lat)
+        fifo_by = {rid: f for rid, f, _ in fifo_mine}
+        order = sorted(lat_by)
+        lat = np.array([lat_by[rid] for rid in order])
+        fifo = np.array([fifo_by[rid] for rid in order])
+        small = np.array([len(base[rid][0]) <= 100_000 for rid in order])
+        fifo_wall = max(end for _, _, end in fifo_mine)
         line = {
             "metric": "sampling service: aggregate edge switches/sec with continuous batching",
-            "value": work / wall, "unit": UNIT, "n_gpus": 1, "steps": len(reqs), "warmup": 1,
-            "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak",
+            "value": work / wall, "unit": UNIT, "n_gpus": world, "steps": len(base), "warmup": 1,
+            "ms_per_step": 1e3 * wall / len(base), "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": f"{len(reqs)} requests, Poisson arrivals at {rate}/s, power-law graphs with "
+            "config": {"workload": f"{len(base)} requests, Poisson arrivals at {rate}/s, power-law graphs with "
                                    f"m log-uniform in [1e3, 1e7], 10-100 global switches each",
                        "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work,
                        "max_rounds_per_step": args.rounds_per_step,
-                       "size_classes": list(classes)},
+                       "size_classes": list(classes),
+                       "parallelism": "single GPU" if world == 1 else
+                       f"requests split by edges x rounds over {world} GPUs"},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max()),
                           "p50_small_requests": float(np.percentile(lat[small], 50)) if small.any() else None},
             "per_request_handles_fifo": {
-                "value": work / (max(o + f for o, f in zip(offsets, finish))),
+                "value": work / fifo_wall,
                 "latency_s": {"p50": float(np.percentile(fifo, 50)), "p99": float(np.percentile(fifo, 99)),
                               "p50_small_requests": float(np.percentile(fifo[small], 50)) if small.any() else None}},
             "identical_to_single_runs": True,
             "rounds_run": rounds_run,
         }
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 

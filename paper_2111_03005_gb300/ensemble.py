@@ -8,6 +8,24 @@ import numpy as np
 from . import gesmc
 
 
+def shard(sizes, world: int) -> list[list[int]]:
+    """Split chains (their edge counts) over `world` GPUs by device
+    footprint, which grows with the edges: largest first, each to the GPU
+    with the fewest edges so far (ties to the lower rank).  Chains are
+    independent, so the shards need no exchange; each keeps its chains in
+    their original order.  Deterministic, so every rank computes the same
+    split on its own."""
+    if world < 1:
+        raise ValueError("world must be at least 1")
+    load = [0] * world
+    owner = [0] * len(sizes)
+    for t in sorted(range(len(sizes)), key=lambda t: (-int(sizes[t]), t)):
+        r = min(range(world), key=lambda r: (load[r], r))
+        owner[t] = r
+        load[r] += int(sizes[t])
+    return [[t for t in range(len(sizes)) if owner[t] == r] for r in range(world)]
+
+
 def run_pool(graphs, seeds, rounds: int, start_round: int = 0, **pool_opts):
     """All graphs in one pool for `rounds` rounds; returns the final lists."""
     total = sum(len(e) for e, _ in graphs)

@@ -65,3 +65,19 @@ def test_sample_keeps_order_and_pairs():
 def test_problem_key_rounds_sizes():
     assert autotune.problem_key("d", 1000, 4096) == autotune.problem_key("d", 1100, 4000)
     assert autotune.problem_key("d", 1000, 4096) != autotune.problem_key("d", 4000, 4096)
+
+
+def test_ensemble_shards_cover_every_chain_once_and_balance_edges():
+    from paper_2111_03005_gb300 import ensemble, inputs
+
+    sizes = [len(e) for e, _ in inputs.ensemble_graphs(256, seed=41, n_lo=100, n_hi=20_000)]
+    for world in (1, 2, 3, 8):
+        shards = ensemble.shard(sizes, world)
+        assert len(shards) == world
+        assert sorted(t for sh in shards for t in sh) == list(range(len(sizes)))
+        assert all(sh == sorted(sh) for sh in shards)
+        loads = [sum(sizes[t] for t in sh) for sh in shards]
+        # greedy largest-first: no shard exceeds the mean by more than the largest chain
+        assert max(loads) - sum(loads) / world <= max(sizes)
+        assert ensemble.shard(sizes, world) == shards          # every rank computes the same split
+    assert ensemble.shard([], 4) == [[], [], [], []]
