@@ -107,7 +107,7 @@ uint64_t filter_bits(uint64_t M) {
 // Offsets of the pieces of a pool's single device allocation.
 struct Layout {
   size_t chains, chain_acc, chain_ell, es_jobs, es_job_of, tfilter, owner_slot, owner_switch, owner_bucket, owner_part, cpos, cedge, prec, pcount, poff, pblk,
-      bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, ocursor, dep,
+      bnd, word, sw, status, list0, list1, ptup, otup, stup, tcount, ocount, ooff, oblk, ocursor, dep,
       E, ctl, st, scratch, total;
 };
 
@@ -149,6 +149,7 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   l.tcount = take(4 * c.tcounts);
   l.ocount = take(4 * c.parts);
   l.ooff = take(4 * (c.parts + 1));
+  l.oblk = take(4 * (c.parts / 1024 + 2));
   l.ocursor = take(4 * c.parts);
   l.dep = take(8 * c.dep);
   l.tfilter = take(filter_bits(M) / 8);
@@ -361,6 +362,7 @@ void pool_bind(gesmc_pool_t p) {
   a.tcount = at<uint32_t>(b, l.tcount);
   a.ocount = at<uint32_t>(b, l.ocount);
   a.ooff = at<uint32_t>(b, l.ooff);
+  a.oblk = at<uint32_t>(b, l.oblk);
   a.ocursor = at<uint32_t>(b, l.ocursor);
   a.dep = at<uint2>(b, l.dep);
   a.ctl = at<Counters>(b, l.ctl);

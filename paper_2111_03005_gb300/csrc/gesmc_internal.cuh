@@ -183,7 +183,8 @@ struct RoundArgs {
   uint4 *stup;
   uint32_t *tcount;   // partition cursors: chain c's partition j at tcount_base + j * tstride (may exceed capt)
   uint32_t *ocount;   // per partition: overflow tuples
-  uint32_t *ooff;     // per partition + 1
+  uint32_t *ooff;     // per partition: offset of its overflow list within its block of 1024 partitions
+  uint32_t *oblk;     // per block of 1024 partitions + 1: exclusive scan of the block sums
   uint32_t *ocursor;  // per partition
   uint2 *dep;
   uint32_t *tfilter;      // target filter: one bit per hash of a target id (all chains)

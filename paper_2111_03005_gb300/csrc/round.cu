@@ -429,24 +429,66 @@ __device__ __forceinline__ uint32_t bucket_offset(const RoundArgs &a, uint32_t b
 }
 
 // Overflow tuples (those that found their partition full), grouped by
-// partition with exact counts.  All three kernels do nothing when there is
-// no overflow, which is the normal case.
+// partition with exact counts.  Every kernel does nothing when there is no
+// overflow, which is the normal case for a single chain.  The partition
+// offsets are scanned like the bucket offsets: blocks of 1024 partitions on
+// many CTAs (local offsets, and the cursors the scatter starts from), then
+// the block sums on one CTA; partition p's list starts at
+// oblk[p / 1024] + ooff[p].
 __global__ void k_overflow_count(RoundArgs a) {
   const uint32_t n = min(a.ctl->ovf_count, a.ovf_cap);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
     atomicAdd(&a.ocount[a.otup[t].w], 1u);
 }
 
-__global__ void __launch_bounds__(1024) k_overflow_scan(RoundArgs a) {
+__global__ void __launch_bounds__(1024) k_overflow_scan_blocks(RoundArgs a) {
   if (a.ctl->ovf_count == 0) return;
-  cta_scan_1024(a.ocount, a.ooff, a.ocursor, a.part_hw, 0xFFFFFFFFu);
+  __shared__ uint32_t warp_tot[32];
+  const uint32_t p = blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t v = p < a.part_hw ? a.ocount[p] : 0u;
+  uint32_t incl = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += u;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = warp_tot[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= (uint32_t)d) t += u;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  if (p < a.part_hw) {
+    const uint32_t local = incl - v + (warp ? warp_tot[warp - 1] : 0u);
+    a.ooff[p] = local;
+    a.ocursor[p] = local;
+  }
+  if (threadIdx.x == 1023) a.oblk[blockIdx.x] = warp_tot[31];
+}
+
+__global__ void __launch_bounds__(1024) k_overflow_scan_top(RoundArgs a) {
+  if (a.ctl->ovf_count == 0) return;
+  const uint32_t nblk = (a.part_hw + 1023) / 1024;
+  cta_scan_1024(a.oblk, a.oblk, nullptr, nblk, 0xFFFFFFFFu);  // oblk[nblk] = all overflow tuples
+}
+
+// Start of partition p's overflow list (p <= part_hw; part_hw gives the end).
+__device__ __forceinline__ uint32_t overflow_offset(const RoundArgs &a, uint32_t p) {
+  return p < a.part_hw ? a.oblk[p >> 10] + a.ooff[p] : a.oblk[(a.part_hw + 1023) >> 10];
 }
 
 __global__ void k_overflow_scatter(RoundArgs a) {
   const uint32_t n = min(a.ctl->ovf_count, a.ovf_cap);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const uint4 r = a.otup[t];
-    const uint32_t dst = atomicAdd(&a.ocursor[r.w], 1u);
+    const uint32_t dst = a.oblk[r.w >> 10] + atomicAdd(&a.ocursor[r.w], 1u);
     if (dst < n) a.stup[dst] = make_uint4(r.x, r.y, r.z, (uint32_t)mix64(((unsigned long long)r.y << 32) | r.x));
   }
 }
@@ -842,7 +884,7 @@ __global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) {
     const uint4 *prim = a.ptup + tbase + (size_t)(part - pbase) * capt;
     const ChainDesc &cd = a.chains[c];
     const uint32_t nprim = min(a.tcount[cd.tcount_base + (part - pbase) * cd.tstride], capt);
-    const uint32_t obeg = ovf ? a.ooff[part] : 0, oend = ovf ? a.ooff[part + 1] : 0;
+    const uint32_t obeg = ovf ? overflow_offset(a, part) : 0, oend = ovf ? overflow_offset(a, part + 1) : 0;
     const uint32_t ntup = nprim + (oend - obeg);
     if (ntup <= (uint32_t)(kGroupR * kGroupThreads)) {
       uint4 r[kGroupR];
@@ -1303,9 +1345,10 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   if (work) {
     const int g = grid_for(a.ovf_cap, 256, num_sms, 2);
     k_overflow_count<<<g, 256, 0, s>>>(a);
-    k_overflow_scan<<<1, 1024, 0, s>>>(a);
+    k_overflow_scan_blocks<<<(a.part_hw + 1023) / 1024 ? (a.part_hw + 1023) / 1024 : 1, 1024, 0, s>>>(a);
+    k_overflow_scan_top<<<1, 1024, 0, s>>>(a);
     k_overflow_scatter<<<g, 256, 0, s>>>(a);
-    n += 3;
+    n += 4;
   }
   mark(kStageGroup);
   if (work) {
