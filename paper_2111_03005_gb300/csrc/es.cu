@@ -41,31 +41,6 @@ __device__ __forceinline__ uint32_t hash32(unsigned long long key) { return (uin
 
 // ---------------------------------------------------------------- the edge set H
 // Open addressing with linear probing from h & mask (h = hash32(key)).
-__device__ __forceinline__ bool hset_contains(const unsigned long long *H, uint32_t mask, unsigned long long key,
-                                              uint32_t h) {
-  uint32_t s = h & mask;
-  for (uint32_t n = 0; n <= mask; ++n) {
-    const unsigned long long cur = __ldcg(&H[s]);
-    if (cur == key) return true;
-    if (cur == kEmptyKey) return false;
-    s = (s + 1) & mask;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void hset_erase(unsigned long long *H, uint32_t mask, unsigned long long key, uint32_t h) {
-  uint32_t s = h & mask;
-  for (uint32_t n = 0; n <= mask; ++n) {
-    const unsigned long long cur = __ldcg(&H[s]);
-    if (cur == key) {
-      H[s] = kTombKey;
-      return;
-    }
-    if (cur == kEmptyKey) return;
-    s = (s + 1) & mask;
-  }
-}
-
 // Insert a key that is not in the set into the first empty or tombstone
 // slot of its probe sequence.  Returns 0 (empty slot taken), 1 (tombstone
 // reused) or -1 (table full).
@@ -80,6 +55,92 @@ __device__ __forceinline__ int hset_insert(unsigned long long *H, uint32_t mask,
     s = (s + 1) & mask;
   }
   return -1;
+}
+
+// Two keys at once: both probe chains advance together, so that their loads
+// are in flight together (one HBM latency per step for the pair).
+// Presence: the first slots' loads are passed in (issued by the caller
+// before other work), bit w of the result says key w is in the set.
+__device__ __forceinline__ uint32_t hset_contains2(const unsigned long long *H, uint32_t mask,
+                                                   const unsigned long long (&key)[2], const uint32_t (&h)[2],
+                                                   unsigned long long (&cur)[2]) {
+  uint32_t s[2] = {h[0] & mask, h[1] & mask}, found = 0, done = 0;
+  for (uint32_t n = 0; n <= mask; ++n) {
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      if ((done >> w) & 1u) continue;
+      if (cur[w] == key[w]) {
+        found |= 1u << w;
+        done |= 1u << w;
+      } else if (cur[w] == kEmptyKey) {
+        done |= 1u << w;
+      } else {
+        s[w] = (s[w] + 1) & mask;
+      }
+    }
+    if (done == 3u) break;
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+      if (!((done >> w) & 1u)) cur[w] = __ldcg(&H[s[w]]);
+  }
+  return found;
+}
+
+__device__ __forceinline__ void hset_erase2(unsigned long long *H, uint32_t mask, const unsigned long long (&key)[2],
+                                            const uint32_t (&h)[2]) {
+  uint32_t s[2] = {h[0] & mask, h[1] & mask}, done = 0;
+  for (uint32_t n = 0; n <= mask && done != 3u; ++n) {
+    unsigned long long cur[2];
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+      if (!((done >> w) & 1u)) cur[w] = __ldcg(&H[s[w]]);
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      if ((done >> w) & 1u) continue;
+      if (cur[w] == key[w]) {
+        H[s[w]] = kTombKey;
+        done |= 1u << w;
+      } else if (cur[w] == kEmptyKey) {
+        done |= 1u << w;
+      } else {
+        s[w] = (s[w] + 1) & mask;
+      }
+    }
+  }
+}
+
+// Insert two keys that are not in the set, each into the first empty or
+// tombstone slot of its probe sequence.  r[w] = 0 (empty slot taken), 1
+// (tombstone reused) or -1 (table full).
+__device__ __forceinline__ void hset_insert2(unsigned long long *H, uint32_t mask, const unsigned long long (&key)[2],
+                                             const uint32_t (&h)[2], int (&r)[2]) {
+  uint32_t s[2] = {h[0] & mask, h[1] & mask}, done = 0;
+  uint32_t left[2] = {mask + 1, mask + 1};  // probes each key may still take
+  r[0] = r[1] = -1;
+  while (done != 3u) {
+    unsigned long long cur[2];
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+      if (!((done >> w) & 1u)) cur[w] = __ldcg(&H[s[w]]);
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      if ((done >> w) & 1u) continue;
+      if (left[w] == 0) {  // every slot looked at: table full
+        done |= 1u << w;
+        continue;
+      }
+      --left[w];
+      if (cur[w] == kEmptyKey || cur[w] == kTombKey) {
+        if (atomicCAS(&H[s[w]], cur[w], key[w]) == cur[w]) {
+          r[w] = cur[w] == kTombKey ? 1 : 0;
+          done |= 1u << w;
+        }
+        // taken meanwhile: look at the same slot again
+      } else {
+        s[w] = (s[w] + 1) & mask;
+      }
+    }
+  }
 }
 
 // ---------------------------------------------------------------- shared memory
@@ -272,21 +333,24 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
       }
     }
     __syncthreads();
-    // erasers and inserters of the superstep; presence of the targets in E at its start
+    // erasers and inserters of the superstep; presence of the targets in E at its start (the first
+    // probes of the edge set are issued before the shared-memory tables are filled, so that they overlap)
     uint32_t pres = 0;
     if (x < n && code == 0) {
+      unsigned long long cur[2] = {__ldcg(&jb.H[h3 & mask]), __ldcg(&jb.H[h4 & mask])};
       uint32_t t = table_slot<S>(sm.skey, e1, h1, true);
       if (t != kNil) sm.sval[t] = x;
       t = table_slot<S>(sm.skey, e2, h2, true);
       if (t != kNil) sm.sval[t] = x;
-      if (hset_contains(jb.H, mask, e3, h3)) pres |= 1u;
-      if (hset_contains(jb.H, mask, e4, h4)) pres |= 2u;
+      const unsigned long long tk[2] = {e3, e4};
+      const uint32_t th[2] = {h3, h4};
       t = table_slot<S>(sm.ikey, e3, h3, true);
       if (t != kNil) sm.tnext[2 * x] = atomicExch(&sm.ihead[t], 2 * x);
       else atomicOr(err, kErrTableFull);
       t = table_slot<S>(sm.ikey, e4, h4, true);
       if (t != kNil) sm.tnext[2 * x + 1] = atomicExch(&sm.ihead[t], 2 * x + 1);
       else atomicOr(err, kErrTableFull);
+      pres = hset_contains2(jb.H, mask, tk, th, cur);
     }
     __syncthreads();
     // waves (Algorithm 1): a switch decided in wave w only uses decisions of earlier waves
@@ -332,8 +396,9 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
     if (legal) {
       jb.E[i] = e3;
       jb.E[j] = e4;
-      hset_erase(jb.H, mask, e1, h1);
-      hset_erase(jb.H, mask, e2, h2);
+      const unsigned long long sk[2] = {e1, e2};
+      const uint32_t shh[2] = {h1, h2};
+      hset_erase2(jb.H, mask, sk, shh);
       atomicAdd(&s_tombs, 2u);
       ++acc;
     } else if (x < n && code == 0) {
@@ -341,9 +406,12 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
     }
     __syncthreads();
     if (legal) {
-      const int r3 = hset_insert(jb.H, mask, e3, h3), r4 = hset_insert(jb.H, mask, e4, h4);
-      if (r3 < 0 || r4 < 0) atomicOr(err, kErrTableFull);
-      const uint32_t reused = (r3 > 0 ? 1u : 0u) + (r4 > 0 ? 1u : 0u);
+      const unsigned long long tk[2] = {e3, e4};
+      const uint32_t th[2] = {h3, h4};
+      int r[2];
+      hset_insert2(jb.H, mask, tk, th, r);
+      if (r[0] < 0 || r[1] < 0) atomicOr(err, kErrTableFull);
+      const uint32_t reused = (r[0] > 0 ? 1u : 0u) + (r[1] > 0 ? 1u : 0u);
       if (reused) atomicSub(&s_tombs, reused);
     }
     __syncthreads();
