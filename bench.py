@@ -41,6 +41,8 @@ WORKLOADS = {
     "gnp_2p22": dict(desc="G(n=2^22, p=16/(n-1)), seed 4", n_log2=22, deg=16.0, seed=4),
     "gnp_2p20": dict(desc="G(n=2^20, p=16/(n-1)), seed 5", n_log2=20, deg=16.0, seed=5),
     "gnp_2p12": dict(desc="G(n=2^12, p=16/(n-1)), seed 7 (tests)", n_log2=12, deg=16.0, seed=7),
+    "gnp_2p27": dict(desc="G(n=2^27, p=16/(n-1)), seed 6: about 1.07e9 edges, 155 GB of device state (near the "
+                          "largest chain one GPU holds)", n_log2=27, deg=16.0, seed=6),
 }
 CPU_SAMPLE = "gnp_2p20"
 

@@ -313,3 +313,33 @@ def test_graph_replay_equals_direct_launches():
     with gesmc.Chain(edges, n=n) as c:
         c.run(12, 77)
         assert np.array_equal(c.edges(), expect)
+
+
+@pytest.mark.slow
+def test_gnp_2p27_largest_size_keeps_degrees_and_simplicity():
+    """G(2^27, 16/(n-1)), about 1.07e9 edges generated on the GPU, near the
+    largest chain one GPU holds (155 GB of state): two global switches keep
+    every node's degree, the edge count, canonical order and simplicity,
+    and accept about every switch (the oracle cannot run this size; these
+    properties hold at any size)."""
+    n = 1 << 27
+    e = gesmc.generate_gnp(n, 16.0 / (n - 1), seed=11)
+    m = e.numel()
+    assert m > 1_000_000_000 and gesmc.gesmc_device_bytes(m) > 0
+
+    def degrees(x):
+        return torch.bincount(x >> 32, minlength=n) + torch.bincount(x & 0xFFFFFFFF, minlength=n)
+
+    deg0 = degrees(e)
+    with gesmc.Chain(e, n=n) as c:
+        del e
+        c.run(2, 5)
+        st = c.stats()
+        out = torch.empty(m, dtype=torch.int64, device="cuda")
+        c.edges(out)
+    assert bool(((out >> 32) < (out & 0xFFFFFFFF)).all())      # canonical, no loops
+    assert torch.equal(degrees(out), deg0)
+    srt = torch.sort(out).values
+    assert not bool((srt[1:] == srt[:-1]).any())                # no repeated edge
+    assert st["accepted"] + st["rejected_exists"] + st["rejected_loop"] + st["lazy"] == 2 * (m // 2)
+    assert st["accepted"] > 0.99 * 2 * (m // 2)
