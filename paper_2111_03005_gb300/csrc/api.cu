@@ -719,14 +719,16 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
     jobs.push_back(jb);
   }
   if (jobs.empty()) return GESMC_OK;
-  // chains that run windows of 1024 switches first, then the rest (each
-  // group keeps chain order); chains with m < 2 have no list to move (their
-  // switches are only counted)
-  std::stable_partition(jobs.begin(), jobs.end(), [](const EsJob &jb) { return es_window(jb.m) == 1024u; });
-  uint32_t nbig = 0;
+  // chains by window size, largest windows first (each group keeps chain
+  // order); chains with m < 2 have no list to move (their switches are only
+  // counted)
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [](const EsJob &x, const EsJob &y) { return es_window(x.m) > es_window(y.m); });
+  uint32_t group[4] = {0, 0, 0, 0};
   for (uint32_t t = 0; t < jobs.size(); ++t) {
     if (jobs[t].m >= 2) job_of[jobs[t].chain] = t;
-    if (es_window(jobs[t].m) == 1024u) ++nbig;
+    const uint32_t w = es_window(jobs[t].m);
+    ++group[w == 1024u ? 0 : w == 256u ? 1 : w == 128u ? 2 : 3];
   }
   EsJob *djobs = at<EsJob>(p->base, p->lay.es_jobs);
   uint32_t *djob_of = at<uint32_t>(p->base, p->lay.es_job_of);
@@ -738,7 +740,8 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   ok &= launch_es_store(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
   ok &= launch_es_set(djobs, nj, err, s, p->num_sms) == cudaSuccess;
   uint32_t run_launches = 0;
-  ok &= launch_es_run(djobs, nbig, nj, a.st, a.chain_accepted, err, s, &run_launches) == cudaSuccess;
+  ok &= launch_es_run(djobs, group, a.st, a.chain_accepted, err, s, p->gstream, p->ev_in, p->ev_out, &run_launches) ==
+        cudaSuccess;
   p->launches += 2ull * ((nj + 65534) / 65535) + run_launches + 2;
   ok &= launch_es_load(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
   uint32_t host_err = 0;

@@ -32,10 +32,15 @@ namespace {
 constexpr uint32_t kNil = 0xFFFFFFFFu;
 constexpr uint32_t kNoTouch = 0xFFFFFFFFu;
 constexpr uint8_t kEsUndecided = 0, kEsLegal = 1, kEsIllegal = 2;
-// Chains with at least this many edges run windows of 1024 switches (their
-// supersteps hold about 0.63 sqrt(m) switches: 450 at 2^19); smaller ones
-// run windows of 256 on CTAs of 256 threads, several per SM.
+// Window sizes by chain size (supersteps hold about 0.63 sqrt(m) switches:
+// 450 at 2^19, 160 at 2^16, 57 at 2^13): chains of at least 2^19 edges run
+// windows of 1024 switches, chains of at least 2^16 windows of 256 on CTAs of
+// 256 threads (six per SM), chains of at least 2^13 windows of 128, smaller
+// ones windows of 32 on one warp each (up to 32 per SM), whose barriers cost
+// next to nothing.
 constexpr uint32_t kEsBigChain = 1u << 19;
+constexpr uint32_t kEsMidChain = 1u << 16;
+constexpr uint32_t kEsSmallChain = 1u << 13;
 
 __device__ __forceinline__ uint32_t hash32(unsigned long long key) { return (uint32_t)mix64(key); }
 
@@ -153,10 +158,10 @@ __device__ __forceinline__ void hset_insert2(unsigned long long *H, uint32_t mas
 template <int B>
 struct EsShape {
   static constexpr int kSlots = 4 * B;
-  static constexpr int kSlotsLog2 = B == 1024 ? 12 : (B == 256 ? 10 : -1);
+  static constexpr int kSlotsLog2 = B == 1024 ? 12 : B == 256 ? 10 : B == 128 ? 9 : B == 32 ? 7 : -1;
   static constexpr size_t kRegion = 16ull * kSlots;
   static constexpr size_t kBytes = kRegion + 4ull * (2 * kSlots + 2 * B) + B;
-  static_assert(kSlotsLog2 > 0, "window of 256 or 1024 switches");
+  static_assert(kSlotsLog2 > 0, "window of 32, 128, 256 or 1024 switches");
 };
 
 template <int B>
@@ -445,7 +450,9 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
 
 size_t es_smem_bytes() { return EsShape<1024>::kBytes; }
 
-uint32_t es_window(uint32_t m) { return m >= kEsBigChain ? 1024u : 256u; }
+uint32_t es_window(uint32_t m) {
+  return m >= kEsBigChain ? 1024u : m >= kEsMidChain ? 256u : m >= kEsSmallChain ? 128u : 32u;
+}
 
 cudaError_t prepare_es_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_es_run<1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -466,18 +473,34 @@ cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_es_run(const EsJob *jobs, uint32_t nbig, uint32_t njobs, StatsDev *stats,
-                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, uint32_t *launches) {
-  // jobs [0, nbig) run windows of 1024 switches, the rest windows of 256
+cudaError_t launch_es_run(const EsJob *jobs, const uint32_t (&group)[4], StatsDev *stats,
+                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, cudaStream_t s2,
+                          cudaEvent_t fork, cudaEvent_t join, uint32_t *launches) {
+  // group[w] jobs with windows of 1024, 256, 128 and 32 switches, in that
+  // order; the two small-window groups run on s2 (after s, and joined back
+  // into s) when there is one, beside the others
+  uint32_t beg[5] = {0, 0, 0, 0, 0};
+  for (int w = 0; w < 4; ++w) beg[w + 1] = beg[w] + group[w];
   uint32_t n = 0;
-  for (uint32_t off = 0; off < nbig; off += 65535u, ++n) {
-    const uint32_t nj = nbig - off < 65535u ? nbig - off : 65535u;
-    k_es_run<1024, 1><<<nj, 1024, EsShape<1024>::kBytes, s>>>(jobs, off, stats, chain_acc, err);
-  }
-  for (uint32_t off = nbig; off < njobs; off += 65535u, ++n) {
-    const uint32_t nj = njobs - off < 65535u ? njobs - off : 65535u;
-    k_es_run<256, 6><<<nj, 256, EsShape<256>::kBytes, s>>>(jobs, off, stats, chain_acc, err);
-  }
+  const bool side = s2 && fork && join && beg[2] > 0 && beg[4] > beg[2];
+  cudaStream_t ss = side ? s2 : s;
+  if (side && (cudaEventRecord(fork, s) != cudaSuccess || cudaStreamWaitEvent(s2, fork, 0) != cudaSuccess))
+    return cudaGetLastError();
+  auto run = [&](int w, cudaStream_t st) {
+    for (uint32_t off = beg[w]; off < beg[w + 1]; off += 65535u, ++n) {
+      const uint32_t nj = beg[w + 1] - off < 65535u ? beg[w + 1] - off : 65535u;
+      if (w == 0) k_es_run<1024, 1><<<nj, 1024, EsShape<1024>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
+      else if (w == 1) k_es_run<256, 6><<<nj, 256, EsShape<256>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
+      else if (w == 2) k_es_run<128, 12><<<nj, 128, EsShape<128>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
+      else k_es_run<32, 32><<<nj, 32, EsShape<32>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
+    }
+  };
+  run(3, ss);
+  run(2, ss);
+  run(0, s);
+  run(1, s);
+  if (side && (cudaEventRecord(join, s2) != cudaSuccess || cudaStreamWaitEvent(s, join, 0) != cudaSuccess))
+    return cudaGetLastError();
   if (launches) *launches = n;
   return cudaGetLastError();
 }

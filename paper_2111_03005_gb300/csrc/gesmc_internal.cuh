@@ -255,15 +255,19 @@ struct EsJob {
 // Shared memory of the ParES kernel (its larger variant); opt-in once per device.
 size_t es_smem_bytes();
 cudaError_t prepare_es_kernels();
-// Switches per window of the ParES kernel for a chain of m edges (1024 for
-// large chains, 256 otherwise).
+// Switches per window of the ParES kernel for a chain of m edges (1024,
+// 256, 128 or 32, by chain size).
 uint32_t es_window(uint32_t m);
 // Edge sets of all jobs rebuilt from their lists.
 cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms);
-// All jobs' switches, one CTA per job: jobs [0, nbig) with windows of 1024,
-// the rest with windows of 256.  *launches receives the number of launches.
-cudaError_t launch_es_run(const EsJob *jobs, uint32_t nbig, uint32_t njobs, StatsDev *stats,
-                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, uint32_t *launches);
+// All jobs' switches, one CTA per job: the first group[0] jobs with windows
+// of 1024, the next group[1] with windows of 256, then group[2] with 128 and
+// group[3] with 32 (these two on s2, forked from and joined back into s
+// through the two events, if given).  *launches receives the number of
+// launches.
+cudaError_t launch_es_run(const EsJob *jobs, const uint32_t (&group)[4], StatsDev *stats,
+                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, cudaStream_t s2,
+                          cudaEvent_t fork, cudaEvent_t join, uint32_t *launches);
 // Lists of the chains with a job (job_of[chain] != kNoChain) out of their
 // slots into the jobs' position-order lists, and back (slots in position
 // order, nothing pending).

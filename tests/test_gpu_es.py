@@ -126,15 +126,18 @@ def test_large_chain_wide_windows_and_rebuild():
 
 
 def test_pool_mixes_wide_and_narrow_windows():
-    """Large and small chains in one call (two kernel variants, jobs
-    reordered by window size): each equals its sequential run."""
+    """Chains for every window size in one call (four kernel variants, the
+    two small ones on a second stream, jobs reordered by window size): each
+    equals its sequential run."""
     n_big = 1 << 17
     graphs = [(inputs.random_simple_graph(300, 900, seed=31), 300),
               (inputs.gnp(n_big, 9.0 / (n_big - 1), seed=22), n_big),
               (inputs.random_simple_graph(2000, 5000, seed=32), 2000),
+              (inputs.random_simple_graph(6000, 20_000, seed=33), 6000),
+              (inputs.random_simple_graph(40_000, 100_000, seed=34), 40_000),
               (np.zeros(0, np.uint64), 4),
               (inputs.gnp(n_big, 9.5 / (n_big - 1), seed=23), n_big)]
-    assert len(graphs[1][0]) >= 1 << 19 and len(graphs[4][0]) >= 1 << 19
+    assert len(graphs[1][0]) >= 1 << 19 and len(graphs[6][0]) >= 1 << 19
     total = sum(len(e) for e, _ in graphs)
     with gesmc.Pool(max_edges=total, max_chains=len(graphs)) as pool:
         ids = [pool.add(e, n=n, seed=500 + t) for t, (e, n) in enumerate(graphs)]
