@@ -189,19 +189,32 @@ def algorithmic_bytes(stage: str, m: int, L: int, nb: int, npart: int, accepted:
     return 0.0
 
 
-def traffic_from_profile(kernel: str, workload: str):
-    """Measured DRAM bytes per launch of `kernel` from the committed ncu
-    summary, if neither the kernels nor the layout (round.cu, api.cu) have
-    changed since it was taken."""
+def traffic_sources_sha256() -> str:
+    """SHA-256 over what a round kernel's DRAM traffic depends on: the round
+    kernels (round.cu), the structures and constants they share
+    (gesmc_internal.cuh), and the layout code of api.cu (chain shapes,
+    capacities, the target filter's size, the pieces of the allocation)."""
     import hashlib
 
+    csrc = os.path.join(ROOT, "paper_2111_03005_gb300", "csrc")
+    api = open(os.path.join(csrc, "api.cu")).read()
+    layout = api[api.index("// Largest m:"):api.index("template <class T>\nT *at(")]
+    h = hashlib.sha256()
+    for part in (open(os.path.join(csrc, "round.cu"), "rb").read(),
+                 open(os.path.join(csrc, "gesmc_internal.cuh"), "rb").read(), layout.encode()):
+        h.update(hashlib.sha256(part).digest())
+    return h.hexdigest()
+
+
+def traffic_from_profile(kernel: str, workload: str):
+    """Measured DRAM bytes per launch of `kernel` from the committed ncu
+    summary, if neither the kernels nor the layout have changed since it was
+    taken (traffic_sources_sha256)."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
     try:
         kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line)
-        for name in ("round.cu", "api.cu"):
-            src = open(os.path.join(ROOT, "paper_2111_03005_gb300", "csrc", name), "rb").read()
-            if kv.get(name.replace(".", "_") + "_sha256", "").strip() != hashlib.sha256(src).hexdigest():
-                return None
+        if kv.get("sources_sha256", "").strip() != traffic_sources_sha256():
+            return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         return None
