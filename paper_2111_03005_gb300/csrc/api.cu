@@ -738,11 +738,30 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
   ok &= cudaMemcpyAsync(djob_of, job_of.data(), 4ull * p->max_chains, cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= cudaMemcpyAsync(djobs, jobs.data(), sizeof(EsJob) * nj, cudaMemcpyHostToDevice, s) == cudaSuccess;
   ok &= launch_es_store(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
-  ok &= launch_es_set(djobs, nj, err, s, p->num_sms) == cudaSuccess;
-  uint32_t run_launches = 0;
-  ok &= launch_es_run(djobs, group, a.st, a.chain_accepted, err, s, p->gstream, p->ev_in, p->ev_out, &run_launches) ==
-        cudaSuccess;
-  p->launches += 2ull * ((nj + 65534) / 65535) + run_launches + 2;
+  const uint64_t set_launches = 2ull * ((nj + 65534) / 65535);
+  ok &= launch_es_set(djobs, nj, err, s, p->num_sms, false) == cudaSuccess;
+  p->launches += set_launches + 2;
+  // chains of the largest window stop when their edge set needs a rebuild;
+  // rebuild those sets on the whole GPU and launch them again until every
+  // job is done (each launch advances every stopped job by a superstep at
+  // least)
+  uint32_t *nstop = &a.ctl->es_stopped;
+  for (uint64_t iter = 0; ok; ++iter) {
+    uint32_t run_launches = 0;
+    const uint32_t groups[4] = {group[0], iter ? 0u : group[1], iter ? 0u : group[2], iter ? 0u : group[3]};
+    if (group[0]) ok &= cudaMemsetAsync(nstop, 0, sizeof(uint32_t), s) == cudaSuccess;
+    ok &= launch_es_run(djobs, groups, a.st, a.chain_accepted, err, nstop, s, p->gstream, p->ev_in, p->ev_out,
+                        &run_launches) == cudaSuccess;
+    p->launches += run_launches;
+    if (!ok || group[0] == 0) break;  // only the largest windows stop
+    uint32_t stopped = 0, e = 0;
+    ok &= cudaMemcpyAsync(&stopped, nstop, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok &= cudaMemcpyAsync(&e, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    ok &= cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok || stopped == 0 || e != 0) break;
+    ok &= launch_es_set(djobs, nj, err, s, p->num_sms, true) == cudaSuccess;
+    p->launches += set_launches;
+  }
   ok &= launch_es_load(a, djobs, djob_of, s, p->num_sms) == cudaSuccess;
   uint32_t host_err = 0;
   ok &= cudaMemcpyAsync(&host_err, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) == cudaSuccess;

@@ -260,9 +260,9 @@ __device__ __forceinline__ void clear_tables(const EsSmem<B> &sm) {
 
 // ---------------------------------------------------------------- kernels
 // H <- empty, for every job (blockIdx.y = job).
-__global__ void k_es_clear(const EsJob *jobs, uint32_t job_off) {
+__global__ void k_es_clear(const EsJob *jobs, uint32_t job_off, bool only_stopped) {
   const EsJob jb = jobs[job_off + blockIdx.y];
-  if (jb.m < 2) return;  // no list, no set
+  if (jb.m < 2 || (only_stopped && !jb.stopped)) return;  // no list, no set; or a set that needs no rebuild
   const unsigned long long cap = 1ull << jb.hlog2;
   const unsigned long long nth = (unsigned long long)gridDim.x * blockDim.x;
   for (unsigned long long s = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; s < cap; s += nth)
@@ -270,9 +270,9 @@ __global__ void k_es_clear(const EsJob *jobs, uint32_t job_off) {
 }
 
 // H <- the entries of E.
-__global__ void k_es_fill(const EsJob *jobs, uint32_t job_off, uint32_t *err) {
+__global__ void k_es_fill(const EsJob *jobs, uint32_t job_off, uint32_t *err, bool only_stopped) {
   const EsJob jb = jobs[job_off + blockIdx.y];
-  if (jb.m < 2) return;
+  if (jb.m < 2 || (only_stopped && !jb.stopped)) return;
   const uint32_t mask = (uint32_t)((1ull << jb.hlog2) - 1);
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < jb.m; s += gridDim.x * blockDim.x) {
     const unsigned long long e = jb.E[s];
@@ -282,9 +282,18 @@ __global__ void k_es_fill(const EsJob *jobs, uint32_t job_off, uint32_t *err) {
 
 // One CTA per job: switches k0 .. k0 + count - 1 of the job's chain, in
 // windows of B switches (thread x holds switch x of the window).
-template <int B, int MIN_BLOCKS>
-__global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uint32_t job_off, StatsDev *stats,
-                                                          unsigned long long *chain_acc, uint32_t *err) {
+// A CTA of the largest variant does not rebuild its chain's edge set itself
+// (one SM reinserting millions of ids): it stops after the superstep that
+// passes the tombstone limit (an eighth of the slots: rebuilds are cheap on
+// the whole GPU, and fewer tombstones keep the probe chains short), records
+// how far it got in jobs_out (k0, count advanced, stopped = 1, *nstop
+// counted), and the host rebuilds the set on the whole GPU and launches the
+// variant again; a finished job is left with count = 0, which a launch
+// again skips.  The smaller variants rebuild in place at a quarter.
+template <int B, bool kStopToRebuild>
+__device__ __forceinline__ void es_run_body(const EsJob *jobs, uint32_t job_off, StatsDev *stats,
+                                            unsigned long long *chain_acc, uint32_t *err, EsJob *jobs_out,
+                                            uint32_t *nstop) {
   constexpr int S = EsShape<B>::kSlots, LOG2 = EsShape<B>::kSlotsLog2;
   const EsJob jb = jobs[job_off + blockIdx.x];
   const EsSmem<B> sm = es_smem<B>();
@@ -295,10 +304,12 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
     if (x == 0 && jb.count) atomicAdd(&stats->lazy, jb.count);
     return;
   }
+  bool stop = false;
   const uint32_t mask = (uint32_t)((1ull << jb.hlog2) - 1);
   if (x == 0) s_tombs = 0;  // the set was built from the list just before
   clear_touch(sm);
   __syncthreads();
+  unsigned long long done = 0;  // switches run before a stop (largest variant)
   for (unsigned long long s = 0; s < jb.count;) {
     const uint32_t win = (uint32_t)min((unsigned long long)B, jb.count - s);
     // sample the window and mark first touches (Algorithm 2's insert_if_min)
@@ -420,17 +431,36 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
       if (reused) atomicSub(&s_tombs, reused);
     }
     __syncthreads();
-    if (s_tombs > (mask >> 2)) {  // rebuild the set from the list
-      for (uint32_t t = x; t <= mask; t += B) jb.H[t] = kEmptyKey;
-      __syncthreads();
-      for (uint32_t t = x; t < jb.m; t += B) {
-        const unsigned long long e = __ldcg(&jb.E[t]);
-        if (hset_insert(jb.H, mask, e, hash32(e)) < 0) atomicOr(err, kErrTableFull);
+    if constexpr (kStopToRebuild) {
+      s += n;
+      if (s_tombs > (mask >> 3)) {  // a rebuild on the whole GPU is cheap: keep the probe chains short
+        stop = s < jb.count;        // the same in every thread; a finished job needs no rebuild
+        done = s;
+        if (stop) break;
       }
-      if (x == 0) s_tombs = 0;
-      __syncthreads();
+    } else {
+      if (s_tombs > (mask >> 2)) {  // rebuild the set from the list on this CTA
+        for (uint32_t t = x; t <= mask; t += B) jb.H[t] = kEmptyKey;
+        __syncthreads();
+        for (uint32_t t = x; t < jb.m; t += B) {
+          const unsigned long long e = __ldcg(&jb.E[t]);
+          if (hset_insert(jb.H, mask, e, hash32(e)) < 0) atomicOr(err, kErrTableFull);
+        }
+        if (x == 0) s_tombs = 0;
+        __syncthreads();
+      }
+      s += n;
     }
-    s += n;
+  }
+  if constexpr (kStopToRebuild) {
+    if (!stop) done = jb.count;
+    if (x == 0) {  // progress of the job (the host launches it again while stopped)
+      EsJob &out = jobs_out[job_off + blockIdx.x];
+      out.k0 = jb.k0 + done;
+      out.count = jb.count - done;
+      out.stopped = stop ? 1u : 0u;
+      if (stop) atomicAdd(nstop, 1u);
+    }
   }
   // counts of this job
   const unsigned a32 = __reduce_add_sync(0xffffffffu, acc);
@@ -446,6 +476,21 @@ __global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uin
   }
 }
 
+// Windows of 32, 128 and 256 switches (the set rebuilt in place).
+template <int B, int MIN_BLOCKS>
+__global__ void __launch_bounds__(B, MIN_BLOCKS) k_es_run(const EsJob *jobs, uint32_t job_off, StatsDev *stats,
+                                                          unsigned long long *chain_acc, uint32_t *err) {
+  es_run_body<B, false>(jobs, job_off, stats, chain_acc, err, nullptr, nullptr);
+}
+
+// Windows of 1024 switches (chains of at least 2^19 edges: the set rebuilt
+// on the whole GPU between launches).
+__global__ void __launch_bounds__(1024, 1) k_es_run_big(EsJob *jobs, uint32_t job_off, StatsDev *stats,
+                                                        unsigned long long *chain_acc, uint32_t *err,
+                                                        uint32_t *nstop) {
+  es_run_body<1024, true>(jobs, job_off, stats, chain_acc, err, jobs, nstop);
+}
+
 }  // namespace
 
 size_t es_smem_bytes() { return EsShape<1024>::kBytes; }
@@ -455,27 +500,28 @@ uint32_t es_window(uint32_t m) {
 }
 
 cudaError_t prepare_es_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_es_run<1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_es_run_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)EsShape<1024>::kBytes);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_es_run<256, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)EsShape<256>::kBytes);
 }
 
-cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms) {
+cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms,
+                          bool only_stopped) {
   for (uint32_t off = 0; off < njobs; off += 65535u) {
     const uint32_t nj = njobs - off < 65535u ? njobs - off : 65535u;
     const uint32_t gx = (uint32_t)((num_sms * 8 + nj - 1) / nj);
     const dim3 grid(gx < 1 ? 1 : gx, nj);
-    k_es_clear<<<grid, 256, 0, s>>>(jobs, off);
-    k_es_fill<<<grid, 256, 0, s>>>(jobs, off, err);
+    k_es_clear<<<grid, 256, 0, s>>>(jobs, off, only_stopped);
+    k_es_fill<<<grid, 256, 0, s>>>(jobs, off, err, only_stopped);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_es_run(const EsJob *jobs, const uint32_t (&group)[4], StatsDev *stats,
-                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, cudaStream_t s2,
-                          cudaEvent_t fork, cudaEvent_t join, uint32_t *launches) {
+cudaError_t launch_es_run(EsJob *jobs, const uint32_t (&group)[4], StatsDev *stats,
+                          unsigned long long *chain_acc, uint32_t *err, uint32_t *nstop, cudaStream_t s,
+                          cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, uint32_t *launches) {
   // group[w] jobs with windows of 1024, 256, 128 and 32 switches, in that
   // order; the two small-window groups run on s2 (after s, and joined back
   // into s) when there is one, beside the others
@@ -489,7 +535,7 @@ cudaError_t launch_es_run(const EsJob *jobs, const uint32_t (&group)[4], StatsDe
   auto run = [&](int w, cudaStream_t st) {
     for (uint32_t off = beg[w]; off < beg[w + 1]; off += 65535u, ++n) {
       const uint32_t nj = beg[w + 1] - off < 65535u ? beg[w + 1] - off : 65535u;
-      if (w == 0) k_es_run<1024, 1><<<nj, 1024, EsShape<1024>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
+      if (w == 0) k_es_run_big<<<nj, 1024, EsShape<1024>::kBytes, st>>>(jobs, off, stats, chain_acc, err, nstop);
       else if (w == 1) k_es_run<256, 6><<<nj, 256, EsShape<256>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
       else if (w == 2) k_es_run<128, 12><<<nj, 128, EsShape<128>::kBytes, st>>>(jobs, off, stats, chain_acc, err);
       else k_es_run<32, 32><<<nj, 32, EsShape<32>::kBytes, st>>>(jobs, off, stats, chain_acc, err);

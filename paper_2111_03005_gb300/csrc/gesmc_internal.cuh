@@ -147,6 +147,7 @@ struct Counters {
   uint32_t cur;         // list (0 or 1) holding the undecided switches of the next wave
   uint32_t wave_next;   // number of the next wave
   uint32_t wave_blocks; // CTAs of the running wave kernel that have finished
+  uint32_t es_stopped;  // ParES jobs stopped for a rebuild of their edge set (per launch)
   unsigned long long pool_round;  // rounds the pool has completed
 };
 
@@ -248,8 +249,9 @@ cudaError_t launch_duplicate_check(const unsigned long long *E, uint32_t m, unsi
 struct EsJob {
   unsigned long long *E;
   unsigned long long *H;
-  unsigned long long seed, k0, count;
-  uint32_t m, hlog2, chain, pad;
+  unsigned long long seed, k0, count;  // the kernel advances k0 and count as it goes
+  uint32_t m, hlog2, chain;
+  uint32_t stopped;  // the kernel stopped this job for a rebuild of its set on the whole GPU
 };
 
 // Shared memory of the ParES kernel (its larger variant); opt-in once per device.
@@ -258,16 +260,19 @@ cudaError_t prepare_es_kernels();
 // Switches per window of the ParES kernel for a chain of m edges (1024,
 // 256, 128 or 32, by chain size).
 uint32_t es_window(uint32_t m);
-// Edge sets of all jobs rebuilt from their lists.
-cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms);
+// Edge sets of all jobs (or only of the stopped ones) rebuilt from their lists.
+cudaError_t launch_es_set(const EsJob *jobs, uint32_t njobs, uint32_t *err, cudaStream_t s, int num_sms,
+                          bool only_stopped);
 // All jobs' switches, one CTA per job: the first group[0] jobs with windows
 // of 1024, the next group[1] with windows of 256, then group[2] with 128 and
 // group[3] with 32 (these two on s2, forked from and joined back into s
 // through the two events, if given).  *launches receives the number of
 // launches.
-cudaError_t launch_es_run(const EsJob *jobs, const uint32_t (&group)[4], StatsDev *stats,
-                          unsigned long long *chain_acc, uint32_t *err, cudaStream_t s, cudaStream_t s2,
-                          cudaEvent_t fork, cudaEvent_t join, uint32_t *launches);
+// Jobs of the largest window stop when their set needs a rebuild (counted
+// in *nstop); the caller rebuilds those sets and launches again.
+cudaError_t launch_es_run(EsJob *jobs, const uint32_t (&group)[4], StatsDev *stats,
+                          unsigned long long *chain_acc, uint32_t *err, uint32_t *nstop, cudaStream_t s,
+                          cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join, uint32_t *launches);
 // Lists of the chains with a job (job_of[chain] != kNoChain) out of their
 // slots into the jobs' position-order lists, and back (slots in position
 // order, nothing pending).
