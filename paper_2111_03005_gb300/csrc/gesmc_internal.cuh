@@ -147,8 +147,8 @@ struct Counters {
   uint32_t cur;         // list (0 or 1) holding the undecided switches of the next wave
   uint32_t wave_next;   // number of the next wave
   uint32_t wave_blocks; // CTAs of the running wave kernel that have finished
-  uint32_t es_stopped;  // ParES jobs stopped for a rebuild of their edge set (per launch)
   unsigned long long pool_round;  // rounds the pool has completed
+  uint32_t es_stopped;  // ParES jobs stopped for a rebuild of their edge set (per launch)
 };
 
 // Device-resident statistics, accumulated over rounds (all chains).
