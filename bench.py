@@ -8,13 +8,14 @@ bit-exact with the sequential CPU oracle (tests/test_gpu_parity.py).
 
 Default workload: G(n = 2^24, p = 16/(n-1)), about 1.34e8 edges, seeded
 synthetic (a stand-in for the paper's SynGnp family).  Device state is about
-13 GB, far above the 129 MB L2, so consecutive steps cannot run out of L2.
+19 GB, far above the 129 MB L2, so consecutive steps cannot run out of L2.
 
 Usage:
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gesmc|reference]
 Under torchrun each rank runs an independent replica of the workload on its
 own GPU (a single chain does not shard); value = all ranks' switches / the
-slowest rank's time.
+slowest rank's time.  The ensemble and serving workloads split their chains
+or requests over the ranks by footprint instead, with no exchange.
 """
 from __future__ import annotations
 
