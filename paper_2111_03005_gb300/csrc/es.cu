@@ -19,10 +19,11 @@
 // the waves of Algorithm 1 are separated by __syncthreads, and the list E
 // (position order) and the edge set H (open addressing over canonical ids,
 // tombstones on erase) live in HBM.  Many chains run as many CTAs of one
-// launch.  A superstep is also cut at kEsBatch switches; any cut into
-// consecutive runs without source dependencies gives the sequential result.
-// When tombstones pass a quarter of the set's slots, the CTA rebuilds the set
-// from the list between supersteps.
+// launch.  A superstep is also cut at the window size (32 to 1024 switches,
+// by the chain's size); any cut into consecutive runs without source
+// dependencies gives the sequential result.  When tombstones pile up, the
+// set is rebuilt from the list between supersteps: in place by the CTA for
+// the smaller windows, on the whole GPU between launches for the largest.
 #include "device_util.cuh"
 #include "gesmc_internal.cuh"
 
@@ -492,8 +493,6 @@ __global__ void __launch_bounds__(1024, 1) k_es_run_big(EsJob *jobs, uint32_t jo
 }
 
 }  // namespace
-
-size_t es_smem_bytes() { return EsShape<1024>::kBytes; }
 
 uint32_t es_window(uint32_t m) {
   return m >= kEsBigChain ? 1024u : m >= kEsMidChain ? 256u : m >= kEsSmallChain ? 128u : 32u;

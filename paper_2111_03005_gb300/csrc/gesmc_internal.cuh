@@ -254,8 +254,7 @@ struct EsJob {
   uint32_t stopped;  // the kernel stopped this job for a rebuild of its set on the whole GPU
 };
 
-// Shared memory of the ParES kernel (its larger variant); opt-in once per device.
-size_t es_smem_bytes();
+// Shared-memory opt-in of the ParES kernels, once per device.
 cudaError_t prepare_es_kernels();
 // Switches per window of the ParES kernel for a chain of m edges (1024,
 // 256, 128 or 32, by chain size).
