@@ -194,16 +194,23 @@ def traffic_sources_sha256() -> str:
     """SHA-256 over what a round kernel's DRAM traffic depends on: the round
     kernels (round.cu), the structures and constants they share
     (gesmc_internal.cuh), and the layout code of api.cu (chain shapes,
-    capacities, the target filter's size, the pieces of the allocation)."""
+    capacities, the target filter's size, the pieces of the allocation),
+    each without its comments and blank lines."""
     import hashlib
+
+    import re
+
+    def code(text: str) -> bytes:  # comments and blank lines do not change a kernel
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.split("\n"))
+        return "\n".join(ln for ln in lines if ln).encode()
 
     csrc = os.path.join(ROOT, "paper_2111_03005_gb300", "csrc")
     api = open(os.path.join(csrc, "api.cu")).read()
     layout = api[api.index("// Largest m:"):api.index("template <class T>\nT *at(")]
     h = hashlib.sha256()
-    for part in (open(os.path.join(csrc, "round.cu"), "rb").read(),
-                 open(os.path.join(csrc, "gesmc_internal.cuh"), "rb").read(), layout.encode()):
-        h.update(hashlib.sha256(part).digest())
+    for part in (open(os.path.join(csrc, "round.cu")).read(), open(os.path.join(csrc, "gesmc_internal.cuh")).read(),
+                 layout):
+        h.update(hashlib.sha256(code(part)).digest())
     return h.hexdigest()
 
 
