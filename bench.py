@@ -473,7 +473,7 @@ def run_ensemble(args):
     layout, tuning = {}, None
     if args.tuple_log2 or args.group_log2:
         layout = {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2}
-    elif not args.no_autotune:
+    elif not args.no_autotune and count_mine:
         # partition size and table load factor timed on a sample of the ensemble itself
         t_tune = time.perf_counter()
         tuning = autotune.tune(graphs, seeds, rounds=3, cache=autotune.TuneCache(args.tune_cache),
