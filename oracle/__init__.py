@@ -78,6 +78,10 @@ def _load():
     lib.orc_global_switch.restype = ctypes.c_int
     lib.orc_run.argtypes = [u64p, u64, u64, u64, u64, u64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Stats), u64p]
     lib.orc_run.restype = ctypes.c_int
+    lib.orc_run_rounds.argtypes = [u64p, u64, u64, u64, u64, u64, ctypes.c_int, u64p, u64p, u64]
+    lib.orc_run_rounds.restype = ctypes.c_int
+    lib.orc_global_switch_rounds.argtypes = [u64p, u64, u32p, u64, ctypes.POINTER(ctypes.c_uint8), u64p, u64p, u64]
+    lib.orc_global_switch_rounds.restype = ctypes.c_int
     lib.orc_es_sample.argtypes = [u64, u64, u64, u64p]
     lib.orc_es_sample.restype = None
     lib.orc_es_run.argtypes = [u64p, u64, u64, u64, u64, ctypes.c_int, ctypes.POINTER(Stats)]
@@ -179,6 +183,48 @@ def run(edges, seed: int, rounds: int, start_round: int = 0, lazy_threshold: int
     if snapshots:
         return e, st.as_dict(), snap
     return e, st.as_dict()
+
+
+MAX_ROUNDS_RECORDED = 64
+
+
+def run_rounds(edges, seed: int, rounds: int, start_round: int = 0, lazy_threshold: int = 0,
+               exact_ell: bool = False):
+    """Algorithm 3 with every global switch performed by Algorithm 1's
+    decide / delay rounds in Jacobi order (Sec. 4, Thm. 2's worst-case
+    scheduler).  Returns (final list, rounds of each global switch,
+    entering) with entering[t, w] = undecided switches entering round w of
+    global switch t (w >= 1; w < MAX_ROUNDS_RECORDED)."""
+    e = _u64(edges)
+    w = np.zeros(rounds, dtype=np.uint64)
+    ent = np.zeros((rounds, MAX_ROUNDS_RECORDED), dtype=np.uint64)
+    code = _load().orc_run_rounds(_p64(e), len(e), seed, start_round, rounds, lazy_threshold, int(exact_ell),
+                                  _p64(w), _p64(ent), MAX_ROUNDS_RECORDED)
+    if code != 0:
+        raise ValueError(f"orc_run_rounds failed: {code}")
+    return e, w.astype(np.int64), ent.astype(np.int64)
+
+
+def global_switch_rounds(edges, pi, ell: int | None = None, skip=None):
+    """One global switch with an explicit permutation, performed by Algorithm
+    1's rounds in Jacobi order.  Returns (new list, rounds, entering)."""
+    e = _u64(edges)
+    m = len(e)
+    p = np.ascontiguousarray(np.asarray(pi, dtype=np.uint32))
+    if len(p) != m:
+        raise ValueError("pi must have length m")
+    ell = m // 2 if ell is None else ell
+    sk = None
+    if skip is not None:
+        sk_arr = np.ascontiguousarray(np.asarray(skip, dtype=np.uint8))
+        sk = sk_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    w = np.zeros(1, dtype=np.uint64)
+    ent = np.zeros(MAX_ROUNDS_RECORDED, dtype=np.uint64)
+    code = _load().orc_global_switch_rounds(_p64(e), m, p.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), ell, sk,
+                                            _p64(w), _p64(ent), MAX_ROUNDS_RECORDED)
+    if code != 0:
+        raise ValueError(f"orc_global_switch_rounds failed: {code}")
+    return e, int(w[0]), ent.astype(np.int64)
 
 
 def es_sample(seed: int, k: int, m: int) -> tuple[int, int, int]:

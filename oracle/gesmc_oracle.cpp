@@ -22,7 +22,7 @@
 //     independent switches sigma_k = (i, j, g), i != j uniform in [m] and g
 //     a fair bit, one after another.
 //
-// Readings where the paper leaves a choice open (each is listed in the design doc):
+// Readings where the paper leaves a choice open:
 //   * Edges are stored canonically, (min << 32) | max (Sec. 5.2 edge ids;
 //     Sec. 2.1 canonical orientation), also right after every accepted switch.
 //   * The random permutation pi of round r is the argsort of 64-bit keys
@@ -305,6 +305,184 @@ int orc_run(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_round, uint64
     }
     if (snapshots) std::memcpy(snapshots + t * m, E, m * sizeof(uint64_t));
   }
+  return ORC_OK;
+}
+
+// ---- Algorithm 1 (ParallelSuperstep) with its rounds in Jacobi order --------
+//
+// Sec. 4 performs a superstep in rounds of decide / delay.  Taken in Jacobi
+// order, every switch still undecided when round w starts is decided from the
+// statuses known when round w - 1 ended, and round w's decisions all take
+// effect at its closing barrier; Thm. 2's "worst-case scheduler" is this
+// order, and it makes the number of rounds a function of the superstep alone.
+//
+// Per switch k with sources e1 = E[i], e2 = E[j] and targets tau(e1, e2, g):
+// T holds (e1, k, ERASE), (e2, k, ERASE), (e3, k, INSERT), (e4, k, INSERT),
+// plus the implicit (e, inf, ERASE, ILLEGAL) for every e in E that no switch
+// erases.  Reading (where Algorithm 1 as printed and Def. 1 part): a switch
+// that Def. 1 rejects without looking at E -- a target is a loop, or the
+// sources share a node (then its targets re-create its sources) -- and a
+// switch the laziness rule skips are stored in T with status ILLEGAL, i.e.
+// known to fail before the first round; they leave U in round 1.
+//
+// A target e of an undecided switch k, with p = the switch that erases e (if
+// any tuple erases it) and q = the smallest switch inserting e whose status
+// is not ILLEGAL, makes k
+//   ILLEGAL   if k < p or s_p = ILLEGAL (e is still in E when k runs), or
+//             if q < k and s_q = LEGAL (an earlier switch inserted e);
+//   UNDECIDED otherwise if p < k and s_p = UNDECIDED, or q < k and
+//             s_q = UNDECIDED (delay to the next round);
+// and k is ILLEGAL if either target says so, else UNDECIDED if either says
+// so, else LEGAL (E[i] <- e3, E[j] <- e4).
+namespace {
+
+enum { kSUndecided = 0, kSLegal = 1, kSIllegal = 2 };
+const uint64_t kInf = ~0ull;
+
+// One superstep: switches k < L over pi's pairs; skip[k] != 0 marks a skipped
+// (lazy) switch.  Rewires E in place; returns the number of rounds and, if
+// entering is given, the undecided switches entering round w at entering[w]
+// (w < max_w; entering[0] is left alone).  Returns 0 rounds for L == 0.
+uint64_t superstep_jacobi(uint64_t* E, uint64_t m, const uint32_t* pi, uint64_t L,
+                          const std::vector<uint8_t>& skip, uint64_t* entering, uint64_t max_w) {
+  struct Sw {
+    uint64_t i, j, e3, e4;
+  };
+  std::vector<Sw> sw(L);
+  std::vector<int> status(L, kSUndecided);
+  std::vector<uint8_t> known(L, 0);  // stored ILLEGAL (Def. 1 rejects it outright, or it is skipped)
+  std::unordered_map<uint64_t, uint64_t> eraser;                 // e -> p
+  std::unordered_map<uint64_t, std::vector<uint64_t>> inserters;  // e -> every k inserting e, ascending
+  const std::unordered_set<uint64_t> in_E(E, E + m);  // the edge set when the superstep starts
+  for (uint64_t k = 0; k < L; ++k) {
+    const uint64_t i = pi[2 * k], j = pi[2 * k + 1];
+    const int g = i < j ? 1 : 0;
+    const uint64_t e1 = E[i], e2 = E[j];
+    const uint32_t u = (uint32_t)(e1 >> 32), v = (uint32_t)e1;
+    const uint32_t x = (uint32_t)(e2 >> 32), y = (uint32_t)e2;
+    const uint32_t a3 = u, b3 = g ? y : x, a4 = v, b4 = g ? x : y;
+    sw[k] = {i, j, pack(a3, b3), pack(a4, b4)};
+    const bool loop = a3 == b3 || a4 == b4;
+    const bool shared = u == x || u == y || v == x || v == y;
+    if (skip[k] || loop || shared) {
+      known[k] = 1;
+      status[k] = kSIllegal;
+    }
+    eraser[e1] = k;  // Obs. 2: a superstep erases each edge at most once
+    eraser[e2] = k;
+    if (!known[k]) {
+      inserters[sw[k].e3].push_back(k);
+      inserters[sw[k].e4].push_back(k);
+    }
+  }
+  std::vector<uint64_t> U;
+  for (uint64_t k = 0; k < L; ++k) U.push_back(k);
+  uint64_t rounds = 0;
+  std::vector<int> prev;
+  while (!U.empty()) {
+    ++rounds;
+    if (entering && rounds < max_w) entering[rounds] = U.size();
+    prev = status;  // statuses as the last round's barrier left them
+    std::vector<uint64_t> D;
+    std::vector<std::pair<uint64_t, int>> decided;
+    for (uint64_t k : U) {
+      if (known[k]) {
+        decided.push_back({k, kSIllegal});
+        continue;
+      }
+      int s = kSLegal;
+      for (int t = 0; t < 2; ++t) {
+        const uint64_t e = t ? sw[k].e4 : sw[k].e3;
+        // lookup(e, ERASE): the tuple of the switch that erases e, else the
+        // implicit ILLEGAL tuple at infinity if e is in E, else none
+        bool has_p = false;
+        uint64_t p = 0;
+        int sp = kSUndecided;
+        auto it = eraser.find(e);
+        if (it != eraser.end()) {
+          has_p = true;
+          p = it->second;
+          sp = prev[p];
+        } else if (in_E.count(e)) {
+          has_p = true;
+          p = kInf;
+          sp = kSIllegal;
+        }
+        // lookup_min(e, INSERT): smallest inserter whose status is not ILLEGAL
+        bool has_q = false;
+        uint64_t q = 0;
+        for (uint64_t c : inserters[e]) {
+          if (prev[c] != kSIllegal) {
+            has_q = true;
+            q = c;
+            break;
+          }
+        }
+        if (has_p && (k < p || sp == kSIllegal)) s = kSIllegal;
+        if (has_q && k > q && prev[q] == kSLegal) s = kSIllegal;
+        if (s != kSIllegal) {
+          if (has_p && k > p && sp == kSUndecided) s = kSUndecided;
+          if (has_q && k > q && prev[q] == kSUndecided) s = kSUndecided;
+        }
+      }
+      if (s == kSUndecided) D.push_back(k);
+      else decided.push_back({k, s});
+    }
+    if (decided.empty()) return ~0ull;  // no progress: impossible for a valid superstep
+    for (const auto& d : decided) {
+      status[d.first] = d.second;
+      if (d.second == kSLegal) {
+        E[sw[d.first].i] = sw[d.first].e3;
+        E[sw[d.first].j] = sw[d.first].e4;
+      }
+    }
+    U.swap(D);
+  }
+  return rounds;
+}
+
+}  // namespace
+
+// Algorithm 3 with each global switch performed by superstep_jacobi above:
+// the same rounds, seed and laziness as orc_run (so the same list results),
+// plus the number of decide / delay rounds of every global switch in
+// rounds_out[t] and, if entering_out is given, the undecided switches entering
+// round w of global switch t at entering_out[t * max_w + w].
+int orc_run_rounds(uint64_t* E, uint64_t m, uint64_t seed, uint64_t start_round, uint64_t rounds,
+                   uint64_t lazy_threshold, int exact_ell, uint64_t* rounds_out, uint64_t* entering_out,
+                   uint64_t max_w) {
+  if (E == nullptr && m > 0) return ORC_E_INVALID;
+  std::vector<uint32_t> pi(m);
+  const uint64_t L = m / 2;
+  std::vector<uint8_t> skip(L);
+  for (uint64_t t = 0; t < rounds; ++t) {
+    const uint64_t r = start_round + t;
+    orc_permutation(seed, r, m, pi.data());
+    uint64_t ell = L;
+    if (exact_ell && lazy_threshold != 0) {
+      ell = 0;
+      for (uint64_t k = 0; k < L; ++k) ell += orc_lazy_word(seed, r, k) >= lazy_threshold ? 1 : 0;
+    }
+    for (uint64_t k = 0; k < L; ++k)
+      skip[k] = exact_ell ? (k >= ell) : (lazy_threshold != 0 && orc_lazy_word(seed, r, k) < lazy_threshold);
+    const uint64_t w = superstep_jacobi(E, m, pi.data(), L, skip,
+                                        entering_out ? entering_out + t * max_w : nullptr, max_w);
+    if (w == ~0ull) return ORC_E_INVARIANT;
+    if (rounds_out) rounds_out[t] = w;
+  }
+  return ORC_OK;
+}
+
+// The same for one global switch with an explicit permutation (as
+// orc_global_switch: the first ell pairs, skip[k] != 0 skips pair k).
+int orc_global_switch_rounds(uint64_t* E, uint64_t m, const uint32_t* pi, uint64_t ell, const uint8_t* skip,
+                             uint64_t* rounds_out, uint64_t* entering_out, uint64_t max_w) {
+  if (ell > m / 2) return ORC_E_INVALID;
+  std::vector<uint8_t> sk(ell, 0);
+  for (uint64_t k = 0; k < ell && skip; ++k) sk[k] = skip[k] ? 1 : 0;
+  const uint64_t w = superstep_jacobi(E, m, pi, ell, sk, entering_out, max_w);
+  if (w == ~0ull) return ORC_E_INVARIANT;
+  if (rounds_out) *rounds_out = w;
   return ORC_OK;
 }
 

@@ -11,6 +11,10 @@
   permutations on tiny graphs, is stochastic and symmetric; G(d) is
   brute-forced from all edge subsets; a chi-squared test of the final graph
   after enough rounds against the uniform distribution on G(d).
+* Algorithm 1's decide / delay rounds in Jacobi order: hand-worked round
+  counts, the same list as the sequential run (Sec. 4: the superstep keeps
+  the sequential outcome), and Thm. 2's corollaries (expected rounds <= 4
+  on regular graphs and when every degree is <= sqrt(m)).
 """
 import itertools
 import json
@@ -48,6 +52,79 @@ def test_hand_worked_global_switches(golden_dir):
         after, st = oracle.global_switch(P(case["edges"]), case["pi"])
         assert np.array_equal(after, P(case["edges_after"])), case["name"]
         assert st["accepted"] == case["accepted"], case["name"]
+
+
+def test_hand_worked_superstep_rounds(golden_dir):
+    # every global case carries the number of decide / delay rounds of
+    # Algorithm 1 in Jacobi order and the undecided switches entering each
+    # round, worked out by hand from Sec. 4's rules
+    cases = json.load(open(os.path.join(golden_dir, "worked_examples.json")))["global"]
+    assert sum(1 for c in cases if c["rounds"] >= 2) >= 6
+    for case in cases:
+        after, rounds, entering = oracle.global_switch_rounds(P(case["edges"]), case["pi"])
+        assert np.array_equal(after, P(case["edges_after"])), case["name"]
+        assert rounds == case["rounds"], case["name"]
+        assert entering[1:1 + rounds].tolist() == case["entering"], case["name"]
+        assert not entering[1 + rounds:].any(), case["name"]
+
+
+def _jacobi_cases():
+    yield "gnp", inputs.gnp(400, 0.02, 1), 0, False
+    yield "power law 2.01", inputs.pld_graph(600, 2.01, 1, 80, seed=3), 0, False
+    yield "power law 2.5", inputs.pld_graph(800, 2.5, 1, 60, seed=4), 0, False
+    yield "dense", inputs.random_simple_graph(30, 300, 5), 0, False
+    yield "lazy", inputs.random_simple_graph(100, 600, 6), 1 << 62, False
+    yield "exact l", inputs.random_simple_graph(100, 601, 7), 1 << 63, True
+    yield "complete", P([(a, b) for a in range(12) for b in range(a + 1, 12)]), 0, False
+
+
+@pytest.mark.parametrize("case", list(range(7)))
+def test_jacobi_rounds_give_the_sequential_list(case):
+    # Sec. 4: the superstep of Algorithm 1 produces the graph of the
+    # sequential run; every global switch of several graphs, both laziness forms
+    name, e0, t, exact = list(_jacobi_cases())[case]
+    want, st = oracle.run(e0, seed=90 + case, rounds=6, lazy_threshold=t, exact_ell=exact)
+    got, rounds, entering = oracle.run_rounds(e0, seed=90 + case, rounds=6, lazy_threshold=t, exact_ell=exact)
+    assert np.array_equal(got, want), name
+    L = len(e0) // 2
+    for w, ent in zip(rounds, entering):
+        assert w >= 1 and ent[1] == L, name
+        assert all(ent[r] > ent[r + 1] for r in range(1, w)), name  # every round decides a switch
+        assert not ent[w + 1:].any(), name
+
+
+def test_rounds_of_special_graphs():
+    # m < 2: no switch, no round
+    for lst in ([], [(3, 9)]):
+        _, rounds, _ = oracle.run_rounds(P(lst), seed=1, rounds=3)
+        assert rounds.tolist() == [0, 0, 0]
+    # a star: every pair shares the centre, so every switch is known to fail
+    # before round 1 (Def. 1) and one round decides them all
+    _, rounds, _ = oracle.run_rounds(P([(0, v) for v in range(1, 12)]), seed=2, rounds=5)
+    assert rounds.tolist() == [1] * 5
+    # a perfect matching: no two switches share a target, so no dependency
+    _, rounds, _ = oracle.run_rounds(P([(2 * v, 2 * v + 1) for v in range(40)]), seed=3, rounds=5)
+    assert rounds.tolist() == [1] * 5
+
+
+def _ring_lattice(n, d):
+    return P([(v, (v + s) % n) for v in range(n) for s in range(1, d // 2 + 1)])
+
+
+@pytest.mark.parametrize("name", ["4-regular ring", "10-regular ring", "gnp, max degree <= sqrt(m)"])
+def test_thm2_corollaries_mean_rounds_at_most_4(name):
+    # Thm. 2 with its corollaries: E[R] <= 4 on d-regular graphs and when
+    # every degree is at most sqrt(m) (expectation over pi; mean of 40 rounds)
+    if name == "4-regular ring":
+        e0 = _ring_lattice(3000, 4)
+    elif name == "10-regular ring":
+        e0 = _ring_lattice(1000, 10)
+    else:
+        e0 = inputs.gnp(2000, 0.004, 8)
+        deg = np.bincount(np.concatenate(oracle.unpack(e0)))
+        assert deg.max() <= math.sqrt(len(e0))
+    _, rounds, _ = oracle.run_rounds(e0, seed=5, rounds=40)
+    assert rounds.mean() <= 4.0, (name, rounds.tolist())
 
 
 # ---------------------------------------------------------------- randomness
