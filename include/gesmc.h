@@ -206,12 +206,19 @@ size_t gesmc_device_bytes(uint64_t m);
  * the process exits.  So m is limited to GESMC_NOALLOC_MAX_EDGES; larger m
  * returns GESMC_E_TOO_LARGE without touching the GPU.  The call makes no
  * device allocation (no cudaMalloc, no allocating library routine).  The
- * first call on a device looks the array's device address up; make that first
- * call before any stream capture on that device.  Every call on a device
- * shares the one array: calls whose device work may overlap (other streams,
- * other host threads) race and must be serialised by the caller.
+ * first call on a device looks the array's device address up and keeps it for
+ * the life of the process; make that first call before any stream capture on
+ * that device.  cudaDeviceReset destroys the array: after a reset of a device,
+ * do not call this entry point on that device again in the same process (the
+ * kept address would be stale).  Every call on a device shares the one array:
+ * calls whose device work may overlap (other streams, other host threads) race
+ * and must be serialised by the caller.  The device and stream must be the
+ * ones `edges` lives on: the call runs on the current device.
  * Returns GESMC_OK, GESMC_E_INVALID, GESMC_E_TOO_LARGE, GESMC_E_LOOP,
- * GESMC_E_RANGE, GESMC_E_MULTI, GESMC_E_CUDA or a round error of gesmc_run. */
+ * GESMC_E_RANGE, GESMC_E_MULTI, GESMC_E_CUDA or a round error of gesmc_run.
+ * On any error other than GESMC_E_TOO_LARGE and GESMC_E_INVALID, `edges` may
+ * have been rewritten in canonical form (min << 32 | max, same positions)
+ * before the error was found; nothing else about it changes. */
 #define GESMC_NOALLOC_MAX_EDGES 65536
 #define GESMC_NOALLOC_SCRATCH_BYTES (20u << 20)
 int gesmc_run_noalloc(uint64_t *edges, uint64_t m, uint64_t n, uint64_t global_switches, uint64_t seed,

@@ -321,22 +321,38 @@ def gesmc_destroy(h):
         load_library().gesmc_destroy(h)
 
 
+def noalloc_stream(edges_device, stream=None):
+    """The stream an allocation-free call on a tensor of `edges_device` runs
+    on: the given torch stream, which must belong to that device, or that
+    device's current stream.  (A raw stream handle is taken as is.)"""
+    import torch
+
+    if stream is None:
+        return torch.cuda.current_stream(edges_device)
+    dev = getattr(stream, "device", None)
+    if dev is not None and torch.device(dev) != torch.device(edges_device):
+        raise ValueError(f"stream is on {dev}, but the edge list is on {edges_device}")
+    return stream
+
+
 def gesmc_run_noalloc(edges, n: int, global_switches: int, seed: int, start_round: int = 0, stream=None):
     """Allocation-free rounds in place on a CUDA tensor of packed ids (int64/uint64).
 
     For callers that may not allocate device memory; m <= NOALLOC_MAX_EDGES.
     The library's fixed scratch array is shared by all calls on a device, so
-    calls whose device work may overlap must be serialised by the caller."""
+    calls whose device work may overlap must be serialised by the caller.
+    The call runs on the tensor's device (made current for the call) and on
+    `stream`, which must belong to that device (default: its current stream)."""
     import torch
 
     if not (isinstance(edges, torch.Tensor) and edges.is_cuda and edges.is_contiguous()
             and edges.dtype in (torch.int64, torch.uint64)):
         raise TypeError("edges must be a contiguous int64/uint64 CUDA tensor")
-    if stream is None:
-        stream = torch.cuda.current_stream()
+    stream = noalloc_stream(edges.device, stream)
     s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
-    _check(load_library().gesmc_run_noalloc(ctypes.c_void_p(edges.data_ptr()), edges.numel(), n, global_switches,
-                                            seed, start_round, s), "gesmc_run_noalloc")
+    with torch.cuda.device(edges.device):
+        _check(load_library().gesmc_run_noalloc(ctypes.c_void_p(edges.data_ptr()), edges.numel(), n,
+                                                global_switches, seed, start_round, s), "gesmc_run_noalloc")
     return edges
 
 

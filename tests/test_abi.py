@@ -82,3 +82,17 @@ def test_sources_are_free_of_x86_only_code():
             if f.endswith((".cu", ".cuh", ".c", ".cpp", ".h")):
                 src = open(os.path.join(ROOT, d, f)).read()
                 assert "immintrin" not in src and "__builtin_ia32" not in src and "march=native" not in src
+
+
+def test_noalloc_binding_refuses_a_stream_of_another_device():
+    # the allocation-free call runs on the edge list's device; a torch stream
+    # that belongs to another device is refused before anything is launched
+    import types
+
+    torch = pytest.importorskip("torch")
+    other = types.SimpleNamespace(device=torch.device("cuda", 1), cuda_stream=0)
+    with pytest.raises(ValueError):
+        gesmc.noalloc_stream(torch.device("cuda", 0), other)
+    same = types.SimpleNamespace(device=torch.device("cuda", 0), cuda_stream=0)
+    assert gesmc.noalloc_stream(torch.device("cuda", 0), same) is same
+    assert gesmc.noalloc_stream(torch.device("cuda", 0), 12345) == 12345  # a raw handle is taken as is

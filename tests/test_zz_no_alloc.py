@@ -62,6 +62,20 @@ def test_noalloc_rejects_too_many_edges_and_bad_input():
     assert noalloc_call(big, 0, 1, 1, 0) == gesmc.GESMC_E_TOO_LARGE
     loop = torch.tensor([(2 << 32) | 2, 1], dtype=torch.int64, device="cuda")
     assert noalloc_call(loop, 10, 1, 1, 0) == gesmc.GESMC_E_LOOP
+    # a rejected list may come back in canonical form (min << 32 | max), at the same positions
+    multi = torch.tensor([(5 << 32) | 1, (1 << 32) | 5, (2 << 32) | 3], dtype=torch.int64, device="cuda")
+    assert noalloc_call(multi, 10, 1, 1, 0) == gesmc.GESMC_E_MULTI
+    assert multi.cpu().tolist() == [(1 << 32) | 5, (1 << 32) | 5, (2 << 32) | 3]
     with pytest.raises(gesmc.GesmcError) as ei:
         gesmc.gesmc_run_noalloc(big, 0, 1, 1)
     assert ei.value.code == gesmc.GESMC_E_TOO_LARGE
+
+
+def test_noalloc_binding_runs_on_the_tensor_device_and_stream():
+    # the binding makes the tensor's device current and runs on a stream of that device
+    edges, n = inputs.workload_gnp_small(seed=1)
+    dev = torch.from_numpy(edges.view(np.int64).copy()).cuda()
+    s = torch.cuda.Stream(device=dev.device)
+    gesmc.gesmc_run_noalloc(dev, n, 2, 9, stream=s)
+    s.synchronize()
+    assert np.array_equal(dev.cpu().numpy().view(np.uint64), allocating_path(edges, n, 2, 9))
