@@ -1,17 +1,27 @@
 #!/usr/bin/env python
 """Throughput of the G-ES-MC global switch round (arXiv 2111.03005) on GB300.
 
-A step is one call of the public API's gesmc_run with 20 global switches
-(Def. 2; Algorithm 3) on the workload below: 20 x floor(m/2) edge switches.
-The metric is attempted edge switches per second.  Every run's result is
-bit-exact with the sequential CPU oracle (tests/test_gpu_parity.py).
+A step is one call of the public API's gesmc_run with R global switches
+(Def. 2; Algorithm 3) on the workload below: R x floor(m/2) edge switches.
+The metric is attempted edge switches per second.  The timed calls replay the
+library's captured CUDA graph of a round (its default path); stage times come
+from one more, untimed step with per-stage CUDA events.
 
-Default workload: G(n = 2^24, p = 16/(n-1)), about 1.34e8 edges, seeded
-synthetic (a stand-in for the paper's SynGnp family).  Device state is about
-19 GB, far above the 129 MB L2, so consecutive steps cannot run out of L2.
+Parity is checked on the run itself: the first warm-up step starts at round 0
+with chain seed 7 and its list is compared with the sequential oracle's
+(stored SHA-256 digests for G(2^24); the oracle run beside it for the small
+workloads).  A mismatch ends the run with an error.
+
+Workloads (seeded synthetic stand-ins for the paper's SynGnp / SynPld):
+  gnp_2p24  (default) G(n = 2^24, p = 16/(n-1)), about 1.34e8 edges, 20 global
+            switches per step; device state about 19 GB, far above the 129 MB L2
+  gnp_small G(n = 1000, p = 0.01), 10 global switches per step
+  pld_1m    Pld([1..1000], gamma = 2.5) on 10^6 nodes by Havel-Hakimi, 100 global
+            switches per step
+The two small ones fit in L2; L2 is flushed between their timed steps.
 
 Usage:
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gesmc|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gesmc|reference] [--workload NAME]
 Under torchrun each rank runs an independent replica of the workload on its
 own GPU (a single chain does not shard); value = all ranks' switches / the
 slowest rank's time.  The ensemble and serving workloads split their chains
@@ -34,16 +44,21 @@ if ROOT not in sys.path:
 
 METRIC = "edge switches/sec on 1 GB300 (bit-exact vs sequential oracle); % random-access HBM roofline"
 UNIT = "edge switches/s"
-ROUNDS_PER_STEP = 20
+CHAIN_SEED = 7
+L2_FLUSH_BYTES = 512 << 20
 
 WORKLOADS = {
     "gnp_2p24": dict(desc="G(n=2^24, p=16/(n-1)), seed 3; 20 global switches per step", n_log2=24, deg=16.0,
-                     seed=3),
-    "gnp_2p22": dict(desc="G(n=2^22, p=16/(n-1)), seed 4", n_log2=22, deg=16.0, seed=4),
-    "gnp_2p20": dict(desc="G(n=2^20, p=16/(n-1)), seed 5", n_log2=20, deg=16.0, seed=5),
-    "gnp_2p12": dict(desc="G(n=2^12, p=16/(n-1)), seed 7 (tests)", n_log2=12, deg=16.0, seed=7),
+                     seed=3, rounds=20, digests="gnp_2p24_round_digests.json"),
+    "gnp_small": dict(desc="G(n=1000, p=0.01), seed 1; 10 global switches per step", gen="gnp_small", seed=1,
+                      rounds=10, oracle_rounds=10),
+    "pld_1m": dict(desc="Pld([1..1000], gamma=2.5) on n=10^6 nodes, even-sum fix, Havel-Hakimi, seed 2; "
+                        "100 global switches per step", gen="pld_1m", seed=2, rounds=100, oracle_rounds=20),
+    "gnp_2p22": dict(desc="G(n=2^22, p=16/(n-1)), seed 4", n_log2=22, deg=16.0, seed=4, rounds=20),
+    "gnp_2p20": dict(desc="G(n=2^20, p=16/(n-1)), seed 5", n_log2=20, deg=16.0, seed=5, rounds=20),
+    "gnp_2p12": dict(desc="G(n=2^12, p=16/(n-1)), seed 7 (tests)", n_log2=12, deg=16.0, seed=7, rounds=20),
     "gnp_2p27": dict(desc="G(n=2^27, p=16/(n-1)), seed 6: about 1.07e9 edges, 155 GB of device state (near the "
-                          "largest chain one GPU holds)", n_log2=27, deg=16.0, seed=6),
+                          "largest chain one GPU holds)", n_log2=27, deg=16.0, seed=6, rounds=20),
 }
 CPU_SAMPLE = "gnp_2p20"
 
@@ -52,8 +67,28 @@ def make_workload(name):
     from paper_2111_03005_gb300 import inputs
 
     w = WORKLOADS[name]
+    if w.get("gen") == "gnp_small":
+        return inputs.workload_gnp_small(seed=w["seed"])
+    if w.get("gen") == "pld_1m":
+        return inputs.workload_pld_1m(seed=w["seed"])
     n = 1 << w["n_log2"]
     return inputs.gnp(n, w["deg"] / (n - 1), w["seed"]), n
+
+
+def list_digest(a) -> str:
+    import hashlib
+
+    import numpy as np
+
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<u8").tobytes()).hexdigest()
+
+
+def stored_digests(name):
+    w = WORKLOADS[name]
+    if not w.get("digests"):
+        return None
+    with open(os.path.join(ROOT, "tests", "golden", w["digests"])) as f:
+        return json.load(f)
 
 
 # --------------------------------------------------------------------- ranks
@@ -244,32 +279,45 @@ def cpu_sample_switches_per_s():
 
 
 def run_reference(args):
+    """The reference arm: the sequential oracle, as it stands, on one host
+    core, on a bounded sample of the workload per step (the default
+    workload: one global switch of the 2^20-node sample with the same degree
+    profile; the small workloads: their own graph, 10 rounds of G(1000, 0.01)
+    or 1 round of the power law per step)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
 
     oracle.build()
-    edges, n = make_workload(CPU_SAMPLE)
+    wl = WORKLOADS[args.workload]
+    if wl.get("oracle_rounds"):
+        edges, n = make_workload(args.workload)
+        per_step = wl["rounds"] if len(edges) < 100_000 else 1
+        sample = (f"{per_step} global switch(es) per step on {wl['desc'].split(';')[0]} (m={len(edges)}), "
+                  f"sequential oracle, 1 thread")
+        sample_desc = wl["desc"]
+    else:
+        edges, n = make_workload(CPU_SAMPLE)
+        per_step = 1
+        sample = (f"1 global switch per step on {WORKLOADS[CPU_SAMPLE]['desc']} (m={len(edges)}), "
+                  f"sequential oracle, 1 thread")
+        sample_desc = WORKLOADS[CPU_SAMPLE]["desc"]
     times, done = [], 0
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        _, st = oracle.run(edges, seed=11 + step, rounds=1)
+        _, st = oracle.run(edges, seed=11 + step, rounds=per_step)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
             done += st["switches"]
     total = sum(times)
     value = done / total
-    sample = (f"1 global switch per step on {WORKLOADS[CPU_SAMPLE]['desc']} (m={len(edges)}), "
-              f"sequential oracle, 1 thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOADS.get(args.workload, {"desc": args.workload})["desc"],
-                   "sample": WORKLOADS[CPU_SAMPLE]["desc"],
-                   "parallelism": "none (CPU)"},
+        "config": {"workload": wl["desc"], "sample": sample_desc, "parallelism": "none (CPU)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -278,6 +326,53 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- GPU arm
+
+def check_parity(chain, name, edges, rounds, seed, world_rank):
+    """Run the first warm-up step and compare its list with the sequential
+    oracle's.  Returns the parity record and, for the small workloads, the
+    oracle's time and switch count (its cpu_baseline)."""
+    import numpy as np
+
+    gold = stored_digests(name)
+    w = WORKLOADS[name]
+    if gold is not None:
+        assert gold["chain_seed"] == seed and gold["start_round"] == 0
+        assert list_digest(edges) == gold["input_sha256"], "the generator gave another graph on this machine"
+        k = min(rounds, len(gold["rounds"]))
+        chain.run(k, seed)
+        got = list_digest(chain.edges())
+        want = gold["rounds"][k - 1]["sha256"]
+        if got != want:
+            raise SystemExit(f"parity FAILED on rank {world_rank}: {name}, list after {k} rounds has SHA-256 {got}, "
+                             f"the sequential oracle's is {want}")
+        acc = sum(r["accepted"] for r in gold["rounds"][:k])
+        if chain.stats()["accepted"] != acc:
+            raise SystemExit(f"parity FAILED on rank {world_rank}: {name}, accepted counts differ")
+        return {"checked": True, "rounds": k, "chain_seed": seed,
+                "against": "stored SHA-256 of the sequential oracle's list after each round "
+                           f"(tests/golden/{w['digests']})"}, None
+    if w.get("oracle_rounds"):
+        import oracle
+
+        oracle.build()
+        k = w["oracle_rounds"]
+        t0 = time.perf_counter()
+        want, st = oracle.run(edges, seed=seed, rounds=k)
+        dt = time.perf_counter() - t0
+        chain.run(k, seed)
+        got = chain.edges()
+        if not np.array_equal(got, want):
+            bad = int(np.flatnonzero(got != want)[0])
+            raise SystemExit(f"parity FAILED on rank {world_rank}: {name}, list after {k} rounds differs from the "
+                             f"sequential oracle's at position {bad}")
+        if chain.stats()["accepted"] != st["accepted"]:
+            raise SystemExit(f"parity FAILED on rank {world_rank}: {name}, accepted counts differ")
+        return ({"checked": True, "rounds": k, "chain_seed": seed,
+                 "against": "the sequential oracle run beside it, whole list compared"},
+                {"seconds": dt, "switches": st["switches"], "rounds": k})
+    return {"checked": False, "why": "no stored oracle result for this workload (the parity tests cover its kernels)"}, \
+        None
+
 
 def run_gesmc(args):
     import numpy as np
@@ -293,9 +388,13 @@ def run_gesmc(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
+    wl = WORKLOADS[args.workload]
+    rounds = wl["rounds"]
     edges, n = make_workload(args.workload)
     m, L = len(edges), len(edges) // 2
-    seed = 1000 + rank
+    seed = CHAIN_SEED
+    state_bytes = gesmc.gesmc_device_bytes(m)
+    flush_l2 = state_bytes < 4 * L2_FLUSH_BYTES
     layout = {"tuple_log2": args.tuple_log2, "group_log2": args.group_log2}
     tuning = None
     if not args.no_autotune and not (args.tuple_log2 or args.group_log2):
@@ -303,7 +402,7 @@ def run_gesmc(args):
         from paper_2111_03005_gb300 import autotune
 
         t_tune = time.perf_counter()
-        tuning = autotune.tune([(edges, n)], [seed], rounds=3, cache=autotune.TuneCache(args.tune_cache))
+        tuning = autotune.tune([(edges, n)], [seed + 1], rounds=3, cache=autotune.TuneCache(args.tune_cache))
         tuning["tuning_s"] = time.perf_counter() - t_tune
         layout = {"tuple_log2": tuning["tuple_log2"], "group_log2": tuning["group_log2"]}
     # create time (the paper's timings include initialisation): validation, edge set and first layout from a
@@ -318,27 +417,45 @@ def run_gesmc(args):
             create_ms.append(1e3 * (time.perf_counter() - t0))
     del d_edges
     chain = gesmc.Chain(edges, n=n, **layout)
-    for _ in range(args.warmup):
-        chain.run(ROUNDS_PER_STEP, seed)
+    # the first warm-up step (from round 0, chain seed 7) is checked against the sequential oracle
+    parity, oracle_time = check_parity(chain, args.workload, edges, rounds, seed, rank)
+    for _ in range(args.warmup - 1):
+        chain.run(rounds, seed)
     chain.reset_stats()
-    chain.set_profiling(True)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev) if flush_l2 else None
     barrier(dist)
     torch.cuda.synchronize()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
-        start.record(stream)
-        for _ in range(args.steps):
-            chain.run(ROUNDS_PER_STEP, seed)
-        stop.record(stream)
-        torch.cuda.synchronize()
+        if flush is None:   # device state far above L2: one event pair around all steps
+            start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for _ in range(args.steps):
+                chain.run(rounds, seed)
+            stop.record(stream)
+            torch.cuda.synchronize()
+            ms_local = start.elapsed_time(stop)
+        else:               # L2-resident state: L2 flushed between steps, each step timed on its own
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for a0, a1 in evs:
+                flush.add_(1)
+                a0.record(stream)
+                chain.run(rounds, seed)
+                a1.record(stream)
+            torch.cuda.synchronize()
+            ms_local = sum(a0.elapsed_time(a1) for a0, a1 in evs)
     barrier(dist)
-    ms_local = start.elapsed_time(stop)
     ms = max_over_ranks(ms_local, dist, dev)
     st = chain.stats()
+    # one more step, untimed, with CUDA events between the stages of every round
+    chain.reset_stats()
+    chain.set_profiling(True)
+    chain.run(rounds, seed)
+    chain.set_profiling(False)
     stage_ms, prof_rounds = chain.stage_times()
     chain.close()
 
-    switches_rank = args.steps * ROUNDS_PER_STEP * L
+    switches_rank = args.steps * rounds * L
     value = world * switches_rank / (ms / 1e3)
 
     # roofline of the dominant kernel, from its live CUDA-event time
@@ -351,24 +468,32 @@ def run_gesmc(args):
     achieved = abytes / (per_stage[dom] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": abytes,
-                "traffic": traffic_from_profile(f"k_{dom}", args.workload)}
+                "traffic": traffic_from_profile(f"k_{dom}", args.workload),
+                "timing": "stage events of one extra untimed step (direct launches)"}
     # whole-round view: all stages' algorithmic bytes over the round time
     round_bytes = sum(algorithmic_bytes(s, m, L, nb, npart, acc_per_round) for s in per_stage)
     round_ms = sum(per_stage.values())
+    hist = st["wave_hist"]
+    top = max((w for w, c in enumerate(hist) if c), default=0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload]["desc"], "n": n, "m": m,
-                   "global_switches_per_step": ROUNDS_PER_STEP, "switches_per_step": ROUNDS_PER_STEP * L,
-                   "l2": "inputs larger than L2 (device state ~%.1f GB)" % (gesmc.gesmc_device_bytes(m) / 1e9),
+        "config": {"workload": wl["desc"], "n": n, "m": m,
+                   "global_switches_per_step": rounds, "switches_per_step": rounds * L,
+                   "l2": ("L2 flushed between timed steps (%d MB written; device state %.2f GB)"
+                          % (L2_FLUSH_BYTES >> 20, state_bytes / 1e9)) if flush_l2 else
+                         "inputs larger than L2 (device state ~%.1f GB)" % (state_bytes / 1e9),
+                   "path": "captured CUDA graph of a round, replayed (the library's default)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "parity": parity,
         "roofline": roofline,
         "round": {"ms": round_ms, "algorithmic_GBps": round_bytes / (round_ms / 1e3) / 1e9,
                   "stages_ms": {k: round(v, 4) for k, v in per_stage.items()}},
         "tuning": dict(layout, autotune=tuning),
         "waves": {"max": st["waves_max"], "mean": st["waves_total"] / max(st["rounds"], 1),
+                  "hist": {str(w): hist[w] for w in range(1, top + 1) if hist[w]},
                   "accept_rate": st["accepted"] / max(st["switches"], 1)},
         "gpu_launches": st["kernel_launches"],
         "create_ms": {"from_device": create_ms[-1]},
@@ -425,21 +550,28 @@ def run_gesmc(args):
             with gesmc.Chain(host_in, n=n, **layout) as c:
                 torch.cuda.synchronize()
                 host_create.append(1e3 * (time.perf_counter() - t0))
-                c.run(ROUNDS_PER_STEP, seed + 7)
+                c.run(rounds, seed + 7)
                 c.edges(host_out)
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
         e2e_t = max_over_ranks(statistics.median(e2e_times), dist, dev)
-        line["e2e"] = {"value": world * ROUNDS_PER_STEP * L / e2e_t, "unit": UNIT,
+        line["e2e"] = {"value": world * rounds * L / e2e_t, "unit": UNIT,
                        "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * m,
-                       "includes": "gesmc_create (H2D copy, validation) + gesmc_run(20) + gesmc_edges (D2H) + destroy",
+                       "includes": f"gesmc_create (H2D copy, validation) + gesmc_run({rounds}) + gesmc_edges (D2H) "
+                                   "+ destroy",
                        "layout": layout}
         line["create_ms"]["from_pinned_host"] = statistics.median(host_create)
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, sw, dt = cpu_sample_switches_per_s()
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"1 global switch ({sw} switches) on {WORKLOADS[CPU_SAMPLE]['desc']}, "
-                                          f"{dt:.1f} s, sequential oracle, 1 thread"}
+        if oracle_time is not None:   # the oracle's run on this workload, done for the parity check
+            line["cpu_baseline"] = {
+                "value": oracle_time["switches"] / oracle_time["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the first {oracle_time['rounds']} global switches ({oracle_time['switches']} switches) of "
+                          f"this workload, {oracle_time['seconds']:.1f} s, sequential oracle, 1 thread"}
+        else:
+            v, sw, dt = cpu_sample_switches_per_s()
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"1 global switch ({sw} switches) on {WORKLOADS[CPU_SAMPLE]['desc']}, "
+                                              f"{dt:.1f} s, sequential oracle, 1 thread"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -463,7 +595,6 @@ def run_ensemble(args):
     dev = torch.device("cuda", local)
     count, rounds = args.chains, 50
     all_graphs = inputs.ensemble_graphs(count, seed=41)
-    L_all = sum(len(e) // 2 for e, _ in all_graphs)
     # several GPUs: the chains are split by footprint, each GPU runs its share in its own pool (no exchange)
     mine = ensemble.shard([len(e) for e, _ in all_graphs], world)[rank]
     graphs = [all_graphs[t] for t in mine]
@@ -481,12 +612,31 @@ def run_ensemble(args):
         tuning["tuning_s"] = time.perf_counter() - t_tune
         layout = {"tuple_log2": tuning["tuple_log2"], "group_log2": tuning["group_log2"]}
     stream = torch.cuda.Stream()
+    gold = None
+    gold_path = os.path.join(ROOT, "tests", "golden", "ensemble_4096_digests.json")
+    if count == 4096 and os.path.exists(gold_path):
+        with open(gold_path) as f:
+            gold = json.load(f)
+        if gold["rounds"] != rounds or gold["seed0"] != 5000 or gold["gen_seed"] != 41:
+            gold = None
     with torch.cuda.stream(stream), gesmc.Pool(max_edges=max(total, 1), max_chains=max(count_mine, 1),
                                                    stream=stream, **layout) as pool:
         t0 = time.perf_counter()
         ids = [pool.add(e, n=n, seed=s) for (e, n), s in zip(graphs, seeds)]
         add_s = time.perf_counter() - t0
-        for _ in range(args.warmup):
+        # the first warm-up step (rounds 0..49 of every chain) against the sequential oracle's stored digests
+        pool.run(rounds)
+        parity = {"checked": False, "why": "stored oracle digests cover the 4096-chain ensemble only"}
+        if gold is not None:
+            bad = [t for t, c in zip(mine, ids) if list_digest(pool.edges(c))[:16] != gold["digests"][t]]
+            bad = sorted(ensemble.gather_shards(dist, {t: 1 for t in bad}))
+            if bad:
+                raise SystemExit(f"parity FAILED: {len(bad)} ensemble chains differ from the sequential oracle "
+                                 f"after {rounds} rounds (first: chain {bad[0]})")
+            parity = {"checked": True, "rounds": rounds, "chains": count,
+                      "against": "stored SHA-256 of each chain's list after 50 rounds of the sequential oracle "
+                                 "(tests/golden/ensemble_4096_digests.json)"}
+        for _ in range(args.warmup - 1):
             pool.run(rounds)
         pool.reset_stats()
         barrier(dist)
@@ -499,7 +649,8 @@ def run_ensemble(args):
             stop.record(stream)
             torch.cuda.synchronize()
         barrier(dist)
-        ms = max_over_ranks(start.elapsed_time(stop), dist, dev)
+        ms_local = start.elapsed_time(stop)
+        ms = max_over_ranks(ms_local, dist, dev)
         st = pool.stats()
         # one more step, untimed, with CUDA events between the stages of every round
         pool.set_profiling(True)
@@ -507,7 +658,9 @@ def run_ensemble(args):
         stage_ms, prof_rounds = pool.stage_times()
         pool.set_profiling(False)
         del ids
-    value = args.steps * rounds * L_all / (ms / 1e3)
+    # all ranks' switches over the slowest rank's time (the shards cover every chain once)
+    value = ensemble.rate_over_ranks(dist, args.steps * rounds * sum(len(e) // 2 for e, _ in graphs), ms_local / 1e3,
+                                     device=dev)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -536,6 +689,7 @@ def run_ensemble(args):
                    "edges": sum(len(e) for e, _ in all_graphs),
                    "parallelism": "single GPU" if world == 1 else
                    f"chains split by footprint over {world} GPUs (rank 0: {count_mine} chains, {total} edges)"},
+        "parity": parity,
         "per_graph_handles": {"value": per_graph, "unit": UNIT, "sample_chains": len(sample),
                               "includes": "create + run + edges per graph, one after another"},
         "autotune": tuning,
@@ -577,7 +731,9 @@ def run_serve(args):
     unit_gaps = rng.exponential(1.0, size=len(base))
     work = sum(r * (len(e) // 2) for e, _, _, r in base)
     cap = max(args.pool_edges, max(len(e) for e, _, _, _ in base))
-    mine = ensemble.shard([len(e) * r for e, _, _, r in base], world)[rank]
+    mine = [r.rid for r in serve.split_requests(
+        [serve.Request(rid=rid, edges=e, n=n, seed=sd, rounds=r) for rid, (e, n, sd, r) in enumerate(base)],
+        world)[rank]]
     # the plain alternative: one handle per request, first come first served on this GPU (service times
     # do not depend on the arrival rate)
     svc, alone = {}, {}

@@ -218,6 +218,25 @@ class Server:
         self.close()
 
 
+def split_requests(requests, world: int) -> list[list]:
+    """Requests split over `world` GPUs by work (edges x rounds; see
+    ensemble.shard), each GPU serving its share of the stream with no
+    exchange; every rank computes the same split."""
+    from .ensemble import shard
+
+    return [[requests[t] for t in part] for part in shard([len(r.edges) * r.rounds for r in requests], world)]
+
+
+def serve_all(requests, **server_opts) -> dict:
+    """Submit every request, serve until idle: {rid: result list}."""
+    with Server(**server_opts) as srv:
+        for r in requests:
+            srv.submit(r)
+        while not srv.idle():
+            srv.step()
+    return {r.rid: r.result for r in requests}
+
+
 def _new_stream():
     import torch
 
