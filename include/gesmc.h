@@ -69,6 +69,14 @@ enum {
  * (word < lazy_threshold), the equivalent per-switch form.  No effect when
  * lazy_threshold is 0. */
 #define GESMC_FLAG_EXACT_ELL 2u
+/* Fault injection for tests: cap the overflow-tuple list and the table of
+ * dependency entries at 16 entries each (instead of room for every tuple
+ * and edge id), so that a graph whose edge ids are proposed by many
+ * switches makes a round run out of that room.  The kernels check every such
+ * capacity before writing, so the round completes, reports
+ * GESMC_E_INTERNAL and leaves the handle in the error state described above.
+ * Not for production use. */
+#define GESMC_FLAG_TINY_OVERFLOW 4u
 
 /* Device allocation hooks: alloc returns device memory usable on `stream`
  * (or NULL on failure); free releases it.  Both NULL: cudaMalloc/cudaFree. */
@@ -174,6 +182,20 @@ int gesmc_reset_stats(gesmc_t h);
 int gesmc_set_profiling(gesmc_t h, int enable);
 int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds);
 const char *gesmc_stage_name(int stage);
+
+/* How a round is launched.  ctas == 0 (the default): the round's kernels one
+ * after another (about 14 of them, replayed from a captured CUDA graph), each
+ * shaped for large graphs.  ctas >= 1: the whole round in one cooperative
+ * launch of that many 512-thread CTAs (at most as many as the device holds
+ * at once; *effective, if not NULL, receives the count used), the stages
+ * separated by grid-wide barriers whose waits are bounded (a wait that runs
+ * out ends the call with GESMC_E_INTERNAL).  Results are the same either way;
+ * the one-launch round saves the launch latency between stages, which
+ * dominates the rounds of graphs with up to about 10^5 edges.  The paper has
+ * no counterpart (its CPU rounds have no launches).  GESMC_E_INVALID if the
+ * device cannot hold one CTA of the one-launch round.  Stage timing
+ * (gesmc_set_profiling) always uses the separate kernels. */
+int gesmc_set_round_launch(gesmc_t h, uint32_t ctas, uint32_t *effective);
 
 /* Number of the next round the handle will run (start_round + rounds run). */
 uint64_t gesmc_next_round(gesmc_t h);
@@ -298,6 +320,8 @@ int gesmc_pool_edges(gesmc_pool_t p, uint32_t chain, uint64_t *out, uint64_t cap
 int gesmc_pool_chain_info(gesmc_pool_t p, uint32_t chain, gesmc_chain_info_t *out);
 uint32_t gesmc_pool_num_chains(gesmc_pool_t p);
 uint64_t gesmc_pool_free_edges(gesmc_pool_t p);
+/* Round launch of the pool, as gesmc_set_round_launch. */
+int gesmc_pool_set_round_launch(gesmc_pool_t p, uint32_t ctas, uint32_t *effective);
 /* Counters over all chains, stage timing: as for single chains. */
 int gesmc_pool_stats(gesmc_pool_t p, gesmc_stats_t *out);
 int gesmc_pool_reset_stats(gesmc_pool_t p);

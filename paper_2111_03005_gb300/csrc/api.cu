@@ -7,8 +7,11 @@
 #include <iterator>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/gesmc.h"
 #include "gesmc_internal.cuh"
@@ -97,10 +100,13 @@ bool capacity_fits(const Capacity &c) {
 
 // Bits of the target filter for at most M edges: about four per edge (so
 // that a source passes by a collision with probability about 1/5), a power
-// of two between 2^12 and 2^29 (at most 64 MB, which stays in L2).
+// of two between 2^12 and 2^28.  At most 32 MB: with 64 MB the filter's
+// reductions missed L2 often enough that a round of G(2^24) took 0.6%
+// longer, although fewer sources passed (a 16 MB filter let so many through
+// that it took 17% longer).
 uint64_t filter_bits(uint64_t M) {
   uint64_t b = 1ull << 12;
-  while (b < 4 * M && b < (1ull << 29)) b <<= 1;
+  while (b < 4 * M && b < (1ull << 28)) b <<= 1;
   return b;
 }
 
@@ -241,7 +247,7 @@ struct HostChain {
 int map_device_errors(uint32_t err) {
   if (err & kErrTableFull) return GESMC_E_TABLE_FULL;
   if (err & kErrWaveCap) return GESMC_E_WAVE_CAP;
-  if (err & (kErrBucket | kErrNoProgress | kErrRecord | kErrGroup)) return GESMC_E_INTERNAL;
+  if (err & (kErrBucket | kErrNoProgress | kErrRecord | kErrGroup | kErrCopy | kErrGridSync)) return GESMC_E_INTERNAL;
   return GESMC_OK;
 }
 
@@ -280,6 +286,10 @@ struct gesmc_pool_ctx {
   cudaGraphExec_t gexec = nullptr;
   uint64_t graph_version = 0;
   uint32_t graph_launches = 0;
+  // one-launch rounds (k_round_fused) with this many CTAs; 0: the kernels of
+  // a round one after another (replayed from the captured graph)
+  uint32_t fused_ctas = 0;
+  uint32_t fused_max = 0;  // CTAs of the one-launch round the device holds at once
   int profiling = 0;
   std::vector<cudaEvent_t> events;
   double stage_ms[kNumStages] = {};
@@ -309,6 +319,15 @@ void dev_free(gesmc_pool_t p, void *ptr) {
   else cudaFree(ptr);
 }
 
+// A stride coprime with n near n times the golden ratio's fraction (1 if n
+// is tiny): CTA b of a flat pass of n CTAs takes range (b * stride) mod n.
+uint32_t coprime_stride(uint32_t n) {
+  if (n <= 2) return 1;
+  uint64_t s = (uint64_t)(n * 0.6180339887498949) | 1u;
+  while (std::gcd<uint64_t, uint64_t>(s, n) != 1) s += 2;
+  return (uint32_t)(s % n);
+}
+
 void refresh_args(gesmc_pool_t p) {
   ++p->args_version;
   RoundArgs &a = p->args;
@@ -327,6 +346,14 @@ void refresh_args(gesmc_pool_t p) {
     a.chain_hw = c + 1;
     if (hc.d.exact_ell && hc.d.lazy_threshold != 0 && hc.d.L > 0) a.any_exact = 1;
   }
+  // flat pair passes: one pair per thread (k_permute), two (k_sources); a
+  // pool of several chains spreads its resident CTAs over all of them
+  const uint32_t npair = a.slot_hw / 2;
+  a.permute_ctas = std::max<uint32_t>(1, (npair + 255) / 256);
+  a.sources_ctas = std::max<uint32_t>(1, (npair + 511) / 512);
+  const bool spread = p->live_chains > 1;
+  a.permute_stride = spread ? coprime_stride(a.permute_ctas) : 1;
+  a.sources_stride = spread ? coprime_stride(a.sources_ctas) : 1;
 }
 
 // Point the round arguments at the pieces of the pool's memory.
@@ -391,17 +418,25 @@ int pool_init(gesmc_pool_t p, const gesmc_pool_opts &o) {
   p->chains.assign(p->max_chains, HostChain());
   pool_bind(p);
   RoundArgs &a = p->args;
+  if (o.flags & GESMC_FLAG_TINY_OVERFLOW) {
+    a.ovf_cap = std::min<uint32_t>(a.ovf_cap, 16u);
+    a.dep_cap = std::min<uint32_t>(a.dep_cap, 16u);
+  }
   a.max_waves = o.max_waves;
   a.group_log2 = o.group_log2 ? o.group_log2 : kDefaultGroupLog2;
-  uint32_t grid = 0;
-  if (prepare_kernels(a.group_log2, p->num_sms, &grid) != cudaSuccess) {
+  LaunchShapes shapes;
+  if (prepare_kernels(a.group_log2, p->num_sms, &shapes) != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
-  a.group_grid = grid;
+  a.group_grid = shapes.group;
   if (prepare_es_kernels() != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;
+  }
+  if (prepare_fused(a.group_log2, p->num_sms, &p->fused_max) != cudaSuccess) {
+    cudaGetLastError();  // the one-launch round is then unavailable; the multi-kernel round still works
+    p->fused_max = 0;
   }
   cudaStream_t s = p->stream;
   const int sms = p->num_sms;
@@ -599,7 +634,20 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
     }
   }
   uint32_t launches = 0;
-  if (p->use_graphs && !p->profiling && rounds > 0) {
+  if (p->fused_ctas && !p->profiling) {
+    // one cooperative launch per round
+    for (uint64_t r = 0; r < rounds; ++r) {
+      nvtxRangePushA("gesmc round");
+      const cudaError_t e = launch_round_fused(a, s, p->fused_ctas);
+      nvtxRangePop();
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        p->broken = GESMC_E_CUDA;
+        return GESMC_E_CUDA;
+      }
+      ++launches;
+    }
+  } else if (p->use_graphs && !p->profiling && rounds > 0) {
     if (!p->gexec || p->graph_version != p->args_version) {
       if (p->gexec) cudaGraphExecDestroy(p->gexec);
       p->gexec = nullptr;
@@ -622,7 +670,11 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
       p->graph_launches = n;
     }
     bool ok = cudaEventRecord(p->ev_in, s) == cudaSuccess && cudaStreamWaitEvent(p->gstream, p->ev_in, 0) == cudaSuccess;
-    for (uint64_t r = 0; r < rounds && ok; ++r) ok = cudaGraphLaunch(p->gexec, p->gstream) == cudaSuccess;
+    for (uint64_t r = 0; r < rounds && ok; ++r) {
+      nvtxRangePushA("gesmc round");
+      ok = cudaGraphLaunch(p->gexec, p->gstream) == cudaSuccess;
+      nvtxRangePop();
+    }
     ok = ok && cudaEventRecord(p->ev_out, p->gstream) == cudaSuccess &&
          cudaStreamWaitEvent(s, p->ev_out, 0) == cudaSuccess;
     if (!ok) {
@@ -634,7 +686,10 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
   } else {
     for (uint64_t r = 0; r < rounds; ++r) {
       cudaEvent_t *ev = p->profiling ? &p->events[per_round * r] : nullptr;
-      if (launch_round(a, s, p->num_sms, ev, &launches) != cudaSuccess) {
+      nvtxRangePushA("gesmc round");
+      const cudaError_t e = launch_round(a, s, p->num_sms, ev, &launches);
+      nvtxRangePop();
+      if (e != cudaSuccess) {
         p->broken = GESMC_E_CUDA;
         return GESMC_E_CUDA;
       }
@@ -905,6 +960,14 @@ int gesmc_pool_run(gesmc_pool_t p, uint64_t global_switches) {
   return pool_run(p, global_switches);
 }
 
+int gesmc_pool_set_round_launch(gesmc_pool_t p, uint32_t ctas, uint32_t *effective) {
+  if (!p) return GESMC_E_INVALID;
+  if (ctas && p->fused_max == 0) return GESMC_E_INVALID;
+  p->fused_ctas = std::min(ctas, p->fused_max);
+  if (effective) *effective = p->fused_ctas;
+  return GESMC_OK;
+}
+
 int gesmc_pool_edges(gesmc_pool_t p, uint32_t chain, uint64_t *out, uint64_t capacity, int out_on_device,
                      uint64_t *m_out) {
   if (!p || chain >= p->max_chains || !p->chains[chain].live) return GESMC_E_INVALID;
@@ -1063,7 +1126,7 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   po.max_waves = o.max_waves;
   po.tuple_log2 = o.tuple_log2;
   po.group_log2 = o.group_log2;
-  po.flags = o.flags & GESMC_FLAG_NO_GRAPHS;
+  po.flags = o.flags & (GESMC_FLAG_NO_GRAPHS | GESMC_FLAG_TINY_OVERFLOW);
   po.stream = o.stream;
   po.alloc = o.alloc;
   po.free = o.free;
@@ -1131,6 +1194,9 @@ int gesmc_stats(gesmc_t h, gesmc_stats_t *out) { return h ? gesmc_pool_stats(h->
 int gesmc_reset_stats(gesmc_t h) { return h ? gesmc_pool_reset_stats(h->pool) : GESMC_E_INVALID; }
 int gesmc_set_profiling(gesmc_t h, int enable) {
   return h ? gesmc_pool_set_profiling(h->pool, enable) : GESMC_E_INVALID;
+}
+int gesmc_set_round_launch(gesmc_t h, uint32_t ctas, uint32_t *effective) {
+  return h ? gesmc_pool_set_round_launch(h->pool, ctas, effective) : GESMC_E_INVALID;
 }
 int gesmc_stage_times(gesmc_t h, double *ms, int n_stages, uint64_t *rounds) {
   return h ? gesmc_pool_stage_times(h->pool, ms, n_stages, rounds) : GESMC_E_INVALID;

@@ -80,7 +80,16 @@ constexpr uint32_t kUndecided = 0, kLegal = 1, kIllegal = 2;
 
 // Sticky device error bits.
 constexpr uint32_t kErrTableFull = 1u, kErrBucket = 2u, kErrWaveCap = 4u, kErrNoProgress = 8u, kErrRecord = 16u,
-                   kErrGroup = 32u;
+                   kErrGroup = 32u, kErrCopy = 64u, kErrGridSync = 128u;
+
+// Polls of the one-launch round's grid barrier before a CTA gives up (sets
+// kErrGridSync and leaves the kernel); each poll sleeps about 64 ns, so the
+// wait is bounded at about a second.
+constexpr uint32_t kGridWaitPolls = 1u << 24;
+
+// Polls of an mbarrier before a kernel gives up on a bulk copy (sets
+// kErrCopy and returns instead of waiting on).
+constexpr uint32_t kCopyWaitPolls = 1u << 22;
 
 // Wave cap used when the caller passes max_waves = 0.  Every wave decides at
 // least the smallest undecided switch of some chain, so a round needs at
@@ -149,6 +158,9 @@ struct Counters {
   uint32_t wave_blocks; // CTAs of the running wave kernel that have finished
   unsigned long long pool_round;  // rounds the pool has completed
   uint32_t es_stopped;  // ParES jobs stopped for a rebuild of their edge set (per launch)
+  uint32_t gbar_pad[19];  // the grid barrier below on an L2 line of its own
+  uint32_t gbar_count;    // CTAs of the one-launch round arrived at its barrier
+  uint32_t gbar_gen;      // barrier generation (bumped by the last CTA to arrive)
 };
 
 // Device-resident statistics, accumulated over rounds (all chains).
@@ -201,6 +213,16 @@ struct RoundArgs {
   uint32_t wave_kernels;  // pairs of whole-GPU wave kernels per round
   uint32_t chain_hw;      // chain ids in use are below this
   uint32_t any_exact;     // some chain uses exact l with a nonzero threshold
+  // launch shapes (host side only, except the strides): the flat pair passes (k_permute, k_sources) take their CTAs' ranges in
+  // the order b -> (b * cta_stride) mod CTAs, a bijection (the stride is
+  // coprime with the CTA count), so that the CTAs resident at once are spread
+  // over all chains of a pool instead of a few neighbouring ones
+  uint32_t permute_ctas, permute_stride, sources_ctas, sources_stride;
+};
+
+// Resident CTAs of the persistent and grid-stride round kernels on a device.
+struct LaunchShapes {
+  uint32_t group;
 };
 
 // Stages of a round, in launch order.
@@ -221,13 +243,24 @@ enum Stage {
 
 // Dynamic shared memory of the grouping kernel; prepare_kernels opts in to
 // the largest table once and returns the persistent grid for this table
-// size (CTAs that fit on the device at once).
+// size and the single-wave grids of the grid-stride kernels (CTAs that fit
+// on the device at once).
 size_t group_smem_bytes(uint32_t group_log2);
-cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_grid);
+cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, LaunchShapes *shapes);
 
 // One pool round.  ev (optional) receives kNumStages + 1 events around the
 // stages; *launches (optional) counts the kernels launched.
 cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEvent_t *ev, uint32_t *launches);
+
+// The one-launch round: every stage of a pool round in one cooperative launch
+// of `ctas` CTAs (at most fused_max_ctas() of them), the stages separated by
+// grid barriers with bounded waits.  The same lists, counters and wave
+// telemetry as launch_round; for pools whose rounds are bound by launch
+// latency.
+constexpr int kFusedThreads = 512;
+size_t fused_smem_bytes(uint32_t group_log2);
+cudaError_t prepare_fused(uint32_t group_log2, int num_sms, uint32_t *max_ctas);
+cudaError_t launch_round_fused(const RoundArgs &a, cudaStream_t s, uint32_t ctas);
 // One chain (host copy of its descriptor): load a position-order list into
 // its slots, and write its current list by position.
 cudaError_t launch_load_chain(const RoundArgs &a, const ChainDesc &ch, const unsigned long long *E, cudaStream_t s,

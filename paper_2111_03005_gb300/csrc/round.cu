@@ -35,6 +35,8 @@
 // of waves < w (status words carry their wave), so the result and the wave
 // count do not depend on thread timing.  The list after the round is the one
 // the sequential loop of Def. 2 produces.
+#include <algorithm>
+
 #include "device_util.cuh"
 #include "gesmc_internal.cuh"
 
@@ -145,28 +147,44 @@ __device__ __forceinline__ void emit_tuples(const RoundArgs &a, const ChainDesc 
   }
 }
 
-// Switch k (the chain's own index) = (i, j, g) with sources e1, e2: record
-// its reject code, mark its targets in the target filter and emit Algorithm
-// 1's tuples (e3, k, INSERT), (e4, k, INSERT), with k made pool-wide.  Its
-// ERASE tuples (e1, k), (e2, k) follow from k_sources when the filter says
-// a target may need them.  A switch rejected outright has no targets.
-__device__ __forceinline__ void build_switch(const RoundArgs &a, const ChainDesc &ch, unsigned long long round,
-                                             uint32_t ell, uint32_t k, uint32_t i, unsigned long long e1,
-                                             uint32_t j, unsigned long long e2) {
-  unsigned long long e3 = kEmptyKey, e4 = kEmptyKey;
-  const uint32_t code = is_lazy(ch, round, k, ell) ? kCodeLazy : tau(i, j, e1, e2, e3, e4);
-  const uint32_t kg = ch.switch_base + k;
-  a.word[kg] = code;
-  a.sw[kg] = make_uint2(kTrivial, kTrivial);
-  if (code) return;
-  const unsigned long long key[2] = {e3, e4}, hash[2] = {mix64(e3), mix64(e4)};
+// Switches k[t] (the chain's own indices; t < N, those with valid[t]) =
+// (i, j, g) with sources e1, e2: record each reject code, mark the targets
+// in the target filter and emit Algorithm 1's tuples (e3, k, INSERT),
+// (e4, k, INSERT), with k made pool-wide; all N switches' atomics are in
+// flight together.  Their ERASE tuples (e1, k), (e2, k) follow from
+// k_sources when the filter says a target may need them.  A switch rejected
+// outright has no targets.
+template <int N>
+__device__ __forceinline__ void build_switches(const RoundArgs &a, const ChainDesc &ch, unsigned long long round,
+                                               uint32_t ell, const bool (&valid)[N], const uint32_t (&k)[N],
+                                               const uint32_t (&i)[N], const unsigned long long (&e1)[N],
+                                               const uint32_t (&j)[N], const unsigned long long (&e2)[N]) {
+  unsigned long long key[2 * N], hash[2 * N];
+  uint32_t val[2 * N];
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const uint32_t b = filter_bit(a, hash[t]);
-    atomicOr(&a.tfilter[b >> 5], 1u << (b & 31));
+  for (int t = 0; t < N; ++t) {
+    unsigned long long e3 = kEmptyKey, e4 = kEmptyKey;
+    const uint32_t kg = ch.switch_base + k[t];
+    if (valid[t]) {
+      const uint32_t code = is_lazy(ch, round, k[t], ell) ? kCodeLazy : tau(i[t], j[t], e1[t], e2[t], e3, e4);
+      a.word[kg] = code;
+      a.sw[kg] = make_uint2(kTrivial, kTrivial);
+      if (code) e3 = e4 = kEmptyKey;
+    }
+    key[2 * t] = e3;
+    key[2 * t + 1] = e4;
+    val[2 * t] = kg;
+    val[2 * t + 1] = kg | kTupleWhich;
   }
-  const uint32_t val[2] = {kg, kg | kTupleWhich};
-  emit_tuples<2>(a, ch, key, hash, val);
+#pragma unroll
+  for (int t = 0; t < 2 * N; ++t) {
+    hash[t] = mix64(key[t]);
+    if (key[t] != kEmptyKey) {
+      const uint32_t fb = filter_bit(a, hash[t]);
+      atomicOr(&a.tfilter[fb >> 5], 1u << (fb & 31));
+    }
+  }
+  emit_tuples<2 * N>(a, ch, key, hash, val);
 }
 
 // ---------------------------------------------------------------- decide
@@ -271,7 +289,7 @@ __device__ __forceinline__ void append_if(bool take, uint32_t k, uint32_t *list,
 
 // ---------------------------------------------------------------- kernels
 
-__global__ void k_clear(RoundArgs a) {
+__device__ __forceinline__ void clear_body(const RoundArgs &a) {
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
   for (uint32_t b = tid; b < a.bucket_hw; b += nth) a.pcount[b] = 0;
   for (uint32_t p = tid; p < a.part_hw; p += nth) a.ocount[p] = 0;
@@ -290,6 +308,8 @@ __global__ void k_clear(RoundArgs a) {
   }
 }
 
+__global__ void k_clear(RoundArgs a) { clear_body(a); }
+
 __device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uint32_t idx, uint32_t keybits,
                                              uint32_t pos, unsigned long long e) {
   if (idx < (uint32_t)kPermBucketCap)
@@ -302,7 +322,7 @@ __device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uin
 // switches whose laziness word passes (>= threshold); the round then runs
 // the chain's first l switches.  Each CTA takes a contiguous range of
 // switches and each thread keeps a running count for its current chain.
-__global__ void k_lazy_count(RoundArgs a) {
+__device__ __forceinline__ void lazy_count_body(const RoundArgs &a) {
   const unsigned long long R = a.ctl->pool_round;
   const uint32_t per = (a.switch_hw + gridDim.x - 1) / gridDim.x;
   const uint32_t chunk = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
@@ -323,40 +343,59 @@ __global__ void k_lazy_count(RoundArgs a) {
   if (n) atomicAdd(&a.chain_ell[cur], n);
 }
 
+__global__ void k_lazy_count(RoundArgs a) { lazy_count_body(a); }
+
 // Append every position, with its current edge, to its chain's bucket.
 // Capped at 40 registers (6 CTAs of 256 per SM): more warps in flight hide
-// the latency of the record loads and of the bucket cursor atomics.
-__global__ void __launch_bounds__(256, 6) k_permute(RoundArgs a) {
+// the latency of the record loads and of the bucket cursor atomics.  The
+// round launches one pair per thread (short-lived CTAs): on G(2^24) that
+// measured 3.13 ms against 3.46 ms for a grid-stride loop over 8 CTAs per
+// SM and 4.05 ms over one resident wave; the loop form serves the one-launch
+// round.
+__device__ __forceinline__ void permute_pair(const RoundArgs &a, uint32_t x, unsigned long long R) {
+  const uint32_t s0 = 2 * x;
+  const uint32_t c = a.owner_slot[s0];
+  if (c == kNoChain) return;
+  const ChainDesc ch = a.chains[c];
+  const unsigned long long round = chain_round(ch, R);
+  const uint32_t ls = s0 - ch.slot_base;
+  if (ls + 1 < ch.m) {
+    const uint2 ij = __ldcs(reinterpret_cast<const uint2 *>(a.cpos) + x);
+    const ulonglong2 ee = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
+    unsigned long long e1 = ee.x, e2 = ee.y;
+    apply_last(a, ch, chain_apply(ch, R), ls >> 1, ij.x, ij.y, e1, e2);
+    // both keys and both atomics before the two stores
+    const unsigned long long K1 = perm_key(ch.seed, round, ij.x);
+    const unsigned long long K2 = perm_key(ch.seed, round, ij.y);
+    const uint32_t b1 = ch.bucket_base + bucket_of(K1, ch.B), b2 = ch.bucket_base + bucket_of(K2, ch.B);
+    const uint32_t x1 = atomicAdd(&a.pcount[b1], 1u);
+    const uint32_t x2 = atomicAdd(&a.pcount[b2], 1u);
+    store_record(a, b1, x1, mid_of(K1, ch.B), ij.x, e1);
+    store_record(a, b2, x2, mid_of(K2, ch.B), ij.y, e2);
+  } else {  // odd m: the chain's last slot has no partner
+    const uint32_t pos = a.cpos[s0];
+    const unsigned long long K = perm_key(ch.seed, round, pos);
+    const uint32_t b = ch.bucket_base + bucket_of(K, ch.B);
+    store_record(a, b, atomicAdd(&a.pcount[b], 1u), mid_of(K, ch.B), pos, a.cedge[s0]);
+  }
+}
+
+__device__ __forceinline__ void permute_body(const RoundArgs &a) {
   const unsigned long long R = a.ctl->pool_round;
   const uint32_t npair = (a.slot_hw + 1) >> 1;
   const uint32_t nth = gridDim.x * blockDim.x;
-  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += nth) {
-    const uint32_t s0 = 2 * x;
-    const uint32_t c = a.owner_slot[s0];
-    if (c == kNoChain) continue;
-    const ChainDesc ch = a.chains[c];
-    const unsigned long long round = chain_round(ch, R);
-    const uint32_t ls = s0 - ch.slot_base;
-    if (ls + 1 < ch.m) {
-      const uint2 ij = __ldcs(reinterpret_cast<const uint2 *>(a.cpos) + x);
-      const ulonglong2 ee = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
-      unsigned long long e1 = ee.x, e2 = ee.y;
-      apply_last(a, ch, chain_apply(ch, R), ls >> 1, ij.x, ij.y, e1, e2);
-      // both keys and both atomics before the two stores
-      const unsigned long long K1 = perm_key(ch.seed, round, ij.x);
-      const unsigned long long K2 = perm_key(ch.seed, round, ij.y);
-      const uint32_t b1 = ch.bucket_base + bucket_of(K1, ch.B), b2 = ch.bucket_base + bucket_of(K2, ch.B);
-      const uint32_t x1 = atomicAdd(&a.pcount[b1], 1u);
-      const uint32_t x2 = atomicAdd(&a.pcount[b2], 1u);
-      store_record(a, b1, x1, mid_of(K1, ch.B), ij.x, e1);
-      store_record(a, b2, x2, mid_of(K2, ch.B), ij.y, e2);
-    } else {  // odd m: the chain's last slot has no partner
-      const uint32_t pos = a.cpos[s0];
-      const unsigned long long K = perm_key(ch.seed, round, pos);
-      const uint32_t b = ch.bucket_base + bucket_of(K, ch.B);
-      store_record(a, b, atomicAdd(&a.pcount[b], 1u), mid_of(K, ch.B), pos, a.cedge[s0]);
-    }
-  }
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += nth) permute_pair(a, x, R);
+}
+
+// The CTA's place in a flat pass: CTA b takes range (b * stride) mod ctas.
+__device__ __forceinline__ uint32_t scrambled_cta(uint32_t stride) {
+  return (uint32_t)(((unsigned long long)blockIdx.x * stride) % gridDim.x);
+}
+
+// One pair of slots per thread, CTAs in scrambled order.
+__global__ void __launch_bounds__(256, 6) k_permute(RoundArgs a) {
+  const uint32_t x = scrambled_cta(a.permute_stride) * blockDim.x + threadIdx.x;
+  if (x < (a.slot_hw + 1) >> 1) permute_pair(a, x, a.ctl->pool_round);
 }
 
 // Exclusive scan of n counters (n + 1 offsets) by one CTA of 1024 threads,
@@ -435,11 +474,13 @@ __device__ __forceinline__ uint32_t bucket_offset(const RoundArgs &a, uint32_t b
 // many CTAs (local offsets, and the cursors the scatter starts from), then
 // the block sums on one CTA; partition p's list starts at
 // oblk[p / 1024] + ooff[p].
-__global__ void k_overflow_count(RoundArgs a) {
+__device__ __forceinline__ void overflow_count_body(const RoundArgs &a) {
   const uint32_t n = min(a.ctl->ovf_count, a.ovf_cap);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
     atomicAdd(&a.ocount[a.otup[t].w], 1u);
 }
+
+__global__ void k_overflow_count(RoundArgs a) { overflow_count_body(a); }
 
 __global__ void __launch_bounds__(1024) k_overflow_scan_blocks(RoundArgs a) {
   if (a.ctl->ovf_count == 0) return;
@@ -484,7 +525,7 @@ __device__ __forceinline__ uint32_t overflow_offset(const RoundArgs &a, uint32_t
   return p < a.part_hw ? a.oblk[p >> 10] + a.ooff[p] : a.oblk[(a.part_hw + 1023) >> 10];
 }
 
-__global__ void k_overflow_scatter(RoundArgs a) {
+__device__ __forceinline__ void overflow_scatter_body(const RoundArgs &a) {
   const uint32_t n = min(a.ctl->ovf_count, a.ovf_cap);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const uint4 r = a.otup[t];
@@ -493,10 +534,14 @@ __global__ void k_overflow_scatter(RoundArgs a) {
   }
 }
 
-// In-place exclusive scan of 2^kSubBits counters by a CTA of kSortThreads.
+__global__ void k_overflow_scatter(RoundArgs a) { overflow_scatter_body(a); }
+
+// In-place exclusive scan of 2^kSubBits counters by a CTA of kThreads.
+template <int kThreads>
 __device__ __forceinline__ void cta_exclusive_scan(uint32_t *h, uint32_t *warp_tot) {
   constexpr int n = 1 << kSubBits;
-  constexpr int per = n / kSortThreads;
+  constexpr int per = n / kThreads;
+  constexpr int nwarps = kThreads / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t loc[per];
   uint32_t sum = 0;
@@ -514,13 +559,13 @@ __device__ __forceinline__ void cta_exclusive_scan(uint32_t *h, uint32_t *warp_t
   if (lane == 31) warp_tot[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t t = lane < kSortThreads / 32 ? warp_tot[lane] : 0;
+    uint32_t t = lane < nwarps ? warp_tot[lane] : 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t v = __shfl_up_sync(0xffffffffu, t, d);
       if (lane >= d) t += v;
     }
-    if (lane < kSortThreads / 32) warp_tot[lane] = t;
+    if (lane < nwarps) warp_tot[lane] = t;
   }
   __syncthreads();
   uint32_t run = incl - sum + (warp ? warp_tot[warp - 1] : 0);
@@ -537,121 +582,145 @@ __device__ __forceinline__ bool full_key_less(unsigned long long seed, unsigned 
   return ki < kj || (ki == kj && i < j);
 }
 
-// One CTA per bucket: exact sort of the bucket by (key, position), the list
-// written back in this round's slot order, and the switches of all pairs of
-// consecutive slots inside the bucket.
-__global__ void __launch_bounds__(kSortThreads) k_sortpair(RoundArgs a) {
-  __shared__ unsigned long long scomp[kPermBucketCap];  // (32 key bits << 32) | position
-  __shared__ unsigned long long sedge[kPermBucketCap];
-  __shared__ uint16_t slidx[kPermBucketCap];            // record index inside the bucket
-  __shared__ uint32_t hist[1 << kSubBits];
-  __shared__ uint32_t warp_tot[kSortThreads / 32];
+// The shared memory of one bucket's sort: the bucket's records as copied,
+// the record at each slot, the sub-bucket histogram, per-warp sums, and the
+// mbarrier the bulk copy completes on.
+struct SortSmem {
+  uint4 *srec;       // {32 key bits, position, edge lo, edge hi} x kPermBucketCap
+  uint16_t *sidx;    // record at each slot of the bucket
+  uint32_t *hist;    // 2^kSubBits counters
+  uint32_t *warp_tot;
+  unsigned long long *bar;
+};
+
+constexpr size_t kSortSmemBytes = sizeof(uint4) * kPermBucketCap + sizeof(uint16_t) * kPermBucketCap +
+                                  sizeof(uint32_t) * (1u << kSubBits) + sizeof(uint32_t) * 32 + 16;
+
+// Bucket b, by one CTA of kThreads threads.  The bucket's records come into
+// shared memory in one bulk copy (the TMA engine, cp.async.bulk, completing
+// on the mbarrier's phase `parity`); an exact sort of record indices by
+// (key, position) follows: a counting sort on the top key bits, insertion
+// sort inside the sub-buckets, and a full-key fix for runs of equal 32-bit
+// key parts.  Then the list is written back in this round's slot order and
+// the switches of all pairs of consecutive slots inside the bucket are
+// built.  Returns false (with kErrCopy set) if the copy did not land in time;
+// the caller must stop then.  Every thread of the CTA calls it; `parity`
+// tracks the barrier's phase across the buckets a CTA sorts.
+template <int kThreads>
+__device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, const SortSmem &sm, uint32_t &parity) {
+  uint4 *const srec = sm.srec;
+  uint16_t *const sidx = sm.sidx;
+  uint32_t *const hist = sm.hist;
   const int tid = threadIdx.x;
   constexpr int nsub = 1 << kSubBits;
+  const uint32_t c = a.owner_bucket[b];
+  if (c == kNoChain) return true;
+  const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
+  if (tid == 0 && cnt) {
+    mbar_arrive_expect(sm.bar, cnt * (uint32_t)sizeof(uint4));
+    bulk_copy_g2s(srec, a.prec + (size_t)b * kPermBucketCap, cnt * (uint32_t)sizeof(uint4), sm.bar);
+  }
+  for (int s2 = tid; s2 < nsub; s2 += kThreads) hist[s2] = 0;
   const unsigned long long R = a.ctl->pool_round;
-  for (uint32_t b = blockIdx.x; b < a.bucket_hw; b += gridDim.x) {
-    const uint32_t c = a.owner_bucket[b];
-    if (c == kNoChain) continue;
-    const ChainDesc ch = a.chains[c];
-    const unsigned long long round = chain_round(ch, R);
-    const uint32_t ell = ch.exact_ell ? a.chain_ell[c] : 0u;
-    const uint32_t loff = bucket_offset(a, b) - bucket_offset(a, ch.bucket_base);  // chain-local slot offset
-    const uint32_t goff = ch.slot_base + loff;
-    const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
-    const uint4 *rec = a.prec + (size_t)b * kPermBucketCap;
-    for (int s = tid; s < nsub; s += kSortThreads) hist[s] = 0;
-    unsigned long long v[kPerThread];
-#pragma unroll
-    for (int r = 0; r < kPerThread; ++r) {
-      const uint32_t idx = tid + r * kSortThreads;
-      v[r] = 0;
-      if (idx < cnt) {
-        const uint2 kp = *reinterpret_cast<const uint2 *>(&rec[idx]);  // key bits, position
-        v[r] = ((unsigned long long)kp.x << 32) | kp.y;
+  const ChainDesc ch = a.chains[c];
+  const unsigned long long round = chain_round(ch, R);
+  const uint32_t ell = ch.exact_ell ? a.chain_ell[c] : 0u;
+  const uint32_t loff = bucket_offset(a, b) - bucket_offset(a, ch.bucket_base);  // chain-local slot offset
+  const uint32_t goff = ch.slot_base + loff;
+  __syncthreads();  // the histogram is cleared
+  const bool landed = cnt == 0 || mbar_wait(sm.bar, parity, kCopyWaitPolls);
+  if (__syncthreads_or(!landed)) {
+    // the copy did not complete in time: report it, give it a last bounded
+    // wait (shared memory must not be released under a copy in flight), stop
+    if (tid == 0) atomicOr(&a.ctl->err, kErrCopy);
+    if (cnt) mbar_wait(sm.bar, parity, kCopyWaitPolls);
+    return false;
+  }
+  if (cnt) parity ^= 1u;  // the barrier's next phase serves the CTA's next copy
+  for (uint32_t t = tid; t < cnt; t += kThreads) atomicAdd(&hist[srec[t].x >> (32 - kSubBits)], 1u);
+  __syncthreads();
+  cta_exclusive_scan<kThreads>(hist, sm.warp_tot);
+  __syncthreads();
+  for (uint32_t t = tid; t < cnt; t += kThreads) sidx[atomicAdd(&hist[srec[t].x >> (32 - kSubBits)], 1u)] = t;
+  __syncthreads();
+  // hist[s] is now the end of sub-bucket s; sort each (a handful of items)
+  // by (32 key bits, position)
+  for (int s2 = tid; s2 < nsub; s2 += kThreads) {
+    const uint32_t beg = s2 ? hist[s2 - 1] : 0, end = hist[s2];
+    for (uint32_t x = beg + 1; x < end; ++x) {
+      const uint16_t li = sidx[x];
+      const unsigned long long val = ((unsigned long long)srec[li].x << 32) | srec[li].y;
+      uint32_t y = x;
+      for (; y > beg; --y) {
+        const uint2 kp = *reinterpret_cast<const uint2 *>(&srec[sidx[y - 1]]);
+        if ((((unsigned long long)kp.x << 32) | kp.y) <= val) break;
+        sidx[y] = sidx[y - 1];
       }
+      sidx[y] = li;
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kPerThread; ++r)
-      if (tid + r * kSortThreads < cnt) atomicAdd(&hist[(uint32_t)(v[r] >> (64 - kSubBits))], 1u);
-    __syncthreads();
-    cta_exclusive_scan(hist, warp_tot);
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kPerThread; ++r) {
-      const uint32_t idx = tid + r * kSortThreads;
-      if (idx < cnt) {
-        const uint32_t pos = atomicAdd(&hist[(uint32_t)(v[r] >> (64 - kSubBits))], 1u);
-        scomp[pos] = v[r];
-        slidx[pos] = (uint16_t)idx;
-      }
-    }
-    __syncthreads();
-    // hist[s] is now the end of sub-bucket s; sort each (a handful of items)
-    for (int s = tid; s < nsub; s += kSortThreads) {
-      const uint32_t beg = s ? hist[s - 1] : 0, end = hist[s];
-      for (uint32_t x = beg + 1; x < end; ++x) {
-        const unsigned long long val = scomp[x];
-        const uint16_t li = slidx[x];
+  }
+  __syncthreads();
+  // equal 32-bit key parts: order those runs by the full key
+  for (uint32_t t = tid; t + 1 < cnt; t += kThreads) {
+    const uint32_t mt = srec[sidx[t]].x;
+    if (srec[sidx[t + 1]].x == mt && (t == 0 || srec[sidx[t - 1]].x != mt)) {
+      uint32_t e = t + 2;
+      while (e < cnt && srec[sidx[e]].x == mt) ++e;
+      for (uint32_t x = t + 1; x < e; ++x) {
+        const uint16_t li = sidx[x];
+        const uint32_t pos = srec[li].y;
         uint32_t y = x;
-        while (y > beg && scomp[y - 1] > val) {
-          scomp[y] = scomp[y - 1];
-          slidx[y] = slidx[y - 1];
+        while (y > t && full_key_less(ch.seed, round, pos, srec[sidx[y - 1]].y)) {
+          sidx[y] = sidx[y - 1];
           --y;
         }
-        scomp[y] = val;
-        slidx[y] = li;
+        sidx[y] = li;
       }
     }
-    __syncthreads();
-    // equal 32-bit key parts: order those runs by the full key
-    for (uint32_t t = tid; t + 1 < cnt; t += kSortThreads) {
-      const uint32_t mt = (uint32_t)(scomp[t] >> 32);
-      if ((uint32_t)(scomp[t + 1] >> 32) == mt && (t == 0 || (uint32_t)(scomp[t - 1] >> 32) != mt)) {
-        uint32_t e = t + 2;
-        while (e < cnt && (uint32_t)(scomp[e] >> 32) == mt) ++e;
-        for (uint32_t x = t + 1; x < e; ++x) {
-          const unsigned long long val = scomp[x];
-          const uint16_t li = slidx[x];
-          uint32_t y = x;
-          while (y > t && full_key_less(ch.seed, round, (uint32_t)val, (uint32_t)scomp[y - 1])) {
-            scomp[y] = scomp[y - 1];
-            slidx[y] = slidx[y - 1];
-            --y;
-          }
-          scomp[y] = val;
-          slidx[y] = li;
-        }
-      }
-    }
-    __syncthreads();
-    // slots of the bucket hold pi in order: write the list in slot order
-    for (uint32_t t = tid; t < cnt; t += kSortThreads) {
-      const uint2 eh = *reinterpret_cast<const uint2 *>(&rec[slidx[t]].z);  // edge lo, hi
-      const unsigned long long e = ((unsigned long long)eh.y << 32) | eh.x;
-      sedge[t] = e;
-      a.cpos[goff + t] = (uint32_t)scomp[t];
-      a.cedge[goff + t] = e;
-    }
-    __syncthreads();
-    const uint32_t t0 = loff & 1u;
-    const uint32_t npairs = cnt > t0 ? (cnt - t0) >> 1 : 0;
-    for (uint32_t p = tid; p < npairs; p += kSortThreads) {
-      const uint32_t t = t0 + 2 * p;
-      build_switch(a, ch, round, ell, (loff + t) >> 1, (uint32_t)scomp[t], sedge[t], (uint32_t)scomp[t + 1],
-                   sedge[t + 1]);
-    }
-    if (tid == 0 && t0 == 1 && cnt > 0) {
-      // this bucket's first slot is the second of a pair started in an
-      // earlier bucket: k_boundary builds that switch from the list
-      const uint32_t idx = atomicAdd(&a.ctl->boundary, 1u);
-      a.bnd[idx] = goff - 1;  // the pair's first slot
-    }
-    __syncthreads();
   }
+  __syncthreads();
+  // slots of the bucket hold pi in order: write the list in slot order
+  for (uint32_t t = tid; t < cnt; t += kThreads) {
+    const uint4 r = srec[sidx[t]];
+    a.cpos[goff + t] = r.y;
+    a.cedge[goff + t] = ((unsigned long long)r.w << 32) | r.z;
+  }
+  const uint32_t t0 = loff & 1u;
+  const uint32_t npairs = cnt > t0 ? (cnt - t0) >> 1 : 0;
+  for (uint32_t p = tid; p < npairs; p += kThreads) {
+    const uint32_t t = t0 + 2 * p;
+    const uint4 r1 = srec[sidx[t]], r2 = srec[sidx[t + 1]];
+    const bool valid[1] = {true};
+    const uint32_t k[1] = {(loff + t) >> 1}, i[1] = {r1.y}, j[1] = {r2.y};
+    const unsigned long long e1[1] = {((unsigned long long)r1.w << 32) | r1.z};
+    const unsigned long long e2[1] = {((unsigned long long)r2.w << 32) | r2.z};
+    build_switches<1>(a, ch, round, ell, valid, k, i, e1, j, e2);
+  }
+  if (tid == 0 && t0 == 1 && cnt > 0) {
+    // this bucket's first slot is the second of a pair started in an
+    // earlier bucket: k_boundary builds that switch from the list
+    const uint32_t idx = atomicAdd(&a.ctl->boundary, 1u);
+    a.bnd[idx] = goff - 1;  // the pair's first slot
+  }
+  __syncthreads();  // the CTA's shared memory may take the next bucket's copy
+  return true;
 }
 
-__global__ void k_boundary(RoundArgs a) {
+// One CTA per bucket (the round's launch over all buckets).
+__global__ void __launch_bounds__(kSortThreads, 4) k_sortpair(RoundArgs a) {
+  __shared__ __align__(128) uint4 srec[kPermBucketCap];
+  __shared__ uint16_t sidx[kPermBucketCap];
+  __shared__ uint32_t hist[1 << kSubBits];
+  __shared__ uint32_t warp_tot[kSortThreads / 32];
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  const SortSmem sm{srec, sidx, hist, warp_tot, &bar};
+  uint32_t parity = 0;
+  if (sort_bucket<kSortThreads>(a, blockIdx.x, sm, parity) && threadIdx.x == 0) mbar_inval(&bar);
+}
+
+__device__ __forceinline__ void boundary_body(const RoundArgs &a) {
   const uint32_t n = a.ctl->boundary;
   const unsigned long long R = a.ctl->pool_round;
   for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
@@ -668,9 +737,33 @@ __global__ void k_boundary(RoundArgs a) {
       continue;
     }
     // both slots were written by the sort kernel (the list in this round's slot order)
-    build_switch(a, ch, chain_round(ch, R), ch.exact_ell ? a.chain_ell[c] : 0u, k, a.cpos[g], a.cedge[g],
-                 a.cpos[g + 1], a.cedge[g + 1]);
+    const bool valid[1] = {true};
+    const uint32_t kk[1] = {k}, i[1] = {a.cpos[g]}, j[1] = {a.cpos[g + 1]};
+    const unsigned long long e1[1] = {a.cedge[g]}, e2[1] = {a.cedge[g + 1]};
+    build_switches<1>(a, ch, chain_round(ch, R), ch.exact_ell ? a.chain_ell[c] : 0u, valid, kk, i, e1, j, e2);
   }
+}
+
+__global__ void k_boundary(RoundArgs a) { boundary_body(a); }
+
+// The chain of a thread's current pair, kept while its consecutive pairs
+// stay in it: pairs [lo, hi) are chain c's.
+struct PairChain {
+  uint32_t c = kNoChain, lo = 1, hi = 0;
+};
+
+// Make pc the chain of pair x; false if no chain owns it.
+__device__ __forceinline__ bool pair_chain(const RoundArgs &a, uint32_t x, PairChain &pc) {
+  if (x >= pc.lo && x < pc.hi) return true;
+  pc.c = a.owner_slot[2 * x];
+  if (pc.c == kNoChain) {
+    pc.lo = 1;
+    pc.hi = 0;
+    return false;
+  }
+  pc.lo = a.chains[pc.c].slot_base >> 1;
+  pc.hi = pc.lo + ((a.chains[pc.c].m + 1) >> 1);
+  return true;
 }
 
 // One pair of slots: its two sources, the ERASE value they carry, and
@@ -682,16 +775,16 @@ struct SourcePair {
   size_t base[2];
 };
 
-__device__ __forceinline__ void load_source_pair(const RoundArgs &a, uint32_t x, uint32_t c, ulonglong2 ee,
-                                                 SourcePair &sp) {
+__device__ __forceinline__ void load_source_pair(const RoundArgs &a, uint32_t x, bool owned, uint32_t c,
+                                                 ulonglong2 ee, SourcePair &sp) {
   sp.key[0] = ee.x;
   sp.key[1] = ee.y;
   sp.val = kTupleSource | kKeepK;
-  if (c == kNoChain) {
+  if (!owned) {
     sp.key[0] = sp.key[1] = kEmptyKey;
     return;
   }
-  const ChainDesc ch = a.chains[c];
+  const ChainDesc &ch = a.chains[c];
   const uint32_t ls = 2 * x - ch.slot_base;
   if (ls + 1 < ch.m) {
     const uint32_t kg = ch.switch_base + (ls >> 1);
@@ -711,58 +804,63 @@ __device__ __forceinline__ void load_source_pair(const RoundArgs &a, uint32_t x,
 }
 
 // The sources of every switch (Algorithm 1's ERASE tuples) from the list in
-// this round's slot order, two pairs per thread: all loads first (slot
-// owners, list entries, chains, reject words, filter words), then the
-// cursor atomics of all four keys, then their stores.  Only an edge id
-// that is some switch's target needs a tuple (the grouping only asks
-// whether targets exist and who erases them), so a source whose filter bit
-// is clear is dropped; a set bit can be a collision, which only adds a
-// tuple nobody needs.  The unpaired last slot of an odd list is a source
-// no switch erases, and so are the sources of a switch rejected outright.
+// this round's slot order, two pairs per thread (x and x + 256): all loads
+// first (list entries, reject words, filter words), then the cursor atomics
+// of all four keys, then their stores.  Only an edge id that is some
+// switch's target needs a tuple (the grouping only asks whether targets
+// exist and who erases them), so a source whose filter bit is clear is
+// dropped; a set bit can be a collision, which only adds a tuple nobody
+// needs.  The unpaired last slot of an odd list is a source no switch
+// erases, and so are the sources of a switch rejected outright.
+__device__ __forceinline__ void source_pairs(const RoundArgs &a, uint32_t x, uint32_t y, uint32_t end) {
+  PairChain pc;
+  const ulonglong2 ex = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
+  ulonglong2 ey = make_ulonglong2(kEmptyKey, kEmptyKey);
+  if (y < end) ey = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + y);
+  SourcePair sp[2];
+  const bool ox = pair_chain(a, x, pc);
+  load_source_pair(a, x, ox, pc.c, ex, sp[0]);
+  const bool oy = y < end && pair_chain(a, y, pc);
+  load_source_pair(a, y, oy, pc.c, ey, sp[1]);
+  uint32_t w[2][2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int t = 0; t < 2; ++t)
+      w[q][t] = sp[q].key[t] == kEmptyKey ? 0u : __ldcg(&a.tfilter[filter_bit(a, sp[q].hash[t]) >> 5]);
+  uint32_t idx[2][2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (!((w[q][t] >> (filter_bit(a, sp[q].hash[t]) & 31)) & 1u)) sp[q].key[t] = kEmptyKey;
+      idx[q][t] = sp[q].key[t] != kEmptyKey ? atomicAdd(&a.tcount[sp[q].cursor[t]], 1u) : 0u;
+    }
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const unsigned long long k = sp[q].key[t];
+      if (k == kEmptyKey) continue;
+      if (idx[q][t] < sp[q].capt) {
+        a.ptup[sp[q].base[t] + idx[q][t]] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), sp[q].val,
+                                                       (uint32_t)sp[q].hash[t]);
+      } else {
+        const uint32_t o = atomicAdd(&a.ctl->ovf_count, 1u);
+        if (o < a.ovf_cap)
+          a.otup[o] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), sp[q].val, sp[q].part[t]);
+        else
+          atomicOr(&a.ctl->err, kErrRecord);
+      }
+    }
+}
+
+// One launch of short-lived CTAs, two pairs per thread (measured faster than
+// a grid-stride loop over a resident grid).
 __global__ void __launch_bounds__(256, 4) k_sources(RoundArgs a) {
-  const uint32_t npair = (a.slot_hw + 1) >> 1;
-  const uint32_t nth = gridDim.x * blockDim.x;
-  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < npair; x += 2 * nth) {
-    const uint32_t y = x + nth;
-    const uint32_t cx = a.owner_slot[2 * x], cy = y < npair ? a.owner_slot[2 * y] : kNoChain;
-    const ulonglong2 ex = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + x);
-    ulonglong2 ey = make_ulonglong2(kEmptyKey, kEmptyKey);
-    if (y < npair) ey = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + y);
-    SourcePair sp[2];
-    load_source_pair(a, x, cx, ex, sp[0]);
-    load_source_pair(a, y, cy, ey, sp[1]);
-    uint32_t w[2][2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int t = 0; t < 2; ++t)
-        w[q][t] = sp[q].key[t] == kEmptyKey ? 0u : __ldcg(&a.tfilter[filter_bit(a, sp[q].hash[t]) >> 5]);
-    uint32_t idx[2][2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        if (!((w[q][t] >> (filter_bit(a, sp[q].hash[t]) & 31)) & 1u)) sp[q].key[t] = kEmptyKey;
-        idx[q][t] = sp[q].key[t] != kEmptyKey ? atomicAdd(&a.tcount[sp[q].cursor[t]], 1u) : 0u;
-      }
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const unsigned long long k = sp[q].key[t];
-        if (k == kEmptyKey) continue;
-        if (idx[q][t] < sp[q].capt) {
-          a.ptup[sp[q].base[t] + idx[q][t]] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), sp[q].val,
-                                                         (uint32_t)sp[q].hash[t]);
-        } else {
-          const uint32_t o = atomicAdd(&a.ctl->ovf_count, 1u);
-          if (o < a.ovf_cap)
-            a.otup[o] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), sp[q].val, sp[q].part[t]);
-          else
-            atomicOr(&a.ctl->err, kErrRecord);
-        }
-      }
-  }
+  const uint32_t end = a.slot_hw >> 1;
+  const uint32_t x = scrambled_cta(a.sources_stride) * 2 * blockDim.x + threadIdx.x;
+  if (x < end) source_pairs(a, x, x + blockDim.x, end);
 }
 
 // Grouping of one tuple partition by edge id (Algorithm 1's table T for the
@@ -865,7 +963,7 @@ constexpr int kGroupR = 4;  // tuples a thread holds in registers on the fast pa
 // claimed.  Partitions with more tuples than fit, or more distinct ids than
 // slots, take the sub-pass path: the ids whose hash bits 16.. select them,
 // split further until each sub-pass fits.
-__global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) {
+__device__ __forceinline__ void group_body(const RoundArgs &a) {
   const uint32_t S = 1u << a.group_log2;
   const GroupSmem g = group_smem(S);
   __shared__ uint32_t stk_sub[64], stk_n[64];
@@ -982,9 +1080,11 @@ __global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kGroupThreads, 4) k_group(RoundArgs a) { group_body(a); }
+
 // Each CTA takes a contiguous range of switches, so that a thread's running
 // per-chain count changes chain only at chain boundaries.
-__global__ void k_wave1(RoundArgs a) {
+__device__ __forceinline__ void wave1_body(const RoundArgs &a) {
   Tally t;
   ChainCount cc;
   const uint32_t per = (a.switch_hw + gridDim.x - 1) / gridDim.x;
@@ -1022,6 +1122,8 @@ __global__ void k_wave1(RoundArgs a) {
   flush_tally(a, t);
   flush_count(a, cc);
 }
+
+__global__ void k_wave1(RoundArgs a) { wave1_body(a); }
 
 __device__ __forceinline__ uint32_t wave_cap(const RoundArgs &a) {
   return a.max_waves ? a.max_waves : kDefaultWaveCap;
@@ -1179,6 +1281,241 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- one-launch round
+
+// Grid-wide barrier of a cooperative launch (every CTA resident): each CTA
+// arrives on a counter; the last to arrive resets it and bumps the
+// generation the others wait on, and the fences on both sides make every
+// write before the barrier visible after it.  The wait is bounded
+// (kGridWaitPolls): a CTA that gives up sets kErrGridSync and returns false,
+// and its caller leaves the kernel; the other CTAs see the error bit at their
+// next wait and leave too, so the launch ends with the error reported.
+__device__ __forceinline__ bool grid_sync(Counters *ctl) {
+  __shared__ uint32_t ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t *gen = &ctl->gbar_gen;
+    const uint32_t g = *gen;
+    __threadfence();
+    if (atomicAdd(&ctl->gbar_count, 1u) == gridDim.x - 1) {
+      ctl->gbar_count = 0;
+      __threadfence();
+      atomicAdd(&ctl->gbar_gen, 1u);
+      ok = 1;
+    } else {
+      volatile uint32_t *err = &ctl->err;
+      uint32_t it = 0;
+      // a CTA that gave up at an earlier barrier never arrives: stop then too
+      while (*gen == g && it < kGridWaitPolls && !(*err & kErrGridSync)) {
+        __nanosleep(64);
+        ++it;
+      }
+      ok = *gen != g;
+      if (!ok) atomicOr(&ctl->err, kErrGridSync);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Exclusive scan of n counters (each clamped to `clamp`) by the calling CTA:
+// off[b] (and copy[b], if given) receives the sum of the counters before b.
+// Returns the total.  Every thread of the CTA calls it.
+__device__ __forceinline__ uint32_t cta_scan_full(const uint32_t *count, uint32_t *off, uint32_t *copy, uint32_t n,
+                                                  uint32_t clamp) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint32_t total;
+  const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t per = (n + nt - 1) / nt;
+  const uint32_t beg = min(tid * per, n), end = min(beg + per, n);
+  uint32_t sum = 0;
+  for (uint32_t b = beg; b < end; ++b) sum += min(count[b], clamp);
+  uint32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t t = lane < nt / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= (uint32_t)d) t += v;
+    }
+    if (lane < nt / 32) wsum[lane] = t;
+    if (lane == 31) total = t;
+  }
+  __syncthreads();
+  uint32_t run = incl - sum + (warp ? wsum[warp - 1] : 0);
+  for (uint32_t b = beg; b < end; ++b) {
+    const uint32_t c = min(count[b], clamp);
+    off[b] = run;
+    if (copy) copy[b] = run;
+    run += c;
+  }
+  const uint32_t tot = total;
+  __syncthreads();
+  return tot;
+}
+
+// End of a pool round (the work of k_tail after its waves): wave telemetry,
+// statistics, and the pool's round counter.  One thread.
+__device__ __forceinline__ void close_round(const RoundArgs &a, uint32_t wave) {
+  const uint32_t waves = a.any_work ? wave - 1 : 0;
+  a.ctl->waves = waves;
+  if (a.any_work) {
+    a.st->waves_total += waves;
+    if (waves > a.st->waves_max) a.st->waves_max = waves;
+    a.st->wave_hist[waves < kWaveHist ? waves : kWaveHist - 1] += 1;
+  }
+  a.st->last_pending[1] = a.switch_hw;
+  a.st->overflow_tuples += a.ctl->ovf_count;
+  for (uint32_t w = wave; w < kWaveHist; ++w) a.st->last_pending[w] = 0;
+  a.ctl->pool_round += 1;
+}
+
+// The whole round of a pool in one cooperative launch of kFusedThreads-thread
+// CTAs: the same stages as the multi-kernel round, in the same order, each
+// spread over the launch's CTAs, with a grid barrier where the multi-kernel
+// round has a kernel boundary.  The offset scans run on CTA 0 (the pools this
+// launch is for have few buckets and partitions), and the waves after the
+// first repeat register / decide until no switch is undecided.  The shared
+// memory holds the sort's arrays and, later, the grouping table.
+__global__ void __launch_bounds__(kFusedThreads, 1) k_round_fused(RoundArgs a) {
+  extern __shared__ __align__(128) uint4 fused_dyn[];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t gtid = blockIdx.x * blockDim.x + tid, nth = gridDim.x * blockDim.x;
+  Counters *const ctl = a.ctl;
+  // an earlier round of this call gave up at a barrier, which may have left
+  // the barrier's counter behind: run nothing (every CTA reads the same
+  // value, since no CTA can set the bit before all have passed the first
+  // barrier below)
+  if (*(volatile uint32_t *)&ctl->err & kErrGridSync) return;
+  clear_body(a);
+  for (uint32_t w = gtid; w <= (a.tfilter_mask >> 5); w += nth) a.tfilter[w] = 0;
+  if (!grid_sync(ctl)) return;
+  uint32_t wave = 2;
+  if (a.any_work) {
+    if (a.any_exact) {
+      lazy_count_body(a);
+      if (!grid_sync(ctl)) return;
+    }
+    permute_body(a);
+    if (!grid_sync(ctl)) return;
+    if (blockIdx.x == 0) {  // bucket offsets: full offsets in poff, zero block offsets
+      cta_scan_full(a.pcount, a.poff, nullptr, a.bucket_hw, (uint32_t)kPermBucketCap);
+      for (uint32_t j = tid; j <= (a.bucket_hw + 1023) / 1024; j += blockDim.x) a.pblk[j] = 0;
+    }
+    if (!grid_sync(ctl)) return;
+    {
+      unsigned char *base = reinterpret_cast<unsigned char *>(fused_dyn);
+      SortSmem sm;
+      sm.srec = reinterpret_cast<uint4 *>(base);
+      sm.sidx = reinterpret_cast<uint16_t *>(base + sizeof(uint4) * kPermBucketCap);
+      sm.hist = reinterpret_cast<uint32_t *>(base + (sizeof(uint4) + sizeof(uint16_t)) * kPermBucketCap);
+      sm.warp_tot = sm.hist + (1u << kSubBits);
+      sm.bar = reinterpret_cast<unsigned long long *>(sm.warp_tot + 32);
+      if (tid == 0) mbar_init(sm.bar, 1);
+      __syncthreads();
+      uint32_t parity = 0;
+      for (uint32_t b = blockIdx.x; b < a.bucket_hw; b += gridDim.x)
+        if (!sort_bucket<kFusedThreads>(a, b, sm, parity)) return;
+      __syncthreads();
+      if (tid == 0) mbar_inval(sm.bar);  // the grouping table takes these bytes next
+    }
+    if (!grid_sync(ctl)) return;
+    boundary_body(a);
+    if (!grid_sync(ctl)) return;
+    const uint32_t npair = a.slot_hw >> 1;
+    for (uint32_t base = blockIdx.x * 2 * blockDim.x; base < npair; base += 2 * nth) {
+      const uint32_t x = base + tid;
+      if (x < npair) source_pairs(a, x, x + blockDim.x, npair);
+    }
+    if (!grid_sync(ctl)) return;
+    if (*(volatile uint32_t *)&ctl->ovf_count) {
+      overflow_count_body(a);
+      if (!grid_sync(ctl)) return;
+      if (blockIdx.x == 0) {  // overflow offsets: full offsets in ooff, zero block offsets, the total last
+        const uint32_t tot = cta_scan_full(a.ocount, a.ooff, a.ocursor, a.part_hw, 0xFFFFFFFFu);
+        const uint32_t nblk = (a.part_hw + 1023) >> 10;
+        for (uint32_t j = tid; j < nblk; j += blockDim.x) a.oblk[j] = 0;
+        if (tid == 0) a.oblk[nblk] = tot;
+      }
+      if (!grid_sync(ctl)) return;
+      overflow_scatter_body(a);
+      if (!grid_sync(ctl)) return;
+    }
+    group_body(a);
+    if (!grid_sync(ctl)) return;
+    wave1_body(a);
+    if (!grid_sync(ctl)) return;
+    // waves 2, 3, ...: undecided switches re-register as inserters, then decide
+    Tally t;
+    ChainCount cc;
+    uint32_t cur = 0, prev_n = a.switch_hw + 1;
+    volatile uint32_t *pend = ctl->pending;
+    for (;;) {
+      const uint32_t n = pend[cur];  // the same for every thread: read after a barrier
+      if (n == 0) break;
+      if (wave > wave_cap(a)) {
+        if (gtid == 0) atomicOr(&ctl->err, kErrWaveCap);
+        break;
+      }
+      if (n >= prev_n) {  // no switch was decided in the last wave: impossible
+        if (gtid == 0) atomicOr(&ctl->err, kErrNoProgress);
+        break;
+      }
+      prev_n = n;
+      const uint32_t *in = cur ? a.list1 : a.list0;
+      uint32_t *out = cur ? a.list0 : a.list1;
+      for (uint32_t idx = gtid; idx < n; idx += nth) {
+        const uint32_t k = in[idx];
+        const uint2 sv = __ldcg(&a.sw[k]);
+        if (sv.x != kTrivial) atomicMin(&a.dep[sv.x].y, k);
+        if (sv.y != kTrivial) atomicMin(&a.dep[sv.y].y, k);
+      }
+      if (gtid == 0) {
+        pend[cur ^ 1] = 0;
+        if (wave < kWaveHist) a.st->last_pending[wave] = n;
+      }
+      if (!grid_sync(ctl)) return;
+      for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += nth) {
+        const uint32_t idx = base + tid;
+        bool wait = false;
+        uint32_t k = 0;
+        if (idx < n) {
+          k = in[idx];
+          const uint2 sv = __ldcg(&a.sw[k]);
+          const int r3 = check_target(a, k, sv.x, wave);
+          const int r4 = check_target(a, k, sv.y, wave);
+          if (r3 == kBad || r4 == kBad) {
+            a.status[k] = (wave << 2) | kIllegal;
+            drop_inserter(a, k, sv);
+            ++t.rej_exists;
+          } else if (r3 == kWait || r4 == kWait) {
+            wait = true;
+          } else {
+            a.status[k] = (wave << 2) | kLegal;
+            ++t.accepted;
+            count_accepted(a, cc, a.owner_switch[k]);
+          }
+        }
+        append_if(wait, k, out, (uint32_t *)&pend[cur ^ 1]);
+      }
+      if (!grid_sync(ctl)) return;
+      cur ^= 1;
+      ++wave;
+    }
+    flush_tally(a, t);
+    flush_count(a, cc);
+  }
+  if (gtid == 0) close_round(a, wave);
+}
+
 // ---------------------------------------------------------------- state in / out
 
 __global__ void k_load_chain(RoundArgs a, ChainDesc ch, const unsigned long long *E) {
@@ -1301,17 +1638,44 @@ inline int grid_for(unsigned long long work, int threads, int num_sms, int per_s
 
 size_t group_smem_bytes(uint32_t group_log2) { return (size_t)kGroupSlotBytes << group_log2; }
 
-cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, uint32_t *group_grid) {
+cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, LaunchShapes *shapes) {
   // opt in to the largest table any pool may use, so that pools with
   // different table sizes never lower each other's limit
   cudaError_t e = cudaFuncSetAttribute(k_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)group_smem_bytes(kMaxGroupLog2));
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group, kGroupThreads, group_smem_bytes(group_log2));
+  auto resident = [num_sms](const void *fn, int threads, size_t smem, uint32_t *grid) {
+    int per_sm = 0;
+    const cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    *grid = (uint32_t)(num_sms * (per_sm > 0 ? per_sm : 1));
+    return r;
+  };
+  e = resident((const void *)k_group, kGroupThreads, group_smem_bytes(group_log2), &shapes->group);
+  return e;
+}
+
+
+
+size_t fused_smem_bytes(uint32_t group_log2) {
+  return std::max(kSortSmemBytes, group_smem_bytes(group_log2));
+}
+
+cudaError_t prepare_fused(uint32_t group_log2, int num_sms, uint32_t *max_ctas) {
+  cudaError_t e = cudaFuncSetAttribute(k_round_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fused_smem_bytes(kMaxGroupLog2));
   if (e != cudaSuccess) return e;
-  *group_grid = (uint32_t)(num_sms * (per_sm > 0 ? per_sm : 1));
-  return cudaSuccess;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_round_fused, kFusedThreads,
+                                                    fused_smem_bytes(group_log2));
+  *max_ctas = (uint32_t)(num_sms * (per_sm > 0 ? per_sm : 0));
+  return e;
+}
+
+cudaError_t launch_round_fused(const RoundArgs &a, cudaStream_t s, uint32_t ctas) {
+  RoundArgs arg = a;
+  void *params[] = {&arg};
+  return cudaLaunchCooperativeKernel((const void *)k_round_fused, dim3(ctas), dim3(kFusedThreads), params,
+                                     fused_smem_bytes(a.group_log2), s);
 }
 
 cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEvent_t *ev, uint32_t *launches) {
@@ -1328,7 +1692,7 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   ++n;
   if (work && a.any_exact) { k_lazy_count<<<grid_for(a.switch_hw, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStagePermute);
-  if (work) { k_permute<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  if (work) { k_permute<<<a.permute_ctas, 256, 0, s>>>(a); ++n; }
   mark(kStageScanPerm);
   if (work) {
     k_scan_perm<<<a.bucket_hw ? (a.bucket_hw + 1023) / 1024 : 1, 1024, 0, s>>>(a);
@@ -1340,7 +1704,7 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   mark(kStageBoundary);
   if (work) { k_boundary<<<grid_for(a.bucket_hw, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
   mark(kStageSources);
-  if (work) { k_sources<<<grid_for((a.slot_hw + 1) / 2, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
+  if (work) { k_sources<<<a.sources_ctas, 256, 0, s>>>(a); ++n; }
   mark(kStageOverflow);
   if (work) {
     const int g = grid_for(a.ovf_cap, 256, num_sms, 2);

@@ -32,6 +32,7 @@ GESMC_E_CAPACITY = -10
 GESMC_E_TOO_LARGE = -11
 FLAG_NO_GRAPHS = 1
 FLAG_EXACT_ELL = 2
+FLAG_TINY_OVERFLOW = 4  # fault injection for tests (see include/gesmc.h)
 CHAIN_EXACT_ELL = 1
 NOALLOC_MAX_EDGES = 65536
 WAVE_HIST = 64
@@ -159,6 +160,9 @@ _SIGNATURES = [
     ("gesmc_pool_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(GesmcStats)]),
     ("gesmc_pool_reset_stats", ctypes.c_int, [ctypes.c_void_p]),
     ("gesmc_pool_set_profiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("gesmc_pool_set_round_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
+                                                   ctypes.POINTER(ctypes.c_uint32)]),
+    ("gesmc_set_round_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     ("gesmc_pool_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_uint64)]),
     # include/gesmc_microbench.h
@@ -239,7 +243,7 @@ def _as_edge_buffer(edges):
 
 def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 0, max_waves: int = 0, stream=None,
                  torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0, graphs: bool = True,
-                 exact_ell: bool = False):
+                 exact_ell: bool = False, tiny_overflow: bool = False):
     """Create a chain handle; returns (handle, keepalive).  Raises GesmcError."""
     import torch
 
@@ -254,7 +258,8 @@ def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 
     opts.max_waves = max_waves
     opts.tuple_log2 = tuple_log2
     opts.group_log2 = group_log2
-    opts.flags = (0 if graphs else FLAG_NO_GRAPHS) | (FLAG_EXACT_ELL if exact_ell else 0)
+    opts.flags = ((0 if graphs else FLAG_NO_GRAPHS) | (FLAG_EXACT_ELL if exact_ell else 0)
+                  | (FLAG_TINY_OVERFLOW if tiny_overflow else 0))
     if stream is None:
         stream = torch.cuda.current_stream()
     opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
@@ -410,6 +415,13 @@ class Chain:
     def set_profiling(self, enable: bool = True):
         gesmc_set_profiling(self._h, enable)
 
+    def set_round_launch(self, ctas: int) -> int:
+        """0: the round's kernels one after another; >= 1: the whole round in
+        one cooperative launch of that many CTAs.  Returns the count used."""
+        eff = ctypes.c_uint32()
+        _check(load_library().gesmc_set_round_launch(self._h, ctas, ctypes.byref(eff)), "gesmc_set_round_launch")
+        return int(eff.value)
+
     def stage_times(self) -> tuple[dict, int]:
         return gesmc_stage_times(self._h)
 
@@ -517,6 +529,14 @@ class Pool:
 
     def set_profiling(self, enable: bool = True):
         _check(load_library().gesmc_pool_set_profiling(self._p, int(enable)), "gesmc_pool_set_profiling")
+
+    def set_round_launch(self, ctas: int) -> int:
+        """0: the round's kernels one after another; >= 1: the whole round in
+        one cooperative launch of that many CTAs.  Returns the count used."""
+        eff = ctypes.c_uint32()
+        _check(load_library().gesmc_pool_set_round_launch(self._p, ctas, ctypes.byref(eff)),
+               "gesmc_pool_set_round_launch")
+        return int(eff.value)
 
     def stage_times(self) -> tuple[dict, int]:
         ms = (ctypes.c_double * NUM_STAGES)()
