@@ -417,6 +417,7 @@ def run_gesmc(args):
             create_ms.append(1e3 * (time.perf_counter() - t0))
     del d_edges
     chain = gesmc.Chain(edges, n=n, **layout)
+    round_ctas = chain.set_round_launch(tuning["round_ctas"]) if tuning and tuning.get("round_ctas") else 0
     # the first warm-up step (from round 0, chain seed 7) is checked against the sequential oracle
     parity, oracle_time = check_parity(chain, args.workload, edges, rounds, seed, rank)
     for _ in range(args.warmup - 1):
@@ -485,7 +486,8 @@ def run_gesmc(args):
                    "l2": ("L2 flushed between timed steps (%d MB written; device state %.2f GB)"
                           % (L2_FLUSH_BYTES >> 20, state_bytes / 1e9)) if flush_l2 else
                          "inputs larger than L2 (device state ~%.1f GB)" % (state_bytes / 1e9),
-                   "path": "captured CUDA graph of a round, replayed (the library's default)",
+                   "path": (f"one cooperative launch per round ({round_ctas} CTAs, the tuner's choice)" if round_ctas
+                            else "captured CUDA graph of a round, replayed (the library's default)"),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "parity": parity,
         "roofline": roofline,
@@ -550,6 +552,8 @@ def run_gesmc(args):
             with gesmc.Chain(host_in, n=n, **layout) as c:
                 torch.cuda.synchronize()
                 host_create.append(1e3 * (time.perf_counter() - t0))
+                if round_ctas:
+                    c.set_round_launch(round_ctas)
                 c.run(rounds, seed + 7)
                 c.edges(host_out)
             torch.cuda.synchronize()
@@ -832,6 +836,58 @@ def run_serve(args):
     return 0
 
 
+def run_round_latency(args):
+    """Time of one round of a small chain alone (G(2500, 8/(n-1)), about 1e4
+    edges), 200 rounds per step: the multi-kernel round (replayed graph)
+    against the one-launch round at several CTA counts, bit-exact against
+    each other and the oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2111_03005_gb300 import gesmc, inputs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = 2500
+    edges = inputs.gnp(n, 8.0 / (n - 1), 21)
+    rounds = 200
+    results, lists = {}, {}
+    want, _ = oracle.run(edges, seed=CHAIN_SEED, rounds=rounds)
+    for ctas in (0, 1, 4, 8, 16, 32, 64, 152):
+        with gesmc.Chain(edges, n=n) as c:
+            used = c.set_round_launch(ctas)
+            c.run(rounds, CHAIN_SEED)          # checked against the oracle
+            lists[ctas] = c.edges()
+            for _ in range(args.warmup - 1):
+                c.run(rounds, CHAIN_SEED)
+            torch.cuda.synchronize()
+            start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            for _ in range(args.steps):
+                c.run(rounds, CHAIN_SEED)
+            stop.record(stream)
+            torch.cuda.synchronize()
+            results[str(used)] = 1e3 * start.elapsed_time(stop) / (args.steps * rounds)
+    exact = all(np.array_equal(v, want) for v in lists.values())
+    if not exact:
+        raise SystemExit("parity FAILED: a round launch differs from the sequential oracle")
+    best = min(results, key=results.get)
+    line = {
+        "metric": "time of one global switch of a small chain alone on the GPU", "value": results[best],
+        "unit": "us per round", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": results[best] * rounds / 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"G(n={n}, p=8/(n-1)), seed 21, m={len(edges)}; {rounds} global switches per step"},
+        "us_per_round": {("multi-kernel (graph replay)" if k == "0" else f"one launch, {k} CTAs"): v
+                         for k, v in results.items()},
+        "best": "multi-kernel" if best == "0" else f"one launch, {best} CTAs",
+        "parity": {"checked": True, "rounds": rounds, "against": "the sequential oracle, every launch mode"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_es(args):
     """ParES (Algorithm 2): ES-MC switches with the sequential outcome, on one
     chain (one CTA) and on a pool of chains (one CTA each), next to the
@@ -912,7 +968,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gesmc", "reference"], default="gesmc")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "es"], default="gnp_2p24")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "es", "round_latency"],
+                    default="gnp_2p24")
     ap.add_argument("--chains", type=int, default=4096, help="ensemble: chains")
     ap.add_argument("--sample", type=int, default=256, help="ensemble: chains run one by one for comparison")
     ap.add_argument("--requests", type=int, default=128, help="serve: requests")
@@ -943,6 +1000,8 @@ def main(argv=None):
         return run_serve(args)
     if args.workload == "es":
         return run_es(args)
+    if args.workload == "round_latency":
+        return run_round_latency(args)
     return run_gesmc(args)
 
 

@@ -9,6 +9,12 @@ Two choices shape a round without changing its result:
   Together with ``tuple_log2`` it fixes the table's load factor, and with it
   the grouping kernel's occupancy (20 bytes of shared memory per slot).
 
+A third choice, for small problems only, is how a round is launched:
+``round_ctas`` = 0 runs the round's kernels one after another (replayed from
+a captured CUDA graph); ``round_ctas`` >= 1 runs the whole round in one
+cooperative launch of that many CTAs (the block-count axis), which saves the
+launch latency between stages that dominates the rounds of small graphs.
+
 Every chain's list after a round is the same under every setting (the
 partitioning only decides where a tuple is grouped, never what is decided).
 The tuner times a few rounds of the caller's own graphs (or a sample of
@@ -26,6 +32,9 @@ import tempfile
 import numpy as np
 
 CANDIDATES = ((9, 10), (9, 11), (10, 11), (10, 12), (11, 11), (11, 12))
+# one-launch round CTA counts tried for problems of at most LAUNCH_TUNE_MAX_EDGES edges
+LAUNCH_CANDIDATES = (0, 8, 16, 32, 64, 152)
+LAUNCH_TUNE_MAX_EDGES = 1 << 21
 
 
 def problem_key(device: str, total_edges: int, chains: int) -> str:
@@ -59,11 +68,12 @@ class TuneCache:
         v = self.data.get(key)
         if not v:
             return None
-        return int(v["tuple_log2"]), int(v["group_log2"])
+        return int(v["tuple_log2"]), int(v["group_log2"]), int(v.get("round_ctas", 0))
 
-    def put(self, key: str, best: tuple, timings: dict):
-        self.data[key] = {"tuple_log2": best[0], "group_log2": best[1],
-                          "timings_ms": {f"{t},{g}": ms for (t, g), ms in timings.items()}}
+    def put(self, key: str, best: tuple, timings: dict, round_ctas: int = 0, launch_timings: dict | None = None):
+        self.data[key] = {"tuple_log2": best[0], "group_log2": best[1], "round_ctas": round_ctas,
+                          "timings_ms": {f"{t},{g}": ms for (t, g), ms in timings.items()},
+                          "launch_timings_ms": {str(c): ms for c, ms in (launch_timings or {}).items()}}
         d = os.path.dirname(self.path)
         if d:
             os.makedirs(d, exist_ok=True)
@@ -82,16 +92,20 @@ def sample_graphs(graphs, seeds, max_chains: int, rng_seed: int = 0):
 
 
 def tune(graphs, seeds, rounds: int = 3, candidates=CANDIDATES, timer=None, cache: TuneCache | None = None,
-         device: str | None = None, problem: tuple | None = None, sample_chains: int = 512) -> dict:
+         device: str | None = None, problem: tuple | None = None, sample_chains: int = 512,
+         launch_candidates=LAUNCH_CANDIDATES) -> dict:
     """Choose (tuple_log2, group_log2) for running `graphs` (a list of
-    (edges, n)) with `seeds` in one pool.
+    (edges, n)) with `seeds` in one pool, and, for a problem of at most
+    LAUNCH_TUNE_MAX_EDGES edges, the round launch (round_ctas).
 
     timer(graphs, seeds, rounds, candidate) -> (milliseconds per round, the
-    first chain's list after the rounds); the default runs a pool on the
-    current CUDA device.  problem = (total edges, chains) names the problem
-    class for the cache (default: the graphs given); the timing itself uses
-    at most sample_chains of the graphs.  Returns a dict with the choice,
-    the timings and whether it came from the cache."""
+    first chain's list after the rounds); candidate is (tuple_log2,
+    group_log2) for the layout and (tuple_log2, group_log2, round_ctas) for
+    the launch.  The default runs a pool on the current CUDA device.
+    problem = (total edges, chains) names the problem class for the cache
+    (default: the graphs given); the timing itself uses at most
+    sample_chains of the graphs.  Returns a dict with the choice, the
+    timings and whether it came from the cache."""
     if timer is None:
         timer = gpu_timer
     if device is None:
@@ -101,7 +115,7 @@ def tune(graphs, seeds, rounds: int = 3, candidates=CANDIDATES, timer=None, cach
     if cache is not None:
         hit = cache.get(key)
         if hit is not None:
-            return {"tuple_log2": hit[0], "group_log2": hit[1], "cached": True, "key": key}
+            return {"tuple_log2": hit[0], "group_log2": hit[1], "round_ctas": hit[2], "cached": True, "key": key}
     g_sample, s_sample = sample_graphs(graphs, seeds, sample_chains)
     timings, first = {}, None
     for cand in candidates:
@@ -112,10 +126,21 @@ def tune(graphs, seeds, rounds: int = 3, candidates=CANDIDATES, timer=None, cach
             raise RuntimeError(f"tuning candidate {cand} changed the result of a round")
         timings[cand] = ms
     best = pick(timings)
+    # the round launch, with the chosen layout, for small problems only (one
+    # launch of at most a few hundred CTAs is too narrow for large graphs)
+    launch_timings, round_ctas = {}, 0
+    if total <= LAUNCH_TUNE_MAX_EDGES and launch_candidates:
+        for ctas in launch_candidates:
+            ms, out = timer(g_sample, s_sample, rounds, (best[0], best[1], ctas))
+            if not np.array_equal(first, out):
+                raise RuntimeError(f"round launch {ctas} changed the result of a round")
+            launch_timings[ctas] = ms
+        round_ctas = pick(launch_timings)
     if cache is not None:
-        cache.put(key, best, timings)
-    return {"tuple_log2": best[0], "group_log2": best[1], "cached": False, "key": key,
+        cache.put(key, best, timings, round_ctas, launch_timings)
+    return {"tuple_log2": best[0], "group_log2": best[1], "round_ctas": round_ctas, "cached": False, "key": key,
             "timings_ms_per_round": {f"{t},{g}": ms for (t, g), ms in timings.items()},
+            "launch_timings_ms_per_round": {str(c): ms for c, ms in launch_timings.items()},
             "sample_chains": len(g_sample)}
 
 
@@ -137,6 +162,8 @@ def gpu_timer(graphs, seeds, rounds: int, cand: tuple):
     with torch.cuda.stream(stream), gesmc.Pool(max_edges=total, max_chains=len(graphs), tuple_log2=cand[0],
                                                 group_log2=cand[1], stream=stream) as pool:
         ids = [pool.add(e, n=n, seed=s) for (e, n), s in zip(graphs, seeds)]
+        if len(cand) > 2:
+            pool.set_round_launch(cand[2])
         pool.run(1)
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         start.record(stream)

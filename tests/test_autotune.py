@@ -28,16 +28,16 @@ def test_tune_times_every_candidate_once_and_caches(tmp_path):
         return times[cand], np.array([1, 2, 3], dtype=np.uint64)
 
     cache = autotune.TuneCache(str(tmp_path / "tune.json"))
-    got = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=cache, device="dev")
+    got = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=cache, device="dev", launch_candidates=())
     assert (got["tuple_log2"], got["group_log2"]) == (10, 11) and not got["cached"]
     assert calls == list(autotune.CANDIDATES)
     # a second tuner over the same problem class reads the file and times nothing
     again = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=autotune.TuneCache(str(tmp_path / "tune.json")),
-                          device="dev")
+                          device="dev", launch_candidates=())
     assert again["cached"] and (again["tuple_log2"], again["group_log2"]) == (10, 11)
     assert len(calls) == len(autotune.CANDIDATES)
     # another device is another problem class
-    other = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=cache, device="other")
+    other = autotune.tune(graphs, seeds, rounds=2, timer=timer, cache=cache, device="other", launch_candidates=())
     assert not other["cached"]
 
 
@@ -48,7 +48,7 @@ def test_tune_rejects_a_candidate_that_changes_the_result():
         return 1.0, np.array([0 if cand == (10, 12) else 1], dtype=np.uint64)
 
     with pytest.raises(RuntimeError):
-        autotune.tune(graphs, seeds, timer=timer, cache=None, device="dev")
+        autotune.tune(graphs, seeds, timer=timer, cache=None, device="dev", launch_candidates=())
 
 
 def test_sample_keeps_order_and_pairs():
@@ -81,3 +81,27 @@ def test_ensemble_shards_cover_every_chain_once_and_balance_edges():
         assert max(loads) - sum(loads) / world <= max(sizes)
         assert ensemble.shard(sizes, world) == shards          # every rank computes the same split
     assert ensemble.shard([], 4) == [[], [], [], []]
+
+
+def test_launch_axis_is_tuned_for_small_problems_only(tmp_path):
+    graphs, seeds = fake_graphs(4)
+    calls = []
+
+    def timer(g, s, rounds, cand):
+        calls.append(cand)
+        ms = {(11, 11): 1.0}.get(cand[:2], 2.0)
+        if len(cand) == 3:
+            ms = {0: 1.0, 8: 0.4, 16: 0.3, 32: 0.35}.get(cand[2], 0.9)
+        return ms, np.array([7], dtype=np.uint64)
+
+    cache = autotune.TuneCache(str(tmp_path / "t.json"))
+    got = autotune.tune(graphs, seeds, timer=timer, cache=cache, device="dev", launch_candidates=(0, 8, 16, 32))
+    assert (got["tuple_log2"], got["group_log2"], got["round_ctas"]) == (11, 11, 16)
+    assert [c for c in calls if len(c) == 3] == [(11, 11, c) for c in (0, 8, 16, 32)]
+    hit = autotune.tune(graphs, seeds, timer=timer, cache=autotune.TuneCache(str(tmp_path / "t.json")), device="dev")
+    assert hit["cached"] and hit["round_ctas"] == 16
+    # a large problem keeps the multi-kernel round and times no launch candidate
+    calls.clear()
+    big = autotune.tune(graphs, seeds, timer=timer, cache=None, device="dev", problem=(1 << 24, 1),
+                        launch_candidates=(0, 8))
+    assert big["round_ctas"] == 0 and all(len(c) == 2 for c in calls)
