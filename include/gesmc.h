@@ -55,7 +55,9 @@ enum {
   GESMC_E_WAVE_CAP = -8,   /* a round needed more waves than opts.max_waves  */
   GESMC_E_INTERNAL = -9,   /* bucket overflow or stalled waves (not expected) */
   GESMC_E_CAPACITY = -10,  /* caller's output buffer too small               */
-  GESMC_E_TOO_LARGE = -11  /* m above GESMC_NOALLOC_MAX_EDGES (no-alloc call) */
+  GESMC_E_TOO_LARGE = -11, /* m above GESMC_NOALLOC_MAX_EDGES (no-alloc call) */
+  GESMC_E_INVARIANT = -12  /* a checked list is not a simple graph with the
+                              starting degree sequence (gesmc_verify)        */
 };
 
 /* Rounds are replayed from a captured CUDA graph of one round (launched on
@@ -77,6 +79,9 @@ enum {
  * GESMC_E_INTERNAL and leaves the handle in the error state described above.
  * Not for production use. */
 #define GESMC_FLAG_TINY_OVERFLOW 4u
+/* Debugging: check the invariants of gesmc_verify on the device after every
+ * round of gesmc_run (rounds then run one call at a time). */
+#define GESMC_FLAG_VERIFY_ROUNDS 8u
 
 /* Device allocation hooks: alloc returns device memory usable on `stream`
  * (or NULL on failure); free releases it.  Both NULL: cudaMalloc/cudaFree. */
@@ -196,6 +201,21 @@ const char *gesmc_stage_name(int stage);
  * device cannot hold one CTA of the one-launch round.  Stage timing
  * (gesmc_set_profiling) always uses the separate kernels. */
 int gesmc_set_round_launch(gesmc_t h, uint32_t ctas, uint32_t *effective);
+
+/* Debug check, on the device, of what every round keeps (Sec. 2.1; Def. 1):
+ * the handle's list is canonical, loop-free, has ids < n, repeats no edge
+ * (so no edge id got two legal inserters in one round, Obs. 2), and has the
+ * degree sequence it was created with.  Degrees are compared through a
+ * 64-bit fingerprint of the multiset of endpoints (the sum over edges of a
+ * fixed hash of each endpoint, mod 2^64), taken when the chain was created.
+ * Returns GESMC_OK or GESMC_E_INVARIANT. */
+int gesmc_verify(gesmc_t h);
+/* The same check on a caller's list: `edges` (m ids, device memory) against
+ * the degree sequence of `reference` (ref_m ids, device memory, e.g. the
+ * starting list), ids < n if n != 0.  Allocates its scratch memory (a
+ * debugging aid).  GESMC_OK, GESMC_E_INVARIANT, GESMC_E_NOMEM or
+ * GESMC_E_INVALID. */
+int gesmc_verify_list(const uint64_t *edges, uint64_t m, const uint64_t *reference, uint64_t ref_m, uint64_t n);
 
 /* Number of the next round the handle will run (start_round + rounds run). */
 uint64_t gesmc_next_round(gesmc_t h);
@@ -320,6 +340,8 @@ int gesmc_pool_edges(gesmc_pool_t p, uint32_t chain, uint64_t *out, uint64_t cap
 int gesmc_pool_chain_info(gesmc_pool_t p, uint32_t chain, gesmc_chain_info_t *out);
 uint32_t gesmc_pool_num_chains(gesmc_pool_t p);
 uint64_t gesmc_pool_free_edges(gesmc_pool_t p);
+/* Debug check of one chain of the pool, as gesmc_verify. */
+int gesmc_pool_verify(gesmc_pool_t p, uint32_t chain);
 /* Round launch of the pool, as gesmc_set_round_launch. */
 int gesmc_pool_set_round_launch(gesmc_pool_t p, uint32_t ctas, uint32_t *effective);
 /* Counters over all chains, stage timing: as for single chains. */

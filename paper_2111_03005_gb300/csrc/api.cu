@@ -242,6 +242,7 @@ struct HostChain {
   ChainShape shape;
   uint64_t n = 0;
   uint64_t es_next = 0;  // ES-MC switches run (numbering of the next one)
+  unsigned long long fp = 0;  // degree fingerprint of the starting list (gesmc_verify)
 };
 
 int map_device_errors(uint32_t err) {
@@ -290,6 +291,7 @@ struct gesmc_pool_ctx {
   // a round one after another (replayed from the captured graph)
   uint32_t fused_ctas = 0;
   uint32_t fused_max = 0;  // CTAs of the one-launch round the device holds at once
+  bool verify_rounds = false;  // GESMC_FLAG_VERIFY_ROUNDS
   int profiling = 0;
   std::vector<cudaEvent_t> events;
   double stage_ms[kNumStages] = {};
@@ -352,6 +354,10 @@ void refresh_args(gesmc_pool_t p) {
   a.permute_ctas = std::max<uint32_t>(1, (npair + 255) / 256);
   a.sources_ctas = std::max<uint32_t>(1, (npair + 511) / 512);
   const bool spread = p->live_chains > 1;
+  uint32_t most_buckets = 0;
+  for (const HostChain &hc : p->chains)
+    if (hc.live) most_buckets = std::max(most_buckets, hc.shape.nb);
+  a.fused_local_offsets = most_buckets <= kLocalOffsetBuckets ? 1u : 0u;
   a.permute_stride = spread ? coprime_stride(a.permute_ctas) : 1;
   a.sources_stride = spread ? coprime_stride(a.sources_ctas) : 1;
 }
@@ -492,6 +498,47 @@ int validate_list(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t n_
   return GESMC_OK;
 }
 
+// Debug check of a device list: invariant flags (loop / not canonical,
+// range, repeated edge) and the degree fingerprint.  set: scratch of `cap`
+// u64 slots (cap >= 2m); words: 4 device words of scratch.  Synchronises s.
+int list_check(const unsigned long long *E, uint64_t m, uint64_t n, unsigned long long *set, uint64_t cap,
+               uint32_t *words, cudaStream_t s, int num_sms, uint32_t *flags_out, unsigned long long *fp_out) {
+  unsigned long long *fp = reinterpret_cast<unsigned long long *>(words + 2);
+  uint32_t host[4] = {0, 0, 0, 0};
+  bool ok = cudaMemsetAsync(words, 0, 16, s) == cudaSuccess;
+  ok &= launch_list_check(E, (uint32_t)m, n, words, fp, s, num_sms) == cudaSuccess;
+  if (m > 0 && set) ok &= launch_duplicate_check(E, (uint32_t)m, set, cap, words, s, num_sms) == cudaSuccess;
+  ok &= cudaMemcpyAsync(host, words, 16, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  *flags_out = host[0];
+  std::memcpy(fp_out, host + 2, 8);
+  return GESMC_OK;
+}
+
+// The chain's list by position (into the pool's staging buffer) against its
+// invariants and its starting degree fingerprint.
+int verify_chain(gesmc_pool_t p, uint32_t chain) {
+  const HostChain &hc = p->chains[chain];
+  const uint64_t m = hc.shape.m;
+  unsigned long long *E = at<unsigned long long>(p->base, p->lay.E);
+  uint32_t *words = at<uint32_t>(p->base, p->lay.scratch) + 4;
+  if (m > 0 && launch_store_chain(p->args, hc.d, E, p->stream, p->num_sms) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  uint32_t flags = 0;
+  unsigned long long fp = 0;
+  // between rounds the overflow-tuple array is free: it holds the set
+  const int rc = list_check(E, m, hc.n, reinterpret_cast<unsigned long long *>(p->args.otup), 2 * p->cap.ovf, words,
+                            p->stream, p->num_sms, &flags, &fp);
+  if (rc != GESMC_OK) return rc;
+  return flags == 0 && fp == hc.fp ? GESMC_OK : GESMC_E_INVARIANT;
+}
+
 void release_ranges(gesmc_pool_t p, const HostChain &hc) {
   p->slots.release(hc.d.slot_base, hc.shape.slots());
   p->switches.release(hc.d.switch_base, hc.shape.L);
@@ -578,6 +625,12 @@ int pool_add_device(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t 
   uint64_t n_eff = 0;
   int rc = validate_list(p, E, m, n, &n_eff);
   if (rc != GESMC_OK) return rc;
+  {  // the starting list's degree fingerprint (gesmc_verify compares against it)
+    uint32_t flags = 0;
+    rc = list_check(E, m, 0, nullptr, 0, at<uint32_t>(p->base, p->lay.scratch) + 4, p->stream, p->num_sms, &flags,
+                    &hc.fp);
+    if (rc != GESMC_OK) return rc;
+  }
   if (!alloc_ranges(p, hc)) return GESMC_E_NOMEM;
   ChainDesc &d = hc.d;
   d.m = hc.shape.m;
@@ -892,6 +945,7 @@ int gesmc_pool_create(const gesmc_pool_opts *opts, gesmc_pool_t *out) {
   p->max_chains = o.max_chains;
   p->tuple_log2 = o.tuple_log2 ? o.tuple_log2 : kDefaultTupleLog2;
   p->use_graphs = !(o.flags & GESMC_FLAG_NO_GRAPHS);
+  p->verify_rounds = (o.flags & GESMC_FLAG_VERIFY_ROUNDS) != 0;
   p->cap = pool_capacity(p->max_edges, p->max_chains, p->tuple_log2);
   if (!capacity_fits(p->cap)) {
     delete p;
@@ -957,13 +1011,69 @@ int gesmc_pool_remove(gesmc_pool_t p, uint32_t chain) {
 
 int gesmc_pool_run(gesmc_pool_t p, uint64_t global_switches) {
   if (!p) return GESMC_E_INVALID;
-  return pool_run(p, global_switches);
+  if (!p->verify_rounds) return pool_run(p, global_switches);
+  // debugging: one round at a time, every chain checked after each
+  DeviceGuard g(p->device);
+  for (uint64_t r = 0; r < global_switches; ++r) {
+    int rc = pool_run(p, 1);
+    for (uint32_t c = 0; rc == GESMC_OK && c < p->max_chains; ++c)
+      if (p->chains[c].live) rc = verify_chain(p, c);
+    if (rc != GESMC_OK) {
+      if (!p->broken) p->broken = rc;
+      return rc;
+    }
+  }
+  return GESMC_OK;
+}
+
+int gesmc_pool_verify(gesmc_pool_t p, uint32_t chain) {
+  if (!p || chain >= p->max_chains || !p->chains[chain].live) return GESMC_E_INVALID;
+  DeviceGuard g(p->device);
+  return verify_chain(p, chain);
+}
+
+int gesmc_verify_list(const uint64_t *edges, uint64_t m, const uint64_t *reference, uint64_t ref_m, uint64_t n) {
+  if ((m && !edges) || (ref_m && !reference) || m > kMaxEdges || ref_m > kMaxEdges) return GESMC_E_INVALID;
+  if (m != ref_m) return GESMC_E_INVARIANT;
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_CUDA;
+  }
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t cap = 2 * m + 16;
+  void *scratch = nullptr;
+  if (cudaMalloc(&scratch, 8 * cap + 64) != cudaSuccess) {
+    cudaGetLastError();
+    return GESMC_E_NOMEM;
+  }
+  uint32_t *words = reinterpret_cast<uint32_t *>(static_cast<char *>(scratch) + 8 * cap);
+  uint32_t fa = 0, fb = 0;
+  unsigned long long pa = 0, pb = 0;
+  int rc = list_check(reinterpret_cast<const unsigned long long *>(edges), m, n,
+                      static_cast<unsigned long long *>(scratch), cap, words, nullptr, sms, &fa, &pa);
+  if (rc == GESMC_OK)
+    rc = list_check(reinterpret_cast<const unsigned long long *>(reference), ref_m, 0, nullptr, 0, words, nullptr, sms,
+                    &fb, &pb);
+  cudaFree(scratch);
+  if (rc != GESMC_OK) return rc;
+  return fa == 0 && pa == pb ? GESMC_OK : GESMC_E_INVARIANT;
 }
 
 int gesmc_pool_set_round_launch(gesmc_pool_t p, uint32_t ctas, uint32_t *effective) {
   if (!p) return GESMC_E_INVALID;
   if (ctas && p->fused_max == 0) return GESMC_E_INVALID;
-  p->fused_ctas = std::min(ctas, p->fused_max);
+  const uint32_t want = std::min(ctas, p->fused_max);
+  if (want != p->fused_ctas) {
+    // the grid barrier's count restarts with the new CTA count
+    DeviceGuard g(p->device);
+    if (cudaMemsetAsync(&p->args.ctl->gbar_arrived, 0, sizeof(unsigned long long), p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return GESMC_E_CUDA;
+    }
+  }
+  p->fused_ctas = want;
   if (effective) *effective = p->fused_ctas;
   return GESMC_OK;
 }
@@ -1102,6 +1212,7 @@ const char *gesmc_strerror(int code) {
     case GESMC_E_INTERNAL: return "internal error (bucket overflow or stalled waves)";
     case GESMC_E_CAPACITY: return "output buffer too small";
     case GESMC_E_TOO_LARGE: return "edge list larger than the no-alloc scratch allows (GESMC_NOALLOC_MAX_EDGES)";
+    case GESMC_E_INVARIANT: return "the list is not a simple graph with the starting degree sequence";
     default: return "unknown error";
   }
 }
@@ -1126,7 +1237,7 @@ int gesmc_create(const uint64_t *edges, uint64_t m, int edges_on_device, const g
   po.max_waves = o.max_waves;
   po.tuple_log2 = o.tuple_log2;
   po.group_log2 = o.group_log2;
-  po.flags = o.flags & (GESMC_FLAG_NO_GRAPHS | GESMC_FLAG_TINY_OVERFLOW);
+  po.flags = o.flags & (GESMC_FLAG_NO_GRAPHS | GESMC_FLAG_TINY_OVERFLOW | GESMC_FLAG_VERIFY_ROUNDS);
   po.stream = o.stream;
   po.alloc = o.alloc;
   po.free = o.free;
@@ -1163,7 +1274,7 @@ int gesmc_run(gesmc_t h, uint64_t global_switches, uint64_t seed) {
       return GESMC_E_CUDA;
     }
   }
-  return pool_run(p, global_switches);
+  return gesmc_pool_run(p, global_switches);
 }
 
 int gesmc_es_run(gesmc_t h, uint64_t switches, uint64_t seed) {
@@ -1195,6 +1306,7 @@ int gesmc_reset_stats(gesmc_t h) { return h ? gesmc_pool_reset_stats(h->pool) : 
 int gesmc_set_profiling(gesmc_t h, int enable) {
   return h ? gesmc_pool_set_profiling(h->pool, enable) : GESMC_E_INVALID;
 }
+int gesmc_verify(gesmc_t h) { return h ? gesmc_pool_verify(h->pool, h->chain) : GESMC_E_INVALID; }
 int gesmc_set_round_launch(gesmc_t h, uint32_t ctas, uint32_t *effective) {
   return h ? gesmc_pool_set_round_launch(h->pool, ctas, effective) : GESMC_E_INVALID;
 }

@@ -112,6 +112,12 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
       : "memory");
 }
 
+// Bulk prefetch of `bytes` of global memory into L2 (no destination, no
+// completion to wait for); 16-byte aligned address, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Wait for phase `parity` of the barrier to complete, at most `limit` polls;
 // false if it did not (the caller reports an error instead of spinning on).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, uint32_t limit) {

@@ -159,8 +159,10 @@ struct Counters {
   unsigned long long pool_round;  // rounds the pool has completed
   uint32_t es_stopped;  // ParES jobs stopped for a rebuild of their edge set (per launch)
   uint32_t gbar_pad[19];  // the grid barrier below on an L2 line of its own
-  uint32_t gbar_count;    // CTAs of the one-launch round arrived at its barrier
-  uint32_t gbar_gen;      // barrier generation (bumped by the last CTA to arrive)
+  // arrivals at the one-launch round's grid barriers, never reset between
+  // launches of the same CTA count (each launch leaves it at a multiple of
+  // its CTA count; the host zeroes it when the count changes)
+  unsigned long long gbar_arrived;
 };
 
 // Device-resident statistics, accumulated over rounds (all chains).
@@ -218,7 +220,12 @@ struct RoundArgs {
   // coprime with the CTA count), so that the CTAs resident at once are spread
   // over all chains of a pool instead of a few neighbouring ones
   uint32_t permute_ctas, permute_stride, sources_ctas, sources_stride;
+  // the one-launch round sums each bucket's chain-local offset itself (every
+  // chain has at most kLocalOffsetBuckets buckets) instead of a scan stage
+  uint32_t fused_local_offsets;
 };
+
+constexpr uint32_t kLocalOffsetBuckets = 4096;
 
 // Resident CTAs of the persistent and grid-stride round kernels on a device.
 struct LaunchShapes {
@@ -271,6 +278,11 @@ cudaError_t launch_store_chain(const RoundArgs &a, const ChainDesc &ch, unsigned
 cudaError_t launch_fill_u32(uint32_t *p, uint32_t n, uint32_t v, cudaStream_t s, int num_sms);
 cudaError_t launch_canonicalise(unsigned long long *E, uint32_t m, unsigned long long n_bound, uint32_t *flags,
                                 uint32_t *max_id, cudaStream_t s, int num_sms);
+// Debug check of a list: kFlagLoop for an entry that is not canonical and
+// loop-free, kFlagRange for an id >= n (if n), and its degree fingerprint
+// added to *fp (zero it first).
+cudaError_t launch_list_check(const unsigned long long *E, uint32_t m, unsigned long long n, uint32_t *flags,
+                              unsigned long long *fp, cudaStream_t s, int num_sms);
 // Repeated edges, with an open-addressing set of `cap` u64 slots as scratch.
 cudaError_t launch_duplicate_check(const unsigned long long *E, uint32_t m, unsigned long long *set,
                                    unsigned long long cap, uint32_t *flags, cudaStream_t s, int num_sms);

@@ -576,6 +576,21 @@ __device__ __forceinline__ void cta_exclusive_scan(uint32_t *h, uint32_t *warp_t
   }
 }
 
+// Sum of v over the CTA's kThreads threads, returned to every thread
+// (warp_tot: kThreads / 32 words of scratch).  Every thread calls it.
+template <int kThreads>
+__device__ __forceinline__ uint32_t cta_sum(uint32_t v, uint32_t *warp_tot) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = v;
+  __syncthreads();
+  uint32_t total = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) total += warp_tot[w];
+  __syncthreads();
+  return total;
+}
+
 __device__ __forceinline__ bool full_key_less(unsigned long long seed, unsigned long long round, uint32_t i,
                                               uint32_t j) {
   const unsigned long long ki = perm_key(seed, round, i), kj = perm_key(seed, round, j);
@@ -607,7 +622,8 @@ constexpr size_t kSortSmemBytes = sizeof(uint4) * kPermBucketCap + sizeof(uint16
 // the caller must stop then.  Every thread of the CTA calls it; `parity`
 // tracks the barrier's phase across the buckets a CTA sorts.
 template <int kThreads>
-__device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, const SortSmem &sm, uint32_t &parity) {
+__device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, const SortSmem &sm, uint32_t &parity,
+                                            bool local_offsets = false) {
   uint4 *const srec = sm.srec;
   uint16_t *const sidx = sm.sidx;
   uint32_t *const hist = sm.hist;
@@ -625,7 +641,16 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
   const ChainDesc ch = a.chains[c];
   const unsigned long long round = chain_round(ch, R);
   const uint32_t ell = ch.exact_ell ? a.chain_ell[c] : 0u;
-  const uint32_t loff = bucket_offset(a, b) - bucket_offset(a, ch.bucket_base);  // chain-local slot offset
+  // chain-local slot offset: from the scanned offsets, or summed here over
+  // the chain's earlier buckets (a small chain in the one-launch round)
+  uint32_t loff;
+  if (local_offsets) {
+    uint32_t sum = 0;
+    for (uint32_t j = ch.bucket_base + tid; j < b; j += kThreads) sum += min(a.pcount[j], (uint32_t)kPermBucketCap);
+    loff = cta_sum<kThreads>(sum, sm.warp_tot);
+  } else {
+    loff = bucket_offset(a, b) - bucket_offset(a, ch.bucket_base);
+  }
   const uint32_t goff = ch.slot_base + loff;
   __syncthreads();  // the histogram is cleared
   const bool landed = cnt == 0 || mbar_wait(sm.bar, parity, kCopyWaitPolls);
@@ -679,12 +704,10 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
     }
   }
   __syncthreads();
-  // slots of the bucket hold pi in order: write the list in slot order
-  for (uint32_t t = tid; t < cnt; t += kThreads) {
-    const uint4 r = srec[sidx[t]];
-    a.cpos[goff + t] = r.y;
-    a.cedge[goff + t] = ((unsigned long long)r.w << 32) | r.z;
-  }
+  // slots of the bucket hold pi in order: write the list in slot order, a
+  // pair of slots (a switch) per thread, and build the switch; a pair's first
+  // slot is even in the pool (chains start on even slots), so both slots go
+  // out in one 8-byte and one 16-byte store
   const uint32_t t0 = loff & 1u;
   const uint32_t npairs = cnt > t0 ? (cnt - t0) >> 1 : 0;
   for (uint32_t p = tid; p < npairs; p += kThreads) {
@@ -694,7 +717,20 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
     const uint32_t k[1] = {(loff + t) >> 1}, i[1] = {r1.y}, j[1] = {r2.y};
     const unsigned long long e1[1] = {((unsigned long long)r1.w << 32) | r1.z};
     const unsigned long long e2[1] = {((unsigned long long)r2.w << 32) | r2.z};
+    *reinterpret_cast<uint2 *>(&a.cpos[goff + t]) = make_uint2(r1.y, r2.y);
+    *reinterpret_cast<ulonglong2 *>(&a.cedge[goff + t]) = make_ulonglong2(e1[0], e2[0]);
     build_switches<1>(a, ch, round, ell, valid, k, i, e1, j, e2);
+  }
+  // the slots in no pair of this bucket: the first (its pair started in the
+  // bucket before) and the last (its pair ends in the next bucket, or m is odd)
+  if (tid < 2 && cnt > 0) {
+    const uint32_t t = tid == 0 ? 0u : cnt - 1;
+    const bool alone = tid == 0 ? t0 == 1 : ((cnt - t0) & 1u) && cnt - 1 >= t0 && !(t0 == 1 && cnt == 1);
+    if (alone) {
+      const uint4 r = srec[sidx[t]];
+      a.cpos[goff + t] = r.y;
+      a.cedge[goff + t] = ((unsigned long long)r.w << 32) | r.z;
+    }
   }
   if (tid == 0 && t0 == 1 && cnt > 0) {
     // this bucket's first slot is the second of a pair started in an
@@ -963,6 +999,18 @@ constexpr int kGroupR = 4;  // tuples a thread holds in registers on the fast pa
 // claimed.  Partitions with more tuples than fit, or more distinct ids than
 // slots, take the sub-pass path: the ids whose hash bits 16.. select them,
 // split further until each sub-pass fits.
+// Bring the own tuples of partition `part` (if it exists and is owned) into
+// L2 with one bulk prefetch (the TMA engine), so that the CTA finds them
+// there when it gets to that partition.
+__device__ __forceinline__ void prefetch_partition(const RoundArgs &a, uint32_t part) {
+  if (part >= a.part_hw) return;
+  const uint32_t c = a.owner_part[part];
+  if (c == kNoChain) return;
+  const ChainDesc &cd = a.chains[c];
+  const uint32_t n = min(a.tcount[cd.tcount_base + (part - cd.part_base) * cd.tstride], cd.capt);
+  if (n) bulk_prefetch_l2(a.ptup + cd.tuple_base + (size_t)(part - cd.part_base) * cd.capt, n * (uint32_t)sizeof(uint4));
+}
+
 __device__ __forceinline__ void group_body(const RoundArgs &a) {
   const uint32_t S = 1u << a.group_log2;
   const GroupSmem g = group_smem(S);
@@ -977,6 +1025,7 @@ __device__ __forceinline__ void group_body(const RoundArgs &a) {
   for (uint32_t part = blockIdx.x; part < a.part_hw; part += gridDim.x) {
     const uint32_t c = a.owner_part[part];
     if (c == kNoChain) continue;
+    if (tid == 0) prefetch_partition(a, part + gridDim.x);
     const uint32_t pbase = a.chains[c].part_base, tbase = a.chains[c].tuple_base, capt = a.chains[c].capt;
     // the partition's tuples: its own region, then its overflow tuples
     const uint4 *prim = a.ptup + tbase + (size_t)(part - pbase) * capt;
@@ -1283,37 +1332,32 @@ __global__ void __launch_bounds__(1024) k_tail(RoundArgs a) {
 
 // ---------------------------------------------------------------- one-launch round
 
-// Grid-wide barrier of a cooperative launch (every CTA resident): each CTA
-// arrives on a counter; the last to arrive resets it and bumps the
-// generation the others wait on, and the fences on both sides make every
-// write before the barrier visible after it.  The wait is bounded
-// (kGridWaitPolls): a CTA that gives up sets kErrGridSync and returns false,
-// and its caller leaves the kernel; the other CTAs see the error bit at their
-// next wait and leave too, so the launch ends with the error reported.
-__device__ __forceinline__ bool grid_sync(Counters *ctl) {
+// Grid-wide barrier of a cooperative launch (every CTA resident).  Arrivals
+// are counted on one monotonic counter: the CTA's thread 0 adds one with
+// release-acquire semantics and polls (acquire) until every CTA has arrived
+// at this barrier, i.e. the count has reached `target`, which every thread
+// advances by the CTA count per barrier.  With the CTA barriers on both
+// sides, every write before the barrier is visible after it.  The wait is
+// bounded (kGridWaitPolls): a CTA that gives up sets kErrGridSync and
+// returns false, and its caller leaves the kernel; the other CTAs see the
+// error bit while they wait and leave too.
+__device__ __forceinline__ bool grid_sync(Counters *ctl, unsigned long long &target) {
   __shared__ uint32_t ok;
+  target += gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile uint32_t *gen = &ctl->gbar_gen;
-    const uint32_t g = *gen;
-    __threadfence();
-    if (atomicAdd(&ctl->gbar_count, 1u) == gridDim.x - 1) {
-      ctl->gbar_count = 0;
-      __threadfence();
-      atomicAdd(&ctl->gbar_gen, 1u);
-      ok = 1;
-    } else {
-      volatile uint32_t *err = &ctl->err;
-      uint32_t it = 0;
-      // a CTA that gave up at an earlier barrier never arrives: stop then too
-      while (*gen == g && it < kGridWaitPolls && !(*err & kErrGridSync)) {
-        __nanosleep(64);
-        ++it;
-      }
-      ok = *gen != g;
-      if (!ok) atomicOr(&ctl->err, kErrGridSync);
+    unsigned long long v;
+    asm volatile("atom.add.acq_rel.gpu.u64 %0, [%1], 1;" : "=l"(v) : "l"(&ctl->gbar_arrived) : "memory");
+    ++v;
+    uint32_t it = 0;
+    while (v < target && it < kGridWaitPolls) {
+      if (*(volatile uint32_t *)&ctl->err & kErrGridSync) break;
+      __nanosleep(20);
+      asm volatile("ld.acquire.gpu.u64 %0, [%1];" : "=l"(v) : "l"(&ctl->gbar_arrived) : "memory");
+      ++it;
     }
-    __threadfence();
+    ok = v >= target;
+    if (!ok) atomicOr(&ctl->err, kErrGridSync);
   }
   __syncthreads();
   return ok != 0;
@@ -1395,22 +1439,34 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_round_fused(RoundArgs a) {
   // value, since no CTA can set the bit before all have passed the first
   // barrier below)
   if (*(volatile uint32_t *)&ctl->err & kErrGridSync) return;
+  // the barrier count this launch starts from: earlier launches (all of this
+  // CTA count) left it at a multiple of the CTA count, and fewer than that
+  // many arrivals of this launch can precede this read
+  __shared__ unsigned long long start_count;
+  if (tid == 0) {
+    const unsigned long long v = *(volatile unsigned long long *)&ctl->gbar_arrived;
+    start_count = v / gridDim.x * gridDim.x;
+  }
+  __syncthreads();
+  unsigned long long target = start_count;
   clear_body(a);
   for (uint32_t w = gtid; w <= (a.tfilter_mask >> 5); w += nth) a.tfilter[w] = 0;
-  if (!grid_sync(ctl)) return;
+  if (!grid_sync(ctl, target)) return;
   uint32_t wave = 2;
   if (a.any_work) {
     if (a.any_exact) {
       lazy_count_body(a);
-      if (!grid_sync(ctl)) return;
+      if (!grid_sync(ctl, target)) return;
     }
     permute_body(a);
-    if (!grid_sync(ctl)) return;
-    if (blockIdx.x == 0) {  // bucket offsets: full offsets in poff, zero block offsets
-      cta_scan_full(a.pcount, a.poff, nullptr, a.bucket_hw, (uint32_t)kPermBucketCap);
-      for (uint32_t j = tid; j <= (a.bucket_hw + 1023) / 1024; j += blockDim.x) a.pblk[j] = 0;
+    if (!grid_sync(ctl, target)) return;
+    if (!a.fused_local_offsets) {
+      if (blockIdx.x == 0) {  // bucket offsets: full offsets in poff, zero block offsets
+        cta_scan_full(a.pcount, a.poff, nullptr, a.bucket_hw, (uint32_t)kPermBucketCap);
+        for (uint32_t j = tid; j <= (a.bucket_hw + 1023) / 1024; j += blockDim.x) a.pblk[j] = 0;
+      }
+      if (!grid_sync(ctl, target)) return;
     }
-    if (!grid_sync(ctl)) return;
     {
       unsigned char *base = reinterpret_cast<unsigned char *>(fused_dyn);
       SortSmem sm;
@@ -1423,36 +1479,36 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_round_fused(RoundArgs a) {
       __syncthreads();
       uint32_t parity = 0;
       for (uint32_t b = blockIdx.x; b < a.bucket_hw; b += gridDim.x)
-        if (!sort_bucket<kFusedThreads>(a, b, sm, parity)) return;
+        if (!sort_bucket<kFusedThreads>(a, b, sm, parity, a.fused_local_offsets != 0)) return;
       __syncthreads();
       if (tid == 0) mbar_inval(sm.bar);  // the grouping table takes these bytes next
     }
-    if (!grid_sync(ctl)) return;
+    if (!grid_sync(ctl, target)) return;
     boundary_body(a);
-    if (!grid_sync(ctl)) return;
+    if (!grid_sync(ctl, target)) return;
     const uint32_t npair = a.slot_hw >> 1;
     for (uint32_t base = blockIdx.x * 2 * blockDim.x; base < npair; base += 2 * nth) {
       const uint32_t x = base + tid;
       if (x < npair) source_pairs(a, x, x + blockDim.x, npair);
     }
-    if (!grid_sync(ctl)) return;
+    if (!grid_sync(ctl, target)) return;
     if (*(volatile uint32_t *)&ctl->ovf_count) {
       overflow_count_body(a);
-      if (!grid_sync(ctl)) return;
+      if (!grid_sync(ctl, target)) return;
       if (blockIdx.x == 0) {  // overflow offsets: full offsets in ooff, zero block offsets, the total last
         const uint32_t tot = cta_scan_full(a.ocount, a.ooff, a.ocursor, a.part_hw, 0xFFFFFFFFu);
         const uint32_t nblk = (a.part_hw + 1023) >> 10;
         for (uint32_t j = tid; j < nblk; j += blockDim.x) a.oblk[j] = 0;
         if (tid == 0) a.oblk[nblk] = tot;
       }
-      if (!grid_sync(ctl)) return;
+      if (!grid_sync(ctl, target)) return;
       overflow_scatter_body(a);
-      if (!grid_sync(ctl)) return;
+      if (!grid_sync(ctl, target)) return;
     }
     group_body(a);
-    if (!grid_sync(ctl)) return;
+    if (!grid_sync(ctl, target)) return;
     wave1_body(a);
-    if (!grid_sync(ctl)) return;
+    if (!grid_sync(ctl, target)) return;
     // waves 2, 3, ...: undecided switches re-register as inserters, then decide
     Tally t;
     ChainCount cc;
@@ -1482,7 +1538,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_round_fused(RoundArgs a) {
         pend[cur ^ 1] = 0;
         if (wave < kWaveHist) a.st->last_pending[wave] = n;
       }
-      if (!grid_sync(ctl)) return;
+      if (!grid_sync(ctl, target)) return;
       for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += nth) {
         const uint32_t idx = base + tid;
         bool wait = false;
@@ -1506,7 +1562,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_round_fused(RoundArgs a) {
         }
         append_if(wait, k, out, (uint32_t *)&pend[cur ^ 1]);
       }
-      if (!grid_sync(ctl)) return;
+      if (!grid_sync(ctl, target)) return;
       cur ^= 1;
       ++wave;
     }
@@ -1624,6 +1680,32 @@ __global__ void k_duplicates(const unsigned long long *E, uint32_t m, unsigned l
     }
     if (!placed) atomicOr(flags, kFlagTableFull);
   }
+}
+
+// Degree fingerprint term of one endpoint: the list's fingerprint is the sum
+// (mod 2^64) over its edges of both endpoints' terms, a function of the
+// multiset of endpoints, i.e. of the degree sequence, which a switch keeps.
+__device__ __forceinline__ unsigned long long endpoint_term(uint32_t v) {
+  return mix64(0x9E3779B97F4A7C15ull + v);
+}
+
+// Debug check of a position-order list: every entry canonical and
+// loop-free (u < v) and in range (v < n, if n), and its degree fingerprint.
+__global__ void k_list_check(const unsigned long long *E, uint32_t m, unsigned long long n, uint32_t *flags,
+                             unsigned long long *fp) {
+  uint32_t f = 0;
+  unsigned long long sum = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const unsigned long long e = E[i];
+    const uint32_t u = (uint32_t)(e >> 32), v = (uint32_t)e;
+    if (!(u < v)) f |= kFlagLoop;
+    if (n && v >= n) f |= kFlagRange;
+    sum += endpoint_term(u) + endpoint_term(v);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+  if ((threadIdx.x & 31) == 0 && sum) atomicAdd(fp, sum);
+  if (f) atomicOr(flags, f);
 }
 
 inline int grid_for(unsigned long long work, int threads, int num_sms, int per_sm) {
@@ -1775,6 +1857,13 @@ cudaError_t launch_fill_u32(uint32_t *p, uint32_t n, uint32_t v, cudaStream_t s,
 cudaError_t launch_canonicalise(unsigned long long *E, uint32_t m, unsigned long long n_bound, uint32_t *flags,
                                 uint32_t *max_id, cudaStream_t s, int num_sms) {
   k_canonicalise<<<grid_for(m, 256, num_sms, 8), 256, 0, s>>>(E, m, n_bound, flags, max_id);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_list_check(const unsigned long long *E, uint32_t m, unsigned long long n, uint32_t *flags,
+                              unsigned long long *fp, cudaStream_t s, int num_sms) {
+  if (m == 0) return cudaSuccess;
+  k_list_check<<<grid_for(m, 256, num_sms, 8), 256, 0, s>>>(E, m, n, flags, fp);
   return cudaGetLastError();
 }
 

@@ -30,9 +30,11 @@ GESMC_E_WAVE_CAP = -8
 GESMC_E_INTERNAL = -9
 GESMC_E_CAPACITY = -10
 GESMC_E_TOO_LARGE = -11
+GESMC_E_INVARIANT = -12
 FLAG_NO_GRAPHS = 1
 FLAG_EXACT_ELL = 2
 FLAG_TINY_OVERFLOW = 4  # fault injection for tests (see include/gesmc.h)
+FLAG_VERIFY_ROUNDS = 8  # debugging: check the invariants on the device after every round
 CHAIN_EXACT_ELL = 1
 NOALLOC_MAX_EDGES = 65536
 WAVE_HIST = 64
@@ -163,6 +165,10 @@ _SIGNATURES = [
     ("gesmc_pool_set_round_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32,
                                                    ctypes.POINTER(ctypes.c_uint32)]),
     ("gesmc_set_round_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
+    ("gesmc_verify", ctypes.c_int, [ctypes.c_void_p]),
+    ("gesmc_pool_verify", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32]),
+    ("gesmc_verify_list", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
+                                         ctypes.c_uint64]),
     ("gesmc_pool_stage_times", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_uint64)]),
     # include/gesmc_microbench.h
@@ -243,7 +249,7 @@ def _as_edge_buffer(edges):
 
 def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 0, max_waves: int = 0, stream=None,
                  torch_allocator: bool = True, tuple_log2: int = 0, group_log2: int = 0, graphs: bool = True,
-                 exact_ell: bool = False, tiny_overflow: bool = False):
+                 exact_ell: bool = False, tiny_overflow: bool = False, verify_rounds: bool = False):
     """Create a chain handle; returns (handle, keepalive).  Raises GesmcError."""
     import torch
 
@@ -259,7 +265,7 @@ def gesmc_create(edges, n: int = 0, lazy_threshold: int = 0, start_round: int = 
     opts.tuple_log2 = tuple_log2
     opts.group_log2 = group_log2
     opts.flags = ((0 if graphs else FLAG_NO_GRAPHS) | (FLAG_EXACT_ELL if exact_ell else 0)
-                  | (FLAG_TINY_OVERFLOW if tiny_overflow else 0))
+                  | (FLAG_TINY_OVERFLOW if tiny_overflow else 0) | (FLAG_VERIFY_ROUNDS if verify_rounds else 0))
     if stream is None:
         stream = torch.cuda.current_stream()
     opts.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream) or 0))
@@ -319,6 +325,13 @@ def gesmc_stage_times(h) -> tuple[dict, int]:
     rounds = ctypes.c_uint64()
     _check(load_library().gesmc_stage_times(h, ms, NUM_STAGES, ctypes.byref(rounds)), "gesmc_stage_times")
     return {gesmc_stage_name(i): float(ms[i]) for i in range(NUM_STAGES)}, int(rounds.value)
+
+
+def gesmc_verify_list(edges, reference, n: int = 0) -> int:
+    """Device check of a list (CUDA tensor of packed ids) against the degree
+    sequence of `reference`: GESMC_OK or GESMC_E_INVARIANT."""
+    return int(load_library().gesmc_verify_list(ctypes.c_void_p(edges.data_ptr()), edges.numel(),
+                                                ctypes.c_void_p(reference.data_ptr()), reference.numel(), n))
 
 
 def gesmc_destroy(h):
@@ -421,6 +434,10 @@ class Chain:
         eff = ctypes.c_uint32()
         _check(load_library().gesmc_set_round_launch(self._h, ctas, ctypes.byref(eff)), "gesmc_set_round_launch")
         return int(eff.value)
+
+    def verify(self) -> int:
+        """Device check of the invariants (simple graph, starting degrees): GESMC_OK or GESMC_E_INVARIANT."""
+        return int(load_library().gesmc_verify(self._h))
 
     def stage_times(self) -> tuple[dict, int]:
         return gesmc_stage_times(self._h)
@@ -537,6 +554,10 @@ class Pool:
         _check(load_library().gesmc_pool_set_round_launch(self._p, ctas, ctypes.byref(eff)),
                "gesmc_pool_set_round_launch")
         return int(eff.value)
+
+    def verify(self, chain: int) -> int:
+        """Device check of one chain's invariants: GESMC_OK or GESMC_E_INVARIANT."""
+        return int(load_library().gesmc_pool_verify(self._p, chain))
 
     def stage_times(self) -> tuple[dict, int]:
         ms = (ctypes.c_double * NUM_STAGES)()
