@@ -759,7 +759,8 @@ def run_serve(args):
         offsets = [offsets_all[rid] for rid in mine]
         with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
                                                      max_rounds_per_step=args.rounds_per_step,
-                                                     size_classes=classes, stream=stream) as srv:
+                                                     size_classes=classes, small_round_ctas=args.small_round_ctas,
+                                                     stream=stream) as srv:
             # warm the kernels of every pool once (one request each, not counted)
             warmed = set()
             for r in reqs:
@@ -818,6 +819,7 @@ def run_serve(args):
                        "pool_edges": cap, "pool_chains": args.pool_chains, "total_switches": work,
                        "max_rounds_per_step": args.rounds_per_step,
                        "size_classes": list(classes),
+                       "small_round_ctas": args.small_round_ctas,
                        "parallelism": "single GPU" if world == 1 else
                        f"requests split by edges x rounds over {world} GPUs"},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -979,6 +981,8 @@ def main(argv=None):
     ap.add_argument("--rounds-per-step", type=int, default=8, help="serve: most rounds between admissions")
     ap.add_argument("--size-classes", default="",
                     help="serve: edge-count bounds of the size classes (one pool each), comma-separated")
+    ap.add_argument("--small-round-ctas", type=int, default=0,
+                    help="serve: one-launch rounds with this many CTAs for size classes of at most 2^17 edges")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")

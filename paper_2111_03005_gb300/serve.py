@@ -59,8 +59,10 @@ class _Lane:
     """One size class of requests: a pool (on its own stream), its queue,
     its admitted requests and the rounds it is running."""
 
-    def __init__(self, max_edges: int, max_chains: int, pool_opts: dict):
+    def __init__(self, max_edges: int, max_chains: int, pool_opts: dict, round_ctas: int = 0):
         self.pool = gesmc.Pool(max_edges=max_edges, max_chains=max_chains, **pool_opts)
+        if round_ctas:
+            self.pool.set_round_launch(round_ctas)
         self.max_edges = max_edges
         self.queue: deque[Request] = deque()
         self.live: dict[int, tuple[Request, int]] = {}  # chain id -> (request, rounds run)
@@ -121,7 +123,11 @@ class Server:
     with one pool (each chain's result depends only on its own inputs)."""
 
     def __init__(self, max_edges: int, max_chains: int, max_rounds_per_step: int = 8, size_classes=(),
-                 small_fraction: float = 0.25, **pool_opts):
+                 small_fraction: float = 0.25, small_round_ctas: int = 0, small_round_max_edges: int = 1 << 17,
+                 **pool_opts):
+        # small_round_ctas >= 1: the pools of size classes bounded by at most
+        # small_round_max_edges edges run each round as one cooperative launch
+        # of that many CTAs (gesmc_pool_set_round_launch)
         if max_rounds_per_step < 1:
             raise ValueError("max_rounds_per_step must be at least 1")
         self.bounds = tuple(int(b) for b in size_classes)
@@ -131,7 +137,9 @@ class Server:
         self.lanes: list[_Lane] = []
         for b in self.bounds:
             opts = dict(pool_opts, stream=_new_stream())
-            self.lanes.append(_Lane(max(b, int(max_edges * small_fraction)), max_chains, opts))
+            # a class of small requests runs each round as one launch (its rounds are launch-bound)
+            ctas = small_round_ctas if b <= small_round_max_edges else 0
+            self.lanes.append(_Lane(max(b, int(max_edges * small_fraction)), max_chains, opts, ctas))
         opts = dict(pool_opts)
         if self.bounds and "stream" not in opts:
             opts["stream"] = _new_stream()
