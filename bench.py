@@ -856,7 +856,7 @@ def run_round_latency(args):
     rounds = 200
     results, lists = {}, {}
     want, _ = oracle.run(edges, seed=CHAIN_SEED, rounds=rounds)
-    for ctas in (0, 1, 4, 8, 16, 32, 64, 152):
+    for ctas in (int(x) for x in args.launch_modes.split(",")):
         with gesmc.Chain(edges, n=n) as c:
             used = c.set_round_launch(ctas)
             c.run(rounds, CHAIN_SEED)          # checked against the oracle
@@ -981,6 +981,8 @@ def main(argv=None):
     ap.add_argument("--rounds-per-step", type=int, default=8, help="serve: most rounds between admissions")
     ap.add_argument("--size-classes", default="",
                     help="serve: edge-count bounds of the size classes (one pool each), comma-separated")
+    ap.add_argument("--launch-modes", default="0,1,4,8,16,32,64,152",
+                    help="round_latency: round launches to time (0: multi-kernel; k: one launch of k CTAs)")
     ap.add_argument("--small-round-ctas", type=int, default=0,
                     help="serve: one-launch rounds with this many CTAs for size classes of at most 2^17 edges")
     ap.add_argument("--no-e2e", action="store_true")
