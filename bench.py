@@ -760,6 +760,7 @@ def run_serve(args):
         with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
                                                      max_rounds_per_step=args.rounds_per_step,
                                                      size_classes=classes, small_round_ctas=args.small_round_ctas,
+                                                     small_rounds_per_step=args.small_rounds_per_step or None,
                                                      stream=stream) as srv:
             # warm the kernels of every pool once (one request each, not counted)
             warmed = set()
@@ -820,6 +821,7 @@ def run_serve(args):
                        "max_rounds_per_step": args.rounds_per_step,
                        "size_classes": list(classes),
                        "small_round_ctas": args.small_round_ctas,
+                       "small_rounds_per_step": args.small_rounds_per_step or args.rounds_per_step,
                        "parallelism": "single GPU" if world == 1 else
                        f"requests split by edges x rounds over {world} GPUs"},
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
@@ -985,6 +987,8 @@ def main(argv=None):
                     help="round_latency: round launches to time (0: multi-kernel; k: one launch of k CTAs)")
     ap.add_argument("--small-round-ctas", type=int, default=0,
                     help="serve: one-launch rounds with this many CTAs for size classes of at most 2^17 edges")
+    ap.add_argument("--small-rounds-per-step", type=int, default=0,
+                    help="serve: most rounds between admissions in the one-launch size classes (0: --rounds-per-step)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access ceiling probe")

@@ -291,6 +291,12 @@ struct gesmc_pool_ctx {
   // a round one after another (replayed from the captured graph)
   uint32_t fused_ctas = 0;
   uint32_t fused_max = 0;  // CTAs of the one-launch round the device holds at once
+  // the one-launch round captured in a graph of its own (replayed per round),
+  // for these args and CTA count; direct launches if capture is refused
+  cudaGraphExec_t fused_exec = nullptr;
+  uint64_t fused_version = 0;
+  uint32_t fused_exec_ctas = 0;
+  bool fused_graph_refused = false;
   bool verify_rounds = false;  // GESMC_FLAG_VERIFY_ROUNDS
   int profiling = 0;
   std::vector<cudaEvent_t> events;
@@ -688,17 +694,57 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
   }
   uint32_t launches = 0;
   if (p->fused_ctas && !p->profiling) {
-    // one cooperative launch per round
-    for (uint64_t r = 0; r < rounds; ++r) {
-      nvtxRangePushA("gesmc round");
-      const cudaError_t e = launch_round_fused(a, s, p->fused_ctas);
-      nvtxRangePop();
-      if (e != cudaSuccess) {
+    // one cooperative launch per round, replayed from a captured graph when
+    // the driver captures it (else launched directly)
+    if (p->use_graphs && !p->fused_graph_refused &&
+        (!p->fused_exec || p->fused_version != p->args_version || p->fused_exec_ctas != p->fused_ctas)) {
+      if (p->fused_exec) cudaGraphExecDestroy(p->fused_exec);
+      p->fused_exec = nullptr;
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const bool launched = launch_round_fused(a, p->gstream, p->fused_ctas) == cudaSuccess;
+        ok = cudaStreamEndCapture(p->gstream, &graph) == cudaSuccess && launched && graph;
+      }
+      ok = ok && cudaGraphInstantiate(&p->fused_exec, graph, 0) == cudaSuccess;
+      if (graph) cudaGraphDestroy(graph);
+      if (!ok) {
+        cudaGetLastError();
+        if (p->fused_exec) cudaGraphExecDestroy(p->fused_exec);
+        p->fused_exec = nullptr;
+        p->fused_graph_refused = true;
+      } else {
+        p->fused_version = p->args_version;
+        p->fused_exec_ctas = p->fused_ctas;
+      }
+    }
+    if (p->fused_exec && !p->fused_graph_refused) {
+      bool ok = cudaEventRecord(p->ev_in, s) == cudaSuccess && cudaStreamWaitEvent(p->gstream, p->ev_in, 0) == cudaSuccess;
+      for (uint64_t r = 0; r < rounds && ok; ++r) {
+        nvtxRangePushA("gesmc round");
+        ok = cudaGraphLaunch(p->fused_exec, p->gstream) == cudaSuccess;
+        nvtxRangePop();
+      }
+      ok = ok && cudaEventRecord(p->ev_out, p->gstream) == cudaSuccess &&
+           cudaStreamWaitEvent(s, p->ev_out, 0) == cudaSuccess;
+      if (!ok) {
         cudaGetLastError();
         p->broken = GESMC_E_CUDA;
         return GESMC_E_CUDA;
       }
-      ++launches;
+      launches = (uint32_t)rounds;
+    } else {
+      for (uint64_t r = 0; r < rounds; ++r) {
+        nvtxRangePushA("gesmc round");
+        const cudaError_t e = launch_round_fused(a, s, p->fused_ctas);
+        nvtxRangePop();
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          p->broken = GESMC_E_CUDA;
+          return GESMC_E_CUDA;
+        }
+        ++launches;
+      }
     }
   } else if (p->use_graphs && !p->profiling && rounds > 0) {
     if (!p->gexec || p->graph_version != p->args_version) {
@@ -915,6 +961,7 @@ void gesmc_pool_destroy(gesmc_pool_t p) {
       dev_free(p, p->base);
     }
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    if (p->fused_exec) cudaGraphExecDestroy(p->fused_exec);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);

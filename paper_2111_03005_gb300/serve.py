@@ -59,11 +59,13 @@ class _Lane:
     """One size class of requests: a pool (on its own stream), its queue,
     its admitted requests and the rounds it is running."""
 
-    def __init__(self, max_edges: int, max_chains: int, pool_opts: dict, round_ctas: int = 0):
+    def __init__(self, max_edges: int, max_chains: int, pool_opts: dict, rounds_per_step: int,
+                 round_ctas: int = 0):
         self.pool = gesmc.Pool(max_edges=max_edges, max_chains=max_chains, **pool_opts)
         if round_ctas:
             self.pool.set_round_launch(round_ctas)
         self.max_edges = max_edges
+        self.rounds_per_step = rounds_per_step
         self.queue: deque[Request] = deque()
         self.live: dict[int, tuple[Request, int]] = {}  # chain id -> (request, rounds run)
         self.rounds_run = 0
@@ -93,7 +95,8 @@ class _Lane:
         self.pool.remove(cid)
         server.done.append(req)
 
-    def rounds_now(self, cap: int) -> int:
+    def rounds_now(self) -> int:
+        cap = self.rounds_per_step
         return min(cap, min(req.rounds - done for req, done in self.live.values())) if self.live else 0
 
     def advance(self, server: "Server", k: int):
@@ -124,12 +127,17 @@ class Server:
 
     def __init__(self, max_edges: int, max_chains: int, max_rounds_per_step: int = 8, size_classes=(),
                  small_fraction: float = 0.25, small_round_ctas: int = 0, small_round_max_edges: int = 1 << 17,
-                 **pool_opts):
+                 small_rounds_per_step: int | None = None, **pool_opts):
         # small_round_ctas >= 1: the pools of size classes bounded by at most
         # small_round_max_edges edges run each round as one cooperative launch
-        # of that many CTAs (gesmc_pool_set_round_launch)
-        if max_rounds_per_step < 1:
-            raise ValueError("max_rounds_per_step must be at least 1")
+        # of that many CTAs (gesmc_pool_set_round_launch), at most
+        # small_rounds_per_step rounds between admissions (default
+        # max_rounds_per_step): their rounds are short, so a larger cap cuts
+        # the host synchronisations per round at the same admission delay
+        if small_rounds_per_step is None:
+            small_rounds_per_step = max_rounds_per_step
+        if max_rounds_per_step < 1 or small_rounds_per_step < 1:
+            raise ValueError("max_rounds_per_step and small_rounds_per_step must be at least 1")
         self.bounds = tuple(int(b) for b in size_classes)
         if list(self.bounds) != sorted(set(self.bounds)) or any(b < 1 for b in self.bounds):
             raise ValueError("size_classes must be increasing positive edge counts")
@@ -139,11 +147,12 @@ class Server:
             opts = dict(pool_opts, stream=_new_stream())
             # a class of small requests runs each round as one launch (its rounds are launch-bound)
             ctas = small_round_ctas if b <= small_round_max_edges else 0
-            self.lanes.append(_Lane(max(b, int(max_edges * small_fraction)), max_chains, opts, ctas))
+            cap = small_rounds_per_step if ctas else max_rounds_per_step
+            self.lanes.append(_Lane(max(b, int(max_edges * small_fraction)), max_chains, opts, cap, ctas))
         opts = dict(pool_opts)
         if self.bounds and "stream" not in opts:
             opts["stream"] = _new_stream()
-        self.lanes.append(_Lane(max_edges, max_chains, opts))
+        self.lanes.append(_Lane(max_edges, max_chains, opts, max_rounds_per_step))
         self.pool = self.lanes[-1].pool  # the only pool without size classes
         self._workers = ThreadPoolExecutor(max_workers=len(self.lanes)) if len(self.lanes) > 1 else None
         self.done: list[Request] = []
@@ -191,7 +200,7 @@ class Server:
             if lane.running is not None:
                 continue
             lane.admit(self)
-            k = lane.rounds_now(self.max_rounds_per_step)
+            k = lane.rounds_now()
             if k == 0:
                 continue
             if self._workers is None:

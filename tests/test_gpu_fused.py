@@ -92,3 +92,20 @@ def test_one_launch_round_wave_cap_reports_an_error():
         c.run(3, 123)
     assert ei.value.code == gesmc.GESMC_E_WAVE_CAP
     c.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_one_launch_rounds_replayed_or_launched_directly(graphs):
+    # several rounds per call (the round's graph replayed, or one cooperative
+    # launch per round without graphs), the CTA count changed between calls
+    edges, n = inputs.workload_gnp_small(seed=2)
+    want, _ = oracle.run(edges, seed=5, rounds=9)
+    with gesmc.Chain(edges, n=n, graphs=graphs) as c:
+        c.set_round_launch(16)
+        c.run(4, 5)
+        c.set_round_launch(48)
+        c.run(3, 5)
+        c.set_round_launch(16)
+        c.run(2, 5)
+        assert np.array_equal(c.edges(), want)
+        assert c.stats()["kernel_launches"] == 9

@@ -15,9 +15,10 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2111_03005_gb300 import ensemble, gesmc, serve  # noqa: E402
 
 
-@pytest.mark.parametrize("rounds_per_step,size_classes,timeout", [(1, (), None), (8, (), None),
-                                                                  (3, (2000,), None), (8, (1000, 5000), 0.0005)])
-def test_served_requests_equal_their_oracle_runs(rounds_per_step, size_classes, timeout):
+@pytest.mark.parametrize("rounds_per_step,size_classes,timeout,small_ctas",
+                         [(1, (), None, 0), (8, (), None, 0), (3, (2000,), None, 0), (8, (1000, 5000), 0.0005, 0),
+                          (4, (2000, 8000), 0.0005, 16)])
+def test_served_requests_equal_their_oracle_runs(rounds_per_step, size_classes, timeout, small_ctas):
     rng = np.random.default_rng(3)
     reqs = []
     for rid in range(24):
@@ -27,8 +28,11 @@ def test_served_requests_equal_their_oracle_runs(rounds_per_step, size_classes, 
                                   start_round=int(rng.integers(0, 5))))
     cap = sum(len(r.edges) for r in reqs) // 3          # not everything fits at once
     cap = max(cap, max(len(r.edges) for r in reqs))
+    # small_ctas: the size classes run one-launch rounds of that many CTAs,
+    # up to three times as many rounds between admissions
     with serve.Server(max_edges=cap, max_chains=8, max_rounds_per_step=rounds_per_step,
-                      size_classes=size_classes) as srv:
+                      size_classes=size_classes, small_round_ctas=small_ctas,
+                      small_rounds_per_step=3 * rounds_per_step if small_ctas else None) as srv:
         assert len(srv.lanes) == len(size_classes) + 1
         arrivals = sorted(rng.integers(0, 30, size=len(reqs)))
         step, nxt = 0, 0
@@ -72,3 +76,15 @@ def test_autotuned_layout_keeps_every_result(tmp_path):
     for t in range(0, len(graphs), 9):
         expect, _ = oracle.run(graphs[t][0], seed=seeds[t], rounds=3)
         assert np.array_equal(pooled[t], expect)
+
+
+def test_autotuned_round_launch_keeps_every_result(tmp_path):
+    # the tuner's launch axis (small problems): every candidate launch must give the same lists
+    from paper_2111_03005_gb300 import autotune
+
+    graphs = inputs.ensemble_graphs(12, seed=13, n_lo=100, n_hi=2000)
+    seeds = [8100 + t for t in range(len(graphs))]
+    choice = autotune.tune(graphs, seeds, rounds=2, cache=autotune.TuneCache(str(tmp_path / "t.json")),
+                           launch_candidates=(0, 8, 32))
+    assert choice["round_ctas"] in (0, 8, 32)
+    assert set(choice["launch_timings_ms_per_round"]) == {"0", "8", "32"}
