@@ -840,6 +840,14 @@ def run_serve(args):
     return 0
 
 
+def _launch_name(k: str) -> str:
+    if k == "0":
+        return "multi-kernel (graph replay)"
+    if k == "resident":
+        return "resident (one CTA, all rounds of a call in one launch)"
+    return f"one launch, {k} CTAs"
+
+
 def run_round_latency(args):
     """Time of one round of a small chain alone (G(2500, 8/(n-1)), about 1e4
     edges), 200 rounds per step: the multi-kernel round (replayed graph)
@@ -858,7 +866,8 @@ def run_round_latency(args):
     rounds = 200
     results, lists = {}, {}
     want, _ = oracle.run(edges, seed=CHAIN_SEED, rounds=rounds)
-    for ctas in (int(x) for x in args.launch_modes.split(",")):
+    modes = [gesmc.ROUND_RESIDENT if x.strip() == "resident" else int(x) for x in args.launch_modes.split(",")]
+    for ctas in modes:
         with gesmc.Chain(edges, n=n) as c:
             used = c.set_round_launch(ctas)
             c.run(rounds, CHAIN_SEED)          # checked against the oracle
@@ -872,7 +881,8 @@ def run_round_latency(args):
                 c.run(rounds, CHAIN_SEED)
             stop.record(stream)
             torch.cuda.synchronize()
-            results[str(used)] = 1e3 * start.elapsed_time(stop) / (args.steps * rounds)
+            results["resident" if used == gesmc.ROUND_RESIDENT else str(used)] = \
+                1e3 * start.elapsed_time(stop) / (args.steps * rounds)
     exact = all(np.array_equal(v, want) for v in lists.values())
     if not exact:
         raise SystemExit("parity FAILED: a round launch differs from the sequential oracle")
@@ -883,9 +893,8 @@ def run_round_latency(args):
         "ms_per_step": results[best] * rounds / 1e3, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"G(n={n}, p=8/(n-1)), seed 21, m={len(edges)}; {rounds} global switches per step"},
-        "us_per_round": {("multi-kernel (graph replay)" if k == "0" else f"one launch, {k} CTAs"): v
-                         for k, v in results.items()},
-        "best": "multi-kernel" if best == "0" else f"one launch, {best} CTAs",
+        "us_per_round": {_launch_name(k): v for k, v in results.items()},
+        "best": _launch_name(best),
         "parity": {"checked": True, "rounds": rounds, "against": "the sequential oracle, every launch mode"},
     }
     print(json.dumps(line), flush=True)
@@ -983,8 +992,9 @@ def main(argv=None):
     ap.add_argument("--rounds-per-step", type=int, default=8, help="serve: most rounds between admissions")
     ap.add_argument("--size-classes", default="",
                     help="serve: edge-count bounds of the size classes (one pool each), comma-separated")
-    ap.add_argument("--launch-modes", default="0,1,4,8,16,32,64,152",
-                    help="round_latency: round launches to time (0: multi-kernel; k: one launch of k CTAs)")
+    ap.add_argument("--launch-modes", default="0,1,4,8,16,32,64,152,resident",
+                    help="round_latency: round launches to time (0: multi-kernel; k: one launch of k CTAs; "
+                         "resident: one CTA per chain for all rounds of a call)")
     ap.add_argument("--small-round-ctas", type=int, default=0,
                     help="serve: one-launch rounds with this many CTAs for size classes of at most 2^17 edges")
     ap.add_argument("--small-rounds-per-step", type=int, default=0,

@@ -55,7 +55,8 @@ enum {
   GESMC_E_WAVE_CAP = -8,   /* a round needed more waves than opts.max_waves  */
   GESMC_E_INTERNAL = -9,   /* bucket overflow or stalled waves (not expected) */
   GESMC_E_CAPACITY = -10,  /* caller's output buffer too small               */
-  GESMC_E_TOO_LARGE = -11, /* m above GESMC_NOALLOC_MAX_EDGES (no-alloc call) */
+  GESMC_E_TOO_LARGE = -11, /* m above GESMC_NOALLOC_MAX_EDGES (no-alloc call), or a chain
+                              too large for resident rounds (GESMC_ROUND_RESIDENT) */
   GESMC_E_INVARIANT = -12  /* a checked list is not a simple graph with the
                               starting degree sequence (gesmc_verify)        */
 };
@@ -199,7 +200,26 @@ const char *gesmc_stage_name(int stage);
  * dominates the rounds of graphs with up to about 10^5 edges.  The paper has
  * no counterpart (its CPU rounds have no launches).  GESMC_E_INVALID if the
  * device cannot hold one CTA of the one-launch round.  Stage timing
- * (gesmc_set_profiling) always uses the separate kernels. */
+ * (gesmc_set_profiling) always uses the separate kernels.
+ *
+ * ctas == GESMC_ROUND_RESIDENT: resident rounds, for small chains.  Each
+ * chain runs on one 1024-thread CTA that keeps its list (one 32-bit word per
+ * edge), the permutation, the switch statuses and a hash table of the round's
+ * target edge ids in shared memory, and runs ALL rounds of a gesmc_run call
+ * in that one launch (plus a one-CTA launch that folds the rounds' wave
+ * counts into the statistics); a round's steps (Philox keys, the counting
+ * sort of the positions, the switches, their erasers and inserters,
+ * Algorithm 1's decide / delay waves, the rewiring) are separated by CTA
+ * barriers only.  Chains qualify with m <= GESMC_RESIDENT_MAX_EDGES and
+ * n <= GESMC_RESIDENT_MAX_NODES (n: the node bound given at creation, else
+ * the largest id + 1); GESMC_E_TOO_LARGE if a chain does not (and, in a pool,
+ * for a later gesmc_pool_add of such a chain).  The same lists, counters and
+ * wave telemetry as the other launches.  This is the dedicated base case the
+ * paper suggests for small graphs (Sec. 7, Conclusions).  Stage
+ * timing has no stages to time in this mode (gesmc_stage_times stays 0). */
+#define GESMC_ROUND_RESIDENT 0xFFFFFFFFu
+#define GESMC_RESIDENT_MAX_EDGES 12288u
+#define GESMC_RESIDENT_MAX_NODES 65536u
 int gesmc_set_round_launch(gesmc_t h, uint32_t ctas, uint32_t *effective);
 
 /* Debug check, on the device, of what every round keeps (Sec. 2.1; Def. 1):

@@ -13,7 +13,9 @@ A third choice, for small problems only, is how a round is launched:
 ``round_ctas`` = 0 runs the round's kernels one after another (replayed from
 a captured CUDA graph); ``round_ctas`` >= 1 runs the whole round in one
 cooperative launch of that many CTAs (the block-count axis), which saves the
-launch latency between stages that dominates the rounds of small graphs.
+launch latency between stages that dominates the rounds of small graphs;
+``round_ctas`` = ROUND_RESIDENT (when every chain is small enough) runs all
+rounds of a call with one CTA per chain and the chain in shared memory.
 
 Every chain's list after a round is the same under every setting (the
 partitioning only decides where a tuple is grouped, never what is decided).
@@ -32,8 +34,13 @@ import tempfile
 import numpy as np
 
 CANDIDATES = ((9, 10), (9, 11), (10, 11), (10, 12), (11, 11), (11, 12))
-# one-launch round CTA counts tried for problems of at most LAUNCH_TUNE_MAX_EDGES edges
-LAUNCH_CANDIDATES = (0, 8, 16, 32, 64, 152)
+# round launches tried for problems of at most LAUNCH_TUNE_MAX_EDGES edges: the
+# multi-kernel round, one-launch rounds of these CTA counts, and resident
+# rounds (0xFFFFFFFF, gesmc.ROUND_RESIDENT; tried only if every chain qualifies)
+ROUND_RESIDENT = 0xFFFFFFFF
+RESIDENT_MAX_EDGES = 12288
+RESIDENT_MAX_NODES = 65536
+LAUNCH_CANDIDATES = (0, 8, 16, 32, 64, 152, ROUND_RESIDENT)
 LAUNCH_TUNE_MAX_EDGES = 1 << 21
 
 
@@ -130,7 +137,10 @@ def tune(graphs, seeds, rounds: int = 3, candidates=CANDIDATES, timer=None, cach
     # launch of at most a few hundred CTAs is too narrow for large graphs)
     launch_timings, round_ctas = {}, 0
     if total <= LAUNCH_TUNE_MAX_EDGES and launch_candidates:
+        resident_ok = all(len(e) <= RESIDENT_MAX_EDGES and n <= RESIDENT_MAX_NODES for e, n in graphs)
         for ctas in launch_candidates:
+            if ctas == ROUND_RESIDENT and not resident_ok:
+                continue
             ms, out = timer(g_sample, s_sample, rounds, (best[0], best[1], ctas))
             if not np.array_equal(first, out):
                 raise RuntimeError(f"round launch {ctas} changed the result of a round")

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgesmc.so")
-SOURCES = ["round.cu", "es.cu", "gen.cu", "api.cu", "microbench.cu"]
+SOURCES = ["round.cu", "resident.cu", "es.cu", "gen.cu", "api.cu", "microbench.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE]
 _lock = threading.Lock()

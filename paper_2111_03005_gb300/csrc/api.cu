@@ -15,6 +15,7 @@
 
 #include "../../include/gesmc.h"
 #include "gesmc_internal.cuh"
+#include "resident.cuh"
 
 using namespace gesmc;
 
@@ -245,6 +246,10 @@ struct HostChain {
   unsigned long long fp = 0;  // degree fingerprint of the starting list (gesmc_verify)
 };
 
+// A chain the resident rounds take: few enough edges for one CTA's shared
+// memory and node ids that fit 16 bits (chains with m < 2 have no rounds to run).
+bool resident_fits(uint64_t m, uint64_t n) { return m < 2 || (m <= kResidentMaxEdges && n <= kResidentMaxNodes); }
+
 int map_device_errors(uint32_t err) {
   if (err & kErrTableFull) return GESMC_E_TABLE_FULL;
   if (err & kErrWaveCap) return GESMC_E_WAVE_CAP;
@@ -297,6 +302,12 @@ struct gesmc_pool_ctx {
   uint64_t fused_version = 0;
   uint32_t fused_exec_ctas = 0;
   bool fused_graph_refused = false;
+  // resident rounds (GESMC_ROUND_RESIDENT): one CTA per chain, the list in
+  // shared memory for all rounds of a call; the chain list for the kernel
+  // (in es_job_of) is rebuilt when the chains change (res_version)
+  bool resident = false;
+  uint64_t res_version = 0;
+  uint32_t res_count[kResidentClasses] = {}, res_max_m[kResidentClasses] = {};  // chains and largest m per class
   bool verify_rounds = false;  // GESMC_FLAG_VERIFY_ROUNDS
   int profiling = 0;
   std::vector<cudaEvent_t> events;
@@ -442,7 +453,7 @@ int pool_init(gesmc_pool_t p, const gesmc_pool_opts &o) {
     return GESMC_E_CUDA;
   }
   a.group_grid = shapes.group;
-  if (prepare_es_kernels() != cudaSuccess) {
+  if (prepare_es_kernels() != cudaSuccess || prepare_resident() != cudaSuccess) {
     cudaGetLastError();
     return GESMC_E_CUDA;
   }
@@ -631,6 +642,7 @@ int pool_add_device(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t 
   uint64_t n_eff = 0;
   int rc = validate_list(p, E, m, n, &n_eff);
   if (rc != GESMC_OK) return rc;
+  if (p->resident && !resident_fits(m, n_eff)) return GESMC_E_TOO_LARGE;
   {  // the starting list's degree fingerprint (gesmc_verify compares against it)
     uint32_t flags = 0;
     rc = list_check(E, m, 0, nullptr, 0, at<uint32_t>(p->base, p->lay.scratch) + 4, p->stream, p->num_sms, &flags,
@@ -681,7 +693,8 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
   const RoundArgs a = p->args;
   if (cudaMemsetAsync(&a.ctl->err, 0, sizeof(uint32_t), s) != cudaSuccess) return GESMC_E_CUDA;
   const size_t per_round = kNumStages + 1;
-  if (p->profiling) {
+  const bool stage_events = p->profiling && !p->resident;  // resident rounds have no separate stages
+  if (stage_events) {
     const size_t need = per_round * (size_t)rounds;
     while (p->events.size() < need) {
       cudaEvent_t e;
@@ -693,7 +706,54 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
     }
   }
   uint32_t launches = 0;
-  if (p->fused_ctas && !p->profiling) {
+  if (p->resident) {
+    // one CTA per chain with two edges or more, all rounds of the call in one
+    // launch (several if the rounds outnumber the wave-count scratch words)
+    if (p->res_version != p->args_version) {
+      // chain ids grouped by class (CTA size), class 0 first
+      std::vector<uint32_t> by_class[kResidentClasses];
+      for (uint32_t k = 0; k < kResidentClasses; ++k) p->res_count[k] = p->res_max_m[k] = 0;
+      for (uint32_t c = 0; c < p->max_chains; ++c) {
+        const HostChain &hc = p->chains[c];
+        if (!hc.live || hc.shape.m < 2) continue;
+        const uint32_t k = resident_class(hc.shape.m);
+        by_class[k].push_back(c);
+        p->res_max_m[k] = std::max(p->res_max_m[k], hc.shape.m);
+      }
+      std::vector<uint32_t> jobs;
+      for (uint32_t k = 0; k < kResidentClasses; ++k) {
+        jobs.insert(jobs.end(), by_class[k].begin(), by_class[k].end());
+        p->res_count[k] = (uint32_t)by_class[k].size();
+      }
+      if (!jobs.empty() && (cudaMemcpyAsync(at<uint32_t>(p->base, p->lay.es_job_of), jobs.data(), 4 * jobs.size(),
+                                            cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                            cudaStreamSynchronize(s) != cudaSuccess)) {
+        cudaGetLastError();
+        return GESMC_E_CUDA;
+      }
+      p->res_version = p->args_version;
+    }
+    // the target filter's words (unused by resident rounds) collect each
+    // round's wave count and the last round's undecided switches per wave
+    uint32_t *scratch = a.tfilter;
+    const uint64_t words = (a.tfilter_mask >> 5) + 1;
+    const uint64_t per_launch = std::min<uint64_t>(kResidentMaxRoundsPerLaunch, words - kWaveHist);
+    for (uint64_t done = 0; done < rounds;) {
+      const uint32_t r = (uint32_t)std::min<uint64_t>(per_launch, rounds - done);
+      const bool final = done + r == rounds;
+      nvtxRangePushA("gesmc resident rounds");
+      bool ok = cudaMemsetAsync(scratch, 0, 4ull * (r + kWaveHist), s) == cudaSuccess;
+      ok = ok && launch_round_resident(a, at<uint32_t>(p->base, p->lay.es_job_of), p->res_count, p->res_max_m, r,
+                                       scratch + kWaveHist, scratch, final, s, &launches) == cudaSuccess;
+      nvtxRangePop();
+      if (!ok) {
+        cudaGetLastError();
+        p->broken = GESMC_E_CUDA;
+        return GESMC_E_CUDA;
+      }
+      done += r;
+    }
+  } else if (p->fused_ctas && !p->profiling) {
     // one cooperative launch per round, replayed from a captured graph when
     // the driver captures it (else launched directly)
     if (p->use_graphs && !p->fused_graph_refused &&
@@ -801,7 +861,7 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
     p->broken = GESMC_E_CUDA;
     return GESMC_E_CUDA;
   }
-  if (p->profiling) {
+  if (stage_events) {
     for (uint64_t r = 0; r < rounds; ++r)
       for (int st = 0; st < kNumStages; ++st) {
         float ms = 0.f;
@@ -1109,6 +1169,15 @@ int gesmc_verify_list(const uint64_t *edges, uint64_t m, const uint64_t *referen
 
 int gesmc_pool_set_round_launch(gesmc_pool_t p, uint32_t ctas, uint32_t *effective) {
   if (!p) return GESMC_E_INVALID;
+  if (ctas == GESMC_ROUND_RESIDENT) {
+    for (const HostChain &hc : p->chains)
+      if (hc.live && !resident_fits(hc.shape.m, hc.n)) return GESMC_E_TOO_LARGE;
+    p->resident = true;
+    p->res_version = 0;
+    if (effective) *effective = GESMC_ROUND_RESIDENT;
+    return GESMC_OK;
+  }
+  p->resident = false;
   if (ctas && p->fused_max == 0) return GESMC_E_INVALID;
   const uint32_t want = std::min(ctas, p->fused_max);
   if (want != p->fused_ctas) {

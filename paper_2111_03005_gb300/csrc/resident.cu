@@ -1,0 +1,586 @@
+// Resident rounds: global switches (Def. 2, performed as Algorithm 1's
+// decide / delay waves) of small chains, one CTA per chain, the chain's list
+// in shared memory from the first round of a call to the last.
+//
+// The paper notes that small graphs are the weak case of a parallel global
+// switch (too little work per round to pay for its synchronisation) and that
+// dedicated base cases would help.  On the GPU a round of the general path
+// is a dozen dependent stages spread over the device; for a chain of about
+// 10^4 edges their barriers or launches cost more than the work.  Here one
+// CTA holds the whole chain: E as one 32-bit word per edge (two 16-bit node
+// ids), the permutation, the switch statuses and a hash table of target
+// edge ids, all in shared memory, so a round's stages are separated by
+// __syncthreads only and nothing goes to global memory between rounds.
+//
+// Per round (round number r of the chain):
+//   1. keys K(i) = Philox4x64-10((i >> 2, r, 0, 0); (seed, 0))[i & 3], the
+//      same keys as the general path; a counting sort of the positions into
+//      about m/2 buckets by the keys' top bits, then each bucket put in (K, i)
+//      order by one thread: the argsort pi.
+//   2. switch k = (pi(2k), pi(2k+1), [pi(2k) < pi(2k+1)]): the outright
+//      rejects (laziness, a loop, a shared node) are ILLEGAL before the first
+//      wave; every other switch enters its two targets into the table, whose
+//      entry keeps the smallest inserter q.
+//   3. an edge of E that is some switch's target records its eraser p, the
+//      switch whose slot holds it (the unpaired slot of an odd m erases
+//      nothing: the edge stays, p = "never").
+//   4. Jacobi waves: an undecided switch k decides from the statuses of
+//      earlier waves only (a status word carries its wave): ILLEGAL if a
+//      target is still there when k runs (erased by a later switch or never,
+//      or its eraser failed, or an earlier inserter succeeded), UNDECIDED if
+//      that depends on a switch not yet decided, else LEGAL.  Where a switch
+//      turned illegal in the last wave, the smallest inserters are recomputed
+//      from the switches that are not illegal.
+//   5. the legal switches write their targets to their two positions.
+// After the last round of the launch the list goes back to the chain's slots
+// in position order with nothing pending, as the general path would leave
+// it after store and reload.
+#include "device_util.cuh"
+#include "gesmc_internal.cuh"
+#include "resident.cuh"
+
+namespace gesmc {
+namespace {
+
+constexpr uint32_t kEmpty32 = 0xFFFFFFFFu;  // no edge packs to this (low id < high id)
+constexpr uint32_t kP16None = 0xFFFFu;      // the id is not in E at the round's start
+constexpr uint32_t kP16Keep = 0xFFFEu;      // in E, erased by no switch
+constexpr uint32_t kQ16None = 0xFFFFu;      // no inserter that is not illegal
+
+struct ResidentJob {
+  const uint32_t *jobs;
+  uint32_t rounds;
+  uint32_t *round_waves;
+  uint32_t *last_pending;
+  uint32_t final;
+  uint32_t wave_cap;
+};
+
+// Byte offsets of a chain's pieces of shared memory (all grow with m).
+struct ResLayout {
+  uint32_t order, status, region, nb_log2, slog2, bytes;
+};
+
+__host__ __device__ inline uint32_t ceil_log2(uint32_t x) {
+  uint32_t b = 0;
+  while ((1u << b) < x) ++b;
+  return b;
+}
+
+__host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline ResLayout res_layout(uint32_t m) {
+  ResLayout l;
+  const uint32_t lg = ceil_log2(m);
+  l.nb_log2 = lg > 6 ? lg - 1 : 5;             // about two keys per bucket, at least 32 buckets
+  l.slog2 = lg + 1 < 6 ? 6 : (lg + 1 > 14 ? 14 : lg + 1);  // >= 2m slots, at most 2^14 (m targets at most)
+  l.order = align16(4 * m);                    // E: u32 per position
+  l.status = l.order + align16(2 * m);         // pi: u16 per slot
+  l.region = l.status + align16(2 * (m / 2));  // status: u16 per switch
+  // the sort's keys (u64 per position) and bucket counts, then the table
+  // (u32 key + u32 {p, q} per slot) in the same bytes
+  const uint32_t sort_bytes = align16(8 * m) + 4 * (1u << l.nb_log2);
+  const uint32_t table_bytes = 8 * (1u << l.slog2);
+  l.bytes = l.region + (sort_bytes > table_bytes ? sort_bytes : table_bytes);
+  return l;
+}
+
+// Canonical 32-bit id of the edge {a, b}: smaller node in the high half.
+__device__ __forceinline__ uint32_t pack16(uint32_t a, uint32_t b) {
+  return a < b ? (a << 16) | b : (b << 16) | a;
+}
+
+// tau of Def. 1 on packed edges (the same rules as tau_g): targets e3, e4
+// and the outright-reject code (a loop, or sources sharing a node).
+__device__ __forceinline__ uint32_t tau16(uint32_t g, uint32_t e1, uint32_t e2, uint32_t &e3, uint32_t &e4) {
+  const uint32_t u = e1 >> 16, v = e1 & 0xFFFFu, x = e2 >> 16, y = e2 & 0xFFFFu;
+  const uint32_t a3 = u, b3 = g ? y : x, a4 = v, b4 = g ? x : y;
+  e3 = pack16(a3, b3);
+  e4 = pack16(a4, b4);
+  if (a3 == b3 || a4 == b4) return kCodeLoop;
+  if (u == x || u == y || v == x || v == y) return kCodeShared;
+  return 0;
+}
+
+__device__ __forceinline__ uint32_t home_slot(uint32_t e, uint32_t slog2) { return (e * 0x9E3779B1u) >> (32 - slog2); }
+
+// Slot of id e in the table (linear probing), claimed if absent; 2^slog2 if
+// the table is full.
+__device__ __forceinline__ uint32_t tab_claim(uint32_t *tkey, uint32_t slog2, uint32_t e) {
+  const uint32_t mask = (1u << slog2) - 1;
+  uint32_t s = home_slot(e, slog2);
+  for (uint32_t n = 0; n <= mask; ++n) {
+    const uint32_t cur = *(volatile uint32_t *)&tkey[s];
+    if (cur == e) return s;
+    if (cur == kEmpty32) {
+      const uint32_t prev = atomicCAS(&tkey[s], kEmpty32, e);
+      if (prev == kEmpty32 || prev == e) return s;
+    }
+    s = (s + 1) & mask;
+  }
+  return mask + 1;
+}
+
+// Slot of id e, or 2^slog2 if absent (no claims run meanwhile).
+__device__ __forceinline__ uint32_t tab_find(const uint32_t *tkey, uint32_t slog2, uint32_t e) {
+  const uint32_t mask = (1u << slog2) - 1;
+  uint32_t s = home_slot(e, slog2);
+  for (uint32_t n = 0; n <= mask; ++n) {
+    const uint32_t cur = tkey[s];
+    if (cur == e) return s;
+    if (cur == kEmpty32) break;
+    s = (s + 1) & mask;
+  }
+  return mask + 1;
+}
+
+// q of an entry (low 16 bits of {p, q}) lowered to k if k is smaller: one
+// atomicMin of the whole word, since p (the high half) does not change while
+// inserters register (all p are "none" in step 2, and fixed by step 3 before
+// any re-registration).
+__device__ __forceinline__ void tab_qmin(uint32_t *tpq, uint32_t s, uint32_t k) {
+  atomicMin(&tpq[s], (tpq[s] & 0xFFFF0000u) | k);
+}
+
+__device__ __forceinline__ bool decided_before(uint32_t st, uint32_t wave) {
+  return (st & 3u) != kUndecided && (st >> 2) < wave;
+}
+
+// Exclusive scan of v[0 .. n) in place; ends with a barrier.
+template <int T>
+__device__ void block_exclusive_scan(uint32_t *v, uint32_t n, uint32_t *warp_sums) {
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, wid = tid >> 5;
+  const uint32_t per = (n + T - 1) / T;
+  const uint32_t lo = min(tid * per, n), hi = min(lo + per, n);
+  uint32_t sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) sum += v[i];
+  uint32_t x = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+    if ((int)lane >= off) x += y;
+  }
+  if (lane == 31) warp_sums[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t w0 = lane < (uint32_t)(T / 32) ? warp_sums[lane] : 0u;
+    uint32_t w = w0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+      if ((int)lane >= off) w += y;
+    }
+    if (lane < (uint32_t)(T / 32)) warp_sums[lane] = w - w0;
+  }
+  __syncthreads();
+  uint32_t run = warp_sums[wid] + x - sum;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const uint32_t c = v[i];
+    v[i] = run;
+    run += c;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+  return x;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, ResidentJob job) {
+  extern __shared__ __align__(16) unsigned char res_dyn[];
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_ell;
+  __shared__ uint32_t s_wave[3][3];  // per wave (mod 3): undecided, decided, turned illegal
+  const uint32_t tid = threadIdx.x;
+  const uint32_t c = job.jobs[blockIdx.x];
+  const ChainDesc ch = a.chains[c];
+  const uint32_t m = ch.m, L = ch.L;
+  if (m < 2 || m > kResidentMaxEdges) return;  // the host sends only chains that qualify
+  const ResLayout lay = res_layout(m);
+  uint32_t *const E = reinterpret_cast<uint32_t *>(res_dyn);
+  uint16_t *const order = reinterpret_cast<uint16_t *>(res_dyn + lay.order);
+  uint16_t *const status = reinterpret_cast<uint16_t *>(res_dyn + lay.status);
+  unsigned long long *const keys = reinterpret_cast<unsigned long long *>(res_dyn + lay.region);
+  uint32_t *const cnt = reinterpret_cast<uint32_t *>(res_dyn + lay.region + align16(8 * m));
+  uint32_t *const tkey = reinterpret_cast<uint32_t *>(res_dyn + lay.region);
+  const uint32_t nb_log2 = lay.nb_log2, nb = 1u << nb_log2, slog2 = lay.slog2, S = 1u << slog2;
+  uint32_t *const tpq = tkey + S;
+  const unsigned long long R0 = *(volatile unsigned long long *)&a.ctl->pool_round;
+
+  // the list by position, with the last round's decision of each pair of
+  // slots applied (Def. 1's rewiring of a legal switch)
+  bool bad = false;
+  const bool apply = R0 > ch.added;
+  for (uint32_t s = tid; s < m; s += T) {
+    const uint32_t pos = a.cpos[ch.slot_base + s];
+    unsigned long long e = a.cedge[ch.slot_base + s];
+    const uint32_t k = s >> 1;
+    if (apply && k < L && (a.status[ch.switch_base + k] & 3u) == kLegal) {
+      const uint32_t s0 = ch.slot_base + 2 * k;
+      unsigned long long e3, e4;
+      tau_g(a.cpos[s0] < a.cpos[s0 + 1] ? 1u : 0u, a.cedge[s0], a.cedge[s0 + 1], e3, e4);
+      e = (s & 1u) ? e4 : e3;
+    }
+    const uint32_t lo = (uint32_t)(e >> 32), hi = (uint32_t)e;
+    if (pos >= m || lo >= hi || hi >= kResidentMaxNodes) {
+      bad = true;
+      continue;
+    }
+    E[pos] = (lo << 16) | hi;
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) atomicOr(&a.ctl->err, kErrRecord);
+    return;
+  }
+
+  uint32_t acc = 0, rloop = 0, rexist = 0, rlazy = 0;  // this thread's tallies
+  const bool exact = ch.exact_ell && ch.lazy_threshold;
+  const bool per_switch = ch.lazy_threshold && !ch.exact_ell;
+  uint32_t err = 0;
+  for (uint32_t t = 0; t < job.rounds && !err; ++t) {
+    const unsigned long long round = ch.start_round + (R0 + t - ch.join);
+    // 1. keys, bucket counts and (exact l) the switches that run
+    for (uint32_t b = tid; b < nb; b += T) cnt[b] = 0;
+    if (tid == 0) s_ell = 0;
+    __syncthreads();
+    for (uint32_t q = tid; 4 * q < m; q += T) {
+      const U64x4 w = philox(q, round, 0, 0, ch.seed, 0);
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t x = 4 * q + u;
+        if (x < m) {
+          keys[x] = w.w[u];
+          atomicAdd(&cnt[(uint32_t)(w.w[u] >> (64 - nb_log2))], 1u);
+        }
+      }
+    }
+    if (exact) {
+      uint32_t n = 0;
+      for (uint32_t q = tid; 4 * q < L; q += T) {
+        const U64x4 w = philox(q, round, 1, 0, ch.seed, 0);
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) n += (4 * q + u < L && w.w[u] >= ch.lazy_threshold) ? 1u : 0u;
+      }
+      n = warp_sum(n);
+      if ((tid & 31u) == 0 && n) atomicAdd(&s_ell, n);
+    }
+    __syncthreads();
+    const uint32_t ell = exact ? s_ell : L;
+    block_exclusive_scan<T>(cnt, nb, s_warp);
+    for (uint32_t x = tid; x < m; x += T) {
+      const uint32_t b = (uint32_t)(keys[x] >> (64 - nb_log2));
+      order[atomicAdd(&cnt[b], 1u)] = (uint16_t)x;
+    }
+    __syncthreads();
+    // cnt[b] is now the end of bucket b: order each bucket by (K, i)
+    for (uint32_t b = tid; b < nb; b += T) {
+      const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
+      for (uint32_t y = lo + 1; y < hi; ++y) {
+        const uint32_t v = order[y];
+        const unsigned long long kv = keys[v];
+        uint32_t z = y;
+        while (z > lo) {
+          const uint32_t u = order[z - 1];
+          const unsigned long long ku = keys[u];
+          if (ku < kv || (ku == kv && u < v)) break;
+          order[z] = (uint16_t)u;
+          --z;
+        }
+        order[z] = (uint16_t)v;
+      }
+    }
+    __syncthreads();
+
+    // 2. switches: outright rejects, targets into the table (keys are dead)
+    for (uint32_t s = tid; s < S; s += T) {
+      tkey[s] = kEmpty32;
+      tpq[s] = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    bool full = false;
+    for (uint32_t q = tid; 4 * q < L; q += T) {
+      U64x4 w = {};
+      if (per_switch) w = philox(q, round, 1, 0, ch.seed, 0);
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t k = 4 * q + u;
+        if (k >= L) break;
+        const uint32_t i = order[2 * k], j = order[2 * k + 1];
+        const bool lazy = exact ? k >= ell : (per_switch && w.w[u] < ch.lazy_threshold);
+        uint32_t e3 = 0, e4 = 0;
+        const uint32_t code = lazy ? kCodeLazy : tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
+        if (code) {
+          status[k] = (uint16_t)kIllegal;  // known before the first wave (wave field 0)
+          if (code == kCodeLazy) ++rlazy;
+          else if (code == kCodeLoop) ++rloop;
+          else ++rexist;
+          continue;
+        }
+        status[k] = (uint16_t)kUndecided;
+        const uint32_t s3 = tab_claim(tkey, slog2, e3), s4 = tab_claim(tkey, slog2, e4);
+        if (s3 >= S || s4 >= S) {
+          full = true;
+          continue;
+        }
+        tab_qmin(tpq, s3, k);
+        tab_qmin(tpq, s4, k);
+      }
+    }
+    if (__syncthreads_or(full)) {
+      err = kErrTableFull;
+      break;
+    }
+
+    // 3. erasers of the edges that are targets
+    for (uint32_t s = tid; s < m; s += T) {
+      const uint32_t slot = tab_find(tkey, slog2, E[order[s]]);
+      if (slot < S) {
+        const uint32_t p = (s >> 1) < L ? (s >> 1) : kP16Keep;
+        atomicAnd(&tpq[slot], (p << 16) | 0xFFFFu);
+      }
+    }
+    if (tid < 9) s_wave[tid / 3][tid % 3] = 0;
+    __syncthreads();
+
+    // 4. waves
+    uint32_t wave = 1, entering = L;
+    bool requeue = false, lost = false;  // lost: a registered target not found (never, by construction)
+    for (;;) {
+      if (job.final && t + 1 == job.rounds && tid == 0 && wave >= 2 && wave < kWaveHist)
+        atomicAdd(&job.last_pending[wave], entering);
+      if (tid < 3) s_wave[(wave + 1) % 3][tid] = 0;  // read two waves ago, written next wave
+      if (requeue) {
+        for (uint32_t s = tid; s < S; s += T)
+          if (tkey[s] != kEmpty32) tpq[s] |= 0xFFFFu;
+        __syncthreads();
+        for (uint32_t k = tid; k < L; k += T) {
+          if ((status[k] & 3u) == kIllegal) continue;
+          const uint32_t i = order[2 * k], j = order[2 * k + 1];
+          uint32_t e3, e4;
+          tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
+          const uint32_t s3 = tab_find(tkey, slog2, e3), s4 = tab_find(tkey, slog2, e4);
+          if (s3 >= S || s4 >= S) {
+            lost = true;
+            continue;
+          }
+          tab_qmin(tpq, s3, k);
+          tab_qmin(tpq, s4, k);
+        }
+        __syncthreads();
+      }
+      uint32_t und = 0, dec = 0, ill = 0;
+      for (uint32_t k = tid; k < L; k += T) {
+        if (status[k] != kUndecided) continue;
+        const uint32_t i = order[2 * k], j = order[2 * k + 1];
+        uint32_t tg[2];
+        tau16(i < j ? 1u : 0u, E[i], E[j], tg[0], tg[1]);
+        bool illegal = false, wait = false;
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const uint32_t sl = tab_find(tkey, slog2, tg[x]);
+          if (sl >= S) {
+            lost = true;
+            break;
+          }
+          const uint32_t pq = tpq[sl];
+          const uint32_t p = pq >> 16, q = pq & 0xFFFFu;
+          if (p != kP16None) {      // the target is in E when the round starts
+            if (p > k) {
+              illegal = true;       // erased after k, or never
+            } else {
+              const uint32_t sp = status[p];
+              if (!decided_before(sp, wave)) wait = true;
+              else if ((sp & 3u) == kIllegal) illegal = true;  // its eraser failed
+            }
+          }
+          if (q != kQ16None && q < k) {  // an earlier switch may insert it first
+            const uint32_t sq = status[q];
+            if (!decided_before(sq, wave)) wait = true;
+            else if ((sq & 3u) == kLegal) illegal = true;
+          }
+        }
+        if (!illegal && wait) {
+          ++und;
+          continue;
+        }
+        status[k] = (uint16_t)((wave << 2) | (illegal ? kIllegal : kLegal));
+        ++dec;
+        ill += illegal ? 1u : 0u;
+      }
+      und = warp_sum(und);
+      dec = warp_sum(dec);
+      ill = warp_sum(ill);
+      uint32_t *const ws = s_wave[wave % 3];
+      if ((tid & 31u) == 0) {
+        if (und) atomicAdd(&ws[0], und);
+        if (dec) atomicAdd(&ws[1], dec);
+        if (ill) atomicAdd(&ws[2], ill);
+      }
+      if (__syncthreads_or(lost)) {
+        err = kErrTableFull;
+        break;
+      }
+      const uint32_t U = ws[0], D = ws[1], I = ws[2];
+      if (U == 0) break;
+      if (D == 0) {             // impossible for a valid round: the smallest undecided switch decides
+        err = kErrNoProgress;
+        break;
+      }
+      if (wave >= job.wave_cap) {
+        err = kErrWaveCap;
+        break;
+      }
+      ++wave;
+      entering = U;
+      requeue = I != 0;
+    }
+    if (err) break;
+    if (tid == 0) atomicMax(&job.round_waves[t], wave);
+
+    // 5. legal switches rewrite their positions
+    for (uint32_t k = tid; k < L; k += T) {
+      const uint32_t st = status[k];
+      if ((st & 3u) == kLegal) {
+        const uint32_t i = order[2 * k], j = order[2 * k + 1];
+        uint32_t e3, e4;
+        tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
+        E[i] = e3;
+        E[j] = e4;
+        ++acc;
+      } else if ((st >> 2) != 0) {
+        ++rexist;               // illegal by a wave: a target was in E when it ran
+      }
+    }
+    __syncthreads();
+  }
+  if (err) {
+    if (tid == 0) atomicOr(&a.ctl->err, err);
+    return;
+  }
+  // the list back to the chain's slots, by position, nothing pending
+  for (uint32_t x = tid; x < m; x += T) {
+    const uint32_t e = E[x];
+    a.cpos[ch.slot_base + x] = x;
+    a.cedge[ch.slot_base + x] = ((unsigned long long)(e >> 16) << 32) | (e & 0xFFFFu);
+  }
+  for (uint32_t k = tid; k < L; k += T) a.status[ch.switch_base + k] = 0u;
+  acc = warp_sum(acc);
+  rloop = warp_sum(rloop);
+  rexist = warp_sum(rexist);
+  rlazy = warp_sum(rlazy);
+  if ((tid & 31u) == 0) {
+    if (acc) {
+      atomicAdd(&a.st->accepted, (unsigned long long)acc);
+      atomicAdd(&a.chain_accepted[c], (unsigned long long)acc);
+    }
+    if (rloop) atomicAdd(&a.st->rej_loop, (unsigned long long)rloop);
+    if (rexist) atomicAdd(&a.st->rej_exists, (unsigned long long)rexist);
+    if (rlazy) atomicAdd(&a.st->lazy, (unsigned long long)rlazy);
+  }
+}
+
+// The launch's rounds into the statistics (each round's wave count is the
+// largest over its chains, as in the general path) and the pool round on.
+__global__ void k_resident_fold(RoundArgs a, ResidentJob job) {
+  __shared__ unsigned long long hist[kWaveHist];
+  __shared__ unsigned long long total, most;
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t i = tid; i < kWaveHist; i += blockDim.x) hist[i] = 0;
+  if (tid == 0) total = most = 0;
+  __syncthreads();
+  for (uint32_t t = tid; t < job.rounds; t += blockDim.x) {
+    const uint32_t w = job.round_waves[t];
+    atomicAdd(&hist[w < kWaveHist ? w : kWaveHist - 1], 1ull);
+    atomicAdd(&total, (unsigned long long)w);
+    atomicMax(&most, (unsigned long long)w);
+  }
+  __syncthreads();
+  if (a.any_work) {
+    for (uint32_t i = tid; i < kWaveHist; i += blockDim.x)
+      if (hist[i]) a.st->wave_hist[i] += hist[i];
+  }
+  if (tid == 0) {
+    if (a.any_work) {
+      a.st->waves_total += total;
+      if (most > a.st->waves_max) a.st->waves_max = most;
+    }
+    if (job.final) {
+      a.ctl->waves = (a.any_work && job.rounds) ? job.round_waves[job.rounds - 1] : 0u;
+      a.st->last_pending[1] = a.switch_hw;
+      for (uint32_t w = 2; w < kWaveHist; ++w) a.st->last_pending[w] = job.last_pending[w];
+    }
+    a.ctl->pool_round += job.rounds;
+  }
+}
+
+// The most edges a chain of each class has (CTAs of 1024, 512, 256 and 128
+// threads).
+constexpr uint32_t kClassMaxEdges[kResidentClasses] = {kResidentMaxEdges, 4096, 2048, 1024};
+
+template <int T>
+cudaError_t launch_class(const RoundArgs &a, const ResidentJob &j, uint32_t n, uint32_t max_m, cudaStream_t s) {
+  k_round_resident<T><<<n, T, res_layout(max_m < 2 ? 2 : max_m).bytes, s>>>(a, j);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t resident_class(uint32_t m) {
+  uint32_t c = 0;
+  while (c + 1 < kResidentClasses && m <= kClassMaxEdges[c + 1]) ++c;
+  return c;
+}
+
+size_t resident_smem_bytes(uint32_t m) { return res_layout(m).bytes; }
+
+cudaError_t prepare_resident() {
+  cudaError_t e = cudaFuncSetAttribute(k_round_resident<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)resident_smem_bytes(kClassMaxEdges[0]));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_round_resident<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)resident_smem_bytes(kClassMaxEdges[1]));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_round_resident<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)resident_smem_bytes(kClassMaxEdges[2]));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_round_resident<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)resident_smem_bytes(kClassMaxEdges[3]));
+  return e;
+}
+
+cudaError_t launch_round_resident(const RoundArgs &a, const uint32_t *jobs, const uint32_t (&count)[kResidentClasses],
+                                  const uint32_t (&max_m)[kResidentClasses], uint32_t rounds, uint32_t *round_waves,
+                                  uint32_t *last_pending, bool final, cudaStream_t s, uint32_t *launches) {
+  ResidentJob j;
+  j.rounds = rounds;
+  j.round_waves = round_waves;
+  j.last_pending = last_pending;
+  j.final = final ? 1u : 0u;
+  // status words hold the wave in 14 bits; a round needs at most L + 1 <= 6145 waves
+  const uint32_t cap = a.max_waves ? a.max_waves : kDefaultWaveCap;
+  j.wave_cap = cap < 16383u ? cap : 16383u;
+  uint32_t off = 0;
+  for (uint32_t c = 0; c < kResidentClasses; ++c) {
+    if (!count[c]) continue;
+    j.jobs = jobs + off;
+    off += count[c];
+    cudaError_t e = cudaSuccess;
+    switch (c) {
+      case 0: e = launch_class<1024>(a, j, count[c], max_m[c], s); break;
+      case 1: e = launch_class<512>(a, j, count[c], max_m[c], s); break;
+      case 2: e = launch_class<256>(a, j, count[c], max_m[c], s); break;
+      default: e = launch_class<128>(a, j, count[c], max_m[c], s); break;
+    }
+    if (e != cudaSuccess) return e;
+    ++*launches;
+  }
+  j.jobs = jobs;
+  k_resident_fold<<<1, 256, 0, s>>>(a, j);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace gesmc

@@ -37,6 +37,11 @@ FLAG_TINY_OVERFLOW = 4  # fault injection for tests (see include/gesmc.h)
 FLAG_VERIFY_ROUNDS = 8  # debugging: check the invariants on the device after every round
 CHAIN_EXACT_ELL = 1
 NOALLOC_MAX_EDGES = 65536
+# round launch: every round of a call in one CTA per chain, the list in shared
+# memory (chains with m <= RESIDENT_MAX_EDGES, n <= RESIDENT_MAX_NODES)
+ROUND_RESIDENT = 0xFFFFFFFF
+RESIDENT_MAX_EDGES = 12288
+RESIDENT_MAX_NODES = 65536
 WAVE_HIST = 64
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -430,7 +435,9 @@ class Chain:
 
     def set_round_launch(self, ctas: int) -> int:
         """0: the round's kernels one after another; >= 1: the whole round in
-        one cooperative launch of that many CTAs.  Returns the count used."""
+        one cooperative launch of that many CTAs; ROUND_RESIDENT: all rounds
+        of a call in one CTA per chain (small chains).  Returns the count used
+        (ROUND_RESIDENT for resident rounds)."""
         eff = ctypes.c_uint32()
         _check(load_library().gesmc_set_round_launch(self._h, ctas, ctypes.byref(eff)), "gesmc_set_round_launch")
         return int(eff.value)
@@ -549,7 +556,9 @@ class Pool:
 
     def set_round_launch(self, ctas: int) -> int:
         """0: the round's kernels one after another; >= 1: the whole round in
-        one cooperative launch of that many CTAs.  Returns the count used."""
+        one cooperative launch of that many CTAs; ROUND_RESIDENT: all rounds
+        of a call in one CTA per chain (small chains).  Returns the count used
+        (ROUND_RESIDENT for resident rounds)."""
         eff = ctypes.c_uint32()
         _check(load_library().gesmc_pool_set_round_launch(self._p, ctas, ctypes.byref(eff)),
                "gesmc_pool_set_round_launch")

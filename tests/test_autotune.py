@@ -105,3 +105,23 @@ def test_launch_axis_is_tuned_for_small_problems_only(tmp_path):
     big = autotune.tune(graphs, seeds, timer=timer, cache=None, device="dev", problem=(1 << 24, 1),
                         launch_candidates=(0, 8))
     assert big["round_ctas"] == 0 and all(len(c) == 2 for c in calls)
+
+
+def test_resident_rounds_are_tried_only_when_every_chain_qualifies():
+    R = autotune.ROUND_RESIDENT
+    calls = []
+
+    def timer(g, s, rounds, cand):
+        calls.append(cand)
+        ms = 1.0 if len(cand) == 2 else {0: 1.0, 8: 0.5, R: 0.2}[cand[2]]
+        return ms, np.array([7], dtype=np.uint64)
+
+    small = [(np.arange(100, dtype=np.uint64), 500), (np.arange(autotune.RESIDENT_MAX_EDGES, dtype=np.uint64), 65536)]
+    got = autotune.tune(small, [1, 2], timer=timer, cache=None, device="dev", launch_candidates=(0, 8, R))
+    assert got["round_ctas"] == R and any(len(c) == 3 and c[2] == R for c in calls)
+    for bad in ([(np.arange(autotune.RESIDENT_MAX_EDGES + 1, dtype=np.uint64), 100000)],
+                [(np.arange(10, dtype=np.uint64), autotune.RESIDENT_MAX_NODES + 1)]):
+        calls.clear()
+        got = autotune.tune(small + bad, [1, 2, 3], timer=timer, cache=None, device="dev",
+                            launch_candidates=(0, 8, R))
+        assert got["round_ctas"] == 8 and all(len(c) == 2 or c[2] != R for c in calls)
