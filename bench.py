@@ -263,6 +263,42 @@ def traffic_from_profile(kernel: str, workload: str):
         return None
 
 
+def resident_sources_sha256() -> str:
+    """SHA-256 over what the resident kernel's instruction count depends on
+    (resident.cu, resident.cuh, device_util.cuh), without comments."""
+    import hashlib
+    import re
+
+    def code(text: str) -> bytes:
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.split("\n"))
+        return "\n".join(ln for ln in lines if ln).encode()
+
+    csrc = os.path.join(ROOT, "paper_2111_03005_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("resident.cu", "resident.cuh", "device_util.cuh"):
+        h.update(hashlib.sha256(code(open(os.path.join(csrc, name)).read())).digest())
+    return h.hexdigest()
+
+
+def resident_inst_from_profile(workload: str):
+    """Warp instructions one resident round of the workload's chain executes
+    (ncu, committed summary), if the kernel has not changed since."""
+    path = os.path.join(ROOT, "profiles", f"inst_k_round_resident_{workload}.txt")
+    try:
+        kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line)
+        if kv.get("sources_sha256", "").strip() != resident_sources_sha256():
+            return None
+        return float(kv["warp_inst_per_round"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# one SM issues at most 4 warp instructions per clock (4 schedulers) at the
+# maximum SM clock of 2070 MHz: the issue-rate peak of a kernel that runs a
+# chain on one CTA
+SM_ISSUE_PEAK_GINST = 4 * 2.070
+
+
 # --------------------------------------------------------------------- CPU legs
 
 def cpu_sample_switches_per_s():
@@ -417,7 +453,12 @@ def run_gesmc(args):
             create_ms.append(1e3 * (time.perf_counter() - t0))
     del d_edges
     chain = gesmc.Chain(edges, n=n, **layout)
-    round_ctas = chain.set_round_launch(tuning["round_ctas"]) if tuning and tuning.get("round_ctas") else 0
+    if args.round_launch == "auto":
+        want = tuning["round_ctas"] if tuning and tuning.get("round_ctas") else 0
+    else:
+        want = gesmc.ROUND_RESIDENT if args.round_launch == "resident" else int(args.round_launch)
+    round_ctas = chain.set_round_launch(want) if want else 0
+    resident = round_ctas == gesmc.ROUND_RESIDENT
     # the first warm-up step (from round 0, chain seed 7) is checked against the sequential oracle
     parity, oracle_time = check_parity(chain, args.workload, edges, rounds, seed, rank)
     for _ in range(args.warmup - 1):
@@ -449,11 +490,20 @@ def run_gesmc(args):
     ms = max_over_ranks(ms_local, dist, dev)
     st = chain.stats()
     # one more step, untimed, with CUDA events between the stages of every round
+    # (resident rounds have no separate stages: the step's time is the kernel's)
     chain.reset_stats()
-    chain.set_profiling(True)
-    chain.run(rounds, seed)
-    chain.set_profiling(False)
-    stage_ms, prof_rounds = chain.stage_times()
+    if resident:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chain.run(rounds, seed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        stage_ms, prof_rounds = {"resident": e0.elapsed_time(e1)}, rounds
+    else:
+        chain.set_profiling(True)
+        chain.run(rounds, seed)
+        chain.set_profiling(False)
+        stage_ms, prof_rounds = chain.stage_times()
     chain.close()
 
     switches_rank = args.steps * rounds * L
@@ -465,12 +515,26 @@ def run_gesmc(args):
     peak, peak_kind = read_peaks()
     per_stage = {k: v / max(prof_rounds, 1) for k, v in stage_ms.items()}
     dom = max(per_stage, key=per_stage.get)
-    abytes = algorithmic_bytes(dom, m, L, nb, npart, acc_per_round)
-    achieved = abytes / (per_stage[dom] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": abytes,
-                "traffic": traffic_from_profile(f"k_{dom}", args.workload),
-                "timing": "stage events of one extra untimed step (direct launches)"}
+    if resident:
+        # the chain never leaves shared memory between rounds: the kernel is
+        # bound by its SM's instruction issue, not by HBM
+        ipr = resident_inst_from_profile(args.workload)
+        rounds_per_s = args.steps * rounds / (ms_local / 1e3)
+        achieved = ipr * rounds_per_s / 1e9 if ipr else None
+        roofline = {"bound": "alu", "kernel": "k_round_resident", "achieved": achieved,
+                    "peak": SM_ISSUE_PEAK_GINST, "unit": "G warp instructions/s (one SM)",
+                    "frac": achieved / SM_ISSUE_PEAK_GINST if achieved else None,
+                    "peak_kind": "one SM's issue rate (4 schedulers x 1 warp instruction per clock x 2070 MHz): "
+                                 "the chain runs on one CTA",
+                    "warp_inst_per_round": ipr, "traffic": None,
+                    "timing": "the timed steps (one launch of the resident kernel per step)"}
+    else:
+        abytes = algorithmic_bytes(dom, m, L, nb, npart, acc_per_round)
+        achieved = abytes / (per_stage[dom] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": abytes,
+                    "traffic": traffic_from_profile(f"k_{dom}", args.workload),
+                    "timing": "stage events of one extra untimed step (direct launches)"}
     # whole-round view: all stages' algorithmic bytes over the round time
     round_bytes = sum(algorithmic_bytes(s, m, L, nb, npart, acc_per_round) for s in per_stage)
     round_ms = sum(per_stage.values())
@@ -486,8 +550,11 @@ def run_gesmc(args):
                    "l2": ("L2 flushed between timed steps (%d MB written; device state %.2f GB)"
                           % (L2_FLUSH_BYTES >> 20, state_bytes / 1e9)) if flush_l2 else
                          "inputs larger than L2 (device state ~%.1f GB)" % (state_bytes / 1e9),
-                   "path": (f"one cooperative launch per round ({round_ctas} CTAs, the tuner's choice)" if round_ctas
-                            else "captured CUDA graph of a round, replayed (the library's default)"),
+                   "path": ("resident rounds: one CTA keeps the chain in shared memory, all rounds of a step "
+                            "in one launch" if resident else
+                            f"one cooperative launch per round ({round_ctas} CTAs)" if round_ctas
+                            else "captured CUDA graph of a round, replayed (the library's default)")
+                           + (" (the tuner's choice)" if args.round_launch == "auto" and round_ctas else ""),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "parity": parity,
         "roofline": roofline,
@@ -503,9 +570,10 @@ def run_gesmc(args):
     clk = clocks.summary()
     line["clocks"] = clk
 
-    line["round"]["bytes_per_switch"] = round_bytes / max(L, 1)
-    line["round"]["frac_of_peak"] = line["round"]["algorithmic_GBps"] / peak
-    line["round"]["streaming_bound_switches_per_s"] = peak * 1e9 / (round_bytes / max(L, 1))
+    if not resident:
+        line["round"]["bytes_per_switch"] = round_bytes / max(L, 1)
+        line["round"]["frac_of_peak"] = line["round"]["algorithmic_GBps"] / peak
+        line["round"]["streaming_bound_switches_per_s"] = peak * 1e9 / (round_bytes / max(L, 1))
     if not args.no_probe:
         # random-access ceiling of this GPU (8-byte accesses over a 4 GB buffer), for context: the round is
         # laid out so that no step depends on it
@@ -534,12 +602,13 @@ def run_gesmc(args):
               for name, kind in (("atomic_add", gesmc.RANDOM_ATOMIC_ADD), ("store", gesmc.RANDOM_STORE),
                                  ("red", gesmc.RANDOM_RED))}
         t_perm = m * (1.0 / l2["atomic_add"] + 1.0 / l2["store"])
-        line["l2_op_roofline"] = {
-            "kernel": "k_permute", "ops_per_launch": 2 * m, "bound_ms": 1e3 * t_perm,
-            "achieved_ms": per_stage.get("permute"), "frac": 1e3 * t_perm / per_stage["permute"],
-            "rates_per_s": l2,
-            "model": "per position: one cursor atomic with return + one record store, L2-resident rates",
-        }
+        if "permute" in per_stage:
+            line["l2_op_roofline"] = {
+                "kernel": "k_permute", "ops_per_launch": 2 * m, "bound_ms": 1e3 * t_perm,
+                "achieved_ms": per_stage.get("permute"), "frac": 1e3 * t_perm / per_stage["permute"],
+                "rates_per_s": l2,
+                "model": "per position: one cursor atomic with return + one record store, L2-resident rates",
+            }
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
@@ -751,6 +820,7 @@ def run_serve(args):
         svc[rid] = time.perf_counter() - t1
     stream = torch.cuda.Stream()
     classes = tuple(int(float(x)) for x in args.size_classes.split(",") if x.strip())
+    small_ctas = gesmc.ROUND_RESIDENT if args.small_round_ctas == "resident" else int(args.small_round_ctas)
     poll = 2e-4 if classes else None   # with several pools, admit to an idle one while another runs
     for rate in [float(x) for x in args.rates.split(",")]:
         offsets_all = (np.cumsum(unit_gaps) - unit_gaps[0]) / rate
@@ -759,7 +829,7 @@ def run_serve(args):
         offsets = [offsets_all[rid] for rid in mine]
         with torch.cuda.stream(stream), serve.Server(max_edges=cap, max_chains=args.pool_chains,
                                                      max_rounds_per_step=args.rounds_per_step,
-                                                     size_classes=classes, small_round_ctas=args.small_round_ctas,
+                                                     size_classes=classes, small_round_ctas=small_ctas,
                                                      small_rounds_per_step=args.small_rounds_per_step or None,
                                                      stream=stream) as srv:
             # warm the kernels of every pool once (one request each, not counted)
@@ -995,8 +1065,12 @@ def main(argv=None):
     ap.add_argument("--launch-modes", default="0,1,4,8,16,32,64,152,resident",
                     help="round_latency: round launches to time (0: multi-kernel; k: one launch of k CTAs; "
                          "resident: one CTA per chain for all rounds of a call)")
-    ap.add_argument("--small-round-ctas", type=int, default=0,
-                    help="serve: one-launch rounds with this many CTAs for size classes of at most 2^17 edges")
+    ap.add_argument("--round-launch", default="auto",
+                    help="chain workloads: how a round is launched (auto: the tuner's choice; 0: multi-kernel; "
+                         "k: one launch of k CTAs; resident: one CTA per chain for all rounds of a step)")
+    ap.add_argument("--small-round-ctas", default="0",
+                    help="serve: one-launch rounds with this many CTAs for size classes of at most 2^17 edges, "
+                         "or 'resident': resident rounds for size classes of at most 10,240 edges")
     ap.add_argument("--small-rounds-per-step", type=int, default=0,
                     help="serve: most rounds between admissions in the one-launch size classes (0: --rounds-per-step)")
     ap.add_argument("--no-e2e", action="store_true")

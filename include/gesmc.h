@@ -218,7 +218,7 @@ const char *gesmc_stage_name(int stage);
  * paper suggests for small graphs (Sec. 7, Conclusions).  Stage
  * timing has no stages to time in this mode (gesmc_stage_times stays 0). */
 #define GESMC_ROUND_RESIDENT 0xFFFFFFFFu
-#define GESMC_RESIDENT_MAX_EDGES 12288u
+#define GESMC_RESIDENT_MAX_EDGES 10240u
 #define GESMC_RESIDENT_MAX_NODES 65536u
 int gesmc_set_round_launch(gesmc_t h, uint32_t ctas, uint32_t *effective);
 

@@ -38,7 +38,7 @@ CANDIDATES = ((9, 10), (9, 11), (10, 11), (10, 12), (11, 11), (11, 12))
 # multi-kernel round, one-launch rounds of these CTA counts, and resident
 # rounds (0xFFFFFFFF, gesmc.ROUND_RESIDENT; tried only if every chain qualifies)
 ROUND_RESIDENT = 0xFFFFFFFF
-RESIDENT_MAX_EDGES = 12288
+RESIDENT_MAX_EDGES = 10240
 RESIDENT_MAX_NODES = 65536
 LAUNCH_CANDIDATES = (0, 8, 16, 32, 64, 152, ROUND_RESIDENT)
 LAUNCH_TUNE_MAX_EDGES = 1 << 21

@@ -1327,7 +1327,9 @@ const char *gesmc_strerror(int code) {
     case GESMC_E_WAVE_CAP: return "wave cap exceeded";
     case GESMC_E_INTERNAL: return "internal error (bucket overflow or stalled waves)";
     case GESMC_E_CAPACITY: return "output buffer too small";
-    case GESMC_E_TOO_LARGE: return "edge list larger than the no-alloc scratch allows (GESMC_NOALLOC_MAX_EDGES)";
+    case GESMC_E_TOO_LARGE:
+      return "edge list too large: above GESMC_NOALLOC_MAX_EDGES (no-alloc call), or above "
+             "GESMC_RESIDENT_MAX_EDGES edges / GESMC_RESIDENT_MAX_NODES nodes (resident rounds)";
     case GESMC_E_INVARIANT: return "the list is not a simple graph with the starting degree sequence";
     default: return "unknown error";
   }

@@ -15,12 +15,13 @@
 // Per round (round number r of the chain):
 //   1. keys K(i) = Philox4x64-10((i >> 2, r, 0, 0); (seed, 0))[i & 3], the
 //      same keys as the general path; a counting sort of the positions into
-//      about m/2 buckets by the keys' top bits, then each bucket put in (K, i)
-//      order by one thread: the argsort pi.
+//      about m/2 buckets by the keys' top bits, then each position's rank in
+//      its bucket in (K, i) order: the argsort pi.
 //   2. switch k = (pi(2k), pi(2k+1), [pi(2k) < pi(2k+1)]): the outright
 //      rejects (laziness, a loop, a shared node) are ILLEGAL before the first
-//      wave; every other switch enters its two targets into the table, whose
-//      entry keeps the smallest inserter q.
+//      wave; every other switch enters its two targets into the table
+//      (ordered linear probing), then registers as an inserter (the entry
+//      keeps the smallest inserter q) and keeps its targets' slots.
 //   3. an edge of E that is some switch's target records its eraser p, the
 //      switch whose slot holds it (the unpaired slot of an odd m erases
 //      nothing: the edge stays, p = "never").
@@ -58,7 +59,7 @@ struct ResidentJob {
 
 // Byte offsets of a chain's pieces of shared memory (all grow with m).
 struct ResLayout {
-  uint32_t order, status, region, nb_log2, slog2, bytes;
+  uint32_t scat, perm, status, region, nb_log2, slog2, bytes;
 };
 
 __host__ __device__ inline uint32_t ceil_log2(uint32_t x) {
@@ -74,8 +75,10 @@ __host__ __device__ inline ResLayout res_layout(uint32_t m) {
   const uint32_t lg = ceil_log2(m);
   l.nb_log2 = lg > 6 ? lg - 1 : 5;             // about two keys per bucket, at least 32 buckets
   l.slog2 = lg + 1 < 6 ? 6 : (lg + 1 > 14 ? 14 : lg + 1);  // >= 2m slots, at most 2^14 (m targets at most)
-  l.order = align16(4 * m);                    // E: u32 per position
-  l.status = l.order + align16(2 * m);         // pi: u16 per slot
+  l.scat = align16(4 * m);                     // E: u32 per position
+  l.perm = l.scat + align16(2 * m);            // positions by bucket (u16 per slot), later the
+                                               // targets' table slots (u32 per switch)
+  l.status = l.perm + align16(2 * m);          // pi: u16 per slot
   l.region = l.status + align16(2 * (m / 2));  // status: u16 per switch
   // the sort's keys (u64 per position) and bucket counts, then the table
   // (u32 key + u32 {p, q} per slot) in the same bytes
@@ -104,31 +107,32 @@ __device__ __forceinline__ uint32_t tau16(uint32_t g, uint32_t e1, uint32_t e2, 
 
 __device__ __forceinline__ uint32_t home_slot(uint32_t e, uint32_t slog2) { return (e * 0x9E3779B1u) >> (32 - slog2); }
 
-// Slot of id e in the table (linear probing), claimed if absent; 2^slog2 if
-// the table is full.
-__device__ __forceinline__ uint32_t tab_claim(uint32_t *tkey, uint32_t slog2, uint32_t e) {
+// Ordered linear probing: id e goes in by atomicMin from its home slot on;
+// a slot keeps the smaller id and the larger one moves on to the next slot,
+// until an id lands in an empty slot or meets its own copy.  False if the
+// table is full.  A slot's id only ever decreases, and an id passes a slot
+// only while the slot holds a smaller id, so every slot between an id's home
+// and its final slot holds a smaller id: a search for e from its home can
+// stop at the first slot whose id is >= e.
+__device__ __forceinline__ bool tab_insert(uint32_t *tkey, uint32_t slog2, uint32_t e) {
   const uint32_t mask = (1u << slog2) - 1;
   uint32_t s = home_slot(e, slog2);
   for (uint32_t n = 0; n <= mask; ++n) {
-    const uint32_t cur = *(volatile uint32_t *)&tkey[s];
-    if (cur == e) return s;
-    if (cur == kEmpty32) {
-      const uint32_t prev = atomicCAS(&tkey[s], kEmpty32, e);
-      if (prev == kEmpty32 || prev == e) return s;
-    }
+    const uint32_t old = atomicMin(&tkey[s], e);
+    if (old == kEmpty32 || old == e) return true;
+    if (old > e) e = old;  // e took the slot; the displaced id moves on
     s = (s + 1) & mask;
   }
-  return mask + 1;
+  return false;
 }
 
-// Slot of id e, or 2^slog2 if absent (no claims run meanwhile).
+// Slot of id e, or 2^slog2 if absent (no insertions run meanwhile).
 __device__ __forceinline__ uint32_t tab_find(const uint32_t *tkey, uint32_t slog2, uint32_t e) {
   const uint32_t mask = (1u << slog2) - 1;
   uint32_t s = home_slot(e, slog2);
   for (uint32_t n = 0; n <= mask; ++n) {
     const uint32_t cur = tkey[s];
-    if (cur == e) return s;
-    if (cur == kEmpty32) break;
+    if (cur >= e) return cur == e ? s : mask + 1;  // (the empty mark is the largest word)
     s = (s + 1) & mask;
   }
   return mask + 1;
@@ -136,8 +140,8 @@ __device__ __forceinline__ uint32_t tab_find(const uint32_t *tkey, uint32_t slog
 
 // q of an entry (low 16 bits of {p, q}) lowered to k if k is smaller: one
 // atomicMin of the whole word, since p (the high half) does not change while
-// inserters register (all p are "none" in step 2, and fixed by step 3 before
-// any re-registration).
+// inserters register (all p are "none" at the first registration, and fixed
+// by step 3 before any re-registration).
 __device__ __forceinline__ void tab_qmin(uint32_t *tpq, uint32_t s, uint32_t k) {
   atomicMin(&tpq[s], (tpq[s] & 0xFFFF0000u) | k);
 }
@@ -201,7 +205,9 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   if (m < 2 || m > kResidentMaxEdges) return;  // the host sends only chains that qualify
   const ResLayout lay = res_layout(m);
   uint32_t *const E = reinterpret_cast<uint32_t *>(res_dyn);
-  uint16_t *const order = reinterpret_cast<uint16_t *>(res_dyn + lay.order);
+  uint16_t *const scat = reinterpret_cast<uint16_t *>(res_dyn + lay.scat);   // positions by bucket
+  uint32_t *const tslot = reinterpret_cast<uint32_t *>(res_dyn + lay.scat);  // later: the targets' slots
+  uint16_t *const perm = reinterpret_cast<uint16_t *>(res_dyn + lay.perm);   // pi
   uint16_t *const status = reinterpret_cast<uint16_t *>(res_dyn + lay.status);
   unsigned long long *const keys = reinterpret_cast<unsigned long long *>(res_dyn + lay.region);
   uint32_t *const cnt = reinterpret_cast<uint32_t *>(res_dyn + lay.region + align16(8 * m));
@@ -239,30 +245,43 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   uint32_t acc = 0, rloop = 0, rexist = 0, rlazy = 0;  // this thread's tallies
   const bool exact = ch.exact_ell && ch.lazy_threshold;
   const bool per_switch = ch.lazy_threshold && !ch.exact_ell;
+  const uint32_t shift = 64 - nb_log2;
   uint32_t err = 0;
   for (uint32_t t = 0; t < job.rounds && !err; ++t) {
     const unsigned long long round = ch.start_round + (R0 + t - ch.join);
-    // 1. keys, bucket counts and (exact l) the switches that run
+    // 1. keys, bucket counts and (exact l) the switches that run; two
+    //    Philox blocks per thread at a time (independent, so they overlap)
     for (uint32_t b = tid; b < nb; b += T) cnt[b] = 0;
     if (tid == 0) s_ell = 0;
     __syncthreads();
-    for (uint32_t q = tid; 4 * q < m; q += T) {
-      const U64x4 w = philox(q, round, 0, 0, ch.seed, 0);
+    const uint32_t nq = (m + 3) / 4;
+    for (uint32_t q = tid; q < nq; q += 2 * T) {
+      const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
+      const U64x4 w1 = philox(q + T, round, 0, 0, ch.seed, 0);
 #pragma unroll
       for (uint32_t u = 0; u < 4; ++u) {
-        const uint32_t x = 4 * q + u;
-        if (x < m) {
-          keys[x] = w.w[u];
-          atomicAdd(&cnt[(uint32_t)(w.w[u] >> (64 - nb_log2))], 1u);
+        const uint32_t x0 = 4 * q + u, x1 = 4 * (q + T) + u;
+        if (x0 < m) {
+          keys[x0] = w0.w[u];
+          atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
+        }
+        if (x1 < m) {
+          keys[x1] = w1.w[u];
+          atomicAdd(&cnt[(uint32_t)(w1.w[u] >> shift)], 1u);
         }
       }
     }
     if (exact) {
       uint32_t n = 0;
-      for (uint32_t q = tid; 4 * q < L; q += T) {
-        const U64x4 w = philox(q, round, 1, 0, ch.seed, 0);
+      const uint32_t nl = (L + 3) / 4;
+      for (uint32_t q = tid; q < nl; q += 2 * T) {
+        const U64x4 w0 = philox(q, round, 1, 0, ch.seed, 0);
+        const U64x4 w1 = philox(q + T, round, 1, 0, ch.seed, 0);
 #pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) n += (4 * q + u < L && w.w[u] >= ch.lazy_threshold) ? 1u : 0u;
+        for (uint32_t u = 0; u < 4; ++u) {
+          n += (4 * q + u < L && w0.w[u] >= ch.lazy_threshold) ? 1u : 0u;
+          n += (4 * (q + T) + u < L && w1.w[u] >= ch.lazy_threshold) ? 1u : 0u;
+        }
       }
       n = warp_sum(n);
       if ((tid & 31u) == 0 && n) atomicAdd(&s_ell, n);
@@ -270,27 +289,22 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
     __syncthreads();
     const uint32_t ell = exact ? s_ell : L;
     block_exclusive_scan<T>(cnt, nb, s_warp);
-    for (uint32_t x = tid; x < m; x += T) {
-      const uint32_t b = (uint32_t)(keys[x] >> (64 - nb_log2));
-      order[atomicAdd(&cnt[b], 1u)] = (uint16_t)x;
-    }
+    for (uint32_t x = tid; x < m; x += T) scat[atomicAdd(&cnt[(uint32_t)(keys[x] >> shift)], 1u)] = (uint16_t)x;
     __syncthreads();
-    // cnt[b] is now the end of bucket b: order each bucket by (K, i)
-    for (uint32_t b = tid; b < nb; b += T) {
+    // cnt[b] is now the end of bucket b; each position's place in its bucket
+    // is the number of the bucket's positions before it in (K, i) order
+    for (uint32_t y = tid; y < m; y += T) {
+      const uint32_t x = scat[y];
+      const unsigned long long kx = keys[x];
+      const uint32_t b = (uint32_t)(kx >> shift);
       const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
-      for (uint32_t y = lo + 1; y < hi; ++y) {
-        const uint32_t v = order[y];
-        const unsigned long long kv = keys[v];
-        uint32_t z = y;
-        while (z > lo) {
-          const uint32_t u = order[z - 1];
-          const unsigned long long ku = keys[u];
-          if (ku < kv || (ku == kv && u < v)) break;
-          order[z] = (uint16_t)u;
-          --z;
-        }
-        order[z] = (uint16_t)v;
+      uint32_t r = 0;
+      for (uint32_t z = lo; z < hi; ++z) {
+        const uint32_t u = scat[z];
+        const unsigned long long ku = keys[u];
+        r += (ku < kx || (ku == kx && u < x)) ? 1u : 0u;
       }
+      perm[lo + r] = (uint16_t)x;
     }
     __syncthreads();
 
@@ -301,42 +315,52 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
     }
     __syncthreads();
     bool full = false;
-    for (uint32_t q = tid; 4 * q < L; q += T) {
-      U64x4 w = {};
-      if (per_switch) w = philox(q, round, 1, 0, ch.seed, 0);
-#pragma unroll
-      for (uint32_t u = 0; u < 4; ++u) {
-        const uint32_t k = 4 * q + u;
-        if (k >= L) break;
-        const uint32_t i = order[2 * k], j = order[2 * k + 1];
-        const bool lazy = exact ? k >= ell : (per_switch && w.w[u] < ch.lazy_threshold);
-        uint32_t e3 = 0, e4 = 0;
-        const uint32_t code = lazy ? kCodeLazy : tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
-        if (code) {
-          status[k] = (uint16_t)kIllegal;  // known before the first wave (wave field 0)
-          if (code == kCodeLazy) ++rlazy;
-          else if (code == kCodeLoop) ++rloop;
-          else ++rexist;
-          continue;
-        }
-        status[k] = (uint16_t)kUndecided;
-        const uint32_t s3 = tab_claim(tkey, slog2, e3), s4 = tab_claim(tkey, slog2, e4);
-        if (s3 >= S || s4 >= S) {
-          full = true;
-          continue;
-        }
-        tab_qmin(tpq, s3, k);
-        tab_qmin(tpq, s4, k);
+    for (uint32_t k = tid; k < L; k += T) {
+      const uint32_t i = perm[2 * k], j = perm[2 * k + 1];
+      const bool lazy =
+          exact ? k >= ell
+                : (per_switch && word_of(philox(k >> 2, round, 1, 0, ch.seed, 0), k & 3) < ch.lazy_threshold);
+      uint32_t e3 = 0, e4 = 0;
+      const uint32_t code = lazy ? kCodeLazy : tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
+      if (code) {
+        status[k] = (uint16_t)kIllegal;  // known before the first wave (wave field 0)
+        if (code == kCodeLazy) ++rlazy;
+        else if (code == kCodeLoop) ++rloop;
+        else ++rexist;
+        continue;
       }
+      status[k] = (uint16_t)kUndecided;
+      if (!tab_insert(tkey, slog2, e3) || !tab_insert(tkey, slog2, e4)) full = true;
     }
     if (__syncthreads_or(full)) {
+      err = kErrTableFull;
+      break;
+    }
+    // every switch that is not known to fail registers as an inserter of its
+    // targets (smallest q per id) and keeps its targets' slots
+    bool lost = false;  // a target not found (never, by construction)
+    for (uint32_t k = tid; k < L; k += T) {
+      if (status[k] != kUndecided) continue;
+      const uint32_t i = perm[2 * k], j = perm[2 * k + 1];
+      uint32_t e3, e4;
+      tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
+      const uint32_t s3 = tab_find(tkey, slog2, e3), s4 = tab_find(tkey, slog2, e4);
+      if (s3 >= S || s4 >= S) {
+        lost = true;
+        continue;
+      }
+      tslot[k] = s3 | (s4 << 16);
+      tab_qmin(tpq, s3, k);
+      tab_qmin(tpq, s4, k);
+    }
+    if (__syncthreads_or(lost)) {
       err = kErrTableFull;
       break;
     }
 
     // 3. erasers of the edges that are targets
     for (uint32_t s = tid; s < m; s += T) {
-      const uint32_t slot = tab_find(tkey, slog2, E[order[s]]);
+      const uint32_t slot = tab_find(tkey, slog2, E[perm[s]]);
       if (slot < S) {
         const uint32_t p = (s >> 1) < L ? (s >> 1) : kP16Keep;
         atomicAnd(&tpq[slot], (p << 16) | 0xFFFFu);
@@ -347,7 +371,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
 
     // 4. waves
     uint32_t wave = 1, entering = L;
-    bool requeue = false, lost = false;  // lost: a registered target not found (never, by construction)
+    bool requeue = false;
     for (;;) {
       if (job.final && t + 1 == job.rounds && tid == 0 && wave >= 2 && wave < kWaveHist)
         atomicAdd(&job.last_pending[wave], entering);
@@ -358,34 +382,20 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
         __syncthreads();
         for (uint32_t k = tid; k < L; k += T) {
           if ((status[k] & 3u) == kIllegal) continue;
-          const uint32_t i = order[2 * k], j = order[2 * k + 1];
-          uint32_t e3, e4;
-          tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
-          const uint32_t s3 = tab_find(tkey, slog2, e3), s4 = tab_find(tkey, slog2, e4);
-          if (s3 >= S || s4 >= S) {
-            lost = true;
-            continue;
-          }
-          tab_qmin(tpq, s3, k);
-          tab_qmin(tpq, s4, k);
+          const uint32_t ts = tslot[k];
+          tab_qmin(tpq, ts & 0xFFFFu, k);
+          tab_qmin(tpq, ts >> 16, k);
         }
         __syncthreads();
       }
       uint32_t und = 0, dec = 0, ill = 0;
       for (uint32_t k = tid; k < L; k += T) {
         if (status[k] != kUndecided) continue;
-        const uint32_t i = order[2 * k], j = order[2 * k + 1];
-        uint32_t tg[2];
-        tau16(i < j ? 1u : 0u, E[i], E[j], tg[0], tg[1]);
+        const uint32_t ts = tslot[k];
         bool illegal = false, wait = false;
 #pragma unroll
         for (int x = 0; x < 2; ++x) {
-          const uint32_t sl = tab_find(tkey, slog2, tg[x]);
-          if (sl >= S) {
-            lost = true;
-            break;
-          }
-          const uint32_t pq = tpq[sl];
+          const uint32_t pq = tpq[x ? ts >> 16 : ts & 0xFFFFu];
           const uint32_t p = pq >> 16, q = pq & 0xFFFFu;
           if (p != kP16None) {      // the target is in E when the round starts
             if (p > k) {
@@ -419,10 +429,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
         if (dec) atomicAdd(&ws[1], dec);
         if (ill) atomicAdd(&ws[2], ill);
       }
-      if (__syncthreads_or(lost)) {
-        err = kErrTableFull;
-        break;
-      }
+      __syncthreads();
       const uint32_t U = ws[0], D = ws[1], I = ws[2];
       if (U == 0) break;
       if (D == 0) {             // impossible for a valid round: the smallest undecided switch decides
@@ -444,7 +451,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
     for (uint32_t k = tid; k < L; k += T) {
       const uint32_t st = status[k];
       if ((st & 3u) == kLegal) {
-        const uint32_t i = order[2 * k], j = order[2 * k + 1];
+        const uint32_t i = perm[2 * k], j = perm[2 * k + 1];
         uint32_t e3, e4;
         tau16(i < j ? 1u : 0u, E[i], E[j], e3, e4);
         E[i] = e3;

@@ -14,7 +14,7 @@ namespace gesmc {
 // A chain runs resident if it has at most kResidentMaxEdges edges and node
 // ids below kResidentMaxNodes (an edge then packs into 32 bits: two 16-bit
 // node ids; positions and switch indices fit 16 bits).
-constexpr uint32_t kResidentMaxEdges = 12288;
+constexpr uint32_t kResidentMaxEdges = 10240;
 constexpr uint64_t kResidentMaxNodes = 1ull << 16;
 // Chains run in classes by size, each with its own CTA size: 1024 threads
 // for more than 4096 edges, 512 up to 4096, 256 up to 2048, 128 up to 1024

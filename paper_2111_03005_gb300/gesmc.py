@@ -40,7 +40,7 @@ NOALLOC_MAX_EDGES = 65536
 # round launch: every round of a call in one CTA per chain, the list in shared
 # memory (chains with m <= RESIDENT_MAX_EDGES, n <= RESIDENT_MAX_NODES)
 ROUND_RESIDENT = 0xFFFFFFFF
-RESIDENT_MAX_EDGES = 12288
+RESIDENT_MAX_EDGES = 10240
 RESIDENT_MAX_NODES = 65536
 WAVE_HIST = 64
 

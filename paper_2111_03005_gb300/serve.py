@@ -64,6 +64,7 @@ class _Lane:
         self.pool = gesmc.Pool(max_edges=max_edges, max_chains=max_chains, **pool_opts)
         if round_ctas:
             self.pool.set_round_launch(round_ctas)
+        self.resident = round_ctas == gesmc.ROUND_RESIDENT
         self.max_edges = max_edges
         self.rounds_per_step = rounds_per_step
         self.queue: deque[Request] = deque()
@@ -133,7 +134,11 @@ class Server:
         # of that many CTAs (gesmc_pool_set_round_launch), at most
         # small_rounds_per_step rounds between admissions (default
         # max_rounds_per_step): their rounds are short, so a larger cap cuts
-        # the host synchronisations per round at the same admission delay
+        # the host synchronisations per round at the same admission delay.
+        # small_round_ctas = gesmc.ROUND_RESIDENT: the classes bounded by at
+        # most gesmc.RESIDENT_MAX_EDGES edges run resident rounds (one CTA per
+        # request, all rounds of a step in one launch); a request with more
+        # than gesmc.RESIDENT_MAX_NODES nodes goes to the next class
         if small_rounds_per_step is None:
             small_rounds_per_step = max_rounds_per_step
         if max_rounds_per_step < 1 or small_rounds_per_step < 1:
@@ -146,7 +151,10 @@ class Server:
         for b in self.bounds:
             opts = dict(pool_opts, stream=_new_stream())
             # a class of small requests runs each round as one launch (its rounds are launch-bound)
-            ctas = small_round_ctas if b <= small_round_max_edges else 0
+            if small_round_ctas == gesmc.ROUND_RESIDENT:
+                ctas = small_round_ctas if b <= gesmc.RESIDENT_MAX_EDGES else 0
+            else:
+                ctas = small_round_ctas if b <= small_round_max_edges else 0
             cap = small_rounds_per_step if ctas else max_rounds_per_step
             self.lanes.append(_Lane(max(b, int(max_edges * small_fraction)), max_chains, opts, cap, ctas))
         opts = dict(pool_opts)
@@ -165,7 +173,7 @@ class Server:
     def _lane_of(self, req: Request) -> _Lane:
         m = len(req.edges)
         for b, lane in zip(self.bounds, self.lanes):
-            if m <= b:
+            if m <= b and not (lane.resident and not 0 < req.n <= gesmc.RESIDENT_MAX_NODES):
                 return lane
         return self.lanes[-1]
 

@@ -17,7 +17,7 @@ from paper_2111_03005_gb300 import ensemble, gesmc, serve  # noqa: E402
 
 @pytest.mark.parametrize("rounds_per_step,size_classes,timeout,small_ctas",
                          [(1, (), None, 0), (8, (), None, 0), (3, (2000,), None, 0), (8, (1000, 5000), 0.0005, 0),
-                          (4, (2000, 8000), 0.0005, 16)])
+                          (4, (2000, 8000), 0.0005, 16), (4, (2000, 8000), 0.0005, 0xFFFFFFFF)])
 def test_served_requests_equal_their_oracle_runs(rounds_per_step, size_classes, timeout, small_ctas):
     rng = np.random.default_rng(3)
     reqs = []
@@ -28,8 +28,9 @@ def test_served_requests_equal_their_oracle_runs(rounds_per_step, size_classes, 
                                   start_round=int(rng.integers(0, 5))))
     cap = sum(len(r.edges) for r in reqs) // 3          # not everything fits at once
     cap = max(cap, max(len(r.edges) for r in reqs))
-    # small_ctas: the size classes run one-launch rounds of that many CTAs,
-    # up to three times as many rounds between admissions
+    # small_ctas: the size classes run one-launch rounds of that many CTAs
+    # (0xFFFFFFFF: resident rounds), up to three times as many rounds between
+    # admissions
     with serve.Server(max_edges=cap, max_chains=8, max_rounds_per_step=rounds_per_step,
                       size_classes=size_classes, small_round_ctas=small_ctas,
                       small_rounds_per_step=3 * rounds_per_step if small_ctas else None) as srv:
