@@ -667,7 +667,7 @@ def run_ensemble(args):
     dist = init_dist(world, "nccl")
     dev = torch.device("cuda", local)
     count, rounds = args.chains, 50
-    all_graphs = inputs.ensemble_graphs(count, seed=41)
+    all_graphs = inputs.ensemble_graphs(count, seed=41, n_hi=args.n_hi)
     # several GPUs: the chains are split by footprint, each GPU runs its share in its own pool (no exchange)
     mine = ensemble.shard([len(e) for e, _ in all_graphs], world)[rank]
     graphs = [all_graphs[t] for t in mine]
@@ -687,7 +687,7 @@ def run_ensemble(args):
     stream = torch.cuda.Stream()
     gold = None
     gold_path = os.path.join(ROOT, "tests", "golden", "ensemble_4096_digests.json")
-    if count == 4096 and os.path.exists(gold_path):
+    if count == 4096 and args.n_hi == 100_000 and os.path.exists(gold_path):
         with open(gold_path) as f:
             gold = json.load(f)
         if gold["rounds"] != rounds or gold["seed0"] != 5000 or gold["gen_seed"] != 41:
@@ -697,9 +697,26 @@ def run_ensemble(args):
         t0 = time.perf_counter()
         ids = [pool.add(e, n=n, seed=s) for (e, n), s in zip(graphs, seeds)]
         add_s = time.perf_counter() - t0
+        if args.round_launch == "auto":
+            launch = tuning["round_ctas"] if tuning and tuning.get("round_ctas") else 0
+        else:
+            launch = gesmc.ROUND_RESIDENT if args.round_launch == "resident" else int(args.round_launch)
+        launch = pool.set_round_launch(launch) if launch else 0
         # the first warm-up step (rounds 0..49 of every chain) against the sequential oracle's stored digests
         pool.run(rounds)
         parity = {"checked": False, "why": "stored oracle digests cover the 4096-chain ensemble only"}
+        if gold is None and count_mine:
+            # other recipes: the sequential oracle, run here, on a sample of the chains
+            import oracle
+
+            pick = sorted(np.random.default_rng(7).choice(count_mine, size=min(6, count_mine),
+                                                          replace=False).tolist())
+            bad = [t for t in pick
+                   if not np.array_equal(pool.edges(ids[t]), oracle.run(graphs[t][0], seed=seeds[t], rounds=rounds)[0])]
+            if bad:
+                raise SystemExit(f"parity FAILED: ensemble chain {mine[bad[0]]} differs from the sequential oracle")
+            parity = {"checked": True, "rounds": rounds, "chains": len(pick),
+                      "against": "the sequential oracle run beside it on a sample of the chains, whole lists compared"}
         if gold is not None:
             bad = [t for t, c in zip(mine, ids) if list_digest(pool.edges(c))[:16] != gold["digests"][t]]
             bad = sorted(ensemble.gather_shards(dist, {t: 1 for t in bad}))
@@ -726,10 +743,13 @@ def run_ensemble(args):
         ms = max_over_ranks(ms_local, dist, dev)
         st = pool.stats()
         # one more step, untimed, with CUDA events between the stages of every round
-        pool.set_profiling(True)
-        pool.run(rounds)
-        stage_ms, prof_rounds = pool.stage_times()
-        pool.set_profiling(False)
+        # (resident rounds have no separate stages)
+        stage_ms, prof_rounds = {}, 0
+        if launch != gesmc.ROUND_RESIDENT:
+            pool.set_profiling(True)
+            pool.run(rounds)
+            stage_ms, prof_rounds = pool.stage_times()
+            pool.set_profiling(False)
         del ids
     # all ranks' switches over the slowest rank's time (the shards cover every chain once)
     value = ensemble.rate_over_ranks(dist, args.steps * rounds * sum(len(e) // 2 for e, _ in graphs), ms_local / 1e3,
@@ -756,10 +776,15 @@ def run_ensemble(args):
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"{count} chains, n log-uniform in [100, 1e5], half G(n, 8/(n-1)), half "
+        "config": {"workload": f"{count} chains, n log-uniform in [100, {'1e5' if args.n_hi == 100_000 else args.n_hi}], "
+                               f"half G(n, 8/(n-1)), half "
                                f"Pld([1..n^(1/(gamma-1))], gamma ~ U[2.2, 3.0]) by Havel-Hakimi; "
                                f"{rounds} global switches per step", "chains": count,
                    "edges": sum(len(e) for e, _ in all_graphs),
+                   "round_launch": ("resident rounds (one CTA per chain, all rounds of a step in one launch)"
+                                    if launch == gesmc.ROUND_RESIDENT else
+                                    f"one cooperative launch per round ({launch} CTAs)" if launch else
+                                    "captured CUDA graph of the multi-kernel round, replayed"),
                    "parallelism": "single GPU" if world == 1 else
                    f"chains split by footprint over {world} GPUs (rank 0: {count_mine} chains, {total} edges)"},
         "parity": parity,
@@ -1054,6 +1079,7 @@ def main(argv=None):
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["ensemble", "serve", "es", "round_latency"],
                     default="gnp_2p24")
     ap.add_argument("--chains", type=int, default=4096, help="ensemble: chains")
+    ap.add_argument("--n-hi", type=int, default=100_000, help="ensemble: largest n of the log-uniform node counts")
     ap.add_argument("--sample", type=int, default=256, help="ensemble: chains run one by one for comparison")
     ap.add_argument("--requests", type=int, default=128, help="serve: requests")
     ap.add_argument("--rates", default="48,76,400", help="serve: arrival rates (requests/s), comma-separated")

@@ -256,18 +256,28 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
     __syncthreads();
     const uint32_t nq = (m + 3) / 4;
     for (uint32_t q = tid; q < nq; q += 2 * T) {
-      const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
-      const U64x4 w1 = philox(q + T, round, 0, 0, ch.seed, 0);
+      if (q + T < nq) {
+        const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
+        const U64x4 w1 = philox(q + T, round, 0, 0, ch.seed, 0);
 #pragma unroll
-      for (uint32_t u = 0; u < 4; ++u) {
-        const uint32_t x0 = 4 * q + u, x1 = 4 * (q + T) + u;
-        if (x0 < m) {
+        for (uint32_t u = 0; u < 4; ++u) {
+          const uint32_t x0 = 4 * q + u, x1 = 4 * (q + T) + u;
           keys[x0] = w0.w[u];
           atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
+          if (x1 < m) {
+            keys[x1] = w1.w[u];
+            atomicAdd(&cnt[(uint32_t)(w1.w[u] >> shift)], 1u);
+          }
         }
-        if (x1 < m) {
-          keys[x1] = w1.w[u];
-          atomicAdd(&cnt[(uint32_t)(w1.w[u] >> shift)], 1u);
+      } else {
+        const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+          const uint32_t x0 = 4 * q + u;
+          if (x0 < m) {
+            keys[x0] = w0.w[u];
+            atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
+          }
         }
       }
     }
@@ -377,8 +387,14 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
         atomicAdd(&job.last_pending[wave], entering);
       if (tid < 3) s_wave[(wave + 1) % 3][tid] = 0;  // read two waves ago, written next wave
       if (requeue) {
-        for (uint32_t s = tid; s < S; s += T)
-          if (tkey[s] != kEmpty32) tpq[s] |= 0xFFFFu;
+        // q of every id some switch registered for goes back to "none" (the
+        // switches known to fail before the first wave never registered)
+        for (uint32_t k = tid; k < L; k += T) {
+          if (status[k] == (uint16_t)kIllegal) continue;
+          const uint32_t ts = tslot[k];
+          atomicOr(&tpq[ts & 0xFFFFu], 0xFFFFu);
+          atomicOr(&tpq[ts >> 16], 0xFFFFu);
+        }
         __syncthreads();
         for (uint32_t k = tid; k < L; k += T) {
           if ((status[k] & 3u) == kIllegal) continue;
