@@ -171,3 +171,28 @@ def test_oversized_request_and_bad_classes_are_refused(fake_pool):
         serve.Server(max_edges=1000, max_chains=4, size_classes=(100, 10))
     with pytest.raises(ValueError):
         serve.Server(max_edges=1000, max_chains=4, max_rounds_per_step=0)
+
+
+def test_resident_small_class_routing_and_rounds_cap(fake_pool, monkeypatch):
+    # small_round_ctas = ROUND_RESIDENT: only classes bounded by RESIDENT_MAX_EDGES
+    # run resident rounds; a request with too many nodes skips such a class;
+    # resident classes take up to small_rounds_per_step rounds per step
+    launches = []
+    monkeypatch.setattr(FakePool, "set_round_launch", lambda self, c: launches.append((self.max_edges, c)) or c,
+                        raising=False)
+    R = gesmc.ROUND_RESIDENT
+    with serve.Server(max_edges=200_000, max_chains=8, max_rounds_per_step=2, size_classes=(5000, 50_000),
+                      small_fraction=0.1, small_round_ctas=R, small_rounds_per_step=7) as srv:
+        assert [lane.resident for lane in srv.lanes] == [True, False, False]
+        assert launches == [(srv.lanes[0].max_edges, R)]
+        small = serve.Request(rid=0, edges=np.arange(100, dtype=np.uint64), n=500, seed=1, rounds=9)
+        wide = serve.Request(rid=1, edges=np.arange(100, dtype=np.uint64), n=gesmc.RESIDENT_MAX_NODES + 1,
+                             seed=2, rounds=9)
+        unknown_n = serve.Request(rid=2, edges=np.arange(100, dtype=np.uint64), n=0, seed=3, rounds=9)
+        assert srv._lane_of(small) is srv.lanes[0]
+        assert srv._lane_of(wide) is srv.lanes[1]
+        assert srv._lane_of(unknown_n) is srv.lanes[1]
+        _serve(srv, [small, wide, unknown_n])
+        assert len(srv.done) == 3
+    runs = [[k for what, k in pool.calls if what == "run"] for pool in fake_pool.instances]
+    assert runs[0] == [7, 2] and all(k <= 2 for k in runs[1])
