@@ -118,7 +118,7 @@ constexpr int kSubBits = 11;
 constexpr int kDefaultTupleLog2 = 10;
 constexpr int kDefaultGroupLog2 = 11;
 constexpr int kMaxGroupLog2 = 13;
-constexpr int kGroupThreads = 512;
+constexpr int kGroupThreads = 1024;
 constexpr int kGroupSlotBytes = 20;
 
 constexpr int kWaveHist = 64;
