@@ -30,8 +30,9 @@
 //      target is still there when k runs (erased by a later switch or never,
 //      or its eraser failed, or an earlier inserter succeeded), UNDECIDED if
 //      that depends on a switch not yet decided, else LEGAL.  Where a switch
-//      turned illegal in the last wave, the smallest inserters are recomputed
-//      from the switches that are not illegal.
+//      turned illegal in the last wave, the smallest inserters of the ids
+//      with two inserters or more are recomputed from the switches that are
+//      not illegal (an id with one inserter is looked at by that one only).
 //   5. the legal switches write their targets to their two positions.
 // After the last round of the launch the list goes back to the chain's slots
 // in position order with nothing pending, as the general path would leave
@@ -59,7 +60,7 @@ struct ResidentJob {
 
 // Byte offsets of a chain's pieces of shared memory (all grow with m).
 struct ResLayout {
-  uint32_t scat, perm, status, region, nb_log2, slog2, bytes;
+  uint32_t scat, perm, status, region, multi, nb_log2, slog2, bytes;
 };
 
 __host__ __device__ inline uint32_t ceil_log2(uint32_t x) {
@@ -84,7 +85,8 @@ __host__ __device__ inline ResLayout res_layout(uint32_t m) {
   // (u32 key + u32 {p, q} per slot) in the same bytes
   const uint32_t sort_bytes = align16(8 * m) + 4 * (1u << l.nb_log2);
   const uint32_t table_bytes = 8 * (1u << l.slog2);
-  l.bytes = l.region + (sort_bytes > table_bytes ? sort_bytes : table_bytes);
+  l.multi = l.region + (sort_bytes > table_bytes ? sort_bytes : table_bytes);
+  l.bytes = l.multi + align16((1u << l.slog2) / 8);  // one bit per table slot: two inserters or more
   return l;
 }
 
@@ -142,9 +144,11 @@ __device__ __forceinline__ uint32_t tab_find(const uint32_t *tkey, uint32_t slog
 // atomicMin of the whole word, since p (the high half) does not change while
 // inserters register (all p are "none" at the first registration, and fixed
 // by step 3 before any re-registration).
-__device__ __forceinline__ void tab_qmin(uint32_t *tpq, uint32_t s, uint32_t k) {
-  atomicMin(&tpq[s], (tpq[s] & 0xFFFF0000u) | k);
+__device__ __forceinline__ uint32_t tab_qmin(uint32_t *tpq, uint32_t s, uint32_t k) {
+  return atomicMin(&tpq[s], (tpq[s] & 0xFFFF0000u) | k);
 }
+
+__device__ __forceinline__ bool is_multi(const uint32_t *multi, uint32_t s) { return (multi[s >> 5] >> (s & 31)) & 1u; }
 
 __device__ __forceinline__ bool decided_before(uint32_t st, uint32_t wave) {
   return (st & 3u) != kUndecided && (st >> 2) < wave;
@@ -197,7 +201,8 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   extern __shared__ __align__(16) unsigned char res_dyn[];
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_ell;
-  __shared__ uint32_t s_wave[3][3];  // per wave (mod 3): undecided, decided, turned illegal
+  __shared__ uint32_t s_wave[3][3];  // per wave (mod 3): undecided, decided, turned illegal on an id
+                                     // with two inserters or more
   const uint32_t tid = threadIdx.x;
   const uint32_t c = job.jobs[blockIdx.x];
   const ChainDesc ch = a.chains[c];
@@ -214,6 +219,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   uint32_t *const tkey = reinterpret_cast<uint32_t *>(res_dyn + lay.region);
   const uint32_t nb_log2 = lay.nb_log2, nb = 1u << nb_log2, slog2 = lay.slog2, S = 1u << slog2;
   uint32_t *const tpq = tkey + S;
+  uint32_t *const multi = reinterpret_cast<uint32_t *>(res_dyn + lay.multi);
   const unsigned long long R0 = *(volatile unsigned long long *)&a.ctl->pool_round;
 
   // the list by position, with the last round's decision of each pair of
@@ -323,6 +329,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
       tkey[s] = kEmpty32;
       tpq[s] = 0xFFFFFFFFu;
     }
+    for (uint32_t w = tid; w < S / 32; w += T) multi[w] = 0;
     __syncthreads();
     bool full = false;
     for (uint32_t k = tid; k < L; k += T) {
@@ -360,8 +367,9 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
         continue;
       }
       tslot[k] = s3 | (s4 << 16);
-      tab_qmin(tpq, s3, k);
-      tab_qmin(tpq, s4, k);
+      // a slot whose q was already set has a second inserter
+      if ((tab_qmin(tpq, s3, k) & 0xFFFFu) != kQ16None) atomicOr(&multi[s3 >> 5], 1u << (s3 & 31));
+      if ((tab_qmin(tpq, s4, k) & 0xFFFFu) != kQ16None) atomicOr(&multi[s4 >> 5], 1u << (s4 & 31));
     }
     if (__syncthreads_or(lost)) {
       err = kErrTableFull;
@@ -387,20 +395,22 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
         atomicAdd(&job.last_pending[wave], entering);
       if (tid < 3) s_wave[(wave + 1) % 3][tid] = 0;  // read two waves ago, written next wave
       if (requeue) {
-        // q of every id some switch registered for goes back to "none" (the
-        // switches known to fail before the first wave never registered)
+        // q of every id with two inserters or more goes back to "none", and
+        // the inserters that are not illegal register again; an id with one
+        // inserter keeps it as q, since only that inserter looks at the id's q
+        // (the switches known to fail before the first wave never registered)
         for (uint32_t k = tid; k < L; k += T) {
           if (status[k] == (uint16_t)kIllegal) continue;
-          const uint32_t ts = tslot[k];
-          atomicOr(&tpq[ts & 0xFFFFu], 0xFFFFu);
-          atomicOr(&tpq[ts >> 16], 0xFFFFu);
+          const uint32_t ts = tslot[k], s3 = ts & 0xFFFFu, s4 = ts >> 16;
+          if (is_multi(multi, s3)) atomicOr(&tpq[s3], 0xFFFFu);
+          if (is_multi(multi, s4)) atomicOr(&tpq[s4], 0xFFFFu);
         }
         __syncthreads();
         for (uint32_t k = tid; k < L; k += T) {
           if ((status[k] & 3u) == kIllegal) continue;
-          const uint32_t ts = tslot[k];
-          tab_qmin(tpq, ts & 0xFFFFu, k);
-          tab_qmin(tpq, ts >> 16, k);
+          const uint32_t ts = tslot[k], s3 = ts & 0xFFFFu, s4 = ts >> 16;
+          if (is_multi(multi, s3)) tab_qmin(tpq, s3, k);
+          if (is_multi(multi, s4)) tab_qmin(tpq, s4, k);
         }
         __syncthreads();
       }
@@ -434,7 +444,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
         }
         status[k] = (uint16_t)((wave << 2) | (illegal ? kIllegal : kLegal));
         ++dec;
-        ill += illegal ? 1u : 0u;
+        ill += (illegal && (is_multi(multi, ts & 0xFFFFu) || is_multi(multi, ts >> 16))) ? 1u : 0u;
       }
       und = warp_sum(und);
       dec = warp_sum(dec);
