@@ -133,14 +133,17 @@ def tune(graphs, seeds, rounds: int = 3, candidates=CANDIDATES, timer=None, cach
             raise RuntimeError(f"tuning candidate {cand} changed the result of a round")
         timings[cand] = ms
     best = pick(timings)
-    # the round launch, with the chosen layout, for small problems only (one
-    # launch of at most a few hundred CTAs is too narrow for large graphs)
+    # launch, with the chosen layout: one-launch rounds for small problems only
+    # (one launch of at most a few hundred CTAs is too narrow for large
+    # graphs); resident rounds whenever every chain qualifies (one CTA per
+    # chain scales with the chains)
     launch_timings, round_ctas = {}, 0
-    if total <= LAUNCH_TUNE_MAX_EDGES and launch_candidates:
-        resident_ok = all(len(e) <= RESIDENT_MAX_EDGES and n <= RESIDENT_MAX_NODES for e, n in graphs)
-        for ctas in launch_candidates:
-            if ctas == ROUND_RESIDENT and not resident_ok:
-                continue
+    resident_ok = all(len(e) <= RESIDENT_MAX_EDGES and 0 < n <= RESIDENT_MAX_NODES for e, n in graphs)
+    cands = [c for c in launch_candidates if c != ROUND_RESIDENT] if total <= LAUNCH_TUNE_MAX_EDGES else []
+    if ROUND_RESIDENT in launch_candidates and resident_ok:
+        cands += [0, ROUND_RESIDENT] if not cands else [ROUND_RESIDENT]
+    if cands:
+        for ctas in dict.fromkeys(cands):
             ms, out = timer(g_sample, s_sample, rounds, (best[0], best[1], ctas))
             if not np.array_equal(first, out):
                 raise RuntimeError(f"round launch {ctas} changed the result of a round")

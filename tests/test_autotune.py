@@ -125,3 +125,18 @@ def test_resident_rounds_are_tried_only_when_every_chain_qualifies():
         got = autotune.tune(small + bad, [1, 2, 3], timer=timer, cache=None, device="dev",
                             launch_candidates=(0, 8, R))
         assert got["round_ctas"] == 8 and all(len(c) == 2 or c[2] != R for c in calls)
+
+
+def test_resident_rounds_are_tried_for_large_pools_of_small_chains():
+    R = autotune.ROUND_RESIDENT
+    calls = []
+
+    def timer(g, s, rounds, cand):
+        calls.append(cand)
+        return (1.0 if len(cand) == 2 else {0: 1.0, R: 0.3}[cand[2]]), np.array([7], dtype=np.uint64)
+
+    graphs = [(np.arange(100, dtype=np.uint64), 500)] * 3
+    got = autotune.tune(graphs, [1, 2, 3], timer=timer, cache=None, device="dev", problem=(1 << 26, 4096),
+                        launch_candidates=(0, 8, 16, R))
+    assert got["round_ctas"] == R
+    assert [c[2] for c in calls if len(c) == 3] == [0, R]   # no one-launch candidate for a large problem

@@ -149,3 +149,37 @@ def test_pool_mixes_wide_and_narrow_windows():
         x, st = oracle.es_run(x, seed=500 + t, switches=30_000)
         assert np.array_equal(outs[t], x), t
         assert infos[t]["es_switches"] == 30_000
+
+
+def test_chain_above_four_million_edges_with_rebuilds():
+    """A chain above 2^22 edges (windows of 1024 switches); 2.4 million
+    switches pass the edge set's rebuild threshold (an eighth of its slots in
+    tombstones) and relaunch the chain after the set is rebuilt on the whole
+    GPU."""
+    n = 600_000
+    edges = inputs.gnp(n, 15.0 / (n - 1), seed=24)
+    assert len(edges) >= 1 << 22
+    st = es_compare(edges, n, seed=8, calls=[3000, 2_400_000])
+    assert st["accepted"] > 2_000_000
+
+
+def test_pool_mixes_window_sizes_with_rebuilds():
+    """Chains of every window size in one call, with enough switches that
+    the largest ones stop for rebuilds of their edge sets on the whole GPU
+    and are launched again while the small ones are done."""
+    n_huge, n_big = 600_000, 1 << 17
+    graphs = [(inputs.gnp(n_huge, 15.0 / (n_huge - 1), seed=25), n_huge),
+              (inputs.random_simple_graph(300, 900, seed=35), 300),
+              (inputs.gnp(n_big, 9.0 / (n_big - 1), seed=26), n_big),
+              (inputs.random_simple_graph(6000, 20_000, seed=36), 6000),
+              (inputs.random_simple_graph(40_000, 100_000, seed=37), 40_000)]
+    assert len(graphs[0][0]) >= 1 << 22 and len(graphs[2][0]) >= 1 << 19
+    total = sum(len(e) for e, _ in graphs)
+    with gesmc.Pool(max_edges=total, max_chains=len(graphs)) as pool:
+        ids = [pool.add(e, n=n, seed=600 + t) for t, (e, n) in enumerate(graphs)]
+        pool.es_run(1_200_000)
+        outs = [pool.edges(c) for c in ids]
+    for t, (e, n) in enumerate(graphs):
+        x = oracle.validate(e, n)[1]
+        x, _ = oracle.es_run(x, seed=600 + t, switches=1_200_000)
+        assert np.array_equal(outs[t], x), t
