@@ -737,14 +737,30 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
     // round's wave count and the last round's undecided switches per wave
     uint32_t *scratch = a.tfilter;
     const uint64_t words = (a.tfilter_mask >> 5) + 1;
-    const uint64_t per_launch = std::min<uint64_t>(kResidentMaxRoundsPerLaunch, words - kWaveHist);
+    uint64_t per_launch = std::min<uint64_t>(kResidentMaxRoundsPerLaunch, words - kWaveHist);
+    // a pool of few chains has its permutations sorted ahead of the rounds
+    // on other SMs, into the permutation records' bytes (unused by resident
+    // rounds): rounds x chains permutations of pstride u16, then their l
+    uint32_t njobs = 0, max_m = 0;
+    for (uint32_t k = 0; k < kResidentClasses; ++k) {
+      njobs += p->res_count[k];
+      max_m = std::max(max_m, p->res_max_m[k]);
+    }
+    const uint32_t pstride = (max_m + 7u) & ~7u;
+    const uint64_t pre_bytes = 16ull * kPermBucketCap * p->cap.buckets;
+    const uint64_t per_round = (uint64_t)njobs * (2ull * pstride + 4);
+    const bool presort = njobs > 0 && 4ull * njobs <= (uint64_t)p->num_sms && per_round <= pre_bytes;
+    if (presort) per_launch = std::min<uint64_t>(per_launch, pre_bytes / per_round);
     for (uint64_t done = 0; done < rounds;) {
       const uint32_t r = (uint32_t)std::min<uint64_t>(per_launch, rounds - done);
       const bool final = done + r == rounds;
       nvtxRangePushA("gesmc resident rounds");
       bool ok = cudaMemsetAsync(scratch, 0, 4ull * (r + kWaveHist), s) == cudaSuccess;
+      uint16_t *pbuf = presort ? reinterpret_cast<uint16_t *>(a.prec) : nullptr;
+      uint32_t *ebuf = presort ? reinterpret_cast<uint32_t *>(pbuf + (uint64_t)r * njobs * pstride) : nullptr;
       ok = ok && launch_round_resident(a, at<uint32_t>(p->base, p->lay.es_job_of), p->res_count, p->res_max_m, r,
-                                       scratch + kWaveHist, scratch, final, s, &launches) == cudaSuccess;
+                                       scratch + kWaveHist, scratch, final, pbuf, ebuf, pstride, s,
+                                       &launches) == cudaSuccess;
       nvtxRangePop();
       if (!ok) {
         cudaGetLastError();

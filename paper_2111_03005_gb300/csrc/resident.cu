@@ -56,6 +56,12 @@ struct ResidentJob {
   uint32_t *last_pending;
   uint32_t final;
   uint32_t wave_cap;
+  // permutations sorted beforehand (null: each CTA sorts its own): round t
+  // of job j at pbuf + (t * njobs + j) * pstride, its l (exact laziness) at
+  // ebuf[t * njobs + j]; job_base = index of jobs[0] among all jobs
+  uint16_t *pbuf;
+  uint32_t *ebuf;
+  uint32_t pstride, njobs, job_base;
 };
 
 // Byte offsets of a chain's pieces of shared memory (all grow with m).
@@ -196,6 +202,87 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
   return x;
 }
 
+// pi of round `round` of chain ch into perm (shared or global memory): keys
+// K(i) = Philox4x64-10((i >> 2, round, 0, 0); (seed, 0))[i & 3] and bucket
+// counts (two Philox blocks per thread at a time, independent so that they
+// overlap), a scan, the positions scattered by bucket, then each position's
+// rank in its bucket in (K, i) order.  Returns l (exact laziness; L
+// otherwise).  Every thread of the CTA calls it; it ends with a barrier.
+template <int T>
+__device__ __forceinline__ uint32_t sort_round(const ChainDesc &ch, unsigned long long round, uint32_t m, uint32_t L,
+                                               uint32_t nb_log2, unsigned long long *keys, uint32_t *cnt,
+                                               uint16_t *scat, uint16_t *perm, uint32_t *s_warp, uint32_t *s_ell) {
+  const uint32_t tid = threadIdx.x, nb = 1u << nb_log2, shift = 64 - nb_log2;
+  const bool exact = ch.exact_ell && ch.lazy_threshold;
+  for (uint32_t b = tid; b < nb; b += T) cnt[b] = 0;
+  if (tid == 0) *s_ell = 0;
+  __syncthreads();
+  const uint32_t nq = (m + 3) / 4;
+  for (uint32_t q = tid; q < nq; q += 2 * T) {
+    if (q + T < nq) {
+      const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
+      const U64x4 w1 = philox(q + T, round, 0, 0, ch.seed, 0);
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t x0 = 4 * q + u, x1 = 4 * (q + T) + u;
+        keys[x0] = w0.w[u];
+        atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
+        if (x1 < m) {
+          keys[x1] = w1.w[u];
+          atomicAdd(&cnt[(uint32_t)(w1.w[u] >> shift)], 1u);
+        }
+      }
+    } else {
+      const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t x0 = 4 * q + u;
+        if (x0 < m) {
+          keys[x0] = w0.w[u];
+          atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
+        }
+      }
+    }
+  }
+  if (exact) {
+    uint32_t n = 0;
+    const uint32_t nl = (L + 3) / 4;
+    for (uint32_t q = tid; q < nl; q += 2 * T) {
+      const U64x4 w0 = philox(q, round, 1, 0, ch.seed, 0);
+      const U64x4 w1 = philox(q + T, round, 1, 0, ch.seed, 0);
+#pragma unroll
+      for (uint32_t u = 0; u < 4; ++u) {
+        n += (4 * q + u < L && w0.w[u] >= ch.lazy_threshold) ? 1u : 0u;
+        n += (4 * (q + T) + u < L && w1.w[u] >= ch.lazy_threshold) ? 1u : 0u;
+      }
+    }
+    n = warp_sum(n);
+    if ((tid & 31u) == 0 && n) atomicAdd(s_ell, n);
+  }
+  __syncthreads();
+  const uint32_t ell = exact ? *s_ell : L;
+  block_exclusive_scan<T>(cnt, nb, s_warp);
+  for (uint32_t x = tid; x < m; x += T) scat[atomicAdd(&cnt[(uint32_t)(keys[x] >> shift)], 1u)] = (uint16_t)x;
+  __syncthreads();
+  // cnt[b] is now the end of bucket b; each position's place in its bucket
+  // is the number of the bucket's positions before it in (K, i) order
+  for (uint32_t y = tid; y < m; y += T) {
+    const uint32_t x = scat[y];
+    const unsigned long long kx = keys[x];
+    const uint32_t b = (uint32_t)(kx >> shift);
+    const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
+    uint32_t r = 0;
+    for (uint32_t z = lo; z < hi; ++z) {
+      const uint32_t u = scat[z];
+      const unsigned long long ku = keys[u];
+      r += (ku < kx || (ku == kx && u < x)) ? 1u : 0u;
+    }
+    perm[lo + r] = (uint16_t)x;
+  }
+  __syncthreads();
+  return ell;
+}
+
 template <int T>
 __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, ResidentJob job) {
   extern __shared__ __align__(16) unsigned char res_dyn[];
@@ -217,7 +304,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   unsigned long long *const keys = reinterpret_cast<unsigned long long *>(res_dyn + lay.region);
   uint32_t *const cnt = reinterpret_cast<uint32_t *>(res_dyn + lay.region + align16(8 * m));
   uint32_t *const tkey = reinterpret_cast<uint32_t *>(res_dyn + lay.region);
-  const uint32_t nb_log2 = lay.nb_log2, nb = 1u << nb_log2, slog2 = lay.slog2, S = 1u << slog2;
+  const uint32_t nb_log2 = lay.nb_log2, slog2 = lay.slog2, S = 1u << slog2;
   uint32_t *const tpq = tkey + S;
   uint32_t *const multi = reinterpret_cast<uint32_t *>(res_dyn + lay.multi);
   const unsigned long long R0 = *(volatile unsigned long long *)&a.ctl->pool_round;
@@ -251,78 +338,20 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   uint32_t acc = 0, rloop = 0, rexist = 0, rlazy = 0;  // this thread's tallies
   const bool exact = ch.exact_ell && ch.lazy_threshold;
   const bool per_switch = ch.lazy_threshold && !ch.exact_ell;
-  const uint32_t shift = 64 - nb_log2;
   uint32_t err = 0;
   for (uint32_t t = 0; t < job.rounds && !err; ++t) {
     const unsigned long long round = ch.start_round + (R0 + t - ch.join);
-    // 1. keys, bucket counts and (exact l) the switches that run; two
-    //    Philox blocks per thread at a time (independent, so they overlap)
-    for (uint32_t b = tid; b < nb; b += T) cnt[b] = 0;
-    if (tid == 0) s_ell = 0;
-    __syncthreads();
-    const uint32_t nq = (m + 3) / 4;
-    for (uint32_t q = tid; q < nq; q += 2 * T) {
-      if (q + T < nq) {
-        const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
-        const U64x4 w1 = philox(q + T, round, 0, 0, ch.seed, 0);
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) {
-          const uint32_t x0 = 4 * q + u, x1 = 4 * (q + T) + u;
-          keys[x0] = w0.w[u];
-          atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
-          if (x1 < m) {
-            keys[x1] = w1.w[u];
-            atomicAdd(&cnt[(uint32_t)(w1.w[u] >> shift)], 1u);
-          }
-        }
-      } else {
-        const U64x4 w0 = philox(q, round, 0, 0, ch.seed, 0);
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) {
-          const uint32_t x0 = 4 * q + u;
-          if (x0 < m) {
-            keys[x0] = w0.w[u];
-            atomicAdd(&cnt[(uint32_t)(w0.w[u] >> shift)], 1u);
-          }
-        }
-      }
+    // 1. pi of this round (sorted here, or beforehand on other SMs) and l
+    uint32_t ell;
+    if (job.pbuf) {
+      const size_t jg = (size_t)t * job.njobs + job.job_base + blockIdx.x;
+      const uint16_t *src = job.pbuf + jg * job.pstride;
+      for (uint32_t y = tid; y < m; y += T) perm[y] = __ldcg(&src[y]);
+      ell = exact ? __ldcg(&job.ebuf[jg]) : L;
+      __syncthreads();
+    } else {
+      ell = sort_round<T>(ch, round, m, L, nb_log2, keys, cnt, scat, perm, s_warp, &s_ell);
     }
-    if (exact) {
-      uint32_t n = 0;
-      const uint32_t nl = (L + 3) / 4;
-      for (uint32_t q = tid; q < nl; q += 2 * T) {
-        const U64x4 w0 = philox(q, round, 1, 0, ch.seed, 0);
-        const U64x4 w1 = philox(q + T, round, 1, 0, ch.seed, 0);
-#pragma unroll
-        for (uint32_t u = 0; u < 4; ++u) {
-          n += (4 * q + u < L && w0.w[u] >= ch.lazy_threshold) ? 1u : 0u;
-          n += (4 * (q + T) + u < L && w1.w[u] >= ch.lazy_threshold) ? 1u : 0u;
-        }
-      }
-      n = warp_sum(n);
-      if ((tid & 31u) == 0 && n) atomicAdd(&s_ell, n);
-    }
-    __syncthreads();
-    const uint32_t ell = exact ? s_ell : L;
-    block_exclusive_scan<T>(cnt, nb, s_warp);
-    for (uint32_t x = tid; x < m; x += T) scat[atomicAdd(&cnt[(uint32_t)(keys[x] >> shift)], 1u)] = (uint16_t)x;
-    __syncthreads();
-    // cnt[b] is now the end of bucket b; each position's place in its bucket
-    // is the number of the bucket's positions before it in (K, i) order
-    for (uint32_t y = tid; y < m; y += T) {
-      const uint32_t x = scat[y];
-      const unsigned long long kx = keys[x];
-      const uint32_t b = (uint32_t)(kx >> shift);
-      const uint32_t lo = b ? cnt[b - 1] : 0u, hi = cnt[b];
-      uint32_t r = 0;
-      for (uint32_t z = lo; z < hi; ++z) {
-        const uint32_t u = scat[z];
-        const unsigned long long ku = keys[u];
-        r += (ku < kx || (ku == kx && u < x)) ? 1u : 0u;
-      }
-      perm[lo + r] = (uint16_t)x;
-    }
-    __syncthreads();
 
     // 2. switches: outright rejects, targets into the table (keys are dead)
     for (uint32_t s = tid; s < S; s += T) {
@@ -515,6 +544,36 @@ __global__ void __launch_bounds__(T, 1024 / T) k_round_resident(RoundArgs a, Res
   }
 }
 
+// The permutations of all rounds of a launch, one CTA per (chain, round),
+// ahead of the resident kernel, for pools of few chains: the keys and the
+// sort depend only on the chain's seed, round number and m, never on its
+// list, so other SMs sort them while the chain's own CTA would otherwise
+// sit in the sort phases of each round.
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_resident_perm(RoundArgs a, ResidentJob job) {
+  extern __shared__ __align__(16) unsigned char res_dyn[];
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_ell;
+  const ChainDesc ch = a.chains[job.jobs[blockIdx.x]];
+  const uint32_t m = ch.m;
+  if (m < 2 || m > kResidentMaxEdges) return;
+  const ResLayout lay = res_layout(m);
+  unsigned long long *const keys = reinterpret_cast<unsigned long long *>(res_dyn);
+  uint32_t *const cnt = reinterpret_cast<uint32_t *>(res_dyn + align16(8 * m));
+  uint16_t *const scat = reinterpret_cast<uint16_t *>(res_dyn + align16(8 * m) + 4 * (1u << lay.nb_log2));
+  const unsigned long long R0 = *(volatile unsigned long long *)&a.ctl->pool_round;
+  const uint32_t t = blockIdx.y;
+  const size_t jg = (size_t)t * job.njobs + job.job_base + blockIdx.x;
+  const uint32_t ell = sort_round<T>(ch, ch.start_round + (R0 + t - ch.join), m, ch.L, lay.nb_log2, keys, cnt, scat,
+                                     job.pbuf + jg * job.pstride, s_warp, &s_ell);
+  if (threadIdx.x == 0) job.ebuf[jg] = ell;
+}
+
+__host__ __device__ inline uint32_t perm_smem_bytes(uint32_t m) {
+  const ResLayout l = res_layout(m < 2 ? 2 : m);
+  return align16(8 * m) + 4 * (1u << l.nb_log2) + align16(2 * m);
+}
+
 // The launch's rounds into the statistics (each round's wave count is the
 // largest over its chains, as in the general path) and the pool round on.
 __global__ void k_resident_fold(RoundArgs a, ResidentJob job) {
@@ -555,6 +614,7 @@ constexpr uint32_t kClassMaxEdges[kResidentClasses] = {kResidentMaxEdges, 4096, 
 
 template <int T>
 cudaError_t launch_class(const RoundArgs &a, const ResidentJob &j, uint32_t n, uint32_t max_m, cudaStream_t s) {
+  if (j.pbuf) k_resident_perm<T><<<dim3(n, j.rounds), T, perm_smem_bytes(max_m), s>>>(a, j);
   k_round_resident<T><<<n, T, res_layout(max_m < 2 ? 2 : max_m).bytes, s>>>(a, j);
   return cudaGetLastError();
 }
@@ -581,14 +641,26 @@ cudaError_t prepare_resident() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_round_resident<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)resident_smem_bytes(kClassMaxEdges[3]));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_resident_perm<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)perm_smem_bytes(kClassMaxEdges[0]));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_resident_perm<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)perm_smem_bytes(kClassMaxEdges[1]));
   return e;
 }
 
 cudaError_t launch_round_resident(const RoundArgs &a, const uint32_t *jobs, const uint32_t (&count)[kResidentClasses],
                                   const uint32_t (&max_m)[kResidentClasses], uint32_t rounds, uint32_t *round_waves,
-                                  uint32_t *last_pending, bool final, cudaStream_t s, uint32_t *launches) {
+                                  uint32_t *last_pending, bool final, uint16_t *pbuf, uint32_t *ebuf, uint32_t pstride,
+                                  cudaStream_t s, uint32_t *launches) {
   ResidentJob j;
   j.rounds = rounds;
+  j.pbuf = pbuf;
+  j.ebuf = ebuf;
+  j.pstride = pstride;
+  j.njobs = 0;
+  for (uint32_t c = 0; c < kResidentClasses; ++c) j.njobs += count[c];
   j.round_waves = round_waves;
   j.last_pending = last_pending;
   j.final = final ? 1u : 0u;
@@ -599,6 +671,7 @@ cudaError_t launch_round_resident(const RoundArgs &a, const uint32_t *jobs, cons
   for (uint32_t c = 0; c < kResidentClasses; ++c) {
     if (!count[c]) continue;
     j.jobs = jobs + off;
+    j.job_base = off;
     off += count[c];
     cudaError_t e = cudaSuccess;
     switch (c) {
@@ -608,7 +681,7 @@ cudaError_t launch_round_resident(const RoundArgs &a, const uint32_t *jobs, cons
       default: e = launch_class<128>(a, j, count[c], max_m[c], s); break;
     }
     if (e != cudaSuccess) return e;
-    ++*launches;
+    *launches += pbuf ? 2 : 1;
   }
   j.jobs = jobs;
   k_resident_fold<<<1, 256, 0, s>>>(a, j);

@@ -38,10 +38,15 @@ cudaError_t prepare_resident();
 // into the statistics and advances the pool round.  round_waves (rounds
 // words) and last_pending (kWaveHist words) must be zero; `final` says
 // whether the call's last round is in this launch (its per-wave undecided
-// counts become the statistics' last-round counts).  *launches is increased
-// by the number of kernels launched.
+// counts become the statistics' last-round counts).  pbuf (optional): room
+// for rounds x jobs permutations of pstride u16 each (pstride >= the largest
+// m, a multiple of 8), ebuf for rounds x jobs words; then each class's
+// permutations are sorted first by a kernel of one CTA per (chain, round) on
+// the other SMs, and the chains' CTAs read them instead of sorting.
+// *launches is increased by the number of kernels launched.
 cudaError_t launch_round_resident(const RoundArgs &a, const uint32_t *jobs, const uint32_t (&count)[kResidentClasses],
                                   const uint32_t (&max_m)[kResidentClasses], uint32_t rounds, uint32_t *round_waves,
-                                  uint32_t *last_pending, bool final, cudaStream_t s, uint32_t *launches);
+                                  uint32_t *last_pending, bool final, uint16_t *pbuf, uint32_t *ebuf, uint32_t pstride,
+                                  cudaStream_t s, uint32_t *launches);
 
 }  // namespace gesmc
