@@ -377,6 +377,14 @@ void refresh_args(gesmc_pool_t p) {
   a.fused_local_offsets = most_buckets <= kLocalOffsetBuckets ? 1u : 0u;
   a.permute_stride = spread ? coprime_stride(a.permute_ctas) : 1;
   a.sources_stride = spread ? coprime_stride(a.sources_ctas) : 1;
+  a.agg_chain = kNoChain;
+  a.agg_pairs = 0;
+  if (p->live_chains == 1)
+    for (uint32_t c = 0; c < p->max_chains; ++c)
+      if (p->chains[c].live && p->chains[c].shape.m >= 2 && p->chains[c].shape.nb <= kAggBuckets) {
+        a.agg_chain = c;
+        a.agg_pairs = (p->chains[c].shape.m + 1) / 2;
+      }
 }
 
 // Point the round arguments at the pieces of the pool's memory.

@@ -223,7 +223,13 @@ struct RoundArgs {
   // the one-launch round sums each bucket's chain-local offset itself (every
   // chain has at most kLocalOffsetBuckets buckets) instead of a scan stage
   uint32_t fused_local_offsets;
+  // the one chain of a pool with a single chain that has at most
+  // kAggBuckets buckets (kNoChain otherwise): its positions are appended by
+  // k_permute_agg, one cursor atomic per bucket and CTA instead of per record
+  uint32_t agg_chain, agg_pairs;  // and its pairs of slots, (m + 1) / 2
 };
+
+constexpr uint32_t kAggBuckets = 8192;
 
 constexpr uint32_t kLocalOffsetBuckets = 4096;
 

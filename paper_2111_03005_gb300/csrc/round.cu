@@ -318,6 +318,89 @@ __device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uin
     atomicOr(&a.ctl->err, kErrBucket);
 }
 
+// The positions of the chain with few buckets (a pool of one chain with at
+// most kAggBuckets buckets), each CTA taking kAggThreads * kAggPairs
+// consecutive pairs of slots: the CTA counts its records per bucket in
+// shared memory (a record's rank among the CTA's records of its bucket comes
+// with it), takes each bucket's range with one cursor atomic, then stores
+// its records (keys recomputed).  With few buckets every cursor takes
+// thousands of same-address atomics per round, which serialise in L2; here
+// it takes one per CTA.  The order of records inside a bucket does not
+// matter: the sort orders them by key and position.
+constexpr int kAggThreads = 1024, kAggPairs = 2;
+
+// The pair of slots x of the chain (its position and edge pair with the last
+// round's decision applied, and the keys).
+__device__ __forceinline__ void agg_pair(const RoundArgs &a, const ChainDesc &ch, unsigned long long R,
+                                         unsigned long long round, uint32_t x, bool &two, uint32_t (&pos)[2],
+                                         unsigned long long (&e)[2], unsigned long long (&K)[2]) {
+  const uint32_t gx = (ch.slot_base >> 1) + x;  // pair index in the pool's slots
+  two = 2 * x + 1 < ch.m;
+  if (two) {
+    const uint2 ij = __ldcs(reinterpret_cast<const uint2 *>(a.cpos) + gx);
+    const ulonglong2 ee = __ldcs(reinterpret_cast<const ulonglong2 *>(a.cedge) + gx);
+    e[0] = ee.x;
+    e[1] = ee.y;
+    apply_last(a, ch, chain_apply(ch, R), x, ij.x, ij.y, e[0], e[1]);
+    pos[0] = ij.x;
+    pos[1] = ij.y;
+  } else {  // odd m: the chain's last slot has no partner
+    pos[0] = a.cpos[2 * gx];
+    e[0] = a.cedge[2 * gx];
+    pos[1] = 0;
+    e[1] = 0;
+  }
+  K[0] = perm_key(ch.seed, round, pos[0]);
+  K[1] = two ? perm_key(ch.seed, round, pos[1]) : 0ull;
+}
+
+__global__ void __launch_bounds__(kAggThreads, 1) k_permute_agg(RoundArgs a) {
+  __shared__ uint32_t sc[kAggBuckets];  // per bucket: the CTA's count, then its base
+  const ChainDesc ch = a.chains[a.agg_chain];
+  const unsigned long long R = a.ctl->pool_round;
+  const unsigned long long round = chain_round(ch, R);
+  const uint32_t tid = threadIdx.x, nb = 1u << ch.B, npair = (ch.m + 1) >> 1;
+  const uint32_t x0 = blockIdx.x * (kAggThreads * kAggPairs) + tid;
+  for (uint32_t b = tid; b < nb; b += kAggThreads) sc[b] = 0;
+  __syncthreads();
+  uint32_t bk[2 * kAggPairs], rk[2 * kAggPairs];
+#pragma unroll
+  for (int j = 0; j < kAggPairs; ++j) {
+    const uint32_t x = x0 + j * kAggThreads;
+    bk[2 * j] = bk[2 * j + 1] = kNoChain;
+    if (x >= npair) continue;
+    bool two;
+    uint32_t pos[2];
+    unsigned long long e[2], K[2];
+    agg_pair(a, ch, R, round, x, two, pos, e, K);
+    bk[2 * j] = bucket_of(K[0], ch.B);
+    rk[2 * j] = atomicAdd(&sc[bk[2 * j]], 1u);
+    if (two) {
+      bk[2 * j + 1] = bucket_of(K[1], ch.B);
+      rk[2 * j + 1] = atomicAdd(&sc[bk[2 * j + 1]], 1u);
+    }
+  }
+  __syncthreads();
+  for (uint32_t b = tid; b < nb; b += kAggThreads) {
+    const uint32_t n = sc[b];
+    if (n) sc[b] = atomicAdd(&a.pcount[ch.bucket_base + b], n);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kAggPairs; ++j) {
+    const uint32_t x = x0 + j * kAggThreads;
+    if (x >= npair) continue;
+    bool two;
+    uint32_t pos[2];
+    unsigned long long e[2], K[2];
+    agg_pair(a, ch, R, round, x, two, pos, e, K);
+    store_record(a, ch.bucket_base + bk[2 * j], sc[bk[2 * j]] + rk[2 * j], mid_of(K[0], ch.B), pos[0], e[0]);
+    if (two)
+      store_record(a, ch.bucket_base + bk[2 * j + 1], sc[bk[2 * j + 1]] + rk[2 * j + 1], mid_of(K[1], ch.B), pos[1],
+                   e[1]);
+  }
+}
+
 // Exact l (Def. 2 as printed): per chain in that mode, the number of its
 // switches whose laziness word passes (>= threshold); the round then runs
 // the chain's first l switches.  Each CTA takes a contiguous range of
@@ -1780,7 +1863,13 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   ++n;
   if (work && a.any_exact) { k_lazy_count<<<grid_for(a.switch_hw, 256, num_sms, 8), 256, 0, s>>>(a); ++n; }
   mark(kStagePermute);
-  if (work) { k_permute<<<a.permute_ctas, 256, 0, s>>>(a); ++n; }
+  if (work && a.agg_chain != kNoChain) {
+    k_permute_agg<<<(a.agg_pairs + kAggThreads * kAggPairs - 1) / (kAggThreads * kAggPairs), kAggThreads, 0, s>>>(a);
+    ++n;
+  } else if (work) {
+    k_permute<<<a.permute_ctas, 256, 0, s>>>(a);
+    ++n;
+  }
   mark(kStageScanPerm);
   if (work) {
     k_scan_perm<<<a.bucket_hw ? (a.bucket_hw + 1023) / 1024 : 1, 1024, 0, s>>>(a);
