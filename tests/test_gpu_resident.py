@@ -228,3 +228,21 @@ def test_few_chains_of_every_class_sorted_ahead():
     for t, (e, n) in enumerate(graphs):
         want, _ = oracle.run(e, seed=80 + t, rounds=12, start_round=t)
         assert np.array_equal(outs[t], want), t
+
+
+def test_many_chains_with_exact_laziness_sorted_in_their_own_ctas():
+    # a pool of many chains sorts each round's permutation in the chain's own
+    # CTA (no presort); exact l is counted there too
+    graphs = inputs.ensemble_graphs(48, seed=43, n_lo=20, n_hi=2000)
+    graphs = [(e, n) for e, n in graphs if len(e) <= gesmc.RESIDENT_MAX_EDGES]
+    total = sum(len(e) for e, _ in graphs)
+    thr = 1 << 62
+    with gesmc.Pool(max_edges=total, max_chains=len(graphs)) as pool:
+        ids = [pool.add(e, n=n, seed=90 + t, lazy_threshold=thr, exact_ell=True)
+               for t, (e, n) in enumerate(graphs)]
+        pool.set_round_launch(RESIDENT)
+        pool.run(6)
+        outs = [pool.edges(c) for c in ids]
+    for t in range(0, len(graphs), 5):
+        want, _ = oracle.run(graphs[t][0], seed=90 + t, rounds=6, lazy_threshold=thr, exact_ell=True)
+        assert np.array_equal(outs[t], want), t
