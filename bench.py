@@ -609,6 +609,16 @@ def run_gesmc(args):
                 "rates_per_s": l2,
                 "model": "per position: one cursor atomic with return + one record store, L2-resident rates",
             }
+        if "sortpair" in per_stage:
+            # the sort kernel's emission: per switch two tuple-cursor atomics with return, two 16-byte
+            # tuple stores and two target-filter reductions, at the same rates
+            t_sort = L * (2.0 / l2["atomic_add"] + 2.0 / l2["store"] + 2.0 / l2["red"])
+            line["l2_op_roofline_sortpair"] = {
+                "kernel": "k_sortpair", "ops_per_launch": 6 * L, "bound_ms": 1e3 * t_sort,
+                "achieved_ms": per_stage["sortpair"], "frac": 1e3 * t_sort / per_stage["sortpair"],
+                "model": "per switch: two cursor atomics with return + two tuple stores + two filter reductions, "
+                         "L2-resident rates (the sort in shared memory and the list's streaming stores come on top)",
+            }
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
