@@ -210,7 +210,10 @@ const char *gesmc_stage_name(int stage);
  * counts into the statistics); a round's steps (Philox keys, the counting
  * sort of the positions, the switches, their erasers and inserters,
  * Algorithm 1's decide / delay waves, the rewiring) are separated by CTA
- * barriers only.  Chains qualify with m <= GESMC_RESIDENT_MAX_EDGES and
+ * barriers only.  When a pool holds few chains, the permutations of the
+ * call's rounds are sorted beforehand by one more launch (one CTA per chain
+ * and round, on the other SMs), and the chains' CTAs load them.  Calls with
+ * more rounds than the pool's scratch space holds take several launches.  Chains qualify with m <= GESMC_RESIDENT_MAX_EDGES and
  * n <= GESMC_RESIDENT_MAX_NODES (n: the node bound given at creation, else
  * the largest id + 1); GESMC_E_TOO_LARGE if a chain does not (and, in a pool,
  * for a later gesmc_pool_add of such a chain).  The same lists, counters and
