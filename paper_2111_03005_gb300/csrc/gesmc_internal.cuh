@@ -105,11 +105,11 @@ constexpr uint32_t kMaxWaveKernels = 8;
 // Permutation buckets: a chain's positions go to 2^B buckets by the top B
 // bits of their key (about 2^kPermAvgLog2 per bucket, at most
 // kPermBucketCap), and each bucket is sorted in shared memory by one CTA.
-constexpr int kSortThreads = 256;
-constexpr int kPermBucketCap = 2048;
-constexpr int kPermAvgLog2 = 10;
+constexpr int kSortThreads = 128;
+constexpr int kPermBucketCap = 1024;
+constexpr int kPermAvgLog2 = 9;
 constexpr int kPerThread = kPermBucketCap / kSortThreads;
-constexpr int kSubBits = 11;
+constexpr int kSubBits = 10;
 
 // Tuple partitions: a chain's tuples go to 2^P partitions by the top P bits
 // of the hash of the edge id (about 2^tuple_log2 tuples each, room for

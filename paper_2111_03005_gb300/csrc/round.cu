@@ -826,7 +826,7 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
 }
 
 // One CTA per bucket (the round's launch over all buckets).
-__global__ void __launch_bounds__(kSortThreads, 4) k_sortpair(RoundArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) k_sortpair(RoundArgs a) {
   __shared__ __align__(128) uint4 srec[kPermBucketCap];
   __shared__ uint16_t sidx[kPermBucketCap];
   __shared__ uint32_t hist[1 << kSubBits];
