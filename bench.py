@@ -624,24 +624,32 @@ def run_gesmc(args):
     if not args.no_e2e:
         host_in = torch.from_numpy(edges.view(np.int64)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        e2e_times, host_create = [], []
+        e2e_times, host_create, phases = [], [], []
         for step in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             with gesmc.Chain(host_in, n=n, **layout) as c:
                 torch.cuda.synchronize()
-                host_create.append(1e3 * (time.perf_counter() - t0))
+                t1 = time.perf_counter()
+                host_create.append(1e3 * (t1 - t0))
                 if round_ctas:
                     c.set_round_launch(round_ctas)
                 c.run(rounds, seed + 7)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
                 c.edges(host_out)
+                torch.cuda.synchronize()
+                t3 = time.perf_counter()
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
+            phases.append((1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2), 1e3 * (time.perf_counter() - t3)))
         e2e_t = max_over_ranks(statistics.median(e2e_times), dist, dev)
         line["e2e"] = {"value": world * rounds * L / e2e_t, "unit": UNIT,
                        "h2d_bytes_per_step": 8 * m, "d2h_bytes_per_step": 8 * m,
                        "includes": f"gesmc_create (H2D copy, validation) + gesmc_run({rounds}) + gesmc_edges (D2H) "
                                    "+ destroy",
+                       "phases_ms": dict(zip(("create", "run", "edges", "destroy"),
+                                             (round(statistics.median(x), 2) for x in zip(*phases)))),
                        "layout": layout}
         line["create_ms"]["from_pinned_host"] = statistics.median(host_create)
     if rank == 0 and world == 1 and not args.no_cpu:
