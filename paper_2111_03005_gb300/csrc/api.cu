@@ -37,12 +37,12 @@ struct ChainShape {
   uint64_t tcounts() const { return (uint64_t)np * tstride(); }
 };
 
-bool chain_shape(uint64_t m, uint32_t tuple_log2, ChainShape *s) {
+bool chain_shape(uint64_t m, uint32_t tuple_log2, uint32_t bucket_log2, ChainShape *s) {
   if (m > kMaxEdges) return false;
   s->m = (uint32_t)m;
   s->L = (uint32_t)(m / 2);
-  uint32_t B = 0;  // permutation buckets of about 2^kPermAvgLog2 positions
-  while ((m >> B) > (1ull << kPermAvgLog2)) ++B;
+  uint32_t B = 0;  // permutation buckets of about 2^(bucket_log2 - 1) positions
+  while ((m >> B) > (1ull << (bucket_log2 - 1))) ++B;
   s->B = B;
   s->nb = 1u << B;
   const uint64_t ntuple = 4ull * s->L + 1;
@@ -61,12 +61,14 @@ bool chain_shape(uint64_t m, uint32_t tuple_log2, ChainShape *s) {
 // chains; each bound holds for any split of the edges into chains.
 struct Capacity {
   uint64_t slots, switches, buckets, parts, tuples, ovf, dep, tcounts;
+  uint32_t bucket_log2;  // room for 2^bucket_log2 records per permutation bucket
 };
 
 Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
   Capacity c;
+  c.bucket_log2 = bucket_log2(M);
   ChainShape one;
-  if (C == 1 && chain_shape(M, tuple_log2, &one)) {
+  if (C == 1 && chain_shape(M, tuple_log2, c.bucket_log2, &one)) {
     // one chain: its own shape, which also covers any smaller chain (every
     // piece of a shape grows with m)
     c.slots = one.slots();
@@ -81,7 +83,7 @@ Capacity pool_capacity(uint64_t M, uint64_t C, uint32_t tuple_log2) {
   }
   c.slots = M + C;
   c.switches = M / 2 + C;
-  c.buckets = 2 * (M >> kPermAvgLog2) + 2 * C;
+  c.buckets = 2 * (M >> (c.bucket_log2 - 1)) + 2 * C;
   const uint64_t ntuple = 2 * M + C;  // bounds the sum over chains of 4L + 1
   c.parts = 2 * (ntuple >> tuple_log2) + 4 * C;
   c.tuples = ntuple + 64 * c.parts;  // bounds the sum over chains of np * capt
@@ -140,7 +142,7 @@ Layout pool_layout(const Capacity &c, uint64_t M, uint64_t C) {
   // the permutation records are dead once the sort has read them, so the
   // overflow tuples sorted by partition (written after the sort, read by the
   // grouping) share their bytes; so does ParES's edge set, between rounds
-  l.prec = take(std::max<uint64_t>(16ull * kPermBucketCap * c.buckets, 16ull * c.ovf));
+  l.prec = take(std::max<uint64_t>((16ull << c.bucket_log2) * c.buckets, 16ull * c.ovf));
   l.stup = l.prec;
   l.pcount = take(4 * c.buckets);
   l.poff = take(4 * (c.buckets + 1));
@@ -427,6 +429,7 @@ void pool_bind(gesmc_pool_t p) {
   a.st = at<StatsDev>(b, l.st);
   a.ovf_cap = (uint32_t)p->cap.ovf;
   a.dep_cap = (uint32_t)p->cap.dep;
+  a.bucket_log2 = p->cap.bucket_log2;
 }
 
 bool valid_opts(const gesmc_pool_opts &o) {
@@ -646,7 +649,7 @@ int pool_add_device(gesmc_pool_t p, unsigned long long *E, uint64_t m, uint64_t 
   if (c == p->max_chains) return GESMC_E_NOMEM;
   HostChain hc;
   std::memset(&hc.d, 0, sizeof(hc.d));
-  if (!chain_shape(m, p->tuple_log2, &hc.shape)) return GESMC_E_INVALID;
+  if (!chain_shape(m, p->tuple_log2, p->cap.bucket_log2, &hc.shape)) return GESMC_E_INVALID;
   uint64_t n_eff = 0;
   int rc = validate_list(p, E, m, n, &n_eff);
   if (rc != GESMC_OK) return rc;
@@ -755,7 +758,7 @@ int pool_run(gesmc_pool_t p, uint64_t rounds) {
       max_m = std::max(max_m, p->res_max_m[k]);
     }
     const uint32_t pstride = (max_m + 7u) & ~7u;
-    const uint64_t pre_bytes = 16ull * kPermBucketCap * p->cap.buckets;
+    const uint64_t pre_bytes = (16ull << p->cap.bucket_log2) * p->cap.buckets;
     const uint64_t per_round = (uint64_t)njobs * (2ull * pstride + 4);
     const bool presort = njobs > 0 && 4ull * njobs <= (uint64_t)p->num_sms && per_round <= pre_bytes;
     if (presort) per_launch = std::min<uint64_t>(per_launch, pre_bytes / per_round);
@@ -945,8 +948,8 @@ int pool_es_run(gesmc_pool_t p, uint64_t switches, uint32_t only) {
       char *base = tup + 16ull * hc.d.tuple_base;
       const uint64_t bytes = 16ull * hc.d.capt << hc.d.P;
       if (8ull * jb.m > bytes) return GESMC_E_INTERNAL;
-      char *hbase = reinterpret_cast<char *>(a.prec) + 16ull * kPermBucketCap * hc.d.bucket_base;
-      const uint64_t hbytes = 16ull * kPermBucketCap * hc.shape.nb;
+      char *hbase = reinterpret_cast<char *>(a.prec) + (16ull << p->cap.bucket_log2) * hc.d.bucket_base;
+      const uint64_t hbytes = (16ull << p->cap.bucket_log2) * hc.shape.nb;
       uint32_t hlog2 = 0;
       while ((16ull << hlog2) <= hbytes && hlog2 < 31) ++hlog2;  // largest 2^h with 8 * 2^h <= room
       if ((1ull << hlog2) < 2ull * jb.m) return GESMC_E_INTERNAL;

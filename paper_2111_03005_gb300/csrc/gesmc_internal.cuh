@@ -103,13 +103,17 @@ constexpr uint32_t kDefaultWaveCap = 10000;
 constexpr uint32_t kMaxWaveKernels = 8;
 
 // Permutation buckets: a chain's positions go to 2^B buckets by the top B
-// bits of their key (about 2^kPermAvgLog2 per bucket, at most
-// kPermBucketCap), and each bucket is sorted in shared memory by one CTA.
-constexpr int kSortThreads = 128;
-constexpr int kPermBucketCap = 1024;
-constexpr int kPermAvgLog2 = 9;
-constexpr int kPerThread = kPermBucketCap / kSortThreads;
-constexpr int kSubBits = 10;
+// bits of their key, each bucket sorted in shared memory by one CTA.  A
+// pool's buckets hold about 2^(c - 1) positions with room for 2^c, c =
+// bucket_log2(max edges): 10 (CTAs of 128 threads, eight per SM) for pools
+// of at most 2^27 edges, whose at most 2^18 buckets keep their write
+// frontiers (one partly filled line per bucket) in L2; 11 (CTAs of 256
+// threads) above that, where twice as many buckets would spill them.
+constexpr uint32_t kBucketLog2Small = 10, kBucketLog2Large = 11;
+constexpr unsigned long long kBucketSmallMaxEdges = 1ull << 27;
+inline uint32_t bucket_log2(unsigned long long max_edges) {
+  return max_edges <= kBucketSmallMaxEdges ? kBucketLog2Small : kBucketLog2Large;
+}
 
 // Tuple partitions: a chain's tuples go to 2^P partitions by the top P bits
 // of the hash of the edge id (about 2^tuple_log2 tuples each, room for
@@ -209,6 +213,7 @@ struct RoundArgs {
   uint32_t slot_hw, switch_hw, bucket_hw, part_hw, tcount_hw;
   uint32_t ovf_cap, dep_cap;
   uint32_t max_waves;
+  uint32_t bucket_log2;  // permutation buckets: room for 2^bucket_log2 records each
   uint32_t group_log2;  // shared-memory grouping table: 2^group_log2 slots
   uint32_t group_grid;  // CTAs of the persistent grouping kernel
   uint32_t any_work;    // some chain has m >= 2

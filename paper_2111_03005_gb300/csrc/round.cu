@@ -312,8 +312,8 @@ __global__ void k_clear(RoundArgs a) { clear_body(a); }
 
 __device__ __forceinline__ void store_record(const RoundArgs &a, uint32_t b, uint32_t idx, uint32_t keybits,
                                              uint32_t pos, unsigned long long e) {
-  if (idx < (uint32_t)kPermBucketCap)
-    a.prec[(size_t)b * kPermBucketCap + idx] = make_uint4(keybits, pos, (uint32_t)e, (uint32_t)(e >> 32));
+  if (idx < (1u << a.bucket_log2))
+    a.prec[((size_t)b << a.bucket_log2) + idx] = make_uint4(keybits, pos, (uint32_t)e, (uint32_t)(e >> 32));
   else
     atomicOr(&a.ctl->err, kErrBucket);
 }
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(1024) k_scan_perm(RoundArgs a) {
   __shared__ uint32_t warp_tot[32];
   const uint32_t b = blockIdx.x * 1024 + threadIdx.x;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t v = b < a.bucket_hw ? min(a.pcount[b], (uint32_t)kPermBucketCap) : 0u;
+  const uint32_t v = b < a.bucket_hw ? min(a.pcount[b], 1u << a.bucket_log2) : 0u;
   uint32_t incl = v;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -619,10 +619,10 @@ __device__ __forceinline__ void overflow_scatter_body(const RoundArgs &a) {
 
 __global__ void k_overflow_scatter(RoundArgs a) { overflow_scatter_body(a); }
 
-// In-place exclusive scan of 2^kSubBits counters by a CTA of kThreads.
-template <int kThreads>
+// In-place exclusive scan of 2^kLog2 counters by a CTA of kThreads.
+template <int kThreads, int kLog2>
 __device__ __forceinline__ void cta_exclusive_scan(uint32_t *h, uint32_t *warp_tot) {
-  constexpr int n = 1 << kSubBits;
+  constexpr int n = 1 << kLog2;
   constexpr int per = n / kThreads;
   constexpr int nwarps = kThreads / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -684,15 +684,18 @@ __device__ __forceinline__ bool full_key_less(unsigned long long seed, unsigned 
 // the record at each slot, the sub-bucket histogram, per-warp sums, and the
 // mbarrier the bulk copy completes on.
 struct SortSmem {
-  uint4 *srec;       // {32 key bits, position, edge lo, edge hi} x kPermBucketCap
+  uint4 *srec;       // {32 key bits, position, edge lo, edge hi}, room for a bucket
   uint16_t *sidx;    // record at each slot of the bucket
-  uint32_t *hist;    // 2^kSubBits counters
+  uint32_t *hist;    // one counter per sub-bucket (as many as the bucket has room for records)
   uint32_t *warp_tot;
   unsigned long long *bar;
 };
 
-constexpr size_t kSortSmemBytes = sizeof(uint4) * kPermBucketCap + sizeof(uint16_t) * kPermBucketCap +
-                                  sizeof(uint32_t) * (1u << kSubBits) + sizeof(uint32_t) * 32 + 16;
+// Shared memory of a sort of buckets with room for 2^log2 records (the
+// sub-bucket histogram has as many counters).
+constexpr size_t sort_smem_bytes(uint32_t log2) {
+  return (sizeof(uint4) + sizeof(uint16_t) + sizeof(uint32_t)) * (size_t(1) << log2) + sizeof(uint32_t) * 32 + 16;
+}
 
 // Bucket b, by one CTA of kThreads threads.  The bucket's records come into
 // shared memory in one bulk copy (the TMA engine, cp.async.bulk, completing
@@ -704,9 +707,11 @@ constexpr size_t kSortSmemBytes = sizeof(uint4) * kPermBucketCap + sizeof(uint16
 // built.  Returns false (with kErrCopy set) if the copy did not land in time;
 // the caller must stop then.  Every thread of the CTA calls it; `parity`
 // tracks the barrier's phase across the buckets a CTA sorts.
-template <int kThreads>
+template <int kThreads, int kLog2>
 __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, const SortSmem &sm, uint32_t &parity,
                                             bool local_offsets = false) {
+  constexpr uint32_t kCap = 1u << kLog2;
+  constexpr int kSubBits = kLog2;  // sub-buckets: about two per record
   uint4 *const srec = sm.srec;
   uint16_t *const sidx = sm.sidx;
   uint32_t *const hist = sm.hist;
@@ -714,10 +719,10 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
   constexpr int nsub = 1 << kSubBits;
   const uint32_t c = a.owner_bucket[b];
   if (c == kNoChain) return true;
-  const uint32_t cnt = min(a.pcount[b], (uint32_t)kPermBucketCap);
+  const uint32_t cnt = min(a.pcount[b], kCap);
   if (tid == 0 && cnt) {
     mbar_arrive_expect(sm.bar, cnt * (uint32_t)sizeof(uint4));
-    bulk_copy_g2s(srec, a.prec + (size_t)b * kPermBucketCap, cnt * (uint32_t)sizeof(uint4), sm.bar);
+    bulk_copy_g2s(srec, a.prec + ((size_t)b << kLog2), cnt * (uint32_t)sizeof(uint4), sm.bar);
   }
   for (int s2 = tid; s2 < nsub; s2 += kThreads) hist[s2] = 0;
   const unsigned long long R = a.ctl->pool_round;
@@ -729,7 +734,7 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
   uint32_t loff;
   if (local_offsets) {
     uint32_t sum = 0;
-    for (uint32_t j = ch.bucket_base + tid; j < b; j += kThreads) sum += min(a.pcount[j], (uint32_t)kPermBucketCap);
+    for (uint32_t j = ch.bucket_base + tid; j < b; j += kThreads) sum += min(a.pcount[j], kCap);
     loff = cta_sum<kThreads>(sum, sm.warp_tot);
   } else {
     loff = bucket_offset(a, b) - bucket_offset(a, ch.bucket_base);
@@ -747,7 +752,7 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
   if (cnt) parity ^= 1u;  // the barrier's next phase serves the CTA's next copy
   for (uint32_t t = tid; t < cnt; t += kThreads) atomicAdd(&hist[srec[t].x >> (32 - kSubBits)], 1u);
   __syncthreads();
-  cta_exclusive_scan<kThreads>(hist, sm.warp_tot);
+  cta_exclusive_scan<kThreads, kSubBits>(hist, sm.warp_tot);
   __syncthreads();
   for (uint32_t t = tid; t < cnt; t += kThreads) sidx[atomicAdd(&hist[srec[t].x >> (32 - kSubBits)], 1u)] = t;
   __syncthreads();
@@ -825,18 +830,22 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
   return true;
 }
 
-// One CTA per bucket (the round's launch over all buckets).
-__global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) k_sortpair(RoundArgs a) {
-  __shared__ __align__(128) uint4 srec[kPermBucketCap];
-  __shared__ uint16_t sidx[kPermBucketCap];
-  __shared__ uint32_t hist[1 << kSubBits];
-  __shared__ uint32_t warp_tot[kSortThreads / 32];
+// One CTA per bucket (the round's launch over all buckets): buckets with
+// room for 2^kLog2 records, CTAs of 2^(kLog2 - 3) threads (1024 threads per
+// SM).
+template <int kLog2>
+__global__ void __launch_bounds__(1 << (kLog2 - 3), 1 << (13 - kLog2)) k_sortpair(RoundArgs a) {
+  constexpr int kThreads = 1 << (kLog2 - 3);
+  __shared__ __align__(128) uint4 srec[1 << kLog2];
+  __shared__ uint16_t sidx[1 << kLog2];
+  __shared__ uint32_t hist[1 << kLog2];
+  __shared__ uint32_t warp_tot[kThreads / 32];
   __shared__ __align__(8) unsigned long long bar;
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
   const SortSmem sm{srec, sidx, hist, warp_tot, &bar};
   uint32_t parity = 0;
-  if (sort_bucket<kSortThreads>(a, blockIdx.x, sm, parity) && threadIdx.x == 0) mbar_inval(&bar);
+  if (sort_bucket<kThreads, kLog2>(a, blockIdx.x, sm, parity) && threadIdx.x == 0) mbar_inval(&bar);
 }
 
 __device__ __forceinline__ void boundary_body(const RoundArgs &a) {
@@ -1551,24 +1560,30 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_round_fused(RoundArgs a) {
     if (!grid_sync(ctl, target)) return;
     if (!a.fused_local_offsets) {
       if (blockIdx.x == 0) {  // bucket offsets: full offsets in poff, zero block offsets
-        cta_scan_full(a.pcount, a.poff, nullptr, a.bucket_hw, (uint32_t)kPermBucketCap);
+        cta_scan_full(a.pcount, a.poff, nullptr, a.bucket_hw, 1u << a.bucket_log2);
         for (uint32_t j = tid; j <= (a.bucket_hw + 1023) / 1024; j += blockDim.x) a.pblk[j] = 0;
       }
       if (!grid_sync(ctl, target)) return;
     }
     {
+      // laid out for the pool's bucket room (the region has room for the largest)
       unsigned char *base = reinterpret_cast<unsigned char *>(fused_dyn);
+      const size_t room = size_t(1) << a.bucket_log2;
       SortSmem sm;
       sm.srec = reinterpret_cast<uint4 *>(base);
-      sm.sidx = reinterpret_cast<uint16_t *>(base + sizeof(uint4) * kPermBucketCap);
-      sm.hist = reinterpret_cast<uint32_t *>(base + (sizeof(uint4) + sizeof(uint16_t)) * kPermBucketCap);
-      sm.warp_tot = sm.hist + (1u << kSubBits);
+      sm.sidx = reinterpret_cast<uint16_t *>(base + sizeof(uint4) * room);
+      sm.hist = reinterpret_cast<uint32_t *>(base + (sizeof(uint4) + sizeof(uint16_t)) * room);
+      sm.warp_tot = sm.hist + room;
       sm.bar = reinterpret_cast<unsigned long long *>(sm.warp_tot + 32);
       if (tid == 0) mbar_init(sm.bar, 1);
       __syncthreads();
       uint32_t parity = 0;
+      const bool local = a.fused_local_offsets != 0;
       for (uint32_t b = blockIdx.x; b < a.bucket_hw; b += gridDim.x)
-        if (!sort_bucket<kFusedThreads>(a, b, sm, parity, a.fused_local_offsets != 0)) return;
+        if (!(a.bucket_log2 == kBucketLog2Small
+                  ? sort_bucket<kFusedThreads, kBucketLog2Small>(a, b, sm, parity, local)
+                  : sort_bucket<kFusedThreads, kBucketLog2Large>(a, b, sm, parity, local)))
+          return;
       __syncthreads();
       if (tid == 0) mbar_inval(sm.bar);  // the grouping table takes these bytes next
     }
@@ -1828,7 +1843,7 @@ cudaError_t prepare_kernels(uint32_t group_log2, int num_sms, LaunchShapes *shap
 
 
 size_t fused_smem_bytes(uint32_t group_log2) {
-  return std::max(kSortSmemBytes, group_smem_bytes(group_log2));
+  return std::max(sort_smem_bytes(kBucketLog2Large), group_smem_bytes(group_log2));
 }
 
 cudaError_t prepare_fused(uint32_t group_log2, int num_sms, uint32_t *max_ctas) {
@@ -1877,7 +1892,13 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
     n += 2;
   }
   mark(kStageSortPair);
-  if (work) { k_sortpair<<<a.bucket_hw, kSortThreads, 0, s>>>(a); ++n; }
+  if (work) {
+    if (a.bucket_log2 == kBucketLog2Small)
+      k_sortpair<kBucketLog2Small><<<a.bucket_hw, 1 << (kBucketLog2Small - 3), 0, s>>>(a);
+    else
+      k_sortpair<kBucketLog2Large><<<a.bucket_hw, 1 << (kBucketLog2Large - 3), 0, s>>>(a);
+    ++n;
+  }
   mark(kStageBoundary);
   if (work) { k_boundary<<<grid_for(a.bucket_hw, 256, num_sms, 2), 256, 0, s>>>(a); ++n; }
   mark(kStageSources);
