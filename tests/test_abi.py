@@ -49,11 +49,14 @@ def test_host_only_entry_points():
     opts = gesmc.GesmcOpts()
     lib.gesmc_opts_default(ctypes.byref(opts))
     assert opts.lazy_threshold == 0 and opts.n == 0 and opts.max_waves == 0
-    # memory plan: about 145 bytes per edge for one chain (buckets of about 1024 positions with room for
-    # 2048, tuple partitions with room for their mean plus a margin, the overflow list for every tuple)
+    # memory plan: about 145 bytes per edge for one chain (permutation buckets with room for twice their
+    # mean, tuple partitions with room for their mean plus a margin, the overflow list for every tuple)
     m = 1 << 20
     b = gesmc.gesmc_device_bytes(m)
     assert 120 * m <= b < 180 * m
+    # the bucket room doubles (and the bucket count halves) above 2^27 edges: the plan stays per edge
+    for m in ((1 << 27) - 1, (1 << 27) + 1):
+        assert 120 * m <= gesmc.gesmc_device_bytes(m) < 180 * m, m
     assert gesmc.gesmc_device_bytes(1 << 31) == 0
     # a 1.2e9-edge chain (the paper's largest graph) fits in 280 GB; near 2^31 edges the tuple storage
     # would need more than 32-bit indices, and such a pool is refused
