@@ -831,10 +831,14 @@ __device__ __forceinline__ bool sort_bucket(const RoundArgs &a, uint32_t b, cons
 }
 
 // One CTA per bucket (the round's launch over all buckets): buckets with
-// room for 2^kLog2 records, CTAs of 2^(kLog2 - 3) threads (1024 threads per
-// SM).
-template <int kLog2>
-__global__ void __launch_bounds__(1 << (kLog2 - 3), 1 << (13 - kLog2)) k_sortpair(RoundArgs a) {
+// room for 2^kLog2 records, CTAs of 2^(kLog2 - 3) threads, kMin of them
+// per SM.  Seven CTAs of 128 threads (70 registers) sorted G(2^24)'s
+// buckets in 3.85 ms per round, against 3.98 with six (80 registers), 4.02-
+// 4.07 with eight (63) and 5.37 with nine (56).  The larger buckets run four
+// CTAs of 256 threads (63 registers; three at 80 took 4.90 against 4.51 ms on
+// the 4096-chain ensemble).
+template <int kLog2, int kMin>
+__global__ void __launch_bounds__(1 << (kLog2 - 3), kMin) k_sortpair(RoundArgs a) {
   constexpr int kThreads = 1 << (kLog2 - 3);
   __shared__ __align__(128) uint4 srec[1 << kLog2];
   __shared__ uint16_t sidx[1 << kLog2];
@@ -1894,9 +1898,9 @@ cudaError_t launch_round(const RoundArgs &a, cudaStream_t s, int num_sms, cudaEv
   mark(kStageSortPair);
   if (work) {
     if (a.bucket_log2 == kBucketLog2Small)
-      k_sortpair<kBucketLog2Small><<<a.bucket_hw, 1 << (kBucketLog2Small - 3), 0, s>>>(a);
+      k_sortpair<kBucketLog2Small, 7><<<a.bucket_hw, 1 << (kBucketLog2Small - 3), 0, s>>>(a);
     else
-      k_sortpair<kBucketLog2Large><<<a.bucket_hw, 1 << (kBucketLog2Large - 3), 0, s>>>(a);
+      k_sortpair<kBucketLog2Large, 4><<<a.bucket_hw, 1 << (kBucketLog2Large - 3), 0, s>>>(a);
     ++n;
   }
   mark(kStageBoundary);
