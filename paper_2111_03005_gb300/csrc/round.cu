@@ -429,12 +429,12 @@ __device__ __forceinline__ void lazy_count_body(const RoundArgs &a) {
 __global__ void k_lazy_count(RoundArgs a) { lazy_count_body(a); }
 
 // Append every position, with its current edge, to its chain's bucket.
-// Capped at 40 registers (6 CTAs of 256 per SM): more warps in flight hide
-// the latency of the record loads and of the bucket cursor atomics.  The
-// round launches one pair per thread (short-lived CTAs): on G(2^24) that
-// measured 3.13 ms against 3.46 ms for a grid-stride loop over 8 CTAs per
-// SM and 4.05 ms over one resident wave; the loop form serves the one-launch
-// round.
+// Five CTAs of 256 per SM (48 registers, no spills): 3.16 ms per round on
+// G(2^24) against 3.20 with six (40 registers and a few spilled) and 3.29
+// with eight (32).  The round launches one pair per thread (short-lived
+// CTAs): that measured 3.13 ms against 3.46 ms for a grid-stride loop over
+// 8 CTAs per SM and 4.05 ms over one resident wave; the loop form serves the
+// one-launch round.
 __device__ __forceinline__ void permute_pair(const RoundArgs &a, uint32_t x, unsigned long long R) {
   const uint32_t s0 = 2 * x;
   const uint32_t c = a.owner_slot[s0];
@@ -476,7 +476,7 @@ __device__ __forceinline__ uint32_t scrambled_cta(uint32_t stride) {
 }
 
 // One pair of slots per thread, CTAs in scrambled order.
-__global__ void __launch_bounds__(256, 6) k_permute(RoundArgs a) {
+__global__ void __launch_bounds__(256, 5) k_permute(RoundArgs a) {
   const uint32_t x = scrambled_cta(a.permute_stride) * blockDim.x + threadIdx.x;
   if (x < (a.slot_hw + 1) >> 1) permute_pair(a, x, a.ctl->pool_round);
 }
